@@ -1,0 +1,128 @@
+"""Planted mistakes: each mutant of the oracle source must fail at least one pin.
+
+The mutations are applied to a copy of oracle/cf_oracle.c in a temporary directory and
+compiled there (CPU only); the oracle itself is never modified.  This shows that the pins
+in test_oracle_pins.py constrain every part of the oracle a plausible mistake could touch:
+the separation, the periodic wrap, the bin edges, the doubling and self pairs of
+auto-correlations, the pi cut, the rp/pi split, angular edges, weights and ravg.
+"""
+import math
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.test_oracle_pins import LATTICE, PERIODIC, RPPI, Cat
+
+MUTANTS = {
+    "drop_dz_term": ("s = s + dz * dz;", "s = s;"),
+    "wrap_wrong_sign": ("if (d > 0.5 * L) d -= L;", "if (d > 0.5 * L) d += L;"),
+    "lower_edge_exclusive": ("if (s < p->e2[0] || s >= p->e2[nb]) return -1;\n        int k",
+                             "if (s <= p->e2[0] || s >= p->e2[nb]) return -1;\n        int k"),
+    "upper_edge_inclusive": ("if (s < p->e2[0] || s >= p->e2[nb]) return -1;\n        int k",
+                             "if (s < p->e2[0] || s > p->e2[nb]) return -1;\n        int k"),
+    "ties_to_lower_bin": ("while (k > 0 && s < e[k]) k--;", "while (k > 0 && s <= e[k]) k--;"),
+    "no_auto_doubling": ("npairs[k] *= 2; wsum[k] *= 2.0; rsum[k] *= 2.0;", ""),
+    "no_self_pairs": ("npairs[k] += (uint64_t)n1;", ""),
+    "pimax_inclusive": ("if (!(pi < p->pimax)) return -1;", "if (!(pi <= p->pimax)) return -1;"),
+    "rp_uses_dz": ("double s = dx * dx + dy * dy;\n    double pi = fabs(dz);",
+                   "double s = dx * dx + dz * dz;\n    double pi = fabs(dz);"),
+    "pi_uses_dy": ("double pi = fabs(dz);", "double pi = fabs(dy);"),
+    "rppi_index_transposed": ("return k * p->npi + m;", "return m * p->nbins + k;"),
+    "theta_full_angle": ("double c = 2.0 * sin(e * (M_PI / 360.0));\n            p->e2[k] = c * c;\n        } else {\n            p->e2[k] = e * e;\n        }\n    }\n    p->npi",
+                         "double c = 2.0 * sin(e * (M_PI / 180.0));\n            p->e2[k] = c * c;\n        } else {\n            p->e2[k] = e * e;\n        }\n    }\n    p->npi"),
+    "weight_sum_not_product": ("double ww = wi * (w2 ? w2[j] : 1.0);", "double ww = wi + (w2 ? w2[j] : 1.0);"),
+    "ravg_squared": ("double c = sqrt(s);", "double c = s;"),
+    "cross_skips_first_row": ("ra[0] = (mode == OR_ROWS || !autoc) ? 0 : i + 1;",
+                              "ra[0] = (mode == OR_ROWS || !autoc) ? 1 : i + 1;"),
+}
+
+
+def _pin_checks(lib):
+    """The quick pins, each returning normally or raising AssertionError."""
+    import gen
+
+    def lattice():
+        out = oracle.count("r", [1, 2, 3, 5, 6], Cat(LATTICE), autocorr=True, periodic=False,
+                           mode="brute", lib=lib)
+        assert out["npairs"].tolist() == [2, 4, 4, 2]
+
+    def lattice_w():
+        d = Cat(LATTICE, w=[1.0, 2.0, 0.5, 4.0])
+        out = oracle.count("r", [1, 2, 3, 5, 6], d, autocorr=True, periodic=False, weighted=True,
+                           ravg=True, mode="brute", lib=lib)
+        assert out["wsum"].tolist() == [4.0, 3.0, 20.0, 8.0]
+        exp = [1.0, (0.5 * 2 + math.sqrt(5)) / 1.5, (8 * math.sqrt(20) + 2 * math.sqrt(13)) / 10, 5.0]
+        np.testing.assert_allclose(out["ravg"], exp, rtol=1e-15)
+
+    def periodic():
+        d = Cat(PERIODIC)
+        out = oracle.count("r", [0, 1, 2, 4, 5], d, autocorr=True, periodic=True, box=8.0,
+                           mode="brute", lib=lib)
+        assert out["npairs"].tolist() == [7, 4, 2, 10]
+        out = oracle.count("r", [0, 1, 2, 4, 5], d, d, autocorr=False, periodic=True, box=8.0,
+                           mode="brute", lib=lib)
+        assert out["npairs"].tolist() == [7, 4, 2, 10]
+
+    def rppi():
+        out = oracle.count("rppi", [1, 2, 3, 5, 6], Cat(RPPI), autocorr=True, periodic=False,
+                           pimax=3.0, npibins=3, mode="brute", lib=lib)
+        exp = np.zeros((4, 3), dtype=np.uint64)
+        exp[0, 1], exp[1, 0], exp[2, 2] = 2, 4, 4
+        assert (out["npairs"] == exp).all()
+
+    def theta():
+        d = Cat([(1, 0, 0), (0, 1, 0), (0, 0, 1), (-1, 0, 0)])
+        out = oracle.count("theta", [60, 90, 180], d, autocorr=True, periodic=False, mode="brute",
+                           lib=lib)
+        assert out["npairs"].tolist() == [0, 10]
+
+    def totals():
+        d = gen.uniform_box(200, 10.0, 51)
+        e = gen.uniform_box(150, 10.0, 52)
+        out = oracle.count("r", [1e-6, 9.0], d, e, autocorr=False, periodic=True, box=10.0, lib=lib)
+        assert int(out["npairs"].sum()) == d.n * e.n
+
+    def ckdtree():
+        from scipy.spatial import cKDTree
+        d = gen.uniform_box(800, 30.0, 11, dtype=np.float64)
+        edges = gen.log_edges(0.5, 10.0, 6)
+        out = oracle.count("r", edges, d, autocorr=True, periodic=True, box=30.0, mode="brute", lib=lib)
+        a = np.stack([d.x, d.y, d.z], 1)
+        t = cKDTree(a, boxsize=30.0)
+        assert out["npairs"].astype(np.int64).tolist() == np.diff(t.count_neighbors(t, edges)).astype(np.int64).tolist()
+
+    return [lattice, lattice_w, periodic, rppi, theta, totals, ckdtree]
+
+
+def _build_mutant(tmp_path, name, old, new):
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "cf_oracle.c")).read()
+    assert src.count(old) >= 1, f"mutation {name} does not apply"
+    mutated = src.replace(old, new, 1)
+    c = tmp_path / f"{name}.c"
+    c.write_text(mutated)
+    so = tmp_path / f"{name}.so"
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", str(c),
+                    "-o", str(so), "-lm"], check=True)
+    return oracle.load(str(so))
+
+
+def test_unmutated_passes_all_pins(orc):
+    for chk in _pin_checks(orc):
+        chk()
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_mutant_is_caught(tmp_path, name):
+    pytest.importorskip("scipy.spatial")
+    old, new = MUTANTS[name]
+    lib = _build_mutant(tmp_path, name, old, new)
+    failed = []
+    for chk in _pin_checks(lib):
+        try:
+            chk()
+        except AssertionError:
+            failed.append(chk.__name__)
+    assert failed, f"mutant {name} passed every pin"
