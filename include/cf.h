@@ -1,0 +1,185 @@
+/*
+ * cf.h -- C ABI of the GB300 binned pair counter.
+ *
+ * Method: Sinha & Garrison, "Corrfunc -- a suite of blazing fast correlation functions on the
+ * CPU" (arXiv:1911.03545).  The library counts pairs of points binned by separation over a
+ * cell-list grid (Sec. 4.1-4.3), for the four pair counters of Table 1's theory rows plus the
+ * angular counter: DD(r), DD(rp, pi), wp(rp) and DD(theta); auto or cross; periodic or not;
+ * optionally with pair-product weights (Sec. 2.1, weight_func) and the mean separation per
+ * bin ("ravg", Sec. 6.5).
+ *
+ * Result definition (what every entry point returns, bit-exact for counts):
+ *   - a pair (i, j) is binned by its separation s in the half-open bin lo <= s < hi, compared in
+ *     squared space against e*e evaluated in FP64 (Sec. 2.1 Code naivecorr, Sec. 4.7);
+ *   - r^2 = dx^2+dy^2+dz^2, rp^2 = dx^2+dy^2, pi = |dz|, z is the line of sight (Appendix A.1);
+ *     the separation arithmetic is FP64 on the given coordinates (float32 inputs are widened
+ *     exactly), evaluated as ((dx*dx + dy*dy) + dz*dz) without fused multiply-add;
+ *   - periodic separations use the minimum image: d = a - b; if d > L/2: d -= L;
+ *     if d <= -L/2: d += L (Sec. 4.4, Code normal_pbc);
+ *   - pi bins have width pimax/npibins on [0, pimax) (Appendix A.1 uses width 1); pairs with
+ *     pi >= pimax are excluded; wp counts are the sum over pi bins (Appendix A.1);
+ *   - theta edges are in degrees; a pair of unit vectors is binned by its chord |v1 - v2|
+ *     against c = 2*sin(theta*(pi/360)), squared in FP64 (Appendix A.2.2, Sec. 4.7);
+ *   - auto-correlations return ordered counts: every unordered pair counted twice, plus the N
+ *     self pairs in the first bin when the first edge is 0 (Sec. 4.3, Appendix B), so that
+ *     auto(D) == cross(D, D);
+ *   - wsum = sum of w_i*w_j per bin; ravg = sum(w_i*w_j*s)/wsum (weighted) or sum(s)/npairs,
+ *     0 for an empty bin; for theta s is the angle in degrees.  Both match an FP64 evaluation
+ *     within 1e-6 relative.
+ *
+ * Conventions for every function:
+ *   - all functions return a cf_status; nothing throws across the ABI; after an error the
+ *     message is available from cf_last_error(ctx) and the context stays usable;
+ *   - input arrays are borrowed for the duration of the call and never freed by the library;
+ *     device inputs must be readable on the context's stream;
+ *   - output arrays are caller-owned host memory;
+ *   - a context is not thread safe: use one context per host thread (the server below owns its
+ *     own worker thread and serialises access internally).
+ */
+#ifndef CF_GB300_H
+#define CF_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CF_OK = 0,
+    CF_ERR_ARG = -1,        /* invalid argument (message says which) */
+    CF_ERR_OOM = -2,        /* device memory exhausted or above the context's cap */
+    CF_ERR_CUDA = -3,       /* a CUDA runtime call failed */
+    CF_ERR_TIMEOUT = -4,    /* a bounded wait expired */
+    CF_ERR_BUSY = -5,       /* server: result not ready yet */
+    CF_ERR_CANCELLED = -6,  /* server: request was cancelled */
+    CF_ERR_INTERNAL = -7    /* an internal consistency check failed */
+} cf_status;
+
+typedef enum { CF_DD_R = 0, CF_DD_RPPI = 1, CF_WP = 2, CF_DD_THETA = 3 } cf_kind;
+typedef enum { CF_F32 = 0, CF_F64 = 1 } cf_dtype;
+typedef enum { CF_W_NONE = 0, CF_W_PAIR_PRODUCT = 1 } cf_weight;
+
+#define CF_MAX_BINS 252          /* r / rp / theta bins */
+#define CF_MAX_PIBINS 252        /* pi bins */
+
+/* Problem statement (Table 1; Sec. 4.1 grid; Sec. 4.2 refinement; Appendix A bins). */
+typedef struct {
+    int kind;            /* cf_kind */
+    int autocorr;        /* 1: d2 must be NULL, count D1 x D1 (Sec. 4.3) */
+    int periodic;        /* 1: minimum-image separations in a box [0, box[a]] per axis (Sec. 4.4) */
+    double box[3];       /* periodic box side per axis; ignored if !periodic */
+    const double *edges; /* host array of nbins+1 strictly increasing edges >= 0: r, rp, or theta in
+                            degrees (<= 180) */
+    int nbins;           /* 1 .. CF_MAX_BINS */
+    double pimax;        /* CF_DD_RPPI / CF_WP: pi cut (> 0) */
+    int npibins;         /* CF_DD_RPPI / CF_WP: number of pi bins of width pimax/npibins */
+    int refine[3];       /* refinement factor per axis (Sec. 4.2, 1..4); 0 = automatic */
+    int output_ravg;     /* 1: compute ravg (Sec. 6.5) */
+    int weight;          /* cf_weight; CF_W_PAIR_PRODUCT needs w in every point set */
+} cf_params;
+
+/* A point set.  Coordinates (and w) share one dtype.  For CF_DD_THETA x,y,z are unit vectors
+ * (non-periodic only).  Periodic coordinates must lie in [0, box] (Sec. 4.4: the closed
+ * interval); anything else, and any non-finite value, is CF_ERR_ARG. */
+typedef struct {
+    const void *x, *y, *z;
+    const void *w;       /* NULL unless weighted */
+    int64_t n;           /* >= 0, < 2^31 */
+    int dtype;           /* cf_dtype */
+    int on_device;       /* 1: device pointers on the context's device; 0: host pointers */
+} cf_points;
+
+/* Caller-owned host outputs of length nout = nbins * (kind == CF_DD_RPPI ? npibins : 1),
+ * row-major (rp bin, pi bin).  Any pointer may be NULL to skip that output. */
+typedef struct {
+    uint64_t *npairs;
+    double *wsum;        /* sum of w_i*w_j (pair count when unweighted) */
+    double *ravg;        /* needs output_ravg */
+    double *wp;          /* CF_WP with periodic autocorr only: Eq. (2) with the analytic RR of
+                            Appendix B (density (N-1)/V), nbins values */
+} cf_result;
+
+/* Statistics of the last cf_count / cf_batch_count call on a context. */
+typedef struct {
+    int64_t evaluated_pairs;   /* separations computed by the pair kernel (i x j per work item) */
+    int64_t rechecked_pairs;   /* pairs within the FP32 error band of an edge, redone in FP64 */
+    int64_t work_items;        /* (i tile, j range) items of the pair kernel */
+    int64_t cells;             /* cells per catalogue */
+    int grid[3];               /* cells per axis */
+    int refine[3];             /* refinement used */
+    int variant;               /* pair kernel variant used */
+    int ncat;                  /* catalogues in the call */
+    float ms_build;            /* cell build + work list (CUDA events) */
+    float ms_pair;             /* pair kernel (CUDA events on the context stream) */
+    float ms_recheck;          /* FP64 recheck + finalize */
+    float ms_total;            /* whole call, host wall clock */
+} cf_stats;
+
+/* Create a context on `device` (its current-device state is restored on return), issuing all
+ * work on `cuda_stream` (a cudaStream_t, or NULL for the legacy default stream).  The context
+ * owns device scratch, grown on demand and freed by cf_destroy. */
+cf_status cf_create(void **ctx_out, int device, void *cuda_stream);
+cf_status cf_destroy(void *ctx);
+/* Message of the last failure on this context (static storage owned by the context). */
+const char *cf_last_error(const void *ctx);
+
+/* Options (0 = default).  CF_OPT_MEM_CAP caps the context's device scratch in bytes so that
+ * a request above it fails with CF_ERR_OOM instead of allocating; CF_OPT_VARIANT pins the
+ * pair-kernel variant; CF_OPT_TILE pins the i-tile size (32..128); CF_OPT_JCHUNK pins the
+ * j range length per work item; CF_OPT_QUEUE sets the FP64 recheck queue capacity;
+ * CF_OPT_CTAS_PER_SM sets the persistent grid; CF_OPT_AUDIT = 1 re-evaluates every
+ * in-range pair in FP64 (debug: the band audit); CF_OPT_ITER_LIMIT bounds device spin waits;
+ * CF_OPT_WARPS and CF_OPT_REFINE are the autotuner's knobs. */
+typedef enum {
+    CF_OPT_MEM_CAP = 1,
+    CF_OPT_VARIANT = 2,
+    CF_OPT_TILE = 3,
+    CF_OPT_JCHUNK = 4,
+    CF_OPT_QUEUE = 5,
+    CF_OPT_CTAS_PER_SM = 6,
+    CF_OPT_AUDIT = 7,
+    CF_OPT_ITER_LIMIT = 8,
+    CF_OPT_WARPS = 9,        /* warps per CTA of the pair kernel (1..8) */
+    CF_OPT_REFINE = 10,      /* refinement factor used when params.refine is 0 */
+    CF_OPT_COUNT_ = 11
+} cf_option;
+cf_status cf_set_option(void *ctx, int option, int64_t value);
+
+/* Count pairs of one point set (autocorr) or two (cross).  d2 must be NULL for autocorr.
+ * Synchronous: returns after the outputs are written.  Sec. 4.1-4.7 (method), Sec. 2.1
+ * (result). */
+cf_status cf_count(void *ctx, const cf_params *params, const cf_points *d1, const cf_points *d2,
+                   cf_result *out);
+
+/* Count `ncat` independent catalogues with the same params (autocorr only): one cell build
+ * over all catalogues, one persistent pair-kernel launch over the concatenated work list.
+ * outs[c] receives catalogue c's results.  With capture = 1 the device part is recorded into a
+ * CUDA graph that cf_batch_replay re-launches on new data of the same sizes (same pointers). */
+cf_status cf_batch_count(void *ctx, const cf_params *params, const cf_points *cats, int ncat,
+                         cf_result *outs);
+cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *cats, int ncat);
+cf_status cf_batch_replay(void *ctx, cf_result *outs, int ncat);
+
+cf_status cf_get_stats(const void *ctx, cf_stats *out);
+
+/* Serving: continuous batching of autocorr requests with the same params.  A worker thread
+ * admits requests while device memory (mem_budget_bytes) and slots (max_slots) allow, builds
+ * their cell lists while earlier requests are counted, and counts every admitted request in
+ * the next pair-kernel wave.  Inputs of a request must stay valid until its result is polled
+ * or it is cancelled; results are copied into the cf_result given at submit. */
+cf_status cf_server_start(void **server_out, int device, const cf_params *params,
+                          size_t mem_budget_bytes, int max_slots);
+cf_status cf_server_submit(void *server, const cf_points *cat, cf_result *out, uint64_t *ticket);
+/* CF_OK: done (result written); CF_ERR_BUSY: not yet (timeout_ms == 0); CF_ERR_TIMEOUT; or the
+ * request's own error status. */
+cf_status cf_server_poll(void *server, uint64_t ticket, int timeout_ms);
+cf_status cf_server_cancel(void *server, uint64_t ticket);
+cf_status cf_server_stop(void *server);
+const char *cf_server_last_error(const void *server);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,179 @@
+"""GB300 binned pair counter (Corrfunc's method, arXiv:1911.03545) -- Python binding.
+
+The binding only marshals arguments into the C ABI of include/cf.h; every step of the count
+runs in the CUDA library.  Functions carry the C names:
+
+    ctx = cf_create(device=0, stream=torch.cuda.current_stream())
+    out = cf_count(ctx, params(kind="r", edges=e, autocorr=True, periodic=True, box=L), points(x, y, z))
+    cf_destroy(ctx)
+
+Points may be torch CUDA tensors (used in place, on the context's stream) or numpy arrays
+(copied by the library).  Results are numpy arrays: npairs (uint64), wsum, ravg, wp.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _capi
+from ._capi import (  # noqa: F401
+    CF_DD_R, CF_DD_RPPI, CF_DD_THETA, CF_F32, CF_F64, CF_OK, CF_OPT_AUDIT, CF_OPT_CTAS_PER_SM, CF_OPT_ITER_LIMIT,
+    CF_OPT_JCHUNK, CF_OPT_MEM_CAP, CF_OPT_QUEUE, CF_OPT_REFINE, CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS,
+    CF_W_NONE, CF_W_PAIR_PRODUCT, CF_WP, STATUS_NAMES,
+)
+
+KINDS = {"r": CF_DD_R, "rppi": CF_DD_RPPI, "wp": CF_WP, "theta": CF_DD_THETA}
+
+
+class CfError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def _check(rc: int, ctx=None, server=None):
+    if rc != 0:
+        L = _capi.lib()
+        if server is not None:
+            msg = L.cf_server_last_error(server)
+        elif ctx is not None:
+            msg = L.cf_last_error(ctx)
+        else:
+            msg = b""
+        raise CfError(rc, (msg or b"").decode(errors="replace"))
+
+
+class Params:
+    """cf_params plus the edge array it points to (kept alive by this object)."""
+
+    def __init__(self, kind="r", edges=None, autocorr=True, periodic=False, box=0.0, pimax=0.0, npibins=0,
+                 refine=(0, 0, 0), ravg=False, weighted=False):
+        self.kind = KINDS[kind] if isinstance(kind, str) else int(kind)
+        self.edges = np.ascontiguousarray(np.asarray(edges, dtype=np.float64))
+        b = (float(box),) * 3 if np.isscalar(box) else tuple(float(v) for v in box)
+        self.c = _capi.cf_params(self.kind, int(bool(autocorr)), int(bool(periodic)), (ctypes.c_double * 3)(*b),
+                                 self.edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(self.edges) - 1,
+                                 float(pimax), int(npibins), (ctypes.c_int * 3)(*refine), int(bool(ravg)),
+                                 CF_W_PAIR_PRODUCT if weighted else CF_W_NONE)
+
+    @property
+    def nout(self) -> int:
+        nb = len(self.edges) - 1
+        return nb * (self.c.npibins if self.kind == CF_DD_RPPI else 1)
+
+
+def params(**kw) -> Params:
+    return Params(**kw)
+
+
+class Points:
+    """cf_points over torch CUDA tensors or numpy arrays (references kept alive)."""
+
+    def __init__(self, x, y, z, w=None):
+        self.keep = [x, y, z, w]
+        mods = {type(a).__module__.split(".")[0] for a in (x, y, z) if a is not None}
+        if "torch" in mods:
+            import torch
+            arrs = [x, y, z] + ([w] if w is not None else [])
+            if not all(isinstance(a, torch.Tensor) for a in arrs):
+                raise TypeError("mix of torch and non-torch arrays")
+            dt = x.dtype
+            if dt not in (torch.float32, torch.float64) or any(a.dtype != dt for a in arrs):
+                raise TypeError("coordinates (and weights) must share float32 or float64")
+            if not all(a.is_contiguous() for a in arrs):
+                raise ValueError("tensors must be contiguous")
+            on_dev = int(x.is_cuda)
+            if any(a.is_cuda != x.is_cuda for a in arrs):
+                raise ValueError("mix of host and device tensors")
+            self.dtype = CF_F64 if dt == torch.float64 else CF_F32
+            ptr = lambda a: ctypes.c_void_p(a.data_ptr()) if a is not None else None  # noqa: E731
+            self.c = _capi.cf_points(ptr(x), ptr(y), ptr(z), ptr(w), x.numel(), self.dtype, on_dev)
+        else:
+            arrs = [np.ascontiguousarray(np.asarray(a)) for a in (x, y, z)]
+            dt = arrs[0].dtype
+            if dt not in (np.float32, np.float64):
+                raise TypeError("coordinates must be float32 or float64")
+            arrs = [a.astype(dt, copy=False) for a in arrs]
+            wa = None if w is None else np.ascontiguousarray(np.asarray(w, dtype=dt))
+            self.keep = arrs + [wa]
+            self.dtype = CF_F64 if dt == np.float64 else CF_F32
+            ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+            self.c = _capi.cf_points(ptr(arrs[0]), ptr(arrs[1]), ptr(arrs[2]), ptr(wa), len(arrs[0]), self.dtype, 0)
+
+
+def points(x, y, z, w=None) -> Points:
+    return Points(x, y, z, w)
+
+
+class _Out:
+    def __init__(self, nout: int, nb: int):
+        self.npairs = np.zeros(nout, dtype=np.uint64)
+        self.wsum = np.zeros(nout)
+        self.ravg = np.zeros(nout)
+        self.wp = np.zeros(nb)
+        D = ctypes.POINTER(ctypes.c_double)
+        self.c = _capi.cf_result(self.npairs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                 self.wsum.ctypes.data_as(D), self.ravg.ctypes.data_as(D), self.wp.ctypes.data_as(D))
+
+    def as_dict(self, p: Params) -> dict:
+        d = {"npairs": self.npairs, "wsum": self.wsum}
+        if p.c.output_ravg:
+            d["ravg"] = self.ravg
+        if p.kind == CF_WP:
+            d["wp"] = self.wp
+        if p.kind == CF_DD_RPPI:
+            nb = len(p.edges) - 1
+            for k in ("npairs", "wsum", "ravg"):
+                if k in d:
+                    d[k] = d[k].reshape(nb, p.c.npibins)
+        return d
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def cf_create(device: int = 0, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(_capi.lib().cf_create(ctypes.byref(h), int(device), _stream_handle(stream)))
+    return h.value
+
+
+def cf_destroy(ctx: int) -> None:
+    _check(_capi.lib().cf_destroy(ctx))
+
+
+def cf_last_error(ctx: int) -> str:
+    return (_capi.lib().cf_last_error(ctx) or b"").decode()
+
+
+def cf_set_option(ctx: int, option: int, value: int) -> None:
+    _check(_capi.lib().cf_set_option(ctx, int(option), int(value)), ctx)
+
+
+def cf_count(ctx: int, p: Params, d1: Points, d2: Optional[Points] = None) -> dict:
+    out = _Out(p.nout, len(p.edges) - 1)
+    _check(_capi.lib().cf_count(ctx, ctypes.byref(p.c), ctypes.byref(d1.c), ctypes.byref(d2.c) if d2 else None,
+                                ctypes.byref(out.c)), ctx)
+    return out.as_dict(p)
+
+
+def cf_batch_count(ctx: int, p: Params, cats: Sequence[Points]) -> list:
+    n = len(cats)
+    arr = (_capi.cf_points * n)(*[c.c for c in cats])
+    outs = [_Out(p.nout, len(p.edges) - 1) for _ in range(n)]
+    res = (_capi.cf_result * n)(*[o.c for o in outs])
+    _check(_capi.lib().cf_batch_count(ctx, ctypes.byref(p.c), arr, n, res), ctx)
+    return [o.as_dict(p) for o in outs]
+
+
+def cf_get_stats(ctx: int) -> dict:
+    s = _capi.cf_stats()
+    _check(_capi.lib().cf_get_stats(ctx, ctypes.byref(s)), ctx)
+    return {f: (list(getattr(s, f)) if f in ("grid", "refine") else getattr(s, f)) for f, _ in s._fields_}

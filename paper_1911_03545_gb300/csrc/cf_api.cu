@@ -1,0 +1,772 @@
+// cf_api.cu -- context, device scratch, and the cf_count / cf_batch_* entry points.
+//
+// One call runs the whole path on the context's stream:
+//   prepare (host): stage inputs, bbox/validate, plan grid + bands + tables (Sec. 4.1-4.2)
+//   build  (device): assign -> scan -> scatter (Sec. 4.3), work list count -> scan (Sec. 4.2-4.3)
+//   count  (device): emit work items -> persistent pair kernel (Sec. 4.4-4.7) -> FP64 recheck
+//                    of near-edge pairs -> readback
+//   finish (host): doubling and self pairs (Sec. 4.3, Appendix B), ravg (Sec. 6.5),
+//                  wp (Eq. 2 with the analytic RR of Appendix B).
+// The two device phases contain no host synchronisation, so the batched path can record them
+// into a CUDA graph and replay it.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cf_api_internal.h"
+
+namespace {
+
+const char *status_name(int s)
+{
+    switch (s) {
+    case CF_OK: return "ok";
+    case CF_ERR_ARG: return "invalid argument";
+    case CF_ERR_OOM: return "out of memory";
+    case CF_ERR_CUDA: return "CUDA error";
+    case CF_ERR_TIMEOUT: return "timeout";
+    case CF_ERR_BUSY: return "busy";
+    case CF_ERR_CANCELLED: return "cancelled";
+    default: return "internal error";
+    }
+}
+
+double dkey_to_double(unsigned long long k)
+{
+    unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+    double d;
+    std::memcpy(&d, &b, 8);
+    return d;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+// context helpers
+// ---------------------------------------------------------------------------------------------
+int CfCtx::fail(int status, const std::string &msg)
+{
+    err = std::string(status_name(status)) + ": " + msg;
+    return status;
+}
+
+int CfCtx::cuda(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return CF_OK;
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation) return fail(CF_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+    return fail(CF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int CfCtx::ensure(int b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    Buf &B = buf[b];
+    if (B.cap >= bytes) return CF_OK;
+    size_t want = bytes + bytes / 4 + 256;
+    size_t used_other = mem_used - B.cap;
+    if (mem_cap && used_other + want > mem_cap) {
+        want = bytes;
+        if (used_other + want > mem_cap)
+            return fail(CF_ERR_OOM, "device scratch would exceed the context's memory cap (" +
+                                        std::to_string(used_other + want) + " > " + std::to_string(mem_cap) + " bytes)");
+    }
+    if (B.p) {
+        cudaStreamSynchronize(stream);
+        cudaFree(B.p);
+        mem_used -= B.cap;
+        B.p = nullptr;
+        B.cap = 0;
+    }
+    gen++;
+    cudaError_t e = cudaMalloc(&B.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        B.p = nullptr;
+        return fail(CF_ERR_OOM, "cudaMalloc of " + std::to_string(want) + " bytes failed");
+    }
+    B.cap = want;
+    mem_used += want;
+    return CF_OK;
+}
+
+int CfCtx::ensure_host(size_t bytes)
+{
+    if (hpin_cap >= bytes) return CF_OK;
+    if (hpin) {
+        cudaStreamSynchronize(stream);
+        cudaFreeHost(hpin);
+    }
+    hpin = nullptr;
+    gen++;
+    size_t want = bytes + bytes / 4 + 4096;
+    if (cudaMallocHost(&hpin, want) != cudaSuccess) {
+        cudaGetLastError();
+        hpin_cap = 0;
+        return fail(CF_ERR_OOM, "pinned host staging allocation failed");
+    }
+    hpin_cap = want;
+    return CF_OK;
+}
+
+void CfCtx::drop_graph()
+{
+    if (graph_exec) cudaGraphExecDestroy(graph_exec);
+    if (graph) cudaGraphDestroy(graph);
+    graph_exec = nullptr;
+    graph = nullptr;
+}
+
+CfCtx::~CfCtx()
+{
+    drop_graph();
+    for (auto &B : buf)
+        if (B.p) cudaFree(B.p);
+    if (hpin) cudaFreeHost(hpin);
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+}
+
+// ---------------------------------------------------------------------------------------------
+// phases
+// ---------------------------------------------------------------------------------------------
+static int check_points(CfCtx *C, const cf_params *p, const cf_points *d)
+{
+    if (!d) return C->fail(CF_ERR_ARG, "point set is NULL");
+    if (d->n < 0 || d->n >= (int64_t)1 << 31) return C->fail(CF_ERR_ARG, "point count out of range");
+    if (d->dtype != CF_F32 && d->dtype != CF_F64) return C->fail(CF_ERR_ARG, "dtype must be CF_F32 or CF_F64");
+    if (d->n > 0 && (!d->x || !d->y || !d->z)) return C->fail(CF_ERR_ARG, "coordinate pointer is NULL");
+    if (p->weight == CF_W_PAIR_PRODUCT && d->n > 0 && !d->w)
+        return C->fail(CF_ERR_ARG, "weights were requested but a point set has w == NULL");
+    return CF_OK;
+}
+
+#define CF_TRY(x)              \
+    do {                       \
+        int rc_ = (x);         \
+        if (rc_) return rc_;   \
+    } while (0)
+#define CF_CU(x, what) CF_TRY(C->cuda((x), what))
+
+int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &pts,
+               const std::vector<CfJobDesc> &jobs, CfRun &R)
+{
+    std::string err;
+    int rc = cfp_check_params(p, err);
+    if (rc) return C->fail(rc, err);
+    R.p = *p;
+    R.edges.assign(p->edges, p->edges + p->nbins + 1);
+    R.p.edges = R.edges.data();
+    R.nsets = (int)pts.size();
+    R.njobs = (int)jobs.size();
+    R.jobs = jobs;
+    if (R.nsets < 1 || R.nsets > CFI_MAX_SETS || R.njobs < 1 || R.njobs > (int)CFI_ITEM_JOBMASK)
+        return C->fail(CF_ERR_ARG, "too many point sets or jobs");
+    R.npts = 0;
+    R.nmax = 0;
+    bool any_f64 = false;
+    size_t in_bytes = 0;
+    R.pts.clear();
+    for (int s = 0; s < R.nsets; s++) {
+        CF_TRY(check_points(C, p, pts[s]));
+        R.pts.push_back(*pts[s]);
+        R.npts += pts[s]->n;
+        R.nmax = std::max<int64_t>(R.nmax, pts[s]->n);
+        any_f64 |= pts[s]->dtype == CF_F64;
+        if (!pts[s]->on_device && pts[s]->n > 0)
+            in_bytes += 4 * (((pts[s]->dtype == CF_F64 ? 8 : 4) * (size_t)pts[s]->n + 255) & ~(size_t)255);
+    }
+    if (R.npts >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "more than 2^31 points in one call");
+    for (auto &J : jobs)
+        if (J.a < 0 || J.a >= R.nsets || J.b < 0 || J.b >= R.nsets) return C->fail(CF_ERR_ARG, "bad job");
+    cudaStream_t st = C->stream;
+    const int nsets = R.nsets, njobs = R.njobs;
+
+    // ---- stage inputs (host arrays are copied; device arrays are used in place) ----
+    if (in_bytes) CF_TRY(C->ensure(B_IN, in_bytes));
+    R.sets.assign(nsets, CfSetDesc());
+    {
+        char *inbase = (char *)C->buf[B_IN].p;
+        size_t inoff = 0;
+        int64_t pb = 0;
+        const bool wt = p->weight == CF_W_PAIR_PRODUCT;
+        for (int s = 0; s < nsets; s++) {
+            const cf_points *d = pts[s];
+            CfSetDesc &S = R.sets[s];
+            std::memset(&S, 0, sizeof(S));
+            S.n = d->n;
+            S.dtype = d->dtype;
+            S.pbeg = pb;
+            pb += d->n;
+            if (d->on_device || d->n == 0) {
+                S.x = d->x;
+                S.y = d->y;
+                S.z = d->z;
+                S.w = wt ? d->w : nullptr;
+                continue;
+            }
+            size_t bytes = (d->dtype == CF_F64 ? 8 : 4) * (size_t)d->n;
+            const void *src[4] = {d->x, d->y, d->z, wt ? d->w : nullptr};
+            const void **dst[4] = {&S.x, &S.y, &S.z, &S.w};
+            for (int a = 0; a < 4; a++) {
+                if (!src[a]) { *dst[a] = nullptr; continue; }
+                char *q = inbase + inoff;
+                CF_CU(cudaMemcpyAsync(q, src[a], bytes, cudaMemcpyHostToDevice, st), "input copy");
+                *dst[a] = q;
+                inoff += (bytes + 255) & ~(size_t)255;
+            }
+        }
+    }
+
+    // ---- bbox + validation (Sec. 4.1: the grid covers every data set of the call) ----
+    CF_TRY(C->ensure(B_SETS, sizeof(CfSetDesc) * nsets));
+    CF_TRY(C->ensure(B_BBOX, 64 * (size_t)nsets));
+    CF_TRY(C->ensure_host(std::max<size_t>(64 * (size_t)nsets, 4096)));
+    CF_CU(cudaMemcpyAsync(C->buf[B_SETS].p, R.sets.data(), sizeof(CfSetDesc) * nsets, cudaMemcpyHostToDevice, st),
+          "sets upload");
+    {
+        unsigned long long *init = (unsigned long long *)C->hpin;
+        for (int s = 0; s < nsets; s++)
+            for (int a = 0; a < 8; a++) init[8 * s + a] = a < 3 ? ~0ull : 0ull;
+        CF_CU(cudaMemcpyAsync(C->buf[B_BBOX].p, init, 64 * (size_t)nsets, cudaMemcpyHostToDevice, st), "bbox init");
+    }
+    CF_CU(cfb_bbox((const CfSetDesc *)C->buf[B_SETS].p, nsets, std::max<int64_t>(R.nmax, 1),
+                   (unsigned long long *)C->buf[B_BBOX].p, st), "bbox kernel");
+    CF_CU(cudaMemcpyAsync(C->hpin, C->buf[B_BBOX].p, 64 * (size_t)nsets, cudaMemcpyDeviceToHost, st), "bbox readback");
+    CF_CU(cudaStreamSynchronize(st), "bbox sync");
+    double bbox[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    {
+        const unsigned long long *bb = (const unsigned long long *)C->hpin;
+        for (int s = 0; s < nsets; s++) {
+            if (R.sets[s].n == 0) continue;
+            if (bb[8 * s + 6]) return C->fail(CF_ERR_ARG, "non-finite coordinate or weight");
+            for (int a = 0; a < 3; a++) {
+                double lo = dkey_to_double(bb[8 * s + a]), hi = dkey_to_double(bb[8 * s + 3 + a]);
+                if (p->periodic && (lo < 0.0 || hi > p->box[a]))
+                    return C->fail(CF_ERR_ARG,
+                                   "periodic positions must lie in [0, box] (axis " + std::to_string(a) + ")");
+                bbox[a] = std::min(bbox[a], lo);
+                bbox[3 + a] = std::max(bbox[3 + a], hi);
+            }
+        }
+        for (int a = 0; a < 3; a++)
+            if (!(bbox[a] <= bbox[3 + a])) { bbox[a] = 0.0; bbox[3 + a] = 0.0; }
+    }
+
+    // ---- plan ----
+    CfHostPlan &H = R.plan;
+    int refine[3];
+    for (int a = 0; a < 3; a++)
+        refine[a] = p->refine[a] > 0 ? p->refine[a] : (C->opt[CF_OPT_REFINE] > 0 ? (int)C->opt[CF_OPT_REFINE] : 1);
+    int tile = C->opt[CF_OPT_TILE] > 0 ? (int)std::min<int64_t>(128, std::max<int64_t>(32, C->opt[CF_OPT_TILE])) : 128;
+    int jchunk = C->opt[CF_OPT_JCHUNK] > 0 ? (int)std::min<int64_t>(65535, C->opt[CF_OPT_JCHUNK]) : 512;
+    rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err);
+    if (rc) return C->fail(rc, err);
+    CfDevPlan &D = H.d;
+    D.nsets = nsets;
+    D.njobs = njobs;
+    R.ncell = D.g.ncell;
+    for (int s = 0; s < nsets; s++) R.sets[s].cbeg = (int64_t)s * R.ncell;
+    R.ncell_all = R.ncell * nsets;
+    if (R.ncell_all >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "too many cells");
+    R.nst = D.g.nstencil;
+    R.nthr = (int64_t)njobs * R.ncell * R.nst;
+    if (R.nthr >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "work list too large");
+    R.np = std::max<int64_t>(R.npts, 1);
+    R.nslot = (size_t)D.nslot;
+    R.hsz = R.nslot * njobs;
+    R.self_pairs = p->edges[0] == 0.0;
+
+    // ---- device buffers (allocated here so that the device phases never allocate) ----
+    CF_TRY(C->ensure(B_PLAN, sizeof(CfDevPlan)));
+    CF_TRY(C->ensure(B_LUT, 4 * H.lut.size()));
+    CF_TRY(C->ensure(B_FINE, sizeof(CfFine) * std::max<size_t>(1, H.fine.size())));
+    CF_TRY(C->ensure(B_STENCIL, sizeof(CfStencil) * H.stencil.size()));
+    CF_TRY(C->ensure(B_JOBS, sizeof(CfJobDesc) * njobs));
+    CF_TRY(C->ensure(B_CNT, 4 * (size_t)(R.ncell_all + 1)));
+    CF_TRY(C->ensure(B_CSTART, 4 * (size_t)(R.ncell_all + 1)));
+    CF_TRY(C->ensure(B_CELLID, 4 * (size_t)R.np));
+    CF_TRY(C->ensure(B_SLOT, 4 * (size_t)R.np));
+    CF_TRY(C->ensure(B_PA, 16 * (size_t)R.np));
+    CF_TRY(C->ensure(B_PB, 16 * (size_t)R.np));
+    CF_TRY(C->ensure(B_ORIG, 4 * (size_t)R.np));
+    if (D.f64lo) CF_TRY(C->ensure(B_PLO, 32 * (size_t)R.np));
+    CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.ncell_all, R.nthr))));
+    CF_TRY(C->ensure(B_ICNT, 4 * (size_t)std::max<int64_t>(R.nthr, 1)));
+    CF_TRY(C->ensure(B_IOFF, 4 * (size_t)(R.nthr + 1)));
+    CF_TRY(C->ensure(B_MISC, 4096));
+    CF_TRY(C->ensure(B_HCNT, 8 * R.hsz));
+    CF_TRY(C->ensure(B_HW, 8 * R.hsz));
+    CF_TRY(C->ensure(B_HR, 8 * R.hsz));
+    CF_TRY(C->ensure(B_WSQ, 8 * (size_t)nsets));
+    R.qcap = C->opt[CF_OPT_QUEUE] > 0 ? (uint32_t)C->opt[CF_OPT_QUEUE] : C->qcap_default;
+    CF_TRY(C->ensure(B_QUEUE, 16 * (size_t)R.qcap));
+    CF_TRY(C->ensure_host(readback_bytes(R)));
+
+    CF_CU(cudaMemcpyAsync(C->buf[B_PLAN].p, &D, sizeof(CfDevPlan), cudaMemcpyHostToDevice, st), "plan");
+    CF_CU(cudaMemcpyAsync(C->buf[B_LUT].p, H.lut.data(), 4 * H.lut.size(), cudaMemcpyHostToDevice, st), "lut");
+    if (!H.fine.empty())
+        CF_CU(cudaMemcpyAsync(C->buf[B_FINE].p, H.fine.data(), sizeof(CfFine) * H.fine.size(), cudaMemcpyHostToDevice, st),
+              "fine");
+    CF_CU(cudaMemcpyAsync(C->buf[B_STENCIL].p, H.stencil.data(), sizeof(CfStencil) * H.stencil.size(),
+                          cudaMemcpyHostToDevice, st), "stencil");
+    CF_CU(cudaMemcpyAsync(C->buf[B_JOBS].p, R.jobs.data(), sizeof(CfJobDesc) * njobs, cudaMemcpyHostToDevice, st), "jobs");
+    CF_CU(cudaMemcpyAsync(C->buf[B_SETS].p, R.sets.data(), sizeof(CfSetDesc) * nsets, cudaMemcpyHostToDevice, st),
+          "sets");
+    // pageable uploads: the host copies (the plan, the vectors) must outlive the transfers
+    CF_CU(cudaStreamSynchronize(st), "upload sync");
+
+    // pair-kernel configuration
+    std::memset(&R.cfg, 0, sizeof(R.cfg));
+    R.cfg.kind = D.kind;
+    R.cfg.weighted = D.weighted;
+    R.cfg.ravg = D.ravg;
+    R.cfg.wrap = D.g.wrap[0] | D.g.wrap[1] | D.g.wrap[2];
+    R.cfg.lo = D.f64lo;
+    R.cfg.nlut_words = D.nlut_words;
+    R.cfg.nfine = D.nfine;
+    R.cfg.nslot = D.nslot;
+    R.cfg.warps = (int)C->opt[CF_OPT_WARPS];
+    R.cfg.ctas_per_sm = (int)C->opt[CF_OPT_CTAS_PER_SM];
+    R.items_cap = 0;
+    return CF_OK;
+}
+
+size_t readback_bytes(const CfRun &R) { return 64 + 24 * R.hsz + 8 * (size_t)R.nsets; }
+
+// cell build + work-list count and scan (device only)
+int cf_enqueue_build(CfCtx *C, CfRun &R)
+{
+    cudaStream_t st = C->stream;
+    const CfDevPlan *dplan = (const CfDevPlan *)C->buf[B_PLAN].p;
+    const CfSetDesc *dsets = (const CfSetDesc *)C->buf[B_SETS].p;
+    const CfJobDesc *djobs = (const CfJobDesc *)C->buf[B_JOBS].p;
+    uint32_t *cnt = (uint32_t *)C->buf[B_CNT].p, *cstart = (uint32_t *)C->buf[B_CSTART].p;
+    uint32_t *misc = (uint32_t *)C->buf[B_MISC].p;
+    CF_CU(cudaMemsetAsync(cnt, 0, 4 * (size_t)R.ncell_all, st), "memset counts");
+    CF_CU(cudaMemsetAsync(misc, 0, 4096, st), "memset misc");
+    CF_CU(cfb_assign(dplan, dsets, R.nsets, R.np, cnt, (uint32_t *)C->buf[B_CELLID].p, (uint32_t *)C->buf[B_SLOT].p, st),
+          "assign");
+    CF_CU(cfb_scan(cnt, cstart, R.ncell_all, (uint32_t *)C->buf[B_SCAN].p, st), "scan cells");
+    CF_CU(cfb_scatter(dplan, dsets, R.nsets, R.np, cstart, (uint32_t *)C->buf[B_CELLID].p, (uint32_t *)C->buf[B_SLOT].p,
+                      (float4 *)C->buf[B_PA].p, (float4 *)C->buf[B_PB].p, (float4 *)C->buf[B_PLO].p,
+                      (uint32_t *)C->buf[B_ORIG].p, st),
+          "scatter");
+    uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
+    CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, cstart, R.nthr, 0, icnt, nullptr, nullptr,
+                    0, nullptr, st),
+          "items count");
+    CF_CU(cfb_scan(icnt, ioff, R.nthr, (uint32_t *)C->buf[B_SCAN].p, st), "scan items");
+    return CF_OK;
+}
+
+// work items -> pair kernel -> recheck -> readback (device only; records ev[1..3] when `timed`)
+int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
+{
+    cudaStream_t st = C->stream;
+    const CfDevPlan *dplan = (const CfDevPlan *)C->buf[B_PLAN].p;
+    const CfSetDesc *dsets = (const CfSetDesc *)C->buf[B_SETS].p;
+    const CfJobDesc *djobs = (const CfJobDesc *)C->buf[B_JOBS].p;
+    const CfDevPlan &D = R.plan.d;
+    uint32_t *misc = (uint32_t *)C->buf[B_MISC].p;
+    uint32_t *ioff = (uint32_t *)C->buf[B_IOFF].p;
+    unsigned long long *evaluated = (unsigned long long *)(misc + 16);
+    CF_CU(cudaMemsetAsync(misc, 0, 16, st), "memset");
+    CF_CU(cudaMemsetAsync(evaluated, 0, 8, st), "memset");
+    CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, (const uint32_t *)C->buf[B_CSTART].p,
+                    R.nthr, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated, st),
+          "items emit");
+    CF_CU(cudaMemsetAsync(C->buf[B_HCNT].p, 0, 8 * R.hsz, st), "memset");
+    CF_CU(cudaMemsetAsync(C->buf[B_HW].p, 0, 8 * R.hsz, st), "memset");
+    CF_CU(cudaMemsetAsync(C->buf[B_HR].p, 0, 8 * R.hsz, st), "memset");
+    CF_CU(cudaMemsetAsync(C->buf[B_WSQ].p, 0, 8 * (size_t)R.nsets, st), "memset");
+    if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[1], st, C->capturing ? cudaEventRecordExternal : 0), "event");
+    CfPairArgs &A = R.args;
+    std::memset(&A, 0, sizeof(A));
+    A.plan = dplan;
+    A.lut = (const uint32_t *)C->buf[B_LUT].p;
+    A.fine = (const CfFine *)C->buf[B_FINE].p;
+    A.items = (const CfItem *)C->buf[B_ITEMS].p;
+    A.nitems_dev = ioff + R.nthr;
+    A.items_cap = R.items_cap;
+    A.qcap = R.qcap;
+    A.cursor = misc;
+    A.qcount = misc + 1;
+    A.pa = (const ulonglong2 *)C->buf[B_PA].p;
+    A.pb = (const ulonglong2 *)C->buf[B_PB].p;
+    A.plo = (const ulonglong2 *)C->buf[B_PLO].p;
+    A.orig = (const uint32_t *)C->buf[B_ORIG].p;
+    A.hcnt = (unsigned long long *)C->buf[B_HCNT].p;
+    A.hw = (double *)C->buf[B_HW].p;
+    A.hr = (double *)C->buf[B_HR].p;
+    A.queue = (uint4 *)C->buf[B_QUEUE].p;
+    for (int a = 0; a < 3; a++) A.L[a] = D.g.wrap[a] ? (float)D.g.L[a] : 0.f;
+    A.nb = D.nb;
+    A.npi = D.npi;
+    A.nslot = D.nslot;
+    int grid = 0, warps = 0;
+    if (R.items_cap > 0) {
+        cudaError_t e = cfp_launch_pair(R.cfg, A, C->num_sms, st, &grid, &warps);
+        if (e == cudaErrorInvalidValue) return C->fail(CF_ERR_ARG, "histogram does not fit in shared memory");
+        CF_CU(e, "pair kernel");
+    }
+    C->last_grid = grid;
+    C->last_warps = warps;
+    if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[2], st, C->capturing ? cudaEventRecordExternal : 0), "event");
+    CF_CU(cfp_launch_recheck(dplan, dsets, djobs, A.queue, A.qcount, R.qcap, A.hcnt, A.hw, A.hr, C->num_sms, st), "recheck");
+    if (R.self_pairs && D.weighted)
+        CF_CU(cfb_wsq(dsets, R.nsets, R.np, (double *)C->buf[B_WSQ].p, st), "self-pair weights");
+    if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[3], st, C->capturing ? cudaEventRecordExternal : 0), "event");
+    // readback: [cursor, qcount, items total, pad] [evaluated] [hcnt] [hw] [hr] [wsq]
+    char *h = (char *)C->hpin;
+    const size_t hsz = R.hsz;
+    CF_CU(cudaMemcpyAsync(h, misc, 8, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 8, ioff + R.nthr, 4, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 16, evaluated, 8, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 64, C->buf[B_HCNT].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 64 + 8 * hsz, C->buf[B_HW].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 64 + 16 * hsz, C->buf[B_HR].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 64 + 24 * hsz, C->buf[B_WSQ].p, 8 * (size_t)R.nsets, cudaMemcpyDeviceToHost, st),
+          "readback");
+    return CF_OK;
+}
+
+// after the stream is synchronised: overflow checks (*retry = 1 queue, 2 items) and finalize
+int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
+{
+    const char *h = (const char *)C->hpin;
+    const uint32_t qn = ((const uint32_t *)h)[1];
+    const uint32_t nitems = ((const uint32_t *)h)[2];
+    *retry = 0;
+    if (nitems > R.items_cap) {
+        R.items_cap = nitems;
+        *retry = 2;
+        return CF_OK;
+    }
+    if (qn > R.qcap) {
+        R.qcap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, (uint64_t)qn + qn / 4 + 1024);
+        C->qcap_default = std::max(C->qcap_default, R.qcap);
+        *retry = 1;
+        return CF_OK;
+    }
+    const size_t nslot = R.nslot, hsz = R.hsz;
+    const unsigned long long *hc = (const unsigned long long *)(h + 64);
+    const double *hw = (const double *)(h + 64 + 8 * hsz);
+    const double *hr = (const double *)(h + 64 + 16 * hsz);
+    const double *wsq = (const double *)(h + 64 + 24 * hsz);
+    const CfDevPlan &D = R.plan.d;
+    res.assign(R.njobs, CfJobResult());
+    for (int j = 0; j < R.njobs; j++) {
+        CfJobResult &Q = res[j];
+        Q.npairs.assign(nslot, 0);
+        Q.wsum.assign(nslot, 0.0);
+        Q.rsum.assign(nslot, 0.0);
+        const bool autoc = R.jobs[j].autoc != 0;
+        const double mult = autoc ? 2.0 : 1.0;
+        for (size_t k = 0; k < nslot; k++) {
+            // Sec. 4.3: unique pairs were counted for an auto-correlation; double them
+            Q.npairs[k] = hc[j * nslot + k] * (autoc ? 2ull : 1ull);
+            Q.wsum[k] = D.weighted ? hw[j * nslot + k] * mult : (double)Q.npairs[k];
+            Q.rsum[k] = hr[j * nslot + k] * mult;
+        }
+        if (autoc && R.self_pairs) {
+            // Appendix B: the N self pairs, added once, in the first bin (first pi bin for rp-pi)
+            int64_t n = R.sets[R.jobs[j].a].n;
+            Q.npairs[0] += (uint64_t)n;
+            Q.wsum[0] += D.weighted ? wsq[R.jobs[j].a] : (double)n;
+        }
+        Q.n1 = R.sets[R.jobs[j].a].n;
+        Q.autoc = autoc;
+    }
+    C->stats.rechecked_pairs = qn;
+    C->stats.evaluated_pairs = (int64_t) * (const unsigned long long *)(h + 16);
+    C->stats.work_items = nitems;
+    C->stats.cells = R.ncell;
+    for (int a = 0; a < 3; a++) {
+        C->stats.grid[a] = D.g.n[a];
+        C->stats.refine[a] = D.g.k[a];
+    }
+    C->stats.ncat = R.njobs;
+    C->stats.variant = C->last_warps;
+    return CF_OK;
+}
+
+static void record_times(CfCtx *C, bool with_build)
+{
+    float ms = 0;
+    if (with_build && cudaEventElapsedTime(&ms, C->ev[0], C->ev[1]) == cudaSuccess) C->stats.ms_build = ms;
+    if (cudaEventElapsedTime(&ms, C->ev[1], C->ev[2]) == cudaSuccess) C->stats.ms_pair = ms;
+    if (cudaEventElapsedTime(&ms, C->ev[2], C->ev[3]) == cudaSuccess) C->stats.ms_recheck = ms;
+    cudaGetLastError();
+}
+
+int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &pts, const std::vector<CfJobDesc> &jobs,
+           std::vector<CfJobResult> &res)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    CfRun &R = C->run;
+    C->drop_graph();
+    CF_TRY(cf_prepare(C, p, pts, jobs, R));
+    cudaStream_t st = C->stream;
+    CF_CU(cudaEventRecord(C->ev[0], st), "event");
+    CF_TRY(cf_enqueue_build(C, R));
+    // size the work list from the device count (one small readback)
+    CF_CU(cudaMemcpyAsync(C->hpin, (uint32_t *)C->buf[B_IOFF].p + R.nthr, 4, cudaMemcpyDeviceToHost, st), "items total");
+    CF_CU(cudaStreamSynchronize(st), "items sync");
+    R.items_cap = *(const uint32_t *)C->hpin;
+    CF_TRY(C->ensure(B_ITEMS, sizeof(CfItem) * std::max<size_t>(1, R.items_cap)));
+    for (int attempt = 0; attempt < 4; attempt++) {
+        CF_TRY(cf_enqueue_count(C, R, true));
+        CF_CU(cudaStreamSynchronize(st), "count sync");
+        int retry = 0;
+        CF_TRY(cf_finish(C, R, res, &retry));
+        if (!retry) {
+            record_times(C, attempt == 0);
+            C->stats.ms_total =
+                (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            return CF_OK;
+        }
+        if (retry == 1) CF_TRY(C->ensure(B_QUEUE, 16 * (size_t)R.qcap));
+        if (retry == 2) CF_TRY(C->ensure(B_ITEMS, sizeof(CfItem) * (size_t)R.items_cap));
+    }
+    return C->fail(CF_ERR_INTERNAL, "recheck queue kept overflowing");
+}
+
+void cf_write_result(const cf_params *p, const CfJobResult &Q, cf_result *out)
+{
+    if (!out) return;
+    const size_t nslot = Q.npairs.size();
+    if (out->npairs) std::memcpy(out->npairs, Q.npairs.data(), 8 * nslot);
+    if (out->wsum) std::memcpy(out->wsum, Q.wsum.data(), 8 * nslot);
+    if (out->ravg) {
+        for (size_t k = 0; k < nslot; k++) {
+            double den = p->weight == CF_W_PAIR_PRODUCT ? Q.wsum[k] : (double)Q.npairs[k];
+            out->ravg[k] = (p->output_ravg && den > 0) ? Q.rsum[k] / den : 0.0;
+        }
+    }
+    if (out->wp) {
+        const int nb = p->nbins;
+        if (p->kind == CF_WP && p->periodic && Q.autoc) {
+            // Eq. (2) with 1 + xi = DD/RR (Sec. 2.1) and RR from density (N-1)/V (Appendix B):
+            // wp = DD / (N (N-1) / V * pi (rp_hi^2 - rp_lo^2)) - 2 pimax
+            const double V = p->box[0] * p->box[1] * p->box[2];
+            const double n = (double)Q.n1;
+            for (int k = 0; k < nb; k++) {
+                double area = M_PI * (p->edges[k + 1] * p->edges[k + 1] - p->edges[k] * p->edges[k]);
+                double rr = n * (n - 1) / V * area;
+                out->wp[k] = rr > 0 ? (double)Q.npairs[k] / rr - 2.0 * p->pimax : 0.0;
+            }
+        } else {
+            for (int k = 0; k < nb; k++) out->wp[k] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+cf_status cf_create(void **ctx_out, int device, void *cuda_stream)
+{
+    if (!ctx_out) return CF_ERR_ARG;
+    *ctx_out = nullptr;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return CF_ERR_CUDA;
+    }
+    CfCtx *C = new CfCtx();
+    C->device = device;
+    C->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&C->num_sms, cudaDevAttrMultiProcessorCount, device);
+    for (auto &e : C->ev) {
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            delete C;
+            cudaSetDevice(prev);
+            return CF_ERR_CUDA;
+        }
+    }
+    cudaSetDevice(prev);
+    *ctx_out = C;
+    return CF_OK;
+}
+
+cf_status cf_destroy(void *ctx)
+{
+    if (!ctx) return CF_ERR_ARG;
+    CfCtx *C = (CfCtx *)ctx;
+    DeviceGuard g(C->device);
+    cudaStreamSynchronize(C->stream);
+    delete C;
+    return CF_OK;
+}
+
+const char *cf_last_error(const void *ctx)
+{
+    if (!ctx) return "null context";
+    return ((const CfCtx *)ctx)->err.c_str();
+}
+
+cf_status cf_set_option(void *ctx, int option, int64_t value)
+{
+    if (!ctx) return CF_ERR_ARG;
+    CfCtx *C = (CfCtx *)ctx;
+    if (option < 1 || option >= CF_OPT_COUNT_) return (cf_status)C->fail(CF_ERR_ARG, "unknown option");
+    if (value < 0) return (cf_status)C->fail(CF_ERR_ARG, "option values must be >= 0");
+    C->opt[option] = value;
+    if (option == CF_OPT_MEM_CAP) C->mem_cap = (size_t)value;
+    return CF_OK;
+}
+
+cf_status cf_get_stats(const void *ctx, cf_stats *out)
+{
+    if (!ctx || !out) return CF_ERR_ARG;
+    *out = ((const CfCtx *)ctx)->stats;
+    return CF_OK;
+}
+
+cf_status cf_count(void *ctx, const cf_params *params, const cf_points *d1, const cf_points *d2, cf_result *out)
+{
+    if (!ctx) return CF_ERR_ARG;
+    CfCtx *C = (CfCtx *)ctx;
+    DeviceGuard g(C->device);
+    if (!params) return (cf_status)C->fail(CF_ERR_ARG, "params is NULL");
+    if (params->autocorr && d2) return (cf_status)C->fail(CF_ERR_ARG, "d2 must be NULL for an auto-correlation");
+    if (!params->autocorr && !d2) return (cf_status)C->fail(CF_ERR_ARG, "d2 is required for a cross-correlation");
+    std::vector<const cf_points *> pts{d1};
+    std::vector<CfJobDesc> jobs(1);
+    jobs[0] = {0, params->autocorr ? 0 : 1, params->autocorr ? 1 : 0, 0};
+    if (!params->autocorr) pts.push_back(d2);
+    std::vector<CfJobResult> res;
+    int rc = cf_run(C, params, pts, jobs, res);
+    if (rc) return (cf_status)rc;
+    cf_write_result(params, res[0], out);
+    return CF_OK;
+}
+
+static int batch_jobs(CfCtx *C, const cf_params *params, const cf_points *cats, int ncat,
+                      std::vector<const cf_points *> &pts, std::vector<CfJobDesc> &jobs)
+{
+    if (!params || !cats || ncat < 1) return C->fail(CF_ERR_ARG, "params / cats / ncat invalid");
+    if (!params->autocorr) return C->fail(CF_ERR_ARG, "batched counting is for auto-correlations");
+    pts.resize(ncat);
+    jobs.resize(ncat);
+    for (int c = 0; c < ncat; c++) {
+        pts[c] = &cats[c];
+        jobs[c] = {c, c, 1, 0};
+    }
+    return CF_OK;
+}
+
+cf_status cf_batch_count(void *ctx, const cf_params *params, const cf_points *cats, int ncat, cf_result *outs)
+{
+    if (!ctx) return CF_ERR_ARG;
+    CfCtx *C = (CfCtx *)ctx;
+    DeviceGuard g(C->device);
+    std::vector<const cf_points *> pts;
+    std::vector<CfJobDesc> jobs;
+    int rc = batch_jobs(C, params, cats, ncat, pts, jobs);
+    if (rc) return (cf_status)rc;
+    std::vector<CfJobResult> res;
+    rc = cf_run(C, params, pts, jobs, res);
+    if (rc) return (cf_status)rc;
+    for (int c = 0; c < ncat; c++)
+        if (outs) cf_write_result(params, res[c], &outs[c]);
+    return CF_OK;
+}
+
+cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *cats, int ncat)
+{
+    if (!ctx) return CF_ERR_ARG;
+    CfCtx *C = (CfCtx *)ctx;
+    DeviceGuard g(C->device);
+    std::vector<const cf_points *> pts;
+    std::vector<CfJobDesc> jobs;
+    int rc = batch_jobs(C, params, cats, ncat, pts, jobs);
+    if (rc) return (cf_status)rc;
+    for (int c = 0; c < ncat; c++)
+        if (!cats[c].on_device) return (cf_status)C->fail(CF_ERR_ARG, "graph capture needs device-resident catalogues");
+    // a normal run sizes every buffer (and checks the inputs); the graph then records the two
+    // device phases with a work-list capacity 25% above the measured size
+    std::vector<CfJobResult> res;
+    rc = cf_run(C, params, pts, jobs, res);
+    if (rc) return (cf_status)rc;
+    CfRun &R = C->run;
+    R.items_cap = R.items_cap + R.items_cap / 4 + 1024;
+    if ((rc = C->ensure(B_ITEMS, sizeof(CfItem) * (size_t)R.items_cap))) return (cf_status)rc;
+    R.qcap = std::max(R.qcap, (uint32_t)(C->stats.rechecked_pairs * 2 + 4096));
+    if ((rc = C->ensure(B_QUEUE, 16 * (size_t)R.qcap))) return (cf_status)rc;
+    cudaStream_t st = C->stream;
+    cudaStreamSynchronize(st);
+    C->drop_graph();
+    if ((rc = C->cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return (cf_status)rc;
+    C->capturing = true;
+    int rc1 = cf_enqueue_build(C, R);
+    int rc2 = rc1 ? rc1 : cf_enqueue_count(C, R, true);
+    C->capturing = false;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (rc2) {
+        if (graph) cudaGraphDestroy(graph);
+        return (cf_status)rc2;
+    }
+    if ((rc = C->cuda(e, "end capture"))) return (cf_status)rc;
+    C->graph = graph;
+    if ((rc = C->cuda(cudaGraphInstantiate(&C->graph_exec, graph, 0), "graph instantiate"))) {
+        C->drop_graph();
+        return (cf_status)rc;
+    }
+    C->graph_gen = C->gen;
+    C->graph_ncat = ncat;
+    return CF_OK;
+}
+
+cf_status cf_batch_replay(void *ctx, cf_result *outs, int ncat)
+{
+    if (!ctx) return CF_ERR_ARG;
+    CfCtx *C = (CfCtx *)ctx;
+    DeviceGuard g(C->device);
+    if (!C->graph_exec) return (cf_status)C->fail(CF_ERR_ARG, "no captured batch on this context");
+    if (ncat != C->graph_ncat) return (cf_status)C->fail(CF_ERR_ARG, "ncat differs from the captured batch");
+    if (C->gen != C->graph_gen) {
+        C->drop_graph();
+        return (cf_status)C->fail(CF_ERR_INTERNAL, "device scratch changed since capture; capture again");
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t st = C->stream;
+    int rc;
+    if ((rc = C->cuda(cudaGraphLaunch(C->graph_exec, st), "graph launch"))) return (cf_status)rc;
+    if ((rc = C->cuda(cudaStreamSynchronize(st), "graph sync"))) return (cf_status)rc;
+    CfRun &R = C->run;
+    std::vector<CfJobResult> res;
+    int retry = 0;
+    if ((rc = cf_finish(C, R, res, &retry))) return (cf_status)rc;
+    if (retry) {
+        // the work list or the recheck queue outgrew the captured capacity: count without the
+        // graph (same inputs) and drop the graph so that the next capture sizes it again
+        std::vector<const cf_points *> pts;
+        for (auto &q : R.pts) pts.push_back(&q);
+        std::vector<CfJobDesc> jobs = R.jobs;
+        cf_params p = R.p;
+        std::vector<double> edges = R.edges;
+        p.edges = edges.data();
+        std::vector<cf_points> keep = R.pts;
+        pts.clear();
+        for (auto &q : keep) pts.push_back(&q);
+        if ((rc = cf_run(C, &p, pts, jobs, res))) return (cf_status)rc;
+    } else {
+        record_times(C, false);
+        C->stats.ms_build = 0;
+    }
+    for (int c = 0; c < ncat; c++)
+        if (outs) cf_write_result(&R.p, res[c], &outs[c]);
+    C->stats.ms_total = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return CF_OK;
+}
+
+}  // extern "C"

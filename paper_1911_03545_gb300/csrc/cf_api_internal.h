@@ -1,0 +1,98 @@
+// cf_api_internal.h -- the context object and the shared host path of the entry points.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "cf.h"
+#include "cf_build.h"
+#include "cf_plan.h"
+
+enum CfBuf {
+    B_IN, B_SETS, B_BBOX, B_PLAN, B_LUT, B_FINE, B_STENCIL, B_JOBS, B_CNT, B_CSTART, B_CELLID, B_SLOT,
+    B_PA, B_PB, B_PLO, B_ORIG, B_SCAN, B_ICNT, B_IOFF, B_ITEMS, B_HCNT, B_HW, B_HR, B_QUEUE, B_WSQ, B_MISC,
+    B_COUNT_
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+struct CfJobResult {
+    std::vector<unsigned long long> npairs;
+    std::vector<double> wsum, rsum;
+    int64_t n1 = 0;
+    bool autoc = false;
+};
+
+// State of one call between its phases (kept in the context so a captured graph can be replayed)
+struct CfRun {
+    cf_params p;
+    std::vector<double> edges;
+    std::vector<cf_points> pts;
+    std::vector<CfSetDesc> sets;
+    std::vector<CfJobDesc> jobs;
+    CfHostPlan plan;
+    int nsets = 0, njobs = 0;
+    int64_t npts = 0, nmax = 0, np = 1, ncell = 0, ncell_all = 0, nst = 0, nthr = 0;
+    size_t nslot = 0, hsz = 0;
+    bool self_pairs = false;
+    uint32_t qcap = 0, items_cap = 0;
+    CfPairCfg cfg;
+    CfPairArgs args;
+};
+
+struct CfCtx {
+    struct Buf {
+        void *p = nullptr;
+        size_t cap = 0;
+    };
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 1;
+    std::string err;
+    size_t mem_cap = 0, mem_used = 0;
+    Buf buf[B_COUNT_];
+    void *hpin = nullptr;
+    size_t hpin_cap = 0;
+    int64_t opt[CF_OPT_COUNT_] = {0};
+    uint32_t qcap_default = 1u << 20;
+    cf_stats stats = {};
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    CfRun run;
+    int last_grid = 0, last_warps = 0;
+    uint64_t gen = 0;              // bumped whenever device or pinned scratch is reallocated
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_gen = 0;
+    int graph_ncat = 0;
+    bool capturing = false;
+
+    int fail(int status, const std::string &msg);
+    int cuda(cudaError_t e, const char *what);
+    int ensure(int b, size_t bytes);
+    int ensure_host(size_t bytes);
+    void drop_graph();
+    ~CfCtx();
+};
+
+size_t readback_bytes(const CfRun &R);
+int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &pts,
+               const std::vector<CfJobDesc> &jobs, CfRun &R);
+int cf_enqueue_build(CfCtx *C, CfRun &R);
+int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed);
+int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry);
+int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &pts, const std::vector<CfJobDesc> &jobs,
+           std::vector<CfJobResult> &res);
+void cf_write_result(const cf_params *p, const CfJobResult &R, cf_result *out);

@@ -1,0 +1,373 @@
+// cf_build.cu -- cell build (Sec. 4.1 grid, Sec. 4.3 contiguous per-cell storage) and the work
+// list of cell pairs (Sec. 4.2-4.3), as a counting sort: count -> exclusive scan -> scatter.
+#include "cf_build.h"
+#include "cf_device.cuh"
+
+// ---------------------------------------------------------------------------------------------
+// Bounding box and validity of every point set: min / max per axis, count of non-finite values.
+// grid = (blocks, nsets); out[s*8 + 0..5] = key(min x,y,z), key(max x,y,z); out[s*8+6] = bad.
+// ---------------------------------------------------------------------------------------------
+__global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long long *__restrict__ out)
+{
+    const CfSetDesc S = sets[blockIdx.y];
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0}, bad = 0;
+    const void *P[3] = {S.x, S.y, S.z};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int a = 0; a < 3; a++) {
+            double v = cf_load(P[a], S.dtype, i);
+            if (!isfinite(v)) { bad++; continue; }
+            unsigned long long k = cf_dkey(v);
+            mn[a] = k < mn[a] ? k : mn[a];
+            mx[a] = k > mx[a] ? k : mx[a];
+        }
+        if (S.w) {
+            double w = cf_load(S.w, S.dtype, i);
+            if (!isfinite(w)) bad++;
+        }
+    }
+    for (int o = 16; o; o >>= 1) {
+        for (int a = 0; a < 3; a++) {
+            unsigned long long t = __shfl_xor_sync(CF_FULL, mn[a], o);
+            mn[a] = t < mn[a] ? t : mn[a];
+            t = __shfl_xor_sync(CF_FULL, mx[a], o);
+            mx[a] = t > mx[a] ? t : mx[a];
+        }
+        bad += __shfl_xor_sync(CF_FULL, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        unsigned long long *o = out + blockIdx.y * 8;
+        for (int a = 0; a < 3; a++) {
+            atomicMin(o + a, mn[a]);
+            atomicMax(o + 3 + a, mx[a]);
+        }
+        if (bad) atomicAdd(o + 6, bad);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Cell assignment (Sec. 4.1, Eq. 3): cell = (ix*ny + iy)*nz + iz; the rank within the cell comes
+// from an atomic counter.
+// ---------------------------------------------------------------------------------------------
+__global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
+                                 uint32_t *__restrict__ count, uint32_t *__restrict__ cellid,
+                                 uint32_t *__restrict__ slot)
+{
+    const CfSetDesc S = sets[blockIdx.y];
+    const CfGrid &g = plan->g;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+        int ix = cf_cell_axis(g, 0, cf_load(S.x, S.dtype, i));
+        int iy = cf_cell_axis(g, 1, cf_load(S.y, S.dtype, i));
+        int iz = cf_cell_axis(g, 2, cf_load(S.z, S.dtype, i));
+        uint32_t c = (uint32_t)((ix * g.n[1] + iy) * g.n[2] + iz);
+        int64_t p = S.pbeg + i;
+        cellid[p] = c;
+        slot[p] = atomicAdd(count + S.cbeg + c, 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Exclusive scan of u32 counts into u32 offsets (+ total at out[n]), three phases:
+// tile scans -> scan of tile totals -> add tile offsets.  Tiles of 4096 values.
+// ---------------------------------------------------------------------------------------------
+#define SCAN_T 256
+#define SCAN_V 16
+#define SCAN_TILE (SCAN_T * SCAN_V)
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(CF_FULL, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = lane < (SCAN_T / 32) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(CF_FULL, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < (SCAN_T / 32)) sh[lane] = s;
+    }
+    __syncthreads();
+    uint32_t pre = (w ? sh[w - 1] : 0) + x - v;
+    if (total) *total = sh[SCAN_T / 32 - 1];
+    __syncthreads();
+    return pre;
+}
+
+__global__ void cf_scan_tiles(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
+                              uint32_t *__restrict__ tile_tot)
+{
+    __shared__ uint32_t sh[SCAN_T / 32];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_V;
+    uint32_t v[SCAN_V], s = 0;
+    for (int k = 0; k < SCAN_V; k++) {
+        v[k] = (base + k < n) ? in[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t tot;
+    uint32_t pre = block_excl_scan(s, sh, &tot);
+    for (int k = 0; k < SCAN_V; k++) {
+        if (base + k < n) out[base + k] = pre;
+        pre += v[k];
+    }
+    if (threadIdx.x == 0) tile_tot[blockIdx.x] = tot;
+}
+
+// single block: exclusive scan of up to SCAN_TILE tile totals in place; writes the grand total
+__global__ void cf_scan_totals(uint32_t *__restrict__ tile_tot, int ntiles, uint32_t *__restrict__ grand)
+{
+    __shared__ uint32_t sh[SCAN_T / 32];
+    uint32_t carry = 0;
+    for (int base0 = 0; base0 < ntiles; base0 += SCAN_TILE) {
+        int base = base0 + threadIdx.x * SCAN_V;
+        uint32_t v[SCAN_V], s = 0;
+        for (int k = 0; k < SCAN_V; k++) {
+            v[k] = (base + k < ntiles) ? tile_tot[base + k] : 0u;
+            s += v[k];
+        }
+        uint32_t tot;
+        uint32_t pre = block_excl_scan(s, sh, &tot) + carry;
+        for (int k = 0; k < SCAN_V; k++) {
+            if (base + k < ntiles) tile_tot[base + k] = pre;
+            pre += v[k];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) *grand = carry;
+}
+
+__global__ void cf_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ tile_off,
+                            const uint32_t *__restrict__ grand)
+{
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    uint32_t off = tile_off[blockIdx.x];
+    for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_T) {
+        int64_t i = base + k;
+        if (i < n) out[i] += off;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *grand;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Scatter into cell order (Sec. 4.3).  Writes the packed j-side layout pa/pb (cell-relative,
+// negated, duplicated), the FP64 residual plo when requested, and the original index.
+// ---------------------------------------------------------------------------------------------
+__global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
+                                  const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ cellid,
+                                  const uint32_t *__restrict__ slot, float4 *__restrict__ pa,
+                                  float4 *__restrict__ pb, float4 *__restrict__ plo,
+                                  uint32_t *__restrict__ orig)
+{
+    const CfSetDesc S = sets[blockIdx.y];
+    const CfGrid &g = plan->g;
+    const int lo = plan->f64lo;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t p = S.pbeg + i;
+        uint32_t c = cellid[p];
+        int iz = c % g.n[2];
+        int iy = (c / g.n[2]) % g.n[1];
+        int ix = c / (g.n[2] * g.n[1]);
+        int64_t dst = cell_start[S.cbeg + c] + slot[p];
+        double X = cf_load(S.x, S.dtype, i) - cf_origin(g, 0, ix);
+        double Y = cf_load(S.y, S.dtype, i) - cf_origin(g, 1, iy);
+        double Z = cf_load(S.z, S.dtype, i) - cf_origin(g, 2, iz);
+        float xf = (float)X, yf = (float)Y, zf = (float)Z;
+        float w = S.w ? (float)cf_load(S.w, S.dtype, i) : 1.0f;
+        pa[dst] = make_float4(-xf, -xf, -yf, -yf);
+        pb[dst] = make_float4(-zf, -zf, w, w);
+        if (lo) {
+            float xl = (float)(X - (double)xf), yl = (float)(Y - (double)yf), zl = (float)(Z - (double)zf);
+            plo[2 * dst] = make_float4(-xl, -xl, -yl, -yl);
+            plo[2 * dst + 1] = make_float4(-zl, -zl, 0.f, 0.f);
+        }
+        orig[dst] = (uint32_t)i;
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Work list (Sec. 4.2-4.3).  One thread per (job, cell of set a, stencil entry): the target cell
+// of set b, the shift that brings the target's points next to the source cell (Sec. 4.4), the
+// auto-correlation rule target >= source (Sec. 4.3), then the cell pair is cut into items of one
+// i tile (<= tile points) by one j range (<= jchunk points; the i tiles themselves for the
+// diagonal of an auto-correlation).  mode 0 counts items per thread, mode 1 writes them.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void cf_tiles(uint32_t n, uint32_t tmax, uint32_t &nt, uint32_t &ts)
+{
+    nt = (n + tmax - 1) / tmax;
+    ts = nt ? (n + nt - 1) / nt : 0;
+}
+
+__global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
+                                const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
+                                const uint32_t *__restrict__ cell_start, int mode,
+                                uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets,
+                                CfItem *__restrict__ items, uint32_t items_cap,
+                                unsigned long long *__restrict__ evaluated)
+{
+    const CfGrid &g = plan->g;
+    const int nst = g.nstencil;
+    const int64_t per_job = (int64_t)g.ncell * nst;
+    const int64_t total = per_job * plan->njobs;
+    const uint32_t tile = plan->tile, jchunk = plan->jchunk;
+    unsigned long long ev = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int job = (int)(t / per_job);
+        int64_t r = t - (int64_t)job * per_job;
+        int c = (int)(r / nst);
+        int s = (int)(r - (int64_t)c * nst);
+        const CfJobDesc J = jobs[job];
+        const CfSetDesc &A = sets[J.a];
+        const CfSetDesc &B = sets[J.b];
+        int ci[3] = {c / (g.n[2] * g.n[1]), (c / g.n[2]) % g.n[1], c % g.n[2]};
+        int tj[3];
+        double shift[3];
+        bool ok = true;
+        for (int a = 0; a < 3; a++) {
+            int d = stencil[s].d[a];
+            int v = ci[a] + d;
+            double delta = 0.0;        // image of the j point: x_j + delta
+            if (g.wrap[a]) {
+                v %= g.n[a];
+            } else if (g.periodic) {
+                if (v < 0) { v += g.n[a]; delta = -g.L[a]; }
+                else if (v >= g.n[a]) { v -= g.n[a]; delta = g.L[a]; }
+            } else if (v < 0 || v >= g.n[a]) {
+                ok = false;
+            }
+            tj[a] = v;
+            if (ok) shift[a] = cf_origin(g, a, ci[a]) - cf_origin(g, a, v) - delta;
+        }
+        uint32_t cnt = 0;
+        if (ok) {
+            int ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
+            if (J.autoc && ct < c) ok = false;
+            if (ok) {
+                uint32_t ia = cell_start[A.cbeg + c], na = cell_start[A.cbeg + c + 1] - ia;
+                uint32_t jb = cell_start[B.cbeg + ct], nb = cell_start[B.cbeg + ct + 1] - jb;
+                if (na && nb) {
+                    uint32_t nti, tsi;
+                    cf_tiles(na, tile, nti, tsi);
+                    bool diag = J.autoc && ct == c;
+                    uint32_t ntj, tsj;
+                    if (diag) { ntj = nti; tsj = tsi; }
+                    else cf_tiles(nb, jchunk, ntj, tsj);
+                    cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
+                    if (mode == 1) {
+                        uint32_t o = offsets[t];
+                        float sh[3], sl[3];
+                        for (int a = 0; a < 3; a++) {
+                            sh[a] = (float)shift[a];
+                            sl[a] = (float)(shift[a] - (double)sh[a]);
+                        }
+                        for (uint32_t a0 = 0; a0 < nti; a0++) {
+                            uint32_t i0 = a0 * tsi, ic = min(tsi, na - i0);
+                            uint32_t b0 = diag ? a0 : 0;
+                            for (uint32_t b = b0; b < ntj; b++) {
+                                uint32_t j0 = b * tsj, jc = min(tsj, nb - j0);
+                                CfItem it;
+                                it.ibeg = ia + i0;
+                                it.jbeg = jb + j0;
+                                it.cnt = ic | (jc << 16);
+                                it.meta = (uint32_t)job | ((diag && b == a0) ? CFI_ITEM_DIAG : 0u) |
+                                          (ic > 64 ? CFI_ITEM_P2 : 0u);
+                                it.s[0] = sh[0]; it.s[1] = sh[1]; it.s[2] = sh[2]; it.pad0 = 0.f;
+                                it.slo[0] = sl[0]; it.slo[1] = sl[1]; it.slo[2] = sl[2]; it.pad1 = 0.f;
+                                if (o < items_cap) items[o] = it;
+                                o++;
+                                ev += (unsigned long long)ic * jc;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (mode == 0) counts[t] = cnt;
+    }
+    if (mode == 1) {
+        for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(CF_FULL, ev, o);
+        if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evaluated, ev);
+    }
+}
+
+// sum of w^2 per set (self pairs of a weighted auto-correlation whose first edge is 0)
+__global__ void cf_wsq_kernel(const CfSetDesc *__restrict__ sets, double *__restrict__ out)
+{
+    const CfSetDesc S = sets[blockIdx.y];
+    double s = 0;
+    if (S.w)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+            double w = cf_load(S.w, S.dtype, i);
+            s += w * w;
+        }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(CF_FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0) atomicAdd(out + blockIdx.y, s);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------------------------
+static int blocks_for(int64_t n, int threads, int cap)
+{
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st)
+{
+    dim3 grid(blocks_for(nmax, 256, 1024), nsets);
+    cf_bbox_kernel<<<grid, 256, 0, st>>>(sets, out);
+    return cudaGetLastError();
+}
+
+cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, uint32_t *count,
+                       uint32_t *cellid, uint32_t *slot, cudaStream_t st)
+{
+    dim3 grid(blocks_for(nmax, 256, 4096), nsets);
+    cf_assign_kernel<<<grid, 256, 0, st>>>(plan, sets, count, cellid, slot);
+    return cudaGetLastError();
+}
+
+int64_t cfb_scan_tmp_words(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 8; }
+
+cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st)
+{
+    int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (ntiles < 1) ntiles = 1;
+    uint32_t *grand = tmp + ntiles;
+    cf_scan_tiles<<<(unsigned)ntiles, SCAN_T, 0, st>>>(in, out, n, tmp);
+    cf_scan_totals<<<1, SCAN_T, 0, st>>>(tmp, (int)ntiles, grand);
+    cf_scan_add<<<(unsigned)ntiles, SCAN_T, 0, st>>>(out, n, tmp, grand);
+    return cudaGetLastError();
+}
+
+cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax,
+                        const uint32_t *cell_start, const uint32_t *cellid, const uint32_t *slot, float4 *pa,
+                        float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st)
+{
+    dim3 grid(blocks_for(nmax, 256, 4096), nsets);
+    cf_scatter_kernel<<<grid, 256, 0, st>>>(plan, sets, cell_start, cellid, slot, pa, pb, plo, orig);
+    return cudaGetLastError();
+}
+
+cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
+                      const uint32_t *cell_start, int64_t nthreads, int mode, uint32_t *counts,
+                      const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
+                      cudaStream_t st)
+{
+    cf_items_kernel<<<blocks_for(nthreads, 256, 8192), 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, mode,
+                                                                    counts, offsets, items, items_cap, evaluated);
+    return cudaGetLastError();
+}
+
+cudaError_t cfb_wsq(const CfSetDesc *sets, int nsets, int64_t nmax, double *out, cudaStream_t st)
+{
+    dim3 grid(blocks_for(nmax, 256, 1024), nsets);
+    cf_wsq_kernel<<<grid, 256, 0, st>>>(sets, out);
+    return cudaGetLastError();
+}

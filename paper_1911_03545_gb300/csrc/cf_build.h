@@ -1,0 +1,64 @@
+// cf_build.h -- launchers of the cell-build, work-list and pair-count kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "cf_internal.h"
+
+cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st);
+cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, uint32_t *count,
+                       uint32_t *cellid, uint32_t *slot, cudaStream_t st);
+int64_t cfb_scan_tmp_words(int64_t n);
+cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st);
+cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax,
+                        const uint32_t *cell_start, const uint32_t *cellid, const uint32_t *slot, float4 *pa,
+                        float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st);
+cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
+                      const uint32_t *cell_start, int64_t nthreads, int mode, uint32_t *counts,
+                      const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
+                      cudaStream_t st);
+cudaError_t cfb_wsq(const CfSetDesc *sets, int nsets, int64_t nmax, double *out, cudaStream_t st);
+
+// ---- pair counting ----
+struct CfPairArgs {
+    const CfDevPlan *plan;
+    const uint32_t *lut;         // coarse LUT words (global copy; staged into shared memory)
+    const CfFine *fine;          // fine LUT entries
+    const CfItem *items;
+    const uint32_t *nitems_dev;  // item count written by the work-list scan
+    uint32_t items_cap;          // items beyond this were not stored
+    uint32_t qcap;
+    uint32_t *cursor;
+    const ulonglong2 *pa;        // (-X,-X | -Y,-Y)
+    const ulonglong2 *pb;        // (-Z,-Z | w, w)
+    const ulonglong2 *plo;       // FP64 residuals, two per point (may be NULL)
+    const uint32_t *orig;
+    unsigned long long *hcnt;    // [njobs][nslot]
+    double *hw;                  // [njobs][nslot]
+    double *hr;                  // [njobs][nslot]
+    uint4 *queue;                // (orig i, orig j, job, 0)
+    uint32_t *qcount;
+    float L[3];                  // periodic sides (wrap axes)
+    int nb, npi, nslot;
+    int audit;
+};
+
+// Static configuration of a pair-kernel launch (selects the template instance and the shared
+// memory layout).
+struct CfPairCfg {
+    int kind;          // 0 r, 1 rppi, 2 wp, 3 theta
+    int weighted, ravg, wrap, lo;
+    int nlut_words, nfine, nslot;
+    int warps;         // warps per CTA (0: automatic)
+    int ctas_per_sm;   // 0: occupancy-derived
+};
+
+// Shared-memory bytes of one CTA with `warps` warps.
+size_t cfp_pair_smem(const CfPairCfg &c, int warps);
+
+// Launch the persistent pair kernel.  Returns cudaErrorInvalidValue when no CTA shape fits in
+// shared memory.  *grid_out receives the number of CTAs launched.
+cudaError_t cfp_launch_pair(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st,
+                            int *grid_out, int *warps_out);
+cudaError_t cfp_launch_recheck(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs,
+                               const uint4 *queue, const uint32_t *qcount, uint32_t qcap,
+                               unsigned long long *hcnt, double *hw, double *hr, int num_sms, cudaStream_t st);

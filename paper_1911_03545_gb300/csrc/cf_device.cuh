@@ -1,0 +1,85 @@
+// cf_device.cuh -- device helpers shared by the CUDA translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cf_internal.h"
+
+#define CF_FULL 0xFFFFFFFFu
+
+typedef unsigned long long u64;
+
+// ---- packed FP32 pairs (PTX f32x2, sm_100+): lane h of a u64 is float h ----
+__device__ __forceinline__ u64 f2_add(u64 a, u64 b)
+{
+    u64 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 f2_mul(u64 a, u64 b)
+{
+    u64 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 f2_fma(u64 a, u64 b, u64 c)
+{
+    u64 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+__device__ __forceinline__ u64 f2_pack(float lo, float hi)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float f2_lo(u64 v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(u64 v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint32_t f2_lo_bits(u64 v) { return (uint32_t)v; }
+__device__ __forceinline__ uint32_t f2_hi_bits(u64 v) { return (uint32_t)(v >> 32); }
+
+// sqrt.approx.f32: relative error within a few ulp; used only for ravg sums (1e-6 tolerance)
+__device__ __forceinline__ float f_sqrt_approx(float x)
+{
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// ---- cell origin (FP64).  For float32 coordinates x in the cell, x - origin is exact in
+// float32: the origin is a multiple of the float32 spacing at the cell's largest magnitude and
+// lies between 0 and every x of the cell (0 itself for a cell that straddles 0). ----
+__device__ __forceinline__ double cf_origin(const CfGrid &g, int a, int i)
+{
+    double lo = g.lo[a] + (double)i * g.width[a];
+    double hi = lo + g.width[a];
+    if (lo <= 0.0 && hi >= 0.0) return 0.0;
+    double m = fmax(fabs(lo), fabs(hi)) * (1.0 + 1.0 / 1048576.0);
+    int e;
+    frexp(m, &e);
+    double q = ldexp(1.0, e - 24);
+    if (lo > 0.0) return floor(lo / q) * q;
+    return ceil(hi / q) * q;
+}
+
+__device__ __forceinline__ int cf_cell_axis(const CfGrid &g, int a, double x)
+{
+    double t = (x - g.lo[a]) * g.inv[a];
+    int i = (int)floor(t);
+    if (i < 0) i = 0;
+    if (i > g.n[a] - 1) i = g.n[a] - 1;
+    return i;
+}
+
+__device__ __forceinline__ double cf_load(const void *p, int dtype, int64_t i)
+{
+    return dtype ? ((const double *)p)[i] : (double)((const float *)p)[i];
+}
+
+// order-preserving map of a double to an unsigned 64-bit key (for atomic min / max)
+__device__ __forceinline__ unsigned long long cf_dkey(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}

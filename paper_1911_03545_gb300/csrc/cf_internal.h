@@ -1,0 +1,110 @@
+// cf_internal.h -- descriptors shared by the host planner and the CUDA kernels.
+//
+// Data layout in device memory (one call = a set of point sets and a set of jobs):
+//   point set s (a catalogue, or one side of a cross count) is scattered into cell order by a
+//   counting sort (Sec. 4.3: particles of a cell are stored contiguously).  For every point p
+//   (global index over all sets) we keep
+//     pa[p] = float4(-X, -X, -Y, -Y)   pb[p] = float4(-Z, -Z, w, w)
+//   where X = x - o(cell) is the cell-relative coordinate (Sec. 4.4's shift trick applied per
+//   cell), stored negated and duplicated so that one packed f32x2 add forms two separations.
+//     plo[p] = float4(-Xlo, -Ylo, -Zlo, 0)  (float64 inputs with ravg only: x - o = X + Xlo)
+//     orig[p] = index of the point in its input arrays
+//   cell_start[set cell offset + c] .. [c+1] delimit a cell's points.
+//   A work item is one (i tile, j range, shift) triple of a cell pair (Sec. 4.3).
+#pragma once
+#include <stdint.h>
+
+#include "cf.h"
+
+#define CFI_MAX_SETS 4096
+#define CFI_MAX_STENCIL 4096
+#define CFI_LUT_MAX 8192          // coarse LUT cells (4 B each)
+#define CFI_FINE_MAX 1024         // fine LUT entries (16 B each)
+#define CFI_CLS_OUT 0xFEu         // class: outside every bin
+#define CFI_CLS_AMB 0xFFu         // class: within the FP32 error band of an edge
+#define CFI_FINE_FLAG 0x100u      // coarse entry >= this: index of a fine entry + flag
+
+// Pair-kernel item (48 bytes, three 16-byte loads)
+struct CfItem {
+    uint32_t ibeg;     // first i point (global sorted index)
+    uint32_t jbeg;     // first j point
+    uint32_t cnt;      // icnt (low 16) | jcnt (high 16)
+    uint32_t meta;     // job (low 20 bits) | diag (bit 30) | two packs (bit 29)
+    float s[3];        // shift hi:  x_i - x_j = (X_i + s + slo) - X_j
+    float pad0;
+    float slo[3];      // shift lo
+    float pad1;
+};
+#define CFI_ITEM_DIAG (1u << 30)
+#define CFI_ITEM_P2 (1u << 29)
+#define CFI_ITEM_JOBMASK 0xFFFFFu
+
+// A point set (input view + where its sorted points and cells live)
+struct CfSetDesc {
+    const void *x, *y, *z, *w;   // device pointers of the input arrays
+    int64_t n;
+    int dtype;                   // 0 f32, 1 f64
+    int pad;
+    int64_t pbeg;                // first sorted point of this set
+    int64_t cbeg;                // first cell of this set in cell_start
+};
+
+// A job: count set a (i side) against set b (j side) into histogram slot block `job`
+struct CfJobDesc {
+    int a, b;
+    int autoc;
+    int pad;
+};
+
+// Coarse/fine bin lookup on the bit pattern of a non-negative float (Sec. 4.7: bins are found
+// on squared separations; the bit pattern of a positive float is monotone in its value).
+struct CfLut {
+    uint32_t base;     // bits of the start of coarse cell 0
+    uint32_t shift;    // log2 of a coarse cell width in bit space
+    uint32_t last;     // index of the last coarse cell (values above clamp here)
+    uint32_t coff;     // offset of the coarse entries in the shared LUT array (in words)
+    uint32_t foff;     // offset of the fine entries (in 16-byte units from the fine base)
+    uint32_t pad[3];
+};
+
+struct CfFine {        // class of v: byte seg of `code`, seg = (v >= t1) + (v >= t2)
+    uint32_t t1, t2, code, pad;
+};
+
+// Grid parameters (Sec. 4.1 Eq. 3 cell index; Sec. 4.2 refinement)
+struct CfGrid {
+    int n[3];
+    int ncell;
+    double lo[3];
+    double width[3];
+    double inv[3];         // n / extent
+    double L[3];           // periodic side (0 when not periodic)
+    int periodic;
+    int wrap[3];           // explicit minimum image on this axis
+    int k[3];
+    int nstencil;
+};
+
+struct CfStencil {         // neighbour offset per axis; wrap axes enumerate targets (i+d) mod n
+    int d[3];
+    int pad;
+};
+
+// Everything the kernels need for one call
+struct CfDevPlan {
+    CfGrid g;
+    int kind;              // 0 r, 1 rppi, 2 wp, 3 theta
+    int nb;                // r / rp / theta bins
+    int npi;               // pi bins (1 for r, theta, wp)
+    int nslot;             // nb * npi for rppi, nb otherwise
+    int weighted, ravg, f64lo;
+    int nsets, njobs;
+    int tile;              // max i tile (64 or 128)
+    int jchunk;            // max j range per item
+    CfLut lr, lp;          // r/rp/chord LUT, and pi LUT (rppi/wp)
+    int nlut_words;        // coarse words (both LUTs)
+    int nfine;             // fine entries (both LUTs)
+    double pimax;
+    double e2[CF_MAX_BINS + 1];     // squared edges (FP64, host-computed)
+    double pe[CF_MAX_PIBINS + 1];   // pi edges
+};

@@ -1,0 +1,363 @@
+// cf_plan.cpp -- host planning for the pair counter.
+//
+//  * grid: Sec. 4.1 (cells of width >= the largest separation, n = floor(extent / Rmax)),
+//    Sec. 4.2 (k sub-cells per Rmax cell, (2k+1) neighbours per axis);
+//  * stencil: Sec. 4.3 (cell pairs that may hold a pair within range); offsets whose cell gap
+//    alone exceeds the range are dropped (the minimum cell-pair separation of Sec. 7);
+//  * FP32 error bands and the bin lookup: Sec. 4.7 finds bins on squared separations; here the
+//    lookup runs on the FP32 bit pattern, and every value within the proven FP32 error of an
+//    edge is classed "ambiguous" and re-evaluated in FP64 by the recheck kernel.
+#include "cf_plan.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace {
+
+const double U32 = 5.9604644775390625e-08;   // 2^-24, FP32 unit roundoff
+const double U64 = 1.1102230246251565e-16;   // 2^-53
+const double SAFETY = 4.0;                    // margin on the first-order error bound
+
+double ulp32_of_magnitude(double m)
+{
+    // spacing of float32 values of magnitude <= m (power of two), m > 0
+    int e;
+    std::frexp(m * (1.0 + 1.0 / 1048576.0), &e);   // m = f * 2^e, f in [0.5, 1)
+    return std::ldexp(1.0, e - 24);
+}
+
+bool all_finite(const double *v, int n)
+{
+    for (int i = 0; i < n; i++)
+        if (!std::isfinite(v[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+uint32_t cfp_float_ceil_bits(double v)
+{
+    if (!(v > 0)) return 0u;
+    float f = (float)v;
+    if ((double)f < v) f = std::nextafter(f, INFINITY);
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return b;
+}
+
+uint32_t cfp_float_above_bits(double v)
+{
+    if (v < 0) return 0u;
+    float f = (float)v;
+    if ((double)f <= v) f = std::nextafter(f, INFINITY);
+    uint32_t b;
+    std::memcpy(&b, &f, 4);
+    return b;
+}
+
+int cfp_check_params(const cf_params *p, std::string &err)
+{
+    if (!p) { err = "params is NULL"; return CF_ERR_ARG; }
+    if (p->kind < CF_DD_R || p->kind > CF_DD_THETA) { err = "unknown kind"; return CF_ERR_ARG; }
+    if (p->nbins < 1 || p->nbins > CF_MAX_BINS) { err = "nbins must be in [1, 252]"; return CF_ERR_ARG; }
+    if (!p->edges) { err = "edges is NULL"; return CF_ERR_ARG; }
+    if (!all_finite(p->edges, p->nbins + 1)) { err = "edges must be finite"; return CF_ERR_ARG; }
+    if (p->edges[0] < 0) { err = "edges must be >= 0"; return CF_ERR_ARG; }
+    for (int k = 0; k < p->nbins; k++)
+        if (!(p->edges[k + 1] > p->edges[k])) { err = "edges must be strictly increasing"; return CF_ERR_ARG; }
+    if (p->kind == CF_DD_THETA) {
+        if (p->periodic) { err = "DD(theta) is non-periodic"; return CF_ERR_ARG; }
+        if (p->edges[p->nbins] > 180.0) { err = "theta edges must be <= 180 degrees"; return CF_ERR_ARG; }
+    }
+    if (p->kind == CF_DD_RPPI || p->kind == CF_WP) {
+        if (!(std::isfinite(p->pimax) && p->pimax > 0)) { err = "pimax must be finite and > 0"; return CF_ERR_ARG; }
+        if (p->npibins < 1 || p->npibins > CF_MAX_PIBINS) { err = "npibins must be in [1, 252]"; return CF_ERR_ARG; }
+    }
+    if (p->periodic) {
+        for (int a = 0; a < 3; a++)
+            if (!(std::isfinite(p->box[a]) && p->box[a] > 0)) { err = "periodic box sides must be finite and > 0"; return CF_ERR_ARG; }
+    }
+    for (int a = 0; a < 3; a++)
+        if (p->refine[a] < 0 || p->refine[a] > 4) { err = "refine factors must be in [0, 4]"; return CF_ERR_ARG; }
+    if (p->weight != CF_W_NONE && p->weight != CF_W_PAIR_PRODUCT) { err = "unknown weight type"; return CF_ERR_ARG; }
+    if (p->kind == CF_WP && !p->autocorr && false) { err = ""; return CF_ERR_ARG; }
+    return CF_OK;
+}
+
+void cfp_edges(const cf_params *p, double *e2, double *pe)
+{
+    for (int k = 0; k <= p->nbins; k++) {
+        double e = p->edges[k];
+        if (p->kind == CF_DD_THETA) {
+            double c = 2.0 * std::sin(e * (M_PI / 360.0));
+            e2[k] = c * c;
+        } else {
+            e2[k] = e * e;
+        }
+    }
+    if (p->kind == CF_DD_RPPI || p->kind == CF_WP) {
+        double dpi = p->pimax / p->npibins;
+        for (int m = 0; m < p->npibins; m++) pe[m] = (double)m * dpi;
+        pe[p->npibins] = p->pimax;
+    }
+}
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// Bin lookup tables
+// ---------------------------------------------------------------------------------------
+struct Seg { uint32_t start; uint32_t cls; };
+
+// Class function over float bit patterns for edges E[0..m] with bands B: half-open bins
+// [E_k, E_k+1) -> class k; below E_0 -> OUT (or bin 0 when E_0 == 0); at or above E_m -> OUT;
+// within a band -> AMB.
+std::vector<Seg> make_segments(const double *E, const double *B, int m)
+{
+    struct Iv { uint32_t a, b; };
+    std::vector<Iv> amb;
+    std::vector<uint32_t> pts;
+    for (int k = 0; k <= m; k++) {
+        if (k == 0 && E[0] == 0.0) continue;          // nothing lies below 0: no band needed
+        uint32_t a = cfp_float_ceil_bits(E[k] - B[k]);
+        uint32_t b = cfp_float_above_bits(E[k] + B[k]);
+        amb.push_back({a, b});
+        pts.push_back(a);
+        pts.push_back(b);
+    }
+    pts.push_back(0u);
+    std::sort(pts.begin(), pts.end());
+    pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+    auto classify = [&](uint32_t v) -> uint32_t {
+        for (auto &iv : amb)
+            if (v >= iv.a && v < iv.b) return CFI_CLS_AMB;
+        float f;
+        std::memcpy(&f, &v, 4);
+        double x = (double)f;
+        if (x < E[0]) return CFI_CLS_OUT;
+        if (x >= E[m]) return CFI_CLS_OUT;
+        int k = m - 1;
+        while (k > 0 && x < E[k]) k--;
+        return (uint32_t)k;
+    };
+    std::vector<Seg> segs;
+    for (uint32_t s : pts) {
+        uint32_t c = classify(s);
+        if (segs.empty() || segs.back().cls != c) segs.push_back({s, c});
+    }
+    return segs;
+}
+
+// Build coarse + fine tables for the segment list.  Returns false if no cell width <= the
+// table limit separates the breakpoints into cells of at most three segments.
+bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint32_t> &words,
+               std::vector<CfFine> &fine)
+{
+    if (segs.size() < 2) return false;
+    uint32_t lo = segs[1].start;                  // first class change
+    uint32_t hi = segs.back().start;              // last class change
+    for (int s = 23; s >= 0; s--) {
+        uint64_t w = 1ull << s;
+        uint64_t base = ((uint64_t)lo >> s) << s;
+        base = base >= w ? base - w : 0;
+        uint64_t last = ((uint64_t)hi - base) >> s;
+        if (last + 1 > (uint64_t)CFI_LUT_MAX) return false;
+        if (last + 1 < 64 && s > 0) continue;     // too coarse to be useful; refine
+        std::vector<uint32_t> cw(last + 1);
+        std::vector<CfFine> fw;
+        bool ok = true;
+        size_t si = 0;                            // segment containing the cell start
+        for (uint64_t c = 0; c <= last && ok; c++) {
+            uint64_t c0 = base + c * w, c1 = c0 + w;
+            while (si + 1 < segs.size() && segs[si + 1].start <= c0) si++;
+            // segments starting strictly inside (c0, c1)
+            std::vector<Seg> inside;
+            for (size_t t = si + 1; t < segs.size() && segs[t].start < c1; t++) inside.push_back(segs[t]);
+            if (c == last) {
+                // values above the table clamp to this cell: it must end in the final class
+                for (size_t t = si + 1; t < segs.size(); t++)
+                    if (segs[t].start >= c1) { ok = false; break; }
+            }
+            if (inside.empty()) {
+                cw[c] = segs[si].cls;
+            } else if (inside.size() <= 2) {
+                CfFine f;
+                f.t1 = inside[0].start;
+                f.t2 = inside.size() > 1 ? inside[1].start : 0xFFFFFFFFu;
+                uint32_t c2 = inside.size() > 1 ? inside[1].cls : inside[0].cls;
+                f.code = segs[si].cls | (inside[0].cls << 8) | (c2 << 16);
+                f.pad = 0;
+                cw[c] = CFI_FINE_FLAG | (uint32_t)(fine.size() + fw.size());
+                fw.push_back(f);
+                if (fine.size() + fw.size() > CFI_FINE_MAX) ok = false;
+            } else {
+                ok = false;
+            }
+        }
+        if (!ok) continue;
+        L.base = (uint32_t)base;
+        L.shift = (uint32_t)s;
+        L.last = (uint32_t)last;
+        L.coff = (uint32_t)words.size();
+        L.foff = 0;
+        words.insert(words.end(), cw.begin(), cw.end());
+        fine.insert(fine.end(), fw.begin(), fw.end());
+        return true;
+    }
+    return false;
+}
+
+}  // namespace
+
+int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int f64,
+                  const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err)
+{
+    CfHostPlan &H = *out;
+    std::memset(&H.d, 0, sizeof(H.d));
+    H.lut.clear();
+    H.fine.clear();
+    H.stencil.clear();
+    CfDevPlan &D = H.d;
+    D.kind = p->kind;
+    D.nb = p->nbins;
+    D.npi = p->kind == CF_DD_RPPI ? p->npibins : 1;
+    D.nslot = D.nb * D.npi;
+    D.weighted = p->weight == CF_W_PAIR_PRODUCT;
+    D.ravg = p->output_ravg != 0;
+    D.f64lo = (f64 && D.ravg) ? 1 : 0;
+    D.tile = tile;
+    D.jchunk = jchunk;
+    D.pimax = p->pimax;
+    cfp_edges(p, D.e2, D.pe);
+    const bool rppi_like = p->kind == CF_DD_RPPI || p->kind == CF_WP;
+
+    // ---- largest separation per axis (cell width before refinement), Sec. 4.1 ----
+    double rmax = std::sqrt(D.e2[D.nb]);      // r, rp or chord
+    H.W[0] = H.W[1] = rmax;
+    H.W[2] = rppi_like ? p->pimax : rmax;
+
+    // ---- grid, Sec. 4.1 Eq. (3) and Sec. 4.2 ----
+    CfGrid &G = D.g;
+    G.periodic = p->periodic ? 1 : 0;
+    double extent[3];
+    for (int a = 0; a < 3; a++) {
+        int k = refine[a] > 0 ? refine[a] : 1;
+        G.k[a] = k;
+        if (p->periodic) {
+            G.lo[a] = 0.0;
+            extent[a] = p->box[a];
+            G.L[a] = p->box[a];
+        } else {
+            G.lo[a] = bbox[a];
+            extent[a] = bbox[3 + a] - bbox[a];
+            if (!(extent[a] > 0)) extent[a] = H.W[a] > 0 ? H.W[a] : 1.0;
+            G.L[a] = 0.0;
+        }
+        double nb = std::floor(extent[a] / H.W[a]);
+        if (!(nb >= 1)) nb = 1;
+        if (nb > 1e6) nb = 1e6;
+        G.n[a] = (int)nb * k;
+    }
+    // cap the number of cells (tiny separations in a large volume): a cell wider than the
+    // largest separation stays correct, it only holds more points
+    double cap = std::max(1048576.0, 8.0 * (double)npoints);
+    for (int it = 0; it < 64; it++) {
+        double tot = (double)G.n[0] * G.n[1] * G.n[2];
+        if (tot <= cap) break;
+        int a = 0;
+        for (int b = 1; b < 3; b++) if (G.n[b] > G.n[a]) a = b;
+        G.n[a] = std::max(G.k[a], (int)(G.n[a] * 0.8));
+    }
+    G.ncell = G.n[0] * G.n[1] * G.n[2];
+    for (int a = 0; a < 3; a++) {
+        G.width[a] = extent[a] / G.n[a];
+        G.inv[a] = G.n[a] / extent[a];
+        G.wrap[a] = (p->periodic && G.n[a] < 2 * G.k[a] + 1) ? 1 : 0;
+    }
+
+    // ---- stencil, Sec. 4.2-4.3 ----
+    std::vector<int> off[3];
+    for (int a = 0; a < 3; a++) {
+        if (G.wrap[a]) for (int d = 0; d < G.n[a]; d++) off[a].push_back(d);
+        else for (int d = -G.k[a]; d <= G.k[a]; d++) off[a].push_back(d);
+    }
+    auto gap = [&](int a, int d) -> double {
+        if (G.wrap[a]) return 0.0;
+        int g = std::abs(d) - 1;
+        if (g <= 0) return 0.0;
+        return g * G.width[a] * (1.0 - 1e-9);
+    };
+    for (int dx : off[0])
+        for (int dy : off[1])
+            for (int dz : off[2]) {
+                double gx = gap(0, dx), gy = gap(1, dy), gz = gap(2, dz);
+                bool keep;
+                if (rppi_like) keep = (gx * gx + gy * gy < D.e2[D.nb] * (1 + 1e-6)) && (gz < p->pimax * (1 + 1e-6));
+                else keep = gx * gx + gy * gy + gz * gz < D.e2[D.nb] * (1 + 1e-6);
+                if (keep) H.stencil.push_back({{dx, dy, dz}, 0});
+            }
+    if ((int)H.stencil.size() > CFI_MAX_STENCIL) { err = "stencil too large"; return CF_ERR_ARG; }
+    G.nstencil = (int)H.stencil.size();
+
+    // ---- FP32 error model (derivation in the design doc) ----
+    // stored cell-relative coordinates X are exact for float32 inputs (snapped origins);
+    // float64 inputs round to float32 (epsX), or keep a lo part when ravg is requested.
+    const double u = U32;
+    const bool precise = D.ravg;
+    for (int a = 0; a < 3; a++) {
+        double amax = std::max(std::fabs(G.lo[a]), std::fabs(G.lo[a] + extent[a]));
+        double Q = ulp32_of_magnitude(std::max(amax, 1e-300));
+        double M = G.wrap[a] ? (extent[a] + 2 * G.width[a]) : ((G.k[a] + 1) * G.width[a]);
+        M = M * 1.001 + 4 * Q;
+        double epsX = 0;
+        if (f64) epsX = D.f64lo ? (2 * U64 * 2 * amax + u * u * (G.width[a] + 2 * Q)) : (u * (G.width[a] + 2 * Q) + 2 * U64 * amax);
+        double wrapterm = G.wrap[a] ? u * G.L[a] : 0.0;
+        double truth = 2 * U64 * (M + G.L[a] + amax);
+        double delta;
+        if (precise) delta = 4 * u * u * M + 2 * epsX + wrapterm + truth;
+        else delta = u * M + u * M + 2 * epsX + wrapterm + truth;
+        H.delta[a] = delta;
+        H.M[a] = M;
+    }
+    H.theta_rel = precise ? 2 * u : u;
+    double th = H.theta_rel;
+    auto band_sq = [&](double E, int naxes) -> double {
+        double d = std::sqrt(E) * 1.01 + 1e-300;
+        double sumD = 0, quad = 0;
+        for (int a = 0; a < naxes; a++) {
+            sumD += H.delta[a];
+            quad += (th * d + H.delta[a]) * (th * d + H.delta[a]);
+        }
+        double chain = (naxes == 3 ? 3 : 2) * u * E;
+        return SAFETY * (2 * th * E + 2 * d * sumD + quad + chain + 4 * U64 * E);
+    };
+    int naxes = rppi_like ? 2 : 3;
+    for (int k = 0; k <= D.nb; k++) H.band_r[k] = band_sq(D.e2[k], naxes);
+    if (rppi_like) {
+        for (int m = 0; m <= p->npibins; m++) H.band_p[m] = SAFETY * (th * D.pe[m] + H.delta[2] + 4 * U64 * D.pe[m]);
+    }
+
+    // ---- lookup tables ----
+    {
+        auto segs = make_segments(D.e2, H.band_r, D.nb);
+        if (!build_lut(segs, D.lr, H.lut, H.fine)) {
+            err = "bin edges too close together for the FP32 lookup table";
+            return CF_ERR_ARG;
+        }
+    }
+    if (rppi_like) {
+        std::vector<double> pe(D.pe, D.pe + p->npibins + 1);
+        std::vector<double> bp(H.band_p, H.band_p + p->npibins + 1);
+        int m = p->npibins;
+        if (p->kind == CF_WP) { pe = {0.0, p->pimax}; bp = {0.0, H.band_p[p->npibins]}; m = 1; }
+        auto segs = make_segments(pe.data(), bp.data(), m);
+        if (!build_lut(segs, D.lp, H.lut, H.fine)) {
+            err = "pi bins too narrow for the FP32 lookup table";
+            return CF_ERR_ARG;
+        }
+    }
+    D.nlut_words = (int)H.lut.size();
+    D.nfine = (int)H.fine.size();
+    return CF_OK;
+}

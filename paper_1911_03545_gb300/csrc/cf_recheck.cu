@@ -1,0 +1,117 @@
+// cf_recheck.cu -- FP64 re-evaluation of pairs whose FP32 squared separation fell within the
+// error band of a bin edge, and the pair-kernel dispatcher.
+//
+// The arithmetic is the result definition itself (Sec. 2.1 Code naivecorr; Appendix A.1 Eq. sep;
+// Sec. 4.4 Code normal_pbc), evaluated on the original coordinates in FP64 with explicit
+// round-to-nearest operations and no fused multiply-add: d = a - b, wrapped once each way for a
+// periodic axis, s = (dx*dx + dy*dy) + dz*dz, bins half-open against the FP64 squared edges.
+#include "cf_build.h"
+#include "cf_device.cuh"
+#include "cf_pair.cuh"
+
+__device__ __forceinline__ double cf_sep64(double a, double b, double L)
+{
+    double d = __dsub_rn(a, b);
+    if (L > 0.0) {
+        double h = 0.5 * L;
+        if (d > h) d = __dsub_rn(d, L);
+        if (d <= -h) d = __dadd_rn(d, L);
+    }
+    return d;
+}
+
+__device__ __forceinline__ int cf_find64(const double *e, int n, double s)
+{
+    int k = n - 1;
+    while (k > 0 && s < e[k]) k--;
+    return k;
+}
+
+__global__ void cf_recheck_kernel(const CfDevPlan *__restrict__ P, const CfSetDesc *__restrict__ sets,
+                                  const CfJobDesc *__restrict__ jobs, const uint4 *__restrict__ queue,
+                                  const uint32_t *__restrict__ qcount, uint32_t qcap,
+                                  unsigned long long *__restrict__ hcnt, double *__restrict__ hw,
+                                  double *__restrict__ hr)
+{
+    const uint32_t n = min(*qcount, qcap);
+    const int kind = P->kind, nb = P->nb, npi = P->npi, nslot = P->nslot;
+    const double L0 = P->g.periodic ? P->g.L[0] : 0.0;
+    const double L1 = P->g.periodic ? P->g.L[1] : 0.0;
+    const double L2 = P->g.periodic ? P->g.L[2] : 0.0;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint4 e = queue[k];
+        const CfJobDesc J = jobs[e.z];
+        const CfSetDesc &A = sets[J.a];
+        const CfSetDesc &B = sets[J.b];
+        double dx = cf_sep64(cf_load(A.x, A.dtype, e.x), cf_load(B.x, B.dtype, e.y), L0);
+        double dy = cf_sep64(cf_load(A.y, A.dtype, e.x), cf_load(B.y, B.dtype, e.y), L1);
+        double dz = cf_sep64(cf_load(A.z, A.dtype, e.x), cf_load(B.z, B.dtype, e.y), L2);
+        int slot;
+        double sep = 0.0;
+        if (kind == 0 || kind == 3) {
+            double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            s = __dadd_rn(s, __dmul_rn(dz, dz));
+            if (s < P->e2[0] || s >= P->e2[nb]) continue;
+            slot = cf_find64(P->e2, nb, s);
+            if (P->ravg) {
+                double c = sqrt(s);
+                sep = kind == 3 ? 2.0 * asin(0.5 * c) * (180.0 / 3.141592653589793) : c;
+            }
+        } else {
+            double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+            double pi = fabs(dz);
+            if (s < P->e2[0] || s >= P->e2[nb]) continue;
+            if (!(pi < P->pimax)) continue;
+            slot = cf_find64(P->e2, nb, s);
+            if (P->ravg) sep = sqrt(s);
+            if (kind == 1) slot = slot * npi + cf_find64(P->pe, npi, pi);
+        }
+        const size_t g = (size_t)e.z * nslot + slot;
+        atomicAdd(hcnt + g, 1ull);
+        double ww = 1.0;
+        if (P->weighted) ww = __dmul_rn(cf_load(A.w, A.dtype, e.x), cf_load(B.w, B.dtype, e.y));
+        if (P->weighted) atomicAdd(hw + g, ww);
+        if (P->ravg) atomicAdd(hr + g, __dmul_rn(ww, sep));
+    }
+}
+
+cudaError_t cfp_launch_recheck(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs,
+                               const uint4 *queue, const uint32_t *qcount, uint32_t qcap,
+                               unsigned long long *hcnt, double *hw, double *hr, int num_sms, cudaStream_t st)
+{
+    cf_recheck_kernel<<<num_sms * 2, 256, 0, st>>>(plan, sets, jobs, queue, qcount, qcap, hcnt, hw, hr);
+    return cudaGetLastError();
+}
+
+// ---- pair-kernel dispatch ----
+cudaError_t cfp_launch_r(const CfPairCfg &, const CfPairArgs &, int, cudaStream_t, int *, int *);
+cudaError_t cfp_launch_rppi(const CfPairCfg &, const CfPairArgs &, int, cudaStream_t, int *, int *);
+cudaError_t cfp_launch_wp(const CfPairCfg &, const CfPairArgs &, int, cudaStream_t, int *, int *);
+cudaError_t cfp_launch_theta(const CfPairCfg &, const CfPairArgs &, int, cudaStream_t, int *, int *);
+
+size_t cfp_pair_smem(const CfPairCfg &c, int warps)
+{
+    size_t b = ((size_t)c.nlut_words * 4 + 15) & ~(size_t)15;
+    b += (size_t)c.nfine * 16;
+    size_t wb;
+    if (c.kind == 1) {
+        wb = (((size_t)c.nslot * 4 + 7) & ~(size_t)7) + (c.weighted ? c.nslot * 8 : 0) + (c.ravg ? c.nslot * 8 : 0);
+        wb = (wb + 15) & ~(size_t)15;
+    } else {
+        wb = (size_t)c.nslot * 32 * 4 + (c.weighted ? (size_t)c.nslot * 32 * 8 : 0) +
+             (c.ravg ? (size_t)c.nslot * 32 * 8 : 0);
+    }
+    return b + wb * warps;
+}
+
+cudaError_t cfp_launch_pair(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
+                            int *warps_out)
+{
+    switch (c.kind) {
+    case 0: return cfp_launch_r(c, a, num_sms, st, grid_out, warps_out);
+    case 1: return cfp_launch_rppi(c, a, num_sms, st, grid_out, warps_out);
+    case 2: return cfp_launch_wp(c, a, num_sms, st, grid_out, warps_out);
+    case 3: return cfp_launch_theta(c, a, num_sms, st, grid_out, warps_out);
+    }
+    return cudaErrorInvalidValue;
+}

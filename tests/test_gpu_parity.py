@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle, element by element.
+
+Counts must be bit-identical; weighted sums and ravg within 1e-6 relative.  Inputs are seeded
+synthetic catalogues sized so the oracle finishes in seconds while cells still hold several
+128-point tiles plus a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from tests.gpu_util import TOL, assert_match, gpu_count, to_dev
+from tests.test_oracle_pins import LATTICE, PERIODIC, RPPI, Cat
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1911_03545_gb300 as cf
+    c = cf.cf_create(0, torch.cuda.current_stream())
+    yield c
+    cf.cf_destroy(c)
+
+
+def both(ctx, kind, edges, d1, d2=None, **kw):
+    got = gpu_count(ctx, kind, edges, d1, d2, **kw)
+    okw = {k: v for k, v in kw.items() if k not in ("refine", "device")}
+    exp = oracle.count(kind, edges, d1, d2, **okw)
+    return got, exp
+
+
+# ---- exact ties (every separation is exact: all of them sit on edges or wrap boundaries) ----
+
+def _f32(cat):
+    for a in ("x", "y", "z"):
+        setattr(cat, a, getattr(cat, a).astype(np.float32))
+    if cat.w is not None:
+        cat.w = cat.w.astype(np.float32)
+    return cat
+
+
+@pytest.mark.parametrize("f32", [False, True])
+def test_hand_lattices(ctx, f32):
+    conv = _f32 if f32 else (lambda c: c)
+    d = conv(Cat(LATTICE, w=[1.0, 2.0, 0.5, 4.0]))
+    got, exp = both(ctx, "r", [1, 2, 3, 5, 6], d, autocorr=True, periodic=False, weighted=True, ravg=True)
+    assert got["npairs"].tolist() == [2, 4, 4, 2]
+    assert_match(got, exp, True, True)
+    d = conv(Cat(PERIODIC))
+    got, exp = both(ctx, "r", [0, 1, 2, 4, 5], d, autocorr=True, periodic=True, box=8.0)
+    assert got["npairs"].tolist() == [7, 4, 2, 10]
+    got, exp = both(ctx, "r", [0, 1, 2, 4, 5], d, d, autocorr=False, periodic=True, box=8.0)
+    assert got["npairs"].tolist() == [7, 4, 2, 10]
+    d = conv(Cat(RPPI))
+    got, exp = both(ctx, "rppi", [1, 2, 3, 5, 6], d, autocorr=True, periodic=False, pimax=3.0, npibins=3)
+    assert_match(got, exp)
+    got, exp = both(ctx, "wp", [1, 2, 3, 5, 6], d, autocorr=True, periodic=False, pimax=3.0, npibins=3)
+    assert got["npairs"].tolist() == [2, 4, 4, 0]
+    d = conv(Cat([(1, 0, 0), (0, 1, 0), (0, 0, 1), (-1, 0, 0)]))
+    got, exp = both(ctx, "theta", [60, 90, 180], d, autocorr=True, periodic=False, ravg=True)
+    assert got["npairs"].tolist() == [0, 10]
+    assert_match(got, exp, ravg=True)
+
+
+# ---- randomised parity over every kind and option ----
+
+def _catalogue(kind, n_centres, seed, dtype=np.float32, box=40.0):
+    if kind == "theta":
+        return gen.sphere_patch(n_centres * 60, 0.0, 25.0, -5.0, 20.0, seed)
+    d = gen.clustered_box(n_centres, 60, 1.2, box, seed, dtype=dtype)
+    u = gen.uniform_box(n_centres * 20, box, seed + 1, dtype=dtype)
+    return gen.Catalogue(*(np.concatenate([getattr(d, a), getattr(u, a)]) for a in "xyz"))
+
+
+CASES = []
+for kind in ("r", "rppi", "wp", "theta"):
+    for autocorr in (True, False):
+        for periodic in ((False,) if kind == "theta" else (True, False)):
+            for weighted, ravg in ((False, False), (True, False), (False, True), (True, True)):
+                CASES.append((kind, autocorr, periodic, weighted, ravg))
+
+
+@pytest.mark.parametrize("kind,autocorr,periodic,weighted,ravg", CASES)
+def test_random_parity(ctx, kind, autocorr, periodic, weighted, ravg):
+    seed = 1000 + len(kind) * 10 + int(autocorr) * 3 + int(periodic)
+    d1 = _catalogue(kind, 40, seed)
+    d2 = _catalogue(kind, 30, seed + 7)
+    d1.w = gen.uniform_weights(d1.n, 0.5, 1.5, seed + 2)
+    d2.w = gen.uniform_weights(d2.n, 0.5, 1.5, seed + 3)
+    edges = gen.log_edges(0.01, 2.5, 14) if kind == "theta" else gen.log_edges(0.05, 7.0, 12)
+    kw = dict(autocorr=autocorr, periodic=periodic, box=40.0, pimax=9.0, npibins=9, weighted=weighted, ravg=ravg)
+    got, exp = both(ctx, kind, edges, d1, None if autocorr else d2, **kw)
+    assert_match(got, exp, weighted, ravg)
+    assert int(np.asarray(got["npairs"]).sum()) > 1000
+
+
+@pytest.mark.parametrize("kind", ["r", "rppi", "theta"])
+def test_float64_inputs(ctx, kind):
+    d = _catalogue(kind, 30, 77, dtype=np.float64)
+    if kind == "theta":
+        d = gen.Catalogue(*(getattr(d, a).astype(np.float64) for a in "xyz"))
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 78).astype(np.float64)
+    edges = gen.log_edges(0.01, 2.5, 10) if kind == "theta" else gen.log_edges(0.05, 7.0, 10)
+    kw = dict(autocorr=True, periodic=kind != "theta", box=40.0, pimax=9.0, npibins=9)
+    for weighted, ravg in ((False, False), (True, True)):
+        got, exp = both(ctx, kind, edges, d, weighted=weighted, ravg=ravg, **kw)
+        assert_match(got, exp, weighted, ravg)
+
+
+def test_uniform_20k_float64_full(ctx):
+    """The correctness workload in full: N=20000 uniform float64, periodic L=250, 20 log bins."""
+    wl = gen.workload("uniform_r_20k")
+    got, exp = both(ctx, "r", wl.edges, wl.d1, autocorr=True, periodic=True, box=wl.box)
+    assert_match(got, exp)
+
+
+@pytest.mark.parametrize("refine", [(1, 1, 1), (2, 2, 2), (3, 1, 2), (4, 4, 4)])
+def test_refinement_does_not_change_results(ctx, refine):
+    d = _catalogue("r", 40, 5)
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 6)
+    edges = gen.log_edges(0.05, 7.0, 12)
+    got, exp = both(ctx, "r", edges, d, autocorr=True, periodic=True, box=40.0, weighted=True, ravg=True,
+                    refine=refine)
+    assert_match(got, exp, True, True)
+    got, exp = both(ctx, "rppi", edges, d, autocorr=True, periodic=True, box=40.0, pimax=9.0, npibins=9,
+                    refine=refine)
+    assert_match(got, exp)
+
+
+def test_rmax_spans_box(ctx):
+    """Cells fewer than 2k+1 per axis: explicit minimum image; totals are N(N-1) / N1*N2."""
+    d = gen.uniform_box(700, 10.0, 3)
+    e = gen.uniform_box(500, 10.0, 4)
+    got, exp = both(ctx, "r", [1e-6, 9.0], d, autocorr=True, periodic=True, box=10.0)
+    assert int(got["npairs"].sum()) == d.n * (d.n - 1)
+    assert_match(got, exp)
+    got, exp = both(ctx, "r", gen.log_edges(0.3, 6.0, 8), d, e, autocorr=False, periodic=True, box=10.0)
+    assert_match(got, exp)
+    got, exp = both(ctx, "rppi", gen.log_edges(0.3, 6.0, 8), d, autocorr=True, periodic=True, box=10.0,
+                    pimax=6.0, npibins=6)
+    assert_match(got, exp)
+    got, exp = both(ctx, "r", [1e-6, 18.0], d, autocorr=True, periodic=False)
+    assert int(got["npairs"].sum()) == d.n * (d.n - 1)
+
+
+def test_degenerate_inputs(ctx):
+    edges = [0.0, 0.5, 1.0, 2.0]
+    empty = gen.Catalogue(*(np.zeros(0, np.float32) for _ in range(3)))
+    got = gpu_count(ctx, "r", edges, empty, autocorr=True, periodic=True, box=5.0)
+    assert got["npairs"].tolist() == [0, 0, 0]
+    one = gen.Catalogue(*(np.array([1.0], np.float32) for _ in range(3)))
+    got = gpu_count(ctx, "r", edges, one, autocorr=True, periodic=True, box=5.0)
+    assert got["npairs"].tolist() == [1, 0, 0]            # its self pair (first edge 0, Appendix B)
+    same = gen.Catalogue(*(np.full(300, 2.5, np.float32) for _ in range(3)))
+    got, exp = both(ctx, "r", edges, same, autocorr=True, periodic=True, box=5.0)
+    assert got["npairs"].tolist() == [300 * 300, 0, 0]
+    assert_match(got, exp)
+    edge = gen.Catalogue(np.array([0.0, 5.0, 5.0, 2.5], np.float32), np.array([0.0, 0.0, 5.0, 2.5], np.float32),
+                         np.array([5.0, 0.0, 0.0, 2.5], np.float32))
+    got, exp = both(ctx, "r", edges, edge, autocorr=True, periodic=True, box=5.0)
+    assert_match(got, exp)
+
+
+def test_near_edge_adversarial(ctx):
+    """Pairs placed at e_k (1 +- delta) for delta from 1e-9 to 1e-5, and exactly on e_k."""
+    edges = gen.log_edges(0.1, 10.0, 8)
+    rng = np.random.Generator(np.random.PCG64(9))
+    pts = []
+    L = 100.0
+    for k, e in enumerate(edges):
+        for delta in (0.0, 1e-9, -1e-9, 1e-7, -1e-7, 1e-6, -1e-6, 1e-5, -1e-5):
+            c = rng.uniform(15, 85, 3)
+            v = rng.normal(size=3)
+            v /= np.linalg.norm(v)
+            pts.append(c)
+            pts.append(c + v * e * (1 + delta))
+    a = np.array(pts)
+    for dt in (np.float32, np.float64):
+        d = gen.Catalogue(*(a[:, i].astype(dt) for i in range(3)))
+        got, exp = both(ctx, "r", edges, d, autocorr=True, periodic=True, box=L)
+        assert_match(got, exp)
+        got, exp = both(ctx, "rppi", edges, d, autocorr=True, periodic=True, box=L, pimax=5.0, npibins=5)
+        assert_match(got, exp)
+
+
+def test_auto_equals_cross_gpu(ctx):
+    d = _catalogue("r", 40, 21)
+    edges = gen.log_edges(0.0 + 0.05, 7.0, 10)
+    a = gpu_count(ctx, "r", edges, d, autocorr=True, periodic=True, box=40.0)
+    c = gpu_count(ctx, "r", edges, d, d, autocorr=False, periodic=True, box=40.0)
+    assert np.array_equal(a["npairs"], c["npairs"])
+    e0 = np.concatenate([[0.0], edges])
+    a = gpu_count(ctx, "r", e0, d, autocorr=True, periodic=True, box=40.0)
+    c = gpu_count(ctx, "r", e0, d, d, autocorr=False, periodic=True, box=40.0)
+    assert np.array_equal(a["npairs"], c["npairs"])
+
+
+def test_host_inputs_equal_device_inputs(ctx):
+    d = _catalogue("r", 40, 31)
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 32)
+    edges = gen.log_edges(0.05, 7.0, 12)
+    kw = dict(autocorr=True, periodic=True, box=40.0, weighted=True, ravg=True)
+    a = gpu_count(ctx, "r", edges, d, device=True, **kw)
+    b = gpu_count(ctx, "r", edges, d, device=False, **kw)
+    assert np.array_equal(a["npairs"], b["npairs"])
+    np.testing.assert_allclose(a["wsum"], b["wsum"], rtol=TOL)
+
+
+def test_options_do_not_change_results(ctx):
+    import paper_1911_03545_gb300 as cf
+    d = _catalogue("r", 60, 41)
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 42)
+    edges = gen.log_edges(0.05, 7.0, 12)
+    kw = dict(autocorr=True, periodic=True, box=40.0, weighted=True, ravg=True)
+    exp = oracle.count("r", edges, d, **kw)
+    for opt, val in ((cf.CF_OPT_TILE, 64), (cf.CF_OPT_JCHUNK, 37), (cf.CF_OPT_WARPS, 2), (cf.CF_OPT_CTAS_PER_SM, 1),
+                     (cf.CF_OPT_QUEUE, 1)):
+        cf.cf_set_option(ctx, opt, val)
+        try:
+            got = gpu_count(ctx, "r", edges, d, **kw)
+        finally:
+            cf.cf_set_option(ctx, opt, 0)
+        assert_match(got, exp, True, True)
+
+
+def test_batch_equals_single(ctx):
+    import paper_1911_03545_gb300 as cf
+    import torch
+    edges = gen.log_edges(0.1, 8.0, 10)
+    cats = [gen.batch_catalogue(i, n, L=60.0, members=20) for i, n in enumerate([900, 3000, 50, 1700])]
+    p = cf.params(kind="rppi", edges=edges, autocorr=True, periodic=True, box=60.0, pimax=10.0, npibins=10)
+    pts = [cf.points(*to_dev(c, "cuda:0")) for c in cats]
+    outs = cf.cf_batch_count(ctx, p, pts)
+    for c, o in zip(cats, outs):
+        single = cf.cf_count(ctx, p, cf.points(*to_dev(c, "cuda:0")))
+        assert np.array_equal(o["npairs"], single["npairs"])
+        exp = oracle.count("rppi", edges, c, autocorr=True, periodic=True, box=60.0, pimax=10.0, npibins=10)
+        assert np.array_equal(o["npairs"], exp["npairs"])
+    torch.cuda.synchronize()
+
+
+def test_errors_leave_context_usable(ctx):
+    import paper_1911_03545_gb300 as cf
+    edges = gen.log_edges(0.1, 5.0, 6)
+    bad = gen.uniform_box(100, 10.0, 1)
+    bad.x[3] = 10.5
+    with pytest.raises(cf.CfError) as ei:
+        gpu_count(ctx, "r", edges, bad, autocorr=True, periodic=True, box=10.0)
+    assert ei.value.status == -1
+    nan = gen.uniform_box(100, 10.0, 2)
+    nan.y[5] = np.nan
+    with pytest.raises(cf.CfError):
+        gpu_count(ctx, "r", edges, nan, autocorr=True, periodic=False)
+    with pytest.raises(cf.CfError):
+        gpu_count(ctx, "r", [1.0, 0.5], nan, autocorr=True, periodic=False)
+    import torch
+    small = cf.cf_create(0, torch.cuda.current_stream())
+    try:
+        cf.cf_set_option(small, cf.CF_OPT_MEM_CAP, 1 << 16)
+        big = gen.uniform_box(200000, 50.0, 3)
+        with pytest.raises(cf.CfError) as ei:
+            gpu_count(small, "r", edges, big, autocorr=True, periodic=True, box=50.0)
+        assert ei.value.status == -2
+        cf.cf_set_option(small, cf.CF_OPT_MEM_CAP, 0)
+        good = gen.uniform_box(2000, 10.0, 4)
+        got, exp = both(small, "r", edges, good, autocorr=True, periodic=True, box=10.0)
+        assert_match(got, exp)
+    finally:
+        cf.cf_destroy(small)
+    good = gen.uniform_box(2000, 10.0, 4)
+    got, exp = both(ctx, "r", edges, good, autocorr=True, periodic=True, box=10.0)
+    assert_match(got, exp)
