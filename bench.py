@@ -1,0 +1,392 @@
+"""Benchmark of the GB300 pair counter (one JSON line on rank 0).
+
+Default workload (the headline configuration): DD(r) auto-correlation, periodic L=420 box,
+N = 1,000,000 clustered float32 points (10,000 centres x 100 members, Gaussian sigma = 1),
+20 log bins 0.1-20, pair-product weights and ravg.  A step is one cf_count of the whole
+workload with inputs already resident in HBM; the metric is pair-distance evaluations per
+second (separations the pair kernel computes), whole job over all ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl gb300|reference]
+
+Multi-GPU runs (torchrun) are independent replicas: the path of one catalogue does not shard
+across GPUs in this build; each rank counts its own copy and `value` sums the ranks' work
+over the slowest rank's time.  `--impl reference` times the FP64 CPU oracle instead (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair-distance evals/s"
+UNIT = "pairs/s"
+FP32_INSTR_PER_PAIR = 6          # 3 FADD (dx, dy, dz) + 1 FMUL + 2 FFMA: the algorithmic minimum
+L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2
+
+WORKLOADS = {
+    "clustered_r_1m": "DD(r) auto, periodic L=420, N=1,000,000 clustered float32 (10,000 centres x 100, "
+                      "sigma=1), 20 log bins 0.1-20, pair-product weights U[0.5,1.5) + ravg",
+    "uniform_r_20k": "DD(r) auto, periodic L=250, N=20,000 uniform float64, 20 log bins 0.1-25",
+    "clustered_rppi_2m": "DD(rp,pi) auto, periodic L=1000, N=2,000,000 clustered float32 (20,000 x 100, "
+                         "sigma=2), 14 log rp bins 0.1-25, pimax=40 with 40 pi bins",
+    "clustered_wp_2m": "wp(rp) auto, periodic L=1000, N=2,000,000 clustered float32, 14 log rp bins 0.1-25, pimax=40",
+    "clustered_rppi_dr": "DR(rp,pi) cross, periodic L=1000, D=2,000,000 clustered x R=4,000,000 uniform float32, "
+                         "14 log rp bins 0.1-25, pimax=40 with 40 pi bins",
+    "sphere_theta_1m": "DD(theta) auto, non-periodic, N=1,000,000 unit vectors (RA 0-90, DEC -10..30 deg) float32, "
+                       "20 log bins 0.001-1 deg",
+}
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _kernel_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("cf_pair.cuh", "cf_device.cuh", "cf_internal.h"):
+        with open(os.path.join(ROOT, "paper_1911_03545_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(workload: str):
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it was taken on the
+    current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "pair_kernel_traffic.txt")
+    try:
+        with open(p) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) >= 3 and not line.startswith("#") and parts[0] == workload:
+                    if parts[1] == _kernel_sha():
+                        return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.index)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(world, v: float, dev) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _sum_over_ranks(world, v: float, dev) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _wl_params(wl, cf):
+    return cf.params(kind=wl.kind, edges=wl.edges, autocorr=wl.autocorr, periodic=wl.periodic, box=wl.box,
+                     pimax=wl.pimax, npibins=wl.npibins, ravg=wl.ravg, weighted=wl.weighted)
+
+
+def _points(cat, weighted, cf, dev=None):
+    import numpy as np
+    import torch
+    arrs = [cat.x, cat.y, cat.z] + ([cat.w] if weighted else [])
+    if dev is None:
+        return cf.points(*[np.ascontiguousarray(a) for a in arrs[:3]], arrs[3] if weighted else None)
+    t = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in arrs]
+    return cf.points(*t[:3], t[3] if weighted else None)
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------------------------
+
+def _oracle_rows_rate(wl, seconds: float, seed: int = 0):
+    """Time the oracle (as it stands) on a bounded random sample of rows of the workload: each
+    row is every ordered pair (i, j) of one point i.  Returns (evals/s, cores, sample text)."""
+    import numpy as np
+
+    import oracle
+    lib = oracle.load()
+    cores = os.cpu_count() or 1
+    n1 = wl.d1.n
+    n2 = wl.d1.n if wl.autocorr else wl.d2.n
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def run(rows):
+        start = int(rng.integers(0, max(1, n1 - rows)))
+        t0 = time.perf_counter()
+        oracle.count(wl.kind, wl.edges, wl.d1, None if wl.autocorr else wl.d2, autocorr=wl.autocorr,
+                     periodic=wl.periodic, box=wl.box, pimax=wl.pimax, npibins=wl.npibins, weighted=wl.weighted,
+                     ravg=wl.ravg, rows=(start, start + rows), nthreads=cores, lib=lib)
+        return time.perf_counter() - t0
+
+    rows = 16
+    t = run(rows)
+    while t < 0.2 and rows < n1:
+        rows = min(n1, rows * 4)
+        t = run(rows)
+    rows = int(min(n1, max(1, rows * seconds / max(t, 1e-6))))
+    t = run(rows)
+    evals = rows * (n2 - (1 if wl.autocorr else 0))
+    sample = (f"{rows} consecutive rows (random start) of the workload, each against all {n2} points, "
+              f"brute-force FP64 oracle, {cores} threads, {t:.1f} s")
+    return evals / t, cores, sample, t
+
+
+def run_reference(args, wl, world, rank):
+    if rank != 0:
+        return 0
+    per_step = max(0.05, 150.0 / max(1, args.steps + args.warmup))
+    rates = []
+    cores, sample = os.cpu_count() or 1, ""
+    t_all = 0.0
+    for s in range(args.warmup + args.steps):
+        rate, cores, sample, t = _oracle_rows_rate(wl, per_step, seed=s)
+        if s >= args.warmup:
+            rates.append(rate)
+            t_all += t
+    value = statistics.fmean(rates)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "name": args.workload},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------------------------
+
+def run_gpu(args, wl, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1911_03545_gb300 as cf
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cf.cf_create(local, stream)
+    p = _wl_params(wl, cf)
+    d1 = _points(wl.d1, wl.weighted, cf, dev)
+    d2 = None if wl.autocorr else _points(wl.d2, wl.weighted, cf, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        cf.cf_count(ctx, p, d1, d2)
+    torch.cuda.synchronize(dev)
+
+    # ---- timed steps, device-resident inputs ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    _barrier(world)
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                       # L2 flush between timed steps (outside the events)
+            evs[k][0].record(stream)
+            out = cf.cf_count(ctx, p, d1, d2)
+            evs[k][1].record(stream)
+            stats.append(cf.cf_get_stats(ctx))
+        torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - wall0
+    _barrier(world)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_dev = sum(step_ms) / 1e3
+    evaluated = stats[-1]["evaluated_pairs"]
+    t_max = _max_over_ranks(world, t_dev, dev)
+    total_evals = _sum_over_ranks(world, float(evaluated) * args.steps, dev)
+    value = total_evals / t_max
+    in_range = int(np.asarray(out["npairs"], dtype=np.float64).sum())
+    pair_ms = [s["ms_pair"] for s in stats]
+    launches = sum(s["kernel_launches"] for s in stats)
+
+    # ---- e2e through the public API with host buffers (H2D of inputs, D2H of results inside) ----
+    h1 = _points(wl.d1, wl.weighted, cf)
+    h2 = None if wl.autocorr else _points(wl.d2, wl.weighted, cf)
+    cf.cf_count(ctx, p, h1, h2)
+    e2e_steps = max(3, min(args.steps, 50))
+    torch.cuda.synchronize(dev)
+    _barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        res = cf.cf_count(ctx, p, h1, h2)
+    torch.cuda.synchronize(dev)
+    t_e2e = _max_over_ranks(world, time.perf_counter() - t0, dev)
+    e2e_value = _sum_over_ranks(world, float(evaluated) * e2e_steps, dev) / t_e2e
+    es = 8 if wl.d1.dtype == np.float64 else 4
+    h2d = (wl.d1.n * (4 if wl.weighted else 3) +
+           (0 if wl.autocorr else wl.d2.n * (4 if wl.weighted else 3))) * es
+    d2h = sum(v.nbytes for v in res.values())
+
+    # ---- roofline of the pair kernel (events on the launching stream, inside the library) ----
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * 128 * sm_max * 1e6 / FP32_INSTR_PER_PAIR
+    achieved = evaluated / (statistics.fmean(pair_ms) / 1e3)
+    clocks = clk.summary()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "flushed between timed steps (512 MB write outside the step events)",
+                   "grid": stats[-1]["grid"], "refine": stats[-1]["refine"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "steps": e2e_steps},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+                     "frac": achieved / peak, "traffic": _traffic(args.workload),
+                     "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / "
+                                   f"{FP32_INSTR_PER_PAIR} instr per pair"},
+        "clocks": clocks,
+        "pair_kernel_ms": statistics.fmean(pair_ms),
+        "evaluated_pairs_per_step": int(evaluated),
+        "in_range_pairs_per_step": in_range,
+        "in_range_pairs_per_s": in_range * args.steps / t_dev,
+        "rechecked_pairs_per_step": int(stats[-1]["rechecked_pairs"]),
+        "work_items": int(stats[-1]["work_items"]),
+        "wall_s_timed_region": wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample, _ = _oracle_rows_rate(wl, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    cf.cf_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="clustered_r_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        args.warmup = 3
+    import gen
+    wl = gen.workload(args.workload)
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, wl, world, rank)
+    return run_gpu(args, wl, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -115,6 +115,8 @@ typedef struct {
     float ms_pair;             /* pair kernel (CUDA events on the context stream) */
     float ms_recheck;          /* FP64 recheck + finalize */
     float ms_total;            /* whole call, host wall clock */
+    int kernel_launches;       /* CUDA kernels this library launched for the call */
+    int pad;
 } cf_stats;
 
 /* Create a context on `device` (its current-device state is restored on return), issuing all
@@ -163,6 +165,29 @@ cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *
 cf_status cf_batch_replay(void *ctx, cf_result *outs, int ncat);
 
 cf_status cf_get_stats(const void *ctx, cf_stats *out);
+
+/* Host-only planning probe (needs no GPU): builds the plan that cf_count would use for
+ * `params` over the bounding box bbox = {xlo, ylo, zlo, xhi, yhi, zhi} of `npoints` points
+ * (any_f64 = 1 if any input is float64) and reports it.  bands_r (nbins+1 values) and bands_p
+ * (npibins+1 values, rp-pi / wp) receive the FP32 error band of each squared edge / pi edge:
+ * an FP32 value within a band of an edge is re-evaluated in FP64.  With nv > 0, `values` are
+ * classified through the same lookup table the pair kernel uses (which = 0: squared r / rp /
+ * chord; which = 1: |dz|): classes[i] = bin index, 0xFE outside every bin, 0xFF within a band.
+ * Grid and refinement: Sec. 4.1-4.2; bins in squared space: Sec. 4.7. */
+typedef struct {
+    int grid[3];
+    int refine[3];
+    int wrap[3];          /* axes with explicit minimum image (periodic, fewer than 2k+1 cells) */
+    int nstencil;         /* neighbour offsets kept after pruning */
+    int lut_cells[2];     /* coarse table cells: squared separation, |dz| */
+    int fine_entries;
+    double width[3];      /* cell width per axis */
+    double theta_rel;     /* relative part of the FP32 separation error bound */
+    double delta[3];      /* absolute part per axis */
+} cf_plan_info;
+cf_status cf_plan_probe(const cf_params *params, const double bbox[6], int64_t npoints, int any_f64,
+                        cf_plan_info *info, double *bands_r, double *bands_p, int which, const float *values,
+                        int64_t nv, uint32_t *classes);
 
 /* Serving: continuous batching of autocorr requests with the same params.  A worker thread
  * admits requests while device memory (mem_budget_bytes) and slots (max_slots) allow, builds

@@ -177,3 +177,90 @@ def cf_get_stats(ctx: int) -> dict:
     s = _capi.cf_stats()
     _check(_capi.lib().cf_get_stats(ctx, ctypes.byref(s)), ctx)
     return {f: (list(getattr(s, f)) if f in ("grid", "refine") else getattr(s, f)) for f, _ in s._fields_}
+
+
+# ---- serving (continuous batching) ----
+_server_keep = {}
+
+
+def cf_server_start(device: int, p: Params, mem_budget_bytes: int, max_slots: int) -> int:
+    h = ctypes.c_void_p()
+    _check(_capi.lib().cf_server_start(ctypes.byref(h), int(device), ctypes.byref(p.c), int(mem_budget_bytes),
+                                       int(max_slots)))
+    _server_keep[h.value] = {"params": p}
+    return h.value
+
+
+def cf_server_submit(server: int, p: Params, cat: Points) -> int:
+    """Queue one catalogue; returns its ticket.  The catalogue arrays must stay alive until the
+    ticket is polled (the binding keeps a reference)."""
+    out = _Out(p.nout, len(p.edges) - 1)
+    t = ctypes.c_uint64()
+    _check(_capi.lib().cf_server_submit(server, ctypes.byref(cat.c), ctypes.byref(out.c), ctypes.byref(t)),
+           server=server)
+    _server_keep[server][t.value] = (out, cat)
+    return t.value
+
+
+def cf_server_poll(server: int, ticket: int, timeout_ms: int = 0):
+    """Returns the result dict when done, None while busy (timeout_ms == 0) or on timeout."""
+    rc = _capi.lib().cf_server_poll(server, ctypes.c_uint64(ticket), int(timeout_ms))
+    if rc in (_capi.CF_ERR_BUSY, _capi.CF_ERR_TIMEOUT):
+        return None
+    keep = _server_keep[server].pop(ticket, None)
+    _check(rc, server=server)
+    return keep[0].as_dict(_server_keep[server]["params"])
+
+
+def cf_server_cancel(server: int, ticket: int) -> None:
+    _check(_capi.lib().cf_server_cancel(server, ctypes.c_uint64(ticket)), server=server)
+
+
+def cf_server_stop(server: int) -> None:
+    _check(_capi.lib().cf_server_stop(server))
+    _server_keep.pop(server, None)
+
+
+def cf_server_last_error(server: int) -> str:
+    return (_capi.lib().cf_server_last_error(server) or b"").decode()
+
+
+def cf_batch_capture(ctx: int, p: Params, cats: Sequence[Points]) -> None:
+    n = len(cats)
+    arr = (_capi.cf_points * n)(*[c.c for c in cats])
+    _check(_capi.lib().cf_batch_capture(ctx, ctypes.byref(p.c), arr, n), ctx)
+
+
+def cf_batch_replay(ctx: int, p: Params, n: int) -> list:
+    outs = [_Out(p.nout, len(p.edges) - 1) for _ in range(n)]
+    res = (_capi.cf_result * n)(*[o.c for o in outs])
+    _check(_capi.lib().cf_batch_replay(ctx, res, n), ctx)
+    return [o.as_dict(p) for o in outs]
+
+
+def cf_plan_probe(p: Params, bbox, npoints: int, any_f64: bool = False, which: int = 0, values=None) -> dict:
+    """Host-only: the plan cf_count would build (grid, bands, table sizes) and, optionally, the
+    table classification of FP32 `values` (see include/cf.h)."""
+    info = _capi.cf_plan_info()
+    nb = len(p.edges) - 1
+    npi = max(1, p.c.npibins)
+    br = np.zeros(nb + 1)
+    bp = np.zeros(npi + 1)
+    bb = np.ascontiguousarray(np.asarray(bbox, dtype=np.float64))
+    D = ctypes.POINTER(ctypes.c_double)
+    if values is None:
+        vals = np.zeros(0, dtype=np.float32)
+    else:
+        vals = np.ascontiguousarray(np.asarray(values, dtype=np.float32))
+    cls = np.zeros(len(vals), dtype=np.uint32)
+    rc = _capi.lib().cf_plan_probe(ctypes.byref(p.c), bb.ctypes.data_as(D), int(npoints), int(bool(any_f64)),
+                                   ctypes.byref(info), br.ctypes.data_as(D), bp.ctypes.data_as(D), int(which),
+                                   vals.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), len(vals),
+                                   cls.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)))
+    _check(rc)
+    out = {f: (list(getattr(info, f)) if hasattr(getattr(info, f), "__len__") else getattr(info, f))
+           for f, _ in info._fields_}
+    out["bands_r"] = br
+    out["bands_p"] = bp[: p.c.npibins + 1] if p.kind in (CF_DD_RPPI, CF_WP) else np.zeros(0)
+    out["classes"] = cls
+    return out

@@ -79,6 +79,22 @@ class cf_stats(ctypes.Structure):
         ("ms_pair", ctypes.c_float),
         ("ms_recheck", ctypes.c_float),
         ("ms_total", ctypes.c_float),
+        ("kernel_launches", ctypes.c_int),
+        ("pad", ctypes.c_int),
+    ]
+
+
+class cf_plan_info(ctypes.Structure):
+    _fields_ = [
+        ("grid", ctypes.c_int * 3),
+        ("refine", ctypes.c_int * 3),
+        ("wrap", ctypes.c_int * 3),
+        ("nstencil", ctypes.c_int),
+        ("lut_cells", ctypes.c_int * 2),
+        ("fine_entries", ctypes.c_int),
+        ("width", ctypes.c_double * 3),
+        ("theta_rel", ctypes.c_double),
+        ("delta", ctypes.c_double * 3),
     ]
 
 
@@ -103,6 +119,10 @@ _PROTOS = {
     "cf_server_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "cf_server_stop": (ctypes.c_int, [_P]),
     "cf_server_last_error": (ctypes.c_char_p, [_P]),
+    "cf_plan_probe": (ctypes.c_int, [ctypes.POINTER(cf_params), ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                     ctypes.c_int, ctypes.POINTER(cf_plan_info), ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                     ctypes.c_int64, ctypes.POINTER(ctypes.c_uint32)]),
 }
 
 _lock = threading.Lock()

@@ -234,6 +234,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     }
     CF_CU(cfb_bbox((const CfSetDesc *)C->buf[B_SETS].p, nsets, std::max<int64_t>(R.nmax, 1),
                    (unsigned long long *)C->buf[B_BBOX].p, st), "bbox kernel");
+    C->launches = 1;
     CF_CU(cudaMemcpyAsync(C->hpin, C->buf[B_BBOX].p, 64 * (size_t)nsets, cudaMemcpyDeviceToHost, st), "bbox readback");
     CF_CU(cudaStreamSynchronize(st), "bbox sync");
     double bbox[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
@@ -359,6 +360,7 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
                     0, nullptr, st),
           "items count");
     CF_CU(cfb_scan(icnt, ioff, R.nthr, (uint32_t *)C->buf[B_SCAN].p, st), "scan items");
+    C->launches += 9;   // assign, 3 scan, scatter, items count, 3 scan
     return CF_OK;
 }
 
@@ -416,8 +418,11 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     C->last_warps = warps;
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[2], st, C->capturing ? cudaEventRecordExternal : 0), "event");
     CF_CU(cfp_launch_recheck(dplan, dsets, djobs, A.queue, A.qcount, R.qcap, A.hcnt, A.hw, A.hr, C->num_sms, st), "recheck");
-    if (R.self_pairs && D.weighted)
+    if (R.self_pairs && D.weighted) {
         CF_CU(cfb_wsq(dsets, R.nsets, R.np, (double *)C->buf[B_WSQ].p, st), "self-pair weights");
+        C->launches++;
+    }
+    C->launches += 2 + (R.items_cap > 0 ? 1 : 0);   // items emit, recheck, pair
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[3], st, C->capturing ? cudaEventRecordExternal : 0), "event");
     // readback: [cursor, qcount, items total, pad] [evaluated] [hcnt] [hw] [hr] [wsq]
     char *h = (char *)C->hpin;
@@ -490,6 +495,7 @@ int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
     }
     C->stats.ncat = R.njobs;
     C->stats.variant = C->last_warps;
+    C->stats.kernel_launches = C->launches;
     return CF_OK;
 }
 

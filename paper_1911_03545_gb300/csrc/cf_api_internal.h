@@ -72,6 +72,7 @@ struct CfCtx {
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     CfRun run;
     int last_grid = 0, last_warps = 0;
+    int launches = 0;              // kernels launched by the current call
     uint64_t gen = 0;              // bumped whenever device or pinned scratch is reallocated
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;

@@ -361,3 +361,64 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
     D.nfine = (int)H.fine.size();
     return CF_OK;
 }
+
+// Host emulation of the kernel's table lookup (same arithmetic as lut_class in cf_pair.cuh).
+uint32_t cfp_lut_class(const CfHostPlan &H, int which, uint32_t vb)
+{
+    const CfLut &L = which ? H.d.lp : H.d.lr;
+    int t = (int)(vb - L.base);
+    t = t > 0 ? t : 0;
+    uint32_t idx = std::min((uint32_t)t >> L.shift, L.last);
+    uint32_t c = H.lut[L.coff + idx];
+    if (c >= CFI_FINE_FLAG) {
+        const CfFine &f = H.fine[c - CFI_FINE_FLAG];
+        uint32_t seg = (vb >= f.t1 ? 1u : 0u) + (vb >= f.t2 ? 1u : 0u);
+        c = (f.code >> (8u * seg)) & 0xFFu;
+    }
+    return c;
+}
+
+extern "C" cf_status cf_plan_probe(const cf_params *params, const double bbox[6], int64_t npoints, int any_f64,
+                                   cf_plan_info *info, double *bands_r, double *bands_p, int which,
+                                   const float *values, int64_t nv, uint32_t *classes)
+{
+    if (!params || !bbox) return CF_ERR_ARG;
+    std::string err;
+    if (cfp_check_params(params, err) != CF_OK) return CF_ERR_ARG;
+    const bool rppi_like = params->kind == CF_DD_RPPI || params->kind == CF_WP;
+    if (which == 1 && !rppi_like && nv > 0) return CF_ERR_ARG;
+    CfHostPlan *H = new CfHostPlan();
+    int refine[3];
+    for (int a = 0; a < 3; a++) refine[a] = params->refine[a] > 0 ? params->refine[a] : 1;
+    int rc = cfp_make_plan(params, bbox, npoints, any_f64, refine, 128, 512, H, err);
+    if (rc) {
+        delete H;
+        return (cf_status)rc;
+    }
+    if (info) {
+        std::memset(info, 0, sizeof(*info));
+        for (int a = 0; a < 3; a++) {
+            info->grid[a] = H->d.g.n[a];
+            info->refine[a] = H->d.g.k[a];
+            info->wrap[a] = H->d.g.wrap[a];
+            info->width[a] = H->d.g.width[a];
+            info->delta[a] = H->delta[a];
+        }
+        info->nstencil = H->d.g.nstencil;
+        info->lut_cells[0] = (int)H->d.lr.last + 1;
+        info->lut_cells[1] = rppi_like ? (int)H->d.lp.last + 1 : 0;
+        info->fine_entries = (int)H->fine.size();
+        info->theta_rel = H->theta_rel;
+    }
+    if (bands_r)
+        for (int k = 0; k <= params->nbins; k++) bands_r[k] = H->band_r[k];
+    if (bands_p && rppi_like)
+        for (int m = 0; m <= params->npibins; m++) bands_p[m] = H->band_p[m];
+    for (int64_t i = 0; i < nv; i++) {
+        uint32_t b;
+        std::memcpy(&b, values + i, 4);
+        classes[i] = cfp_lut_class(*H, which, b);
+    }
+    delete H;
+    return CF_OK;
+}
