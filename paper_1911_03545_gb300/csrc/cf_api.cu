@@ -262,7 +262,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     for (int a = 0; a < 3; a++)
         refine[a] = p->refine[a] > 0 ? p->refine[a] : (C->opt[CF_OPT_REFINE] > 0 ? (int)C->opt[CF_OPT_REFINE] : 1);
     int tile = C->opt[CF_OPT_TILE] > 0 ? (int)std::min<int64_t>(128, std::max<int64_t>(32, C->opt[CF_OPT_TILE])) : 128;
-    int jchunk = C->opt[CF_OPT_JCHUNK] > 0 ? (int)std::min<int64_t>(65535, C->opt[CF_OPT_JCHUNK]) : 512;
+    int jchunk = C->opt[CF_OPT_JCHUNK] > 0 ? (int)std::min<int64_t>(CFI_JMAX, C->opt[CF_OPT_JCHUNK]) : CFI_JMAX;
     rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err);
     if (rc) return C->fail(rc, err);
     CfDevPlan &D = H.d;

@@ -23,6 +23,8 @@
 #define CFI_CLS_OUT 0xFEu         // class: outside every bin
 #define CFI_CLS_AMB 0xFFu         // class: within the FP32 error band of an edge
 #define CFI_FINE_FLAG 0x100u      // coarse entry >= this: index of a fine entry + flag
+#define CFI_QN 2048               // per-warp candidate ring (entries of 16 bits)
+#define CFI_JMAX 512              // longest j range of a work item (9-bit j in a candidate)
 
 // Pair-kernel item (48 bytes, three 16-byte loads)
 struct CfItem {
@@ -105,6 +107,8 @@ struct CfDevPlan {
     int nlut_words;        // coarse words (both LUTs)
     int nfine;             // fine entries (both LUTs)
     double pimax;
+    float cut_r;           // candidate cut on the FP32 squared separation (above the last band)
+    float cut_p;           // candidate cut on the FP32 |dz| (rp-pi / wp)
     double e2[CF_MAX_BINS + 1];     // squared edges (FP64, host-computed)
     double pe[CF_MAX_PIBINS + 1];   // pi edges
 };

@@ -1,19 +1,29 @@
 // cf_pair.cuh -- the persistent pair kernel (template; instantiated per kind in cf_pair_*.cu).
 //
-// Sec. 4.3-4.7 on a GPU: every warp repeatedly takes one work item -- an i tile of one cell
-// (<= 128 points, two per lane per pack) against a j range of a neighbour cell -- from a global
-// atomic cursor.  The i points sit in registers already translated by the cell-pair shift
-// (Sec. 4.4, Code corrfunc_pbc: the shift is added once per i, not per pair).  Each j point is
-// a broadcast load; the three separations and the squared distance of two pairs are formed by
-// packed FP32x2 add / mul / fma on cell-relative coordinates.  The bin is found on the bit
-// pattern of the FP32 squared separation with a coarse table (Sec. 4.7: squared space, no
-// sqrt); cells of the table that hold an edge resolve through a fine entry of <= 2 thresholds.
-// A value within the proven FP32 error band of an edge is not binned here: the pair goes to a
-// queue and is re-evaluated in FP64 by the recheck kernel, so counts equal the FP64 result.
+// Sec. 4.3-4.7 on a GPU.  Every warp repeatedly takes one work item -- an i tile of one cell
+// (<= 128 points, four per lane as two packed pairs) against a j range (<= 512 points) of a
+// neighbour cell -- from a global atomic cursor.  The i points sit in registers already
+// translated by the cell-pair shift (Sec. 4.4, Code corrfunc_pbc: the shift is added once per
+// i, not per pair).  Each j point is a broadcast load.
+//
+// Phase A (every pair): the separations and squared distance of two pairs at a time are formed
+// by packed FP32x2 add / mul / fma on cell-relative coordinates, and each pair is tested
+// against one cut just above the last bin edge (Sec. 4.7: squared space, no sqrt).  A lane
+// gathers the outcome of 32 pairs (8 j points x 4 i points) in a bit mask.
+// Compaction: the warp scans the mask counts and appends the candidate pairs, 16 bits each
+// (i slot, j), to a per-warp ring in shared memory.
+// Phase B (candidates only, 32 or 64 per pass, all lanes busy): the squared separation is
+// formed again (with the shift's low part and the TwoSum residual of the i translation when
+// ravg needs relative accuracy), its bin is looked up on the FP32 bit pattern through a coarse
+// table (cells holding an edge resolve through a fine entry of <= 2 thresholds).  A value
+// within the proven FP32 error band of an edge is not binned: the pair goes to a global queue
+// and is re-evaluated in FP64 by the recheck kernel, so counts equal the FP64 result.
+//
 // Histograms live in shared memory per warp (Sec. 4.8: private histograms, merged once): for
-// r / theta / wp one private copy per lane (no conflicts, no atomics contention; weighted sums
-// are Kahan-compensated FP32), for rp-pi one copy per warp with shared atomics.  They are
-// merged into the global FP64/u64 histogram when a warp moves to another job and at exit.
+// r / theta / wp one private copy per lane (no bank conflicts, no contention; weighted sums
+// Kahan-compensated in FP32), for rp-pi one copy per warp updated by shared atomics (FP64 for
+// weighted sums).  They are merged into the global histogram when a warp moves to another job
+// and at exit.
 #pragma once
 #include "cf_build.h"
 #include "cf_device.cuh"
@@ -21,22 +31,28 @@
 namespace cfpair {
 
 constexpr int KIND_R = 0, KIND_RPPI = 1, KIND_WP = 2, KIND_THETA = 3;
+constexpr uint32_t QM = CFI_QN - 1;
 
-__device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+__host__ __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-template <int KIND, bool W, bool R>
-__host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int nslot)
+// per-warp shared memory: candidate ring | i-tile stage | histogram
+__host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int kind, bool W, bool R, int nslot)
 {
-    if (KIND == KIND_RPPI) {
+    if (kind == KIND_RPPI) {
         uint32_t b = ((uint32_t)nslot * 4u + 7u) & ~7u;
         if (W) b += nslot * 8u;
         if (R) b += nslot * 8u;
-        return (b + 15u) & ~15u;
+        return align16(b);
     }
     uint32_t b = nslot * 32u * 4u;
     if (W) b += nslot * 32u * 8u;
     if (R) b += nslot * 32u * 8u;
     return b;
+}
+__host__ __device__ __forceinline__ uint32_t warp_stage_bytes(bool R) { return 128u * (R ? 32u : 16u); }
+__host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, int nslot)
+{
+    return CFI_QN * 2u + warp_stage_bytes(R) + warp_hist_bytes(kind, W, R, nslot);
 }
 
 __device__ __forceinline__ void kahan_add(float2 *p, float v)
@@ -75,30 +91,31 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - (s - bb)) + (b - bb);
 }
 
+__device__ __forceinline__ float wrap1(float d, float L, float invL) { return fmaf(-L, rintf(d * invL), d); }
+
 __device__ __forceinline__ u64 wrap2(u64 d, float L, float invL)
 {
-    float a = f2_lo(d), b = f2_hi(d);
-    a = fmaf(-L, rintf(a * invL), a);
-    b = fmaf(-L, rintf(b * invL), b);
-    return f2_pack(a, b);
+    return f2_pack(wrap1(f2_lo(d), L, invL), wrap1(f2_hi(d), L, invL));
 }
 
 template <int KIND, bool W, bool R, bool WRAP, bool LO>
 struct Warp {
-    // per-kernel constants
     const CfPairArgs &a;
     Lut lr, lp;
     const CfFine *fine;
     uint32_t *h_cnt;        // lane-private [nslot][32] or per-warp [nslot]
     float2 *h_w, *h_r;      // lane-private Kahan pairs
     double *h_wd, *h_rd;    // per-warp FP64 (rp-pi)
+    uint16_t *ring;         // candidate ring: (i slot << 9) | j
+    float4 *stage;          // i tile: (s.x, s.y, s.z, w) [, (e.x, e.y, e.z, 0)]
     int lane, nb, npi, nslot;
-    uint32_t icnt;          // points of the current i tile (wrap mode masks empty slots with it)
+    uint32_t icnt, ibeg, jbeg, job, head, tail;
+    float cut_r, cut_p;
     float Lx, Ly, Lz, iLx, iLy, iLz;
 
     __device__ Warp(const CfPairArgs &args) : a(args) {}
 
-    __device__ __forceinline__ void push(uint32_t ip, uint32_t jp, uint32_t job)
+    __device__ __forceinline__ void push(uint32_t ip, uint32_t jp)
     {
         uint32_t k = atomicAdd(a.qcount, 1u);
         if (k < a.qcap) a.queue[k] = make_uint4(a.orig[ip], a.orig[jp], job, 0u);
@@ -126,140 +143,210 @@ struct Warp {
         }
     }
 
-    // one pair (one half of a packed result)
-    template <bool DIAG>
-    __device__ __forceinline__ void bin3(uint32_t vb, float wp, uint32_t il, uint32_t j, uint32_t ibeg,
-                                         uint32_t jbeg, uint32_t job)
+    // Phase B for one candidate (valid == false: the lane only takes part in the warp's flow)
+    __device__ __forceinline__ void finish(uint32_t code, bool valid)
     {
-        uint32_t c = lut_class(lr, fine, vb);
-        bool live = (!DIAG || j > il) && (!WRAP || il < icnt);
-        if (c < (uint32_t)nb) {
-            if (live) acc_lp(c, __uint_as_float(vb), wp);
-        } else if (c == CFI_CLS_AMB) {
-            if (live) push(ibeg + il, jbeg + j, job);
+        const uint32_t il = code >> 9, j = code & (CFI_JMAX - 1);
+        const float4 S = stage[R ? 2 * il : il];
+        const ulonglong2 A = __ldg(a.pa + jbeg + j), B = __ldg(a.pb + jbeg + j);
+        float dx = S.x + f2_lo(A.x), dy = S.y + f2_lo(A.y), dz = S.z + f2_lo(B.x);
+        if (R) {
+            const float4 E = stage[2 * il + 1];
+            float ex = E.x, ey = E.y, ez = E.z;
+            if (LO) {
+                const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(jbeg + j));
+                const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(jbeg + j) + 1);
+                ex = ex + f2_lo(C.x);
+                ey = ey + f2_lo(C.y);
+                ez = ez + f2_lo(D.x);
+            }
+            dx = dx + ex;
+            dy = dy + ey;
+            dz = dz + ez;
+        }
+        if (WRAP) {
+            if (Lx > 0.f) dx = wrap1(dx, Lx, iLx);
+            if (Ly > 0.f) dy = wrap1(dy, Ly, iLy);
+            if (Lz > 0.f) dz = wrap1(dz, Lz, iLz);
+        }
+        const float wp = W ? S.w * f2_lo(B.y) : 0.f;
+        if (KIND == KIND_R || KIND == KIND_THETA) {
+            float d2 = dx * dx;
+            d2 = fmaf(dy, dy, d2);
+            d2 = fmaf(dz, dz, d2);
+            const uint32_t c = lut_class(lr, fine, __float_as_uint(d2));
+            if (valid && c < (uint32_t)nb) acc_lp(c, d2, wp);
+            else if (valid && c == CFI_CLS_AMB) push(ibeg + il, jbeg + j);
+        } else {
+            float rp2 = dx * dx;
+            rp2 = fmaf(dy, dy, rp2);
+            const uint32_t cz = lut_class(lp, fine, __float_as_uint(fabsf(dz)));
+            const uint32_t cr = lut_class(lr, fine, __float_as_uint(rp2));
+            if (valid && cz != CFI_CLS_OUT && cr != CFI_CLS_OUT) {
+                if (cr < (uint32_t)nb && cz < CFI_CLS_OUT) {
+                    if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, rp2, wp);
+                    else acc_lp(cr, rp2, wp);
+                } else {
+                    push(ibeg + il, jbeg + j);
+                }
+            }
         }
     }
 
-    template <bool DIAG>
-    __device__ __forceinline__ void bin2(uint32_t rb, uint32_t zb, float wp, uint32_t il, uint32_t j,
-                                         uint32_t ibeg, uint32_t jbeg, uint32_t job)
+    // drain K*32 candidates (or the `count` left at the end) from the ring
+    template <int K>
+    __device__ __forceinline__ void drain(uint32_t count)
     {
-        uint32_t cz = lut_class(lp, fine, zb);
-        if (cz == CFI_CLS_OUT) return;
-        uint32_t cr = lut_class(lr, fine, rb);
-        bool live = (!DIAG || j > il) && (!WRAP || il < icnt);
-        if (cr < (uint32_t)nb && cz < CFI_CLS_OUT) {
-            if (live) {
-                if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, __uint_as_float(rb), wp);
-                else acc_lp(cr, __uint_as_float(rb), wp);
-            }
-        } else if (cr != CFI_CLS_OUT) {
-            if (live) push(ibeg + il, jbeg + j, job);
+        uint32_t code[K];
+        bool v[K];
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const uint32_t idx = lane + 32u * k;
+            v[k] = idx < count;
+            code[k] = v[k] ? ring[(head + idx) & QM] : 0u;
         }
+#pragma unroll
+        for (int k = 0; k < K; k++) finish(code[k], v[k]);
+        head += count;
+        __syncwarp();
     }
 
     template <int P, bool DIAG>
     __device__ __forceinline__ void run(const CfItem &it)
     {
-        const uint32_t icnt = it.cnt & 0xFFFFu, jcnt = it.cnt >> 16;
-        const uint32_t job = it.meta & CFI_ITEM_JOBMASK;
-        this->icnt = icnt;
-        u64 sx[P], sy[P], sz[P], ex[P], ey[P], ez[P], wi[P];
+        icnt = it.cnt & 0xFFFFu;
+        const uint32_t jcnt = it.cnt >> 16;
+        ibeg = it.ibeg;
+        jbeg = it.jbeg;
+        job = it.meta & CFI_ITEM_JOBMASK;
+        // ---- i tile: translate by the shift (TwoSum residual kept for the precise phase B) ----
+        u64 sx[P], sy[P], sz[P];
 #pragma unroll
         for (int p = 0; p < P; p++) {
-            float vs[3][2], ve[3][2], vw[2];
+            float vs[3][2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
-                uint32_t il = lane + 32u * (2 * p + h);
+                const uint32_t il = lane + 32u * (2 * p + h);
+                float4 Sv = make_float4(1e18f, 1e18f, 1e18f, 0.f), Ev = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (il < icnt) {
-                    const ulonglong2 A = a.pa[it.ibeg + il], B = a.pb[it.ibeg + il];
-                    float X[3] = {-f2_lo(A.x), -f2_lo(A.y), -f2_lo(B.x)};
-                    vw[h] = f2_lo(B.y);
+                    const ulonglong2 A = a.pa[ibeg + il], B = a.pb[ibeg + il];
+                    const float X[3] = {-f2_lo(A.x), -f2_lo(A.y), -f2_lo(B.x)};
                     float XL[3] = {0.f, 0.f, 0.f};
                     if (LO) {
-                        const ulonglong2 C = a.plo[2 * (size_t)(it.ibeg + il)], D = a.plo[2 * (size_t)(it.ibeg + il) + 1];
+                        const ulonglong2 C = a.plo[2 * (size_t)(ibeg + il)], D = a.plo[2 * (size_t)(ibeg + il) + 1];
                         XL[0] = -f2_lo(C.x);
                         XL[1] = -f2_lo(C.y);
                         XL[2] = -f2_lo(D.x);
                     }
+                    float s[3], e[3];
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
                         if (R) {
-                            float s, e;
-                            two_sum(X[d], it.s[d], s, e);
-                            vs[d][h] = s;
-                            ve[d][h] = (e + it.slo[d]) + XL[d];
+                            two_sum(X[d], it.s[d], s[d], e[d]);
+                            e[d] = (e[d] + it.slo[d]) + XL[d];
                         } else {
-                            vs[d][h] = X[d] + it.s[d];
-                            ve[d][h] = 0.f;
+                            s[d] = X[d] + it.s[d];
+                            e[d] = 0.f;
                         }
                     }
+                    Sv = make_float4(s[0], s[1], s[2], f2_lo(B.y));
+                    Ev = make_float4(e[0], e[1], e[2], 0.f);
+                }
+                // empty slots sit far outside every bin (1e18^2 < FLT_MAX); in wrap mode the
+                // minimum image would fold them back, so there they are also masked by icnt
+                vs[0][h] = Sv.x;
+                vs[1][h] = Sv.y;
+                vs[2][h] = Sv.z;
+                if (R) {
+                    stage[2 * il] = Sv;
+                    stage[2 * il + 1] = Ev;
                 } else {
-                    // empty slot: far outside every bin (1e18^2 < FLT_MAX); in wrap mode the
-                    // minimum image would fold it back, so there the slot is also masked by icnt
-#pragma unroll
-                    for (int d = 0; d < 3; d++) { vs[d][h] = 1e18f; ve[d][h] = 0.f; }
-                    vw[h] = 0.f;
+                    stage[il] = Sv;
                 }
             }
             sx[p] = f2_pack(vs[0][0], vs[0][1]);
             sy[p] = f2_pack(vs[1][0], vs[1][1]);
             sz[p] = f2_pack(vs[2][0], vs[2][1]);
-            ex[p] = f2_pack(ve[0][0], ve[0][1]);
-            ey[p] = f2_pack(ve[1][0], ve[1][1]);
-            ez[p] = f2_pack(ve[2][0], ve[2][1]);
-            wi[p] = f2_pack(vw[0], vw[1]);
         }
-        const ulonglong2 *__restrict__ pa = a.pa + it.jbeg;
-        const ulonglong2 *__restrict__ pb = a.pb + it.jbeg;
-#pragma unroll 2
-        for (uint32_t j = 0; j < jcnt; j++) {
-            const ulonglong2 A = __ldg(pa + j), B = __ldg(pb + j);
-            u64 lx = 0, ly = 0, lz = 0;
-            if (LO) {
-                const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(it.jbeg + j));
-                const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(it.jbeg + j) + 1);
-                lx = C.x;
-                ly = C.y;
-                lz = D.x;
-            }
+        __syncwarp();
+        head = tail = 0;
+        constexpr int JB = 16 / P;          // j points per block: 32 pair slots per lane
+        const ulonglong2 *__restrict__ pa = a.pa + jbeg;
+        const ulonglong2 *__restrict__ pb = a.pb + jbeg;
+        for (uint32_t j0 = 0; j0 < jcnt; j0 += JB) {
+            // ---- phase A ----
+            uint32_t mask = 0;
 #pragma unroll
-            for (int p = 0; p < P; p++) {
-                u64 dx = f2_add(sx[p], A.x), dy = f2_add(sy[p], A.y), dz = f2_add(sz[p], B.x);
-                if (R) {
-                    dx = f2_add(dx, LO ? f2_add(ex[p], lx) : ex[p]);
-                    dy = f2_add(dy, LO ? f2_add(ey[p], ly) : ey[p]);
-                    dz = f2_add(dz, LO ? f2_add(ez[p], lz) : ez[p]);
-                }
-                if (WRAP) {
-                    if (Lx > 0.f) dx = wrap2(dx, Lx, iLx);
-                    if (Ly > 0.f) dy = wrap2(dy, Ly, iLy);
-                    if (Lz > 0.f) dz = wrap2(dz, Lz, iLz);
-                }
-                u64 wp = 0;
-                if (W) wp = f2_mul(wi[p], B.y);
-                const uint32_t il0 = lane + 64u * p, il1 = il0 + 32u;
-                if (KIND == KIND_R || KIND == KIND_THETA) {
-                    u64 d2 = f2_mul(dx, dx);
-                    d2 = f2_fma(dy, dy, d2);
-                    d2 = f2_fma(dz, dz, d2);
-                    bin3<DIAG>(f2_lo_bits(d2), f2_lo(wp), il0, j, it.ibeg, it.jbeg, job);
-                    bin3<DIAG>(f2_hi_bits(d2), f2_hi(wp), il1, j, it.ibeg, it.jbeg, job);
-                } else {
-                    u64 rp2 = f2_mul(dx, dx);
-                    rp2 = f2_fma(dy, dy, rp2);
-                    u64 adz = dz & 0x7FFFFFFF7FFFFFFFull;
-                    bin2<DIAG>(f2_lo_bits(rp2), f2_lo_bits(adz), f2_lo(wp), il0, j, it.ibeg, it.jbeg, job);
-                    bin2<DIAG>(f2_hi_bits(rp2), f2_hi_bits(adz), f2_hi(wp), il1, j, it.ibeg, it.jbeg, job);
+            for (int jj = 0; jj < JB; jj++) {
+                const uint32_t j = j0 + jj;
+                if (j < jcnt) {
+                    const ulonglong2 A = __ldg(pa + j), B = __ldg(pb + j);
+#pragma unroll
+                    for (int p = 0; p < P; p++) {
+                        u64 dx = f2_add(sx[p], A.x), dy = f2_add(sy[p], A.y), dz = f2_add(sz[p], B.x);
+                        if (WRAP) {
+                            if (Lx > 0.f) dx = wrap2(dx, Lx, iLx);
+                            if (Ly > 0.f) dy = wrap2(dy, Ly, iLy);
+                            if (Lz > 0.f) dz = wrap2(dz, Lz, iLz);
+                        }
+                        bool c0, c1;
+                        if (KIND == KIND_R || KIND == KIND_THETA) {
+                            u64 d2 = f2_mul(dx, dx);
+                            d2 = f2_fma(dy, dy, d2);
+                            d2 = f2_fma(dz, dz, d2);
+                            c0 = f2_lo(d2) < cut_r;
+                            c1 = f2_hi(d2) < cut_r;
+                        } else {
+                            u64 rp2 = f2_mul(dx, dx);
+                            rp2 = f2_fma(dy, dy, rp2);
+                            c0 = f2_lo(rp2) < cut_r && fabsf(f2_lo(dz)) < cut_p;
+                            c1 = f2_hi(rp2) < cut_r && fabsf(f2_hi(dz)) < cut_p;
+                        }
+                        const uint32_t il0 = lane + 64u * p, il1 = il0 + 32u;
+                        if (DIAG) {
+                            c0 = c0 && j > il0;
+                            c1 = c1 && j > il1;
+                        }
+                        if (WRAP) {
+                            c0 = c0 && il0 < icnt;
+                            c1 = c1 && il1 < icnt;
+                        }
+                        const int bit = jj * 2 * P + 2 * p;
+                        mask |= (c0 ? 1u : 0u) << bit;
+                        mask |= (c1 ? 1u : 0u) << (bit + 1);
+                    }
                 }
             }
+            // ---- compaction into the warp's ring ----
+            const uint32_t n = __popc(mask);
+            uint32_t pre = n;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(CF_FULL, pre, o);
+                if (lane >= o) pre += t;
+            }
+            const uint32_t tot = __shfl_sync(CF_FULL, pre, 31);
+            uint32_t pos = tail + pre - n;
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const uint32_t q = (uint32_t)b % (2 * P), jj = (uint32_t)b / (2 * P);
+                ring[pos & QM] = (uint16_t)(((lane + 32u * q) << 9) | (j0 + jj));
+                pos++;
+            }
+            tail += tot;
+            __syncwarp();
+            // ---- phase B ----
+            while (tail - head >= 64) drain<2>(64);
         }
+        while (tail - head >= 32) drain<1>(32);
+        if (tail != head) drain<1>(tail - head);
     }
 
-    __device__ void flush(uint32_t job)
+    __device__ void flush(uint32_t jb)
     {
         __syncwarp();
-        const size_t g0 = (size_t)job * nslot;
+        const size_t g0 = (size_t)jb * nslot;
         for (int sl = lane; sl < nslot; sl += 32) {
             unsigned long long c = 0;
             double ws = 0.0, rs = 0.0;
@@ -301,14 +388,17 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
     const int nlw = P->nlut_words, nf = P->nfine;
     uint32_t *s_lut = (uint32_t *)smem;
     CfFine *s_fine = (CfFine *)(smem + align16(4u * nlw));
-    unsigned char *hist = (unsigned char *)(s_fine + nf);
+    unsigned char *wbase = (unsigned char *)(s_fine + nf);
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
-    const uint32_t wb = warp_hist_bytes<KIND, W, R>(a.nslot);
+    const uint32_t wb = warp_bytes(KIND, W, R, a.nslot);
+    const uint32_t hoff = CFI_QN * 2u + warp_stage_bytes(R);
+    unsigned char *my = wbase + (size_t)(threadIdx.x >> 5) * wb;
     {
-        uint32_t *h = (uint32_t *)hist;
-        const uint32_t words = wb * (blockDim.x >> 5) / 4u;
-        for (uint32_t i = threadIdx.x; i < words; i += blockDim.x) h[i] = 0u;
+        // zero this warp's histogram (the ring and the stage need no initial value)
+        uint32_t *h = (uint32_t *)(my + hoff);
+        const uint32_t words = warp_hist_bytes(KIND, W, R, a.nslot) / 4u;
+        for (uint32_t i = threadIdx.x & 31; i < words; i += 32) h[i] = 0u;
     }
     __syncthreads();
 
@@ -320,21 +410,24 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
     w.fine = s_fine;
     w.lr = {P->lr.base, P->lr.shift, P->lr.last, s_lut + P->lr.coff};
     w.lp = {P->lp.base, P->lp.shift, P->lp.last, s_lut + P->lp.coff};
+    w.cut_r = P->cut_r;
+    w.cut_p = P->cut_p;
     w.Lx = a.L[0]; w.Ly = a.L[1]; w.Lz = a.L[2];
     w.iLx = a.L[0] > 0.f ? 1.0f / a.L[0] : 0.f;
     w.iLy = a.L[1] > 0.f ? 1.0f / a.L[1] : 0.f;
     w.iLz = a.L[2] > 0.f ? 1.0f / a.L[2] : 0.f;
-    unsigned char *my = hist + (size_t)(threadIdx.x >> 5) * wb;
-    w.h_cnt = (uint32_t *)my;
+    w.ring = (uint16_t *)my;
+    w.stage = (float4 *)(my + CFI_QN * 2u);
+    w.h_cnt = (uint32_t *)(my + hoff);
     if (KIND == KIND_RPPI) {
         uint32_t o = ((uint32_t)a.nslot * 4u + 7u) & ~7u;
-        w.h_wd = (double *)(my + o);
-        w.h_rd = (double *)(my + o + (W ? a.nslot * 8u : 0u));
+        w.h_wd = (double *)(my + hoff + o);
+        w.h_rd = (double *)(my + hoff + o + (W ? a.nslot * 8u : 0u));
         w.h_w = w.h_r = nullptr;
     } else {
         uint32_t o = a.nslot * 32u * 4u;
-        w.h_w = (float2 *)(my + o);
-        w.h_r = (float2 *)(my + o + (W ? a.nslot * 32u * 8u : 0u));
+        w.h_w = (float2 *)(my + hoff + o);
+        w.h_r = (float2 *)(my + hoff + o + (W ? a.nslot * 32u * 8u : 0u));
         w.h_wd = w.h_rd = nullptr;
     }
 

@@ -321,21 +321,44 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
         H.M[a] = M;
     }
     H.theta_rel = precise ? 2 * u : u;
-    double th = H.theta_rel;
-    auto band_sq = [&](double E, int naxes) -> double {
+    auto band_sq = [&](double E, int naxes, double th, const double *delta) -> double {
         double d = std::sqrt(E) * 1.01 + 1e-300;
         double sumD = 0, quad = 0;
         for (int a = 0; a < naxes; a++) {
-            sumD += H.delta[a];
-            quad += (th * d + H.delta[a]) * (th * d + H.delta[a]);
+            sumD += delta[a];
+            quad += (th * d + delta[a]) * (th * d + delta[a]);
         }
         double chain = (naxes == 3 ? 3 : 2) * u * E;
         return SAFETY * (2 * th * E + 2 * d * sumD + quad + chain + 4 * U64 * E);
     };
     int naxes = rppi_like ? 2 : 3;
-    for (int k = 0; k <= D.nb; k++) H.band_r[k] = band_sq(D.e2[k], naxes);
+    for (int k = 0; k <= D.nb; k++) H.band_r[k] = band_sq(D.e2[k], naxes, H.theta_rel, H.delta);
     if (rppi_like) {
-        for (int m = 0; m <= p->npibins; m++) H.band_p[m] = SAFETY * (th * D.pe[m] + H.delta[2] + 4 * U64 * D.pe[m]);
+        for (int m = 0; m <= p->npibins; m++)
+            H.band_p[m] = SAFETY * (H.theta_rel * D.pe[m] + H.delta[2] + 4 * U64 * D.pe[m]);
+    }
+    // Candidate cut of the pair kernel's first phase, which forms the squared separation without
+    // the low-order shift and cell residual terms (the first-order "non-precise" model): twice
+    // that model's band above the last edge, so every pair the second phase could bin or send to
+    // the FP64 recheck passes the cut.
+    {
+        double dnp[3];
+        for (int a = 0; a < 3; a++) {
+            double amax = std::max(std::fabs(G.lo[a]), std::fabs(G.lo[a] + extent[a]));
+            double Q = ulp32_of_magnitude(std::max(amax, 1e-300));
+            double epsX = f64 ? (u * (G.width[a] + 2 * Q) + 2 * U64 * amax) : 0.0;
+            double wrapterm = G.wrap[a] ? u * G.L[a] : 0.0;
+            dnp[a] = 2 * u * H.M[a] + 2 * epsX + wrapterm + 2 * U64 * (H.M[a] + G.L[a] + amax);
+        }
+        double Emax = D.e2[D.nb];
+        double cut = Emax + 2 * band_sq(Emax, naxes, u, dnp) + H.band_r[D.nb];
+        D.cut_r = std::nextafter((float)cut, INFINITY);
+        if (rppi_like) {
+            double cp = p->pimax + 2 * SAFETY * (u * p->pimax + dnp[2]) + H.band_p[p->npibins];
+            D.cut_p = std::nextafter((float)cp, INFINITY);
+        } else {
+            D.cut_p = INFINITY;
+        }
     }
 
     // ---- lookup tables ----

@@ -91,17 +91,8 @@ cudaError_t cfp_launch_theta(const CfPairCfg &, const CfPairArgs &, int, cudaStr
 
 size_t cfp_pair_smem(const CfPairCfg &c, int warps)
 {
-    size_t b = ((size_t)c.nlut_words * 4 + 15) & ~(size_t)15;
-    b += (size_t)c.nfine * 16;
-    size_t wb;
-    if (c.kind == 1) {
-        wb = (((size_t)c.nslot * 4 + 7) & ~(size_t)7) + (c.weighted ? c.nslot * 8 : 0) + (c.ravg ? c.nslot * 8 : 0);
-        wb = (wb + 15) & ~(size_t)15;
-    } else {
-        wb = (size_t)c.nslot * 32 * 4 + (c.weighted ? (size_t)c.nslot * 32 * 8 : 0) +
-             (c.ravg ? (size_t)c.nslot * 32 * 8 : 0);
-    }
-    return b + wb * warps;
+    size_t b = cfpair::align16(4u * (uint32_t)c.nlut_words) + (size_t)c.nfine * 16;
+    return b + (size_t)cfpair::warp_bytes(c.kind, c.weighted != 0, c.ravg != 0, c.nslot) * warps;
 }
 
 cudaError_t cfp_launch_pair(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
