@@ -275,6 +275,12 @@ def run_gpu(args, wl, world, rank, local):
     d1 = _points(wl.d1, wl.weighted, cf, dev)
     d2 = None if wl.autocorr else _points(wl.d2, wl.weighted, cf, dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    from paper_1911_03545_gb300 import tune
+    npts = wl.d1.n + (0 if wl.autocorr else wl.d2.n)
+    tuned = tune.tune(ctx, p, d1, d2, device_name=torch.cuda.get_device_name(dev), npoints=npts,
+                      use_cache=not args.no_tune_cache) if not args.no_tune else dict(tune.DEFAULT)
+    if args.no_tune:
+        tune.apply(ctx, tuned)
 
     for _ in range(args.warmup):
         cf.cf_count(ctx, p, d1, d2)
@@ -339,7 +345,7 @@ def run_gpu(args, wl, world, rank, local):
         "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "flushed between timed steps (512 MB write outside the step events)",
-                   "grid": stats[-1]["grid"], "refine": stats[-1]["refine"]},
+                   "grid": stats[-1]["grid"], "refine": stats[-1]["refine"], "tuned": tuned},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "steps": e2e_steps},
         "gpu_launches": int(launches),
@@ -368,21 +374,219 @@ def run_gpu(args, wl, world, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------------------------------------
+# batched and served forms (256 mock catalogues)
+# ---------------------------------------------------------------------------------------------
+
+BATCH_DESC = ("256 mock catalogues, periodic L=250, N log-uniform in [5e4, 8e5] (sum 6.9e7), 50-member clusters "
+              "sigma=1, DD(rp,pi) auto, 14 log rp bins 0.1-20, pimax=40 with 40 pi bins, float32")
+
+
+def _batch_setup(ncat):
+    import gen
+    sizes = gen.batch_sizes()[:ncat]
+    cats = [gen.batch_catalogue(i, n) for i, n in enumerate(sizes)]
+    return sizes, cats
+
+
+def _batch_params(cf):
+    import gen
+    return cf.params(kind="rppi", edges=gen.log_edges(0.1, 20.0, 14), autocorr=True, periodic=True, box=250.0,
+                     pimax=40.0, npibins=40)
+
+
+def run_batch(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1911_03545_gb300 as cf
+    from paper_1911_03545_gb300 import tune
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    sizes, cats = _batch_setup(args.ncat)
+    p = _batch_params(cf)
+    pts = [_points(c, False, cf, dev) for c in cats]
+    ctx = cf.cf_create(local, stream)
+    med = int(np.argsort(sizes)[len(sizes) // 2])
+    tuned = tune.tune(ctx, p, pts[med], None, device_name=torch.cuda.get_device_name(dev), npoints=sizes[med],
+                      use_cache=not args.no_tune_cache)
+    # one at a time (the plain path: one cf_count per catalogue)
+    singles = [cf.cf_count(ctx, p, q) for q in pts[:4]]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    singles = [cf.cf_count(ctx, p, q) for q in pts]
+    t_single = time.perf_counter() - t0
+    pair_ms_single = 0.0
+    # batched: one cell build + one persistent pair kernel over all catalogues
+    outs = cf.cf_batch_count(ctx, p, pts)
+    times, pair_ms = [], []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        outs = cf.cf_batch_count(ctx, p, pts)
+        times.append(time.perf_counter() - t0)
+        pair_ms.append(cf.cf_get_stats(ctx)["ms_pair"])
+    st = cf.cf_get_stats(ctx)
+    # graph-captured replay of the same batch
+    cf.cf_batch_capture(ctx, p, pts)
+    gtimes = []
+    for _ in range(max(1, args.steps)):
+        t0 = time.perf_counter()
+        gouts = cf.cf_batch_replay(ctx, p, len(pts))
+        gtimes.append(time.perf_counter() - t0)
+    parity = all(np.array_equal(a["npairs"], b["npairs"]) and np.array_equal(a["npairs"], g["npairs"])
+                 for a, b, g in zip(singles, outs, gouts))
+    t_batch = min(times)
+    t_graph = min(gtimes)
+    best = min(t_batch, t_graph)
+    peaks = _peaks()
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / FP32_INSTR_PER_PAIR
+    achieved = st["evaluated_pairs"] / (min(pair_ms) / 1e3)
+    line = {
+        "metric": "batched catalogues/s", "value": len(pts) / best, "unit": "catalogues/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * best, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": BATCH_DESC if args.ncat == 256 else BATCH_DESC.replace("256", str(args.ncat)),
+                   "name": "batch", "ncat": len(pts), "points": int(sum(sizes)), "tuned": tuned},
+        "one_at_a_time": {"value": len(pts) / t_single, "unit": "catalogues/s", "seconds": t_single},
+        "batched": {"value": len(pts) / t_batch, "seconds": t_batch},
+        "graph_replay": {"value": len(pts) / t_graph, "seconds": t_graph},
+        "speedup_vs_one_at_a_time": t_single / best,
+        "parity_batched_vs_single": parity,
+        "evaluated_pairs": int(st["evaluated_pairs"]), "work_items": int(st["work_items"]),
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
+                     "frac": achieved / peak, "traffic": None},
+        "pair_kernel_ms": min(pair_ms), "gpu_launches": int(st["kernel_launches"]),
+    }
+    print(json.dumps(line), flush=True)
+    cf.cf_destroy(ctx)
+    return 0
+
+
+def run_serve(args, world, rank, local):
+    """Poisson arrivals at a fraction of the measured capacity; p50 / p99 latency."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1911_03545_gb300 as cf
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    sizes, cats = _batch_setup(args.ncat)
+    p = _batch_params(cf)
+    hosts = [cf.points(c.x, c.y, c.z) for c in cats]
+    srv = cf.cf_server_start(local, p, args.serve_budget << 30, args.serve_slots)
+
+    def drain(tickets, t_sub, done):
+        pending = dict(tickets)
+        while pending:
+            for tk in list(pending):
+                r = cf.cf_server_poll(srv, tk, 0)
+                if r is not None:
+                    done[pending.pop(tk)] = (time.perf_counter(), r)
+            time.sleep(0.0002)
+
+    # capacity: everything submitted at once (the server batches continuously)
+    for _ in range(2):
+        t0 = time.perf_counter()
+        tks = {cf.cf_server_submit(srv, p, h): i for i, h in enumerate(hosts)}
+        done = {}
+        drain(tks, None, done)
+        cap_s = time.perf_counter() - t0
+    capacity = len(hosts) / cap_s
+    rate = args.serve_load * capacity
+    rng = np.random.Generator(np.random.PCG64(7))
+    nreq = args.serve_requests
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
+    order = rng.integers(0, len(hosts), size=nreq)
+    import threading
+    submit_t = {}
+    tickets = {}
+    lock = threading.Lock()
+    finished = {}
+    stop = threading.Event()
+
+    def poller():
+        while not stop.is_set() or tickets:
+            with lock:
+                items = list(tickets.items())
+            for tk, k in items:
+                r = cf.cf_server_poll(srv, tk, 0)
+                if r is not None:
+                    finished[k] = (time.perf_counter(), r)
+                    with lock:
+                        tickets.pop(tk, None)
+            time.sleep(0.0002)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t_start = time.perf_counter()
+    for k in range(nreq):
+        now = time.perf_counter() - t_start
+        if arrivals[k] > now:
+            time.sleep(arrivals[k] - now)
+        ts = time.perf_counter()
+        tk = cf.cf_server_submit(srv, p, hosts[int(order[k])])
+        with lock:
+            tickets[tk] = k
+            submit_t[k] = ts
+    stop.set()
+    th.join()
+    t_total = time.perf_counter() - t_start
+    lat = np.array([finished[k][0] - submit_t[k] for k in range(nreq)]) * 1e3
+    # every served result equals the batched result of the same catalogue
+    ctx = cf.cf_create(local, torch.cuda.current_stream(dev))
+    ref = cf.cf_batch_count(ctx, p, [_points(c, False, cf, dev) for c in cats])
+    cf.cf_destroy(ctx)
+    ok = all(np.array_equal(finished[k][1]["npairs"], ref[int(order[k])]["npairs"]) for k in range(nreq))
+    cf.cf_server_stop(srv)
+    line = {
+        "metric": "served catalogues/s", "value": nreq / t_total, "unit": "catalogues/s", "n_gpus": 1,
+        "steps": nreq, "warmup": 2, "ms_per_step": float(np.mean(lat)), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": BATCH_DESC, "name": "serve", "arrivals": "Poisson", "load": args.serve_load,
+                   "capacity_catalogues_per_s": capacity, "budget_gib": args.serve_budget, "slots": args.serve_slots,
+                   "inputs": "host numpy arrays (copied by the server)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                       "p99": float(np.percentile(lat, 99)), "mean": float(np.mean(lat)), "max": float(np.max(lat))},
+        "results_equal_batched": ok,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="clustered_r_1m", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="clustered_r_1m", choices=sorted(WORKLOADS) + ["batch256", "serve"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--no-tune-cache", action="store_true")
+    ap.add_argument("--ncat", type=int, default=256)
+    ap.add_argument("--serve-load", type=float, default=0.8)
+    ap.add_argument("--serve-requests", type=int, default=1024)
+    ap.add_argument("--serve-budget", type=int, default=16, help="GiB")
+    ap.add_argument("--serve-slots", type=int, default=64)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3
+    world, rank, local = _dist()
+    if args.workload == "batch256":
+        return run_batch(args, world, rank, local)
+    if args.workload == "serve":
+        return run_serve(args, world, rank, local)
     import gen
     wl = gen.workload(args.workload)
-    world, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, wl, world, rank)
     return run_gpu(args, wl, world, rank, local)

@@ -122,6 +122,7 @@ void CfCtx::drop_graph()
 CfCtx::~CfCtx()
 {
     drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
     for (auto &B : buf)
         if (B.p) cudaFree(B.p);
     if (hpin) cudaFreeHost(hpin);
@@ -707,13 +708,20 @@ cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *
     if ((rc = C->ensure(B_ITEMS, sizeof(CfItem) * (size_t)R.items_cap))) return (cf_status)rc;
     R.qcap = std::max(R.qcap, (uint32_t)(C->stats.rechecked_pairs * 2 + 4096));
     if ((rc = C->ensure(B_QUEUE, 16 * (size_t)R.qcap))) return (cf_status)rc;
-    cudaStream_t st = C->stream;
-    cudaStreamSynchronize(st);
+    cudaStream_t user = C->stream;
+    cudaStreamSynchronize(user);
     C->drop_graph();
+    // record on a context-owned stream (the legacy default stream cannot be captured); the
+    // graph is launched on the context's own stream by cf_batch_replay
+    if (!C->cap_stream && (rc = C->cuda(cudaStreamCreateWithFlags(&C->cap_stream, cudaStreamNonBlocking), "stream")))
+        return (cf_status)rc;
+    cudaStream_t st = C->cap_stream;
     if ((rc = C->cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return (cf_status)rc;
     C->capturing = true;
+    C->stream = st;
     int rc1 = cf_enqueue_build(C, R);
     int rc2 = rc1 ? rc1 : cf_enqueue_count(C, R, true);
+    C->stream = user;
     C->capturing = false;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(st, &graph);

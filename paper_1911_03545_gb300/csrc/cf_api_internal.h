@@ -79,6 +79,7 @@ struct CfCtx {
     uint64_t graph_gen = 0;
     int graph_ncat = 0;
     bool capturing = false;
+    cudaStream_t cap_stream = nullptr;   // stream used to record the batch graph
 
     int fail(int status, const std::string &msg);
     int cuda(cudaError_t e, const char *what);

@@ -1,0 +1,111 @@
+"""Autotuner for the pair-counting launch configuration.
+
+Knobs (all results are identical across them; only speed changes):
+  refine  sub-cells per Rmax cell (Sec. 4.2): 1, 2, 3
+  warps   warps per CTA of the persistent pair kernel (CTA shape; occupancy follows from the
+          shared-memory histograms): 4, 6, 8
+  tile    i-tile size (i points held in registers per warp item): 64, 128
+  jchunk  j range per work item (staging depth of the j stream): 128, 256, 512
+
+The tuner times `cf_count` on the caller's own catalogue with each candidate (a coordinate
+descent from the default), keeps the fastest, and caches it in a JSON file keyed by device name,
+kind, options and an occupancy class (log2 of the mean number of points per Rmax cell).  The cache
+path is $CF_TUNE_CACHE, else ~/.cache/cf_gb300_tune.json.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import time
+
+from . import CF_OPT_JCHUNK, CF_OPT_REFINE, CF_OPT_TILE, CF_OPT_WARPS, cf_count, cf_get_stats, cf_set_option
+
+KNOBS = {"refine": [1, 2, 3], "warps": [8, 6, 4], "tile": [128, 64], "jchunk": [512, 256, 128]}
+OPT = {"refine": CF_OPT_REFINE, "warps": CF_OPT_WARPS, "tile": CF_OPT_TILE, "jchunk": CF_OPT_JCHUNK}
+DEFAULT = {"refine": 1, "warps": 8, "tile": 128, "jchunk": 512}
+
+
+def cache_path() -> str:
+    return os.environ.get("CF_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cf_gb300_tune.json"))
+
+
+def occupancy_class(p, npoints: int) -> int:
+    """log2 of the mean points per cell of the unrefined grid (Sec. 4.1)."""
+    from . import cf_plan_probe
+    import numpy as np
+    box = list(p.c.box) if p.c.periodic else [1.0, 1.0, 1.0]
+    bb = [0.0, 0.0, 0.0] + box
+    info = cf_plan_probe(p, bb, max(1, npoints))
+    cells = max(1, int(np.prod(info["grid"])))
+    return int(round(math.log2(max(1.0, npoints / cells))))
+
+
+def _key(device_name: str, p, npoints: int) -> str:
+    return "|".join([device_name, str(p.kind), f"w{p.c.weight}", f"r{p.c.output_ravg}", f"p{p.c.periodic}",
+                     f"n{len(p.edges) - 1}", f"occ{occupancy_class(p, npoints)}"])
+
+
+def apply(ctx, cfg: dict) -> None:
+    for k, v in cfg.items():
+        cf_set_option(ctx, OPT[k], int(v))
+
+
+def reset(ctx) -> None:
+    apply(ctx, {k: 0 for k in OPT})
+
+
+def _time(ctx, p, d1, d2, reps: int) -> float:
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        cf_count(ctx, p, d1, d2)
+        st = cf_get_stats(ctx)
+        wall = time.perf_counter() - t0
+        best = min(best, (st["ms_build"] + st["ms_pair"] + st["ms_recheck"]) / 1e3 or wall)
+    return best
+
+
+def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, reps: int = 2,
+         use_cache: bool = True, log=None) -> dict:
+    """Return the best configuration for this workload (and leave it applied on ctx)."""
+    key = _key(device_name, p, npoints or 1)
+    path = cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            with open(path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        cfg = cache[key]["cfg"]
+        apply(ctx, cfg)
+        return cfg
+    cfg = dict(DEFAULT)
+    apply(ctx, cfg)
+    _time(ctx, p, d1, d2, 1)                      # warm up
+    best_t = _time(ctx, p, d1, d2, reps)
+    trials = [(dict(cfg), best_t)]
+    for knob, values in KNOBS.items():
+        for v in values:
+            if v == cfg[knob]:
+                continue
+            cand = dict(cfg)
+            cand[knob] = v
+            apply(ctx, cand)
+            t = _time(ctx, p, d1, d2, reps)
+            trials.append((dict(cand), t))
+            if log:
+                log(f"tune {cand} {t * 1e3:.3f} ms")
+            if t < best_t:
+                best_t, cfg = t, cand
+    apply(ctx, cfg)
+    if use_cache:
+        cache[key] = {"cfg": cfg, "ms": best_t * 1e3,
+                      "trials": [{"cfg": c, "ms": t * 1e3} for c, t in trials]}
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path + ".tmp", "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(path + ".tmp", path)
+    return cfg

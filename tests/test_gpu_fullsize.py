@@ -1,0 +1,56 @@
+"""Full-size parity: the measured workloads at their full sizes, in the launch configuration
+bench.py times, against expected histograms the FP64 oracle wrote (tests/golden/make_golden.py).
+
+Counts must be bit-identical; weighted sums and ravg within 1e-6 relative.  A fingerprint of the
+generated arrays guards against a generator that produces different inputs on another machine.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gen
+from tests.golden.make_golden import fingerprint, workload
+from tests.gpu_util import TOL, to_dev
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+NAMES = sorted(f[5:-5] for f in os.listdir(GOLDEN) if f.startswith("full_") and f.endswith(".json"))
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1911_03545_gb300 as cf
+    c = cf.cf_create(0, torch.cuda.current_stream())
+    yield c
+    cf.cf_destroy(c)
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_full_size_against_oracle(ctx, name):
+    import paper_1911_03545_gb300 as cf
+    with open(os.path.join(GOLDEN, f"full_{name}.json")) as f:
+        gold = json.load(f)
+    wl = workload(name)
+    if fingerprint(wl.d1, wl.d2) != gold["fingerprint"]:
+        pytest.skip("this machine's generator produced different inputs than the golden file's")
+    p = cf.params(kind=wl.kind, edges=wl.edges, autocorr=wl.autocorr, periodic=wl.periodic, box=wl.box,
+                  pimax=wl.pimax, npibins=wl.npibins, weighted=wl.weighted, ravg=wl.ravg)
+
+    def pts(c):
+        t = to_dev(c, "cuda:0", wl.weighted)
+        return cf.points(*t[:3], t[3] if wl.weighted else None)
+
+    got = cf.cf_count(ctx, p, pts(wl.d1), None if wl.autocorr else pts(wl.d2))
+    n = np.asarray(got["npairs"]).ravel().astype(np.uint64)
+    e = np.asarray(gold["npairs"], dtype=np.uint64)
+    assert np.array_equal(n, e), np.argwhere(n != e)[:10]
+    if wl.weighted:
+        np.testing.assert_allclose(np.asarray(got["wsum"]).ravel(), gold["wsum"], rtol=TOL, atol=0)
+    if wl.ravg:
+        np.testing.assert_allclose(np.asarray(got["ravg"]).ravel(), gold["ravg"], rtol=TOL, atol=0)
