@@ -19,11 +19,12 @@
 #define CFI_MAX_SETS 4096
 #define CFI_MAX_STENCIL 4096
 #define CFI_LUT_MAX 8192          // coarse LUT cells (4 B each)
+#define CFI_LUT_TARGET 4096       // preferred coarse cells per table
 #define CFI_FINE_MAX 1024         // fine LUT entries (16 B each)
 #define CFI_CLS_OUT 0xFEu         // class: outside every bin
 #define CFI_CLS_AMB 0xFFu         // class: within the FP32 error band of an edge
 #define CFI_FINE_FLAG 0x100u      // coarse entry >= this: index of a fine entry + flag
-#define CFI_QN 2048               // per-warp candidate ring (entries of 16 bits)
+#define CFI_QN 1024               // per-warp candidate ring entries
 #define CFI_JMAX 512              // longest j range of a work item (9-bit j in a candidate)
 
 // Pair-kernel item (48 bytes, three 16-byte loads)
@@ -66,7 +67,8 @@ struct CfLut {
     uint32_t last;     // index of the last coarse cell (values above clamp here)
     uint32_t coff;     // offset of the coarse entries in the shared LUT array (in words)
     uint32_t foff;     // offset of the fine entries (in 16-byte units from the fine base)
-    uint32_t pad[3];
+    uint32_t tail;     // bits from which every value is outside all bins
+    uint32_t pad[2];
 };
 
 struct CfFine {        // class of v: byte seg of `code`, seg = (v >= t1) + (v >= t2)

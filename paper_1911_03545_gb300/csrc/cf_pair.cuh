@@ -7,17 +7,18 @@
 // i, not per pair).  Each j point is a broadcast load.
 //
 // Phase A (every pair): the separations and squared distance of two pairs at a time are formed
-// by packed FP32x2 add / mul / fma on cell-relative coordinates, and each pair is tested
-// against one cut just above the last bin edge (Sec. 4.7: squared space, no sqrt).  A lane
-// gathers the outcome of 32 pairs (8 j points x 4 i points) in a bit mask.
-// Compaction: the warp scans the mask counts and appends the candidate pairs, 16 bits each
-// (i slot, j), to a per-warp ring in shared memory.
-// Phase B (candidates only, 32 or 64 per pass, all lanes busy): the squared separation is
-// formed again (with the shift's low part and the TwoSum residual of the i translation when
-// ravg needs relative accuracy), its bin is looked up on the FP32 bit pattern through a coarse
-// table (cells holding an edge resolve through a fine entry of <= 2 thresholds).  A value
-// within the proven FP32 error band of an edge is not binned: the pair goes to a global queue
-// and is re-evaluated in FP64 by the recheck kernel, so counts equal the FP64 result.
+// by packed FP32x2 add / mul / fma on cell-relative coordinates -- with the shift's low part and
+// the TwoSum residual of the i translation when ravg needs relative accuracy -- and each pair is
+// tested against one cut: the FP32 value above which every value lies outside all bins (Sec.
+// 4.7: squared space, no sqrt).  A lane keeps the values of a block of 16 pairs (4 j points x 4
+// i points) in a lane-private buffer and their outcome in a bit mask.
+// Compaction: the warp scans the mask counts and appends each candidate -- its FP32 value (and
+// |dz| for rp-pi / wp) and a 16-bit code (i slot, j) -- to a per-warp ring in shared memory.
+// Phase B (candidates only, 32 or 64 per pass, all lanes busy): the bin of the stored value is
+// looked up on its FP32 bit pattern through a coarse table (cells holding an edge resolve
+// through a fine entry of <= 2 thresholds).  A value within the proven FP32 error band of an
+// edge is not binned: the pair goes to a global queue and is re-evaluated in FP64 by the
+// recheck kernel, so counts equal the FP64 result.
 //
 // Histograms live in shared memory per warp (Sec. 4.8: private histograms, merged once): for
 // r / theta / wp one private copy per lane (no bank conflicts, no contention; weighted sums
@@ -35,7 +36,11 @@ constexpr uint32_t QM = CFI_QN - 1;
 
 __host__ __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-// per-warp shared memory: candidate ring | i-tile stage | histogram
+// per-warp shared memory: block buffer | candidate ring | i weights | histogram
+//   block buffer: the FP32 values phase A formed for one block of 16 pair slots per lane,
+//                 [j][lane][slot] (and the same for |dz| in rp-pi and wp)
+//   ring:         CFI_QN candidates: value bits (u32) [, |dz| bits (u32)], code (u16)
+constexpr uint32_t SLOTS_PER_BLOCK = 16;
 __host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int kind, bool W, bool R, int nslot)
 {
     if (kind == KIND_RPPI) {
@@ -49,10 +54,13 @@ __host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int kind, bool W, b
     if (R) b += nslot * 32u * 8u;
     return b;
 }
-__host__ __device__ __forceinline__ uint32_t warp_stage_bytes(bool R) { return 128u * (R ? 32u : 16u); }
+__host__ __device__ __forceinline__ bool has_z(int kind) { return kind == KIND_RPPI || kind == KIND_WP; }
+__host__ __device__ __forceinline__ uint32_t warp_buf_bytes(int kind) { return SLOTS_PER_BLOCK * 32u * 4u * (has_z(kind) ? 2u : 1u); }
+__host__ __device__ __forceinline__ uint32_t warp_ring_bytes(int kind) { return CFI_QN * (has_z(kind) ? 10u : 6u); }
+__host__ __device__ __forceinline__ uint32_t warp_stage_bytes(bool W) { return W ? 128u * 4u : 0u; }
 __host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, int nslot)
 {
-    return CFI_QN * 2u + warp_stage_bytes(R) + warp_hist_bytes(kind, W, R, nslot);
+    return warp_buf_bytes(kind) + warp_ring_bytes(kind) + warp_stage_bytes(W) + warp_hist_bytes(kind, W, R, nslot);
 }
 
 __device__ __forceinline__ void kahan_add(float2 *p, float v)
@@ -106,8 +114,10 @@ struct Warp {
     uint32_t *h_cnt;        // lane-private [nslot][32] or per-warp [nslot]
     float2 *h_w, *h_r;      // lane-private Kahan pairs
     double *h_wd, *h_rd;    // per-warp FP64 (rp-pi)
-    uint16_t *ring;         // candidate ring: (i slot << 9) | j
-    float4 *stage;          // i tile: (s.x, s.y, s.z, w) [, (e.x, e.y, e.z, 0)]
+    float *buf, *bufz;      // block buffer: [j][lane][slot]
+    uint32_t *ring_d, *ring_z;
+    uint16_t *ring_c;       // candidate code: (i slot << 9) | j
+    float *stage_w;         // weights of the i tile
     int lane, nb, npi, nslot;
     uint32_t icnt, ibeg, jbeg, job, head, tail;
     float cut_r, cut_p;
@@ -143,49 +153,27 @@ struct Warp {
         }
     }
 
+    __device__ __forceinline__ float weight(uint32_t il, uint32_t j) const
+    {
+        return stage_w[il] * __ldg(reinterpret_cast<const float *>(a.pb + jbeg + j) + 2);
+    }
+
     // Phase B for one candidate (valid == false: the lane only takes part in the warp's flow)
-    __device__ __forceinline__ void finish(uint32_t code, bool valid)
+    __device__ __forceinline__ void finish(uint32_t vb, uint32_t zb, uint32_t code, bool valid)
     {
         const uint32_t il = code >> 9, j = code & (CFI_JMAX - 1);
-        const float4 S = stage[R ? 2 * il : il];
-        const ulonglong2 A = __ldg(a.pa + jbeg + j), B = __ldg(a.pb + jbeg + j);
-        float dx = S.x + f2_lo(A.x), dy = S.y + f2_lo(A.y), dz = S.z + f2_lo(B.x);
-        if (R) {
-            const float4 E = stage[2 * il + 1];
-            float ex = E.x, ey = E.y, ez = E.z;
-            if (LO) {
-                const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(jbeg + j));
-                const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(jbeg + j) + 1);
-                ex = ex + f2_lo(C.x);
-                ey = ey + f2_lo(C.y);
-                ez = ez + f2_lo(D.x);
-            }
-            dx = dx + ex;
-            dy = dy + ey;
-            dz = dz + ez;
-        }
-        if (WRAP) {
-            if (Lx > 0.f) dx = wrap1(dx, Lx, iLx);
-            if (Ly > 0.f) dy = wrap1(dy, Ly, iLy);
-            if (Lz > 0.f) dz = wrap1(dz, Lz, iLz);
-        }
-        const float wp = W ? S.w * f2_lo(B.y) : 0.f;
         if (KIND == KIND_R || KIND == KIND_THETA) {
-            float d2 = dx * dx;
-            d2 = fmaf(dy, dy, d2);
-            d2 = fmaf(dz, dz, d2);
-            const uint32_t c = lut_class(lr, fine, __float_as_uint(d2));
-            if (valid && c < (uint32_t)nb) acc_lp(c, d2, wp);
+            const uint32_t c = lut_class(lr, fine, vb);
+            if (valid && c < (uint32_t)nb) acc_lp(c, __uint_as_float(vb), W ? weight(il, j) : 0.f);
             else if (valid && c == CFI_CLS_AMB) push(ibeg + il, jbeg + j);
         } else {
-            float rp2 = dx * dx;
-            rp2 = fmaf(dy, dy, rp2);
-            const uint32_t cz = lut_class(lp, fine, __float_as_uint(fabsf(dz)));
-            const uint32_t cr = lut_class(lr, fine, __float_as_uint(rp2));
+            const uint32_t cz = lut_class(lp, fine, zb);
+            const uint32_t cr = lut_class(lr, fine, vb);
             if (valid && cz != CFI_CLS_OUT && cr != CFI_CLS_OUT) {
                 if (cr < (uint32_t)nb && cz < CFI_CLS_OUT) {
-                    if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, rp2, wp);
-                    else acc_lp(cr, rp2, wp);
+                    const float wp = W ? weight(il, j) : 0.f;
+                    if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, __uint_as_float(vb), wp);
+                    else acc_lp(cr, __uint_as_float(vb), wp);
                 } else {
                     push(ibeg + il, jbeg + j);
                 }
@@ -197,16 +185,19 @@ struct Warp {
     template <int K>
     __device__ __forceinline__ void drain(uint32_t count)
     {
-        uint32_t code[K];
+        uint32_t vb[K], zb[K], code[K];
         bool v[K];
 #pragma unroll
         for (int k = 0; k < K; k++) {
             const uint32_t idx = lane + 32u * k;
+            const uint32_t e = (head + idx) & QM;
             v[k] = idx < count;
-            code[k] = v[k] ? ring[(head + idx) & QM] : 0u;
+            vb[k] = ring_d[e];
+            zb[k] = has_z(KIND) ? ring_z[e] : 0u;
+            code[k] = ring_c[e];
         }
 #pragma unroll
-        for (int k = 0; k < K; k++) finish(code[k], v[k]);
+        for (int k = 0; k < K; k++) finish(vb[k], zb[k], code[k], v[k]);
         head += count;
         __syncwarp();
     }
@@ -214,20 +205,26 @@ struct Warp {
     template <int P, bool DIAG>
     __device__ __forceinline__ void run(const CfItem &it)
     {
+        constexpr int SL = 2 * P;                           // pair slots per j per lane
+        constexpr int JB = SLOTS_PER_BLOCK / SL;            // j points per block
         icnt = it.cnt & 0xFFFFu;
         const uint32_t jcnt = it.cnt >> 16;
         ibeg = it.ibeg;
         jbeg = it.jbeg;
         job = it.meta & CFI_ITEM_JOBMASK;
-        // ---- i tile: translate by the shift (TwoSum residual kept for the precise phase B) ----
-        u64 sx[P], sy[P], sz[P];
+        // ---- i tile: translate by the shift; with ravg keep the TwoSum residual too ----
+        u64 sx[P], sy[P], sz[P], ex[P], ey[P], ez[P];
 #pragma unroll
         for (int p = 0; p < P; p++) {
-            float vs[3][2];
+            float vs[3][2], ve[3][2];
 #pragma unroll
             for (int h = 0; h < 2; h++) {
                 const uint32_t il = lane + 32u * (2 * p + h);
-                float4 Sv = make_float4(1e18f, 1e18f, 1e18f, 0.f), Ev = make_float4(0.f, 0.f, 0.f, 0.f);
+                float w = 0.f;
+#pragma unroll
+                for (int d = 0; d < 3; d++) { vs[d][h] = 1e18f; ve[d][h] = 0.f; }
+                // empty slots sit far outside every bin (1e18^2 < FLT_MAX); in wrap mode the
+                // minimum image would fold them back, so there they are also masked by icnt
                 if (il < icnt) {
                     const ulonglong2 A = a.pa[ibeg + il], B = a.pb[ibeg + il];
                     const float X[3] = {-f2_lo(A.x), -f2_lo(A.y), -f2_lo(B.x)};
@@ -238,52 +235,57 @@ struct Warp {
                         XL[1] = -f2_lo(C.y);
                         XL[2] = -f2_lo(D.x);
                     }
-                    float s[3], e[3];
 #pragma unroll
                     for (int d = 0; d < 3; d++) {
                         if (R) {
-                            two_sum(X[d], it.s[d], s[d], e[d]);
-                            e[d] = (e[d] + it.slo[d]) + XL[d];
+                            float s, e;
+                            two_sum(X[d], it.s[d], s, e);
+                            vs[d][h] = s;
+                            ve[d][h] = (e + it.slo[d]) + XL[d];
                         } else {
-                            s[d] = X[d] + it.s[d];
-                            e[d] = 0.f;
+                            vs[d][h] = X[d] + it.s[d];
                         }
                     }
-                    Sv = make_float4(s[0], s[1], s[2], f2_lo(B.y));
-                    Ev = make_float4(e[0], e[1], e[2], 0.f);
+                    w = f2_lo(B.y);
                 }
-                // empty slots sit far outside every bin (1e18^2 < FLT_MAX); in wrap mode the
-                // minimum image would fold them back, so there they are also masked by icnt
-                vs[0][h] = Sv.x;
-                vs[1][h] = Sv.y;
-                vs[2][h] = Sv.z;
-                if (R) {
-                    stage[2 * il] = Sv;
-                    stage[2 * il + 1] = Ev;
-                } else {
-                    stage[il] = Sv;
-                }
+                if (W) stage_w[il] = w;
             }
             sx[p] = f2_pack(vs[0][0], vs[0][1]);
             sy[p] = f2_pack(vs[1][0], vs[1][1]);
             sz[p] = f2_pack(vs[2][0], vs[2][1]);
+            ex[p] = f2_pack(ve[0][0], ve[0][1]);
+            ey[p] = f2_pack(ve[1][0], ve[1][1]);
+            ez[p] = f2_pack(ve[2][0], ve[2][1]);
         }
         __syncwarp();
         head = tail = 0;
-        constexpr int JB = 16 / P;          // j points per block: 32 pair slots per lane
         const ulonglong2 *__restrict__ pa = a.pa + jbeg;
         const ulonglong2 *__restrict__ pb = a.pb + jbeg;
         for (uint32_t j0 = 0; j0 < jcnt; j0 += JB) {
-            // ---- phase A ----
+            // ---- phase A: the exact FP32 value phase B will bin, one cut per pair ----
             uint32_t mask = 0;
 #pragma unroll
             for (int jj = 0; jj < JB; jj++) {
                 const uint32_t j = j0 + jj;
                 if (j < jcnt) {
                     const ulonglong2 A = __ldg(pa + j), B = __ldg(pb + j);
+                    u64 lx = 0, ly = 0, lz = 0;
+                    if (LO) {
+                        const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(jbeg + j));
+                        const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(jbeg + j) + 1);
+                        lx = C.x;
+                        ly = C.y;
+                        lz = D.x;
+                    }
+                    float dv[SL], zv[SL];
 #pragma unroll
                     for (int p = 0; p < P; p++) {
                         u64 dx = f2_add(sx[p], A.x), dy = f2_add(sy[p], A.y), dz = f2_add(sz[p], B.x);
+                        if (R) {
+                            dx = f2_add(dx, LO ? f2_add(ex[p], lx) : ex[p]);
+                            dy = f2_add(dy, LO ? f2_add(ey[p], ly) : ey[p]);
+                            dz = f2_add(dz, LO ? f2_add(ez[p], lz) : ez[p]);
+                        }
                         if (WRAP) {
                             if (Lx > 0.f) dx = wrap2(dx, Lx, iLx);
                             if (Ly > 0.f) dy = wrap2(dy, Ly, iLy);
@@ -294,13 +296,20 @@ struct Warp {
                             u64 d2 = f2_mul(dx, dx);
                             d2 = f2_fma(dy, dy, d2);
                             d2 = f2_fma(dz, dz, d2);
-                            c0 = f2_lo(d2) < cut_r;
-                            c1 = f2_hi(d2) < cut_r;
+                            dv[2 * p] = f2_lo(d2);
+                            dv[2 * p + 1] = f2_hi(d2);
+                            c0 = dv[2 * p] < cut_r;
+                            c1 = dv[2 * p + 1] < cut_r;
                         } else {
                             u64 rp2 = f2_mul(dx, dx);
                             rp2 = f2_fma(dy, dy, rp2);
-                            c0 = f2_lo(rp2) < cut_r && fabsf(f2_lo(dz)) < cut_p;
-                            c1 = f2_hi(rp2) < cut_r && fabsf(f2_hi(dz)) < cut_p;
+                            const u64 adz = dz & 0x7FFFFFFF7FFFFFFFull;
+                            dv[2 * p] = f2_lo(rp2);
+                            dv[2 * p + 1] = f2_hi(rp2);
+                            zv[2 * p] = f2_lo(adz);
+                            zv[2 * p + 1] = f2_hi(adz);
+                            c0 = dv[2 * p] < cut_r && zv[2 * p] < cut_p;
+                            c1 = dv[2 * p + 1] < cut_r && zv[2 * p + 1] < cut_p;
                         }
                         const uint32_t il0 = lane + 64u * p, il1 = il0 + 32u;
                         if (DIAG) {
@@ -311,9 +320,17 @@ struct Warp {
                             c0 = c0 && il0 < icnt;
                             c1 = c1 && il1 < icnt;
                         }
-                        const int bit = jj * 2 * P + 2 * p;
+                        const int bit = jj * SL + 2 * p;
                         mask |= (c0 ? 1u : 0u) << bit;
                         mask |= (c1 ? 1u : 0u) << (bit + 1);
+                    }
+                    float *bp = buf + ((uint32_t)jj * 32u + lane) * SL;
+                    if (P == 2) *reinterpret_cast<float4 *>(bp) = make_float4(dv[0], dv[1], dv[2], dv[3]);
+                    else *reinterpret_cast<float2 *>(bp) = make_float2(dv[0], dv[1]);
+                    if (has_z(KIND)) {
+                        float *zp = bufz + ((uint32_t)jj * 32u + lane) * SL;
+                        if (P == 2) *reinterpret_cast<float4 *>(zp) = make_float4(zv[0], zv[1], zv[2], zv[3]);
+                        else *reinterpret_cast<float2 *>(zp) = make_float2(zv[0], zv[1]);
                     }
                 }
             }
@@ -328,10 +345,14 @@ struct Warp {
             const uint32_t tot = __shfl_sync(CF_FULL, pre, 31);
             uint32_t pos = tail + pre - n;
             while (mask) {
-                const int b = __ffs(mask) - 1;
+                const uint32_t b = (uint32_t)(__ffs(mask) - 1);
                 mask &= mask - 1;
-                const uint32_t q = (uint32_t)b % (2 * P), jj = (uint32_t)b / (2 * P);
-                ring[pos & QM] = (uint16_t)(((lane + 32u * q) << 9) | (j0 + jj));
+                const uint32_t q = b % SL, jj = b / SL;
+                const uint32_t e = pos & QM;
+                const uint32_t o = (jj * 32u + lane) * SL + q;
+                ring_d[e] = __float_as_uint(buf[o]);
+                if (has_z(KIND)) ring_z[e] = __float_as_uint(bufz[o]);
+                ring_c[e] = (uint16_t)(((lane + 32u * q) << 9) | (j0 + jj));
                 pos++;
             }
             tail += tot;
@@ -392,10 +413,10 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
     const uint32_t wb = warp_bytes(KIND, W, R, a.nslot);
-    const uint32_t hoff = CFI_QN * 2u + warp_stage_bytes(R);
+    const uint32_t hoff = warp_buf_bytes(KIND) + warp_ring_bytes(KIND) + warp_stage_bytes(W);
     unsigned char *my = wbase + (size_t)(threadIdx.x >> 5) * wb;
     {
-        // zero this warp's histogram (the ring and the stage need no initial value)
+        // zero this warp's histogram (the buffers need no initial value)
         uint32_t *h = (uint32_t *)(my + hoff);
         const uint32_t words = warp_hist_bytes(KIND, W, R, a.nslot) / 4u;
         for (uint32_t i = threadIdx.x & 31; i < words; i += 32) h[i] = 0u;
@@ -416,8 +437,18 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
     w.iLx = a.L[0] > 0.f ? 1.0f / a.L[0] : 0.f;
     w.iLy = a.L[1] > 0.f ? 1.0f / a.L[1] : 0.f;
     w.iLz = a.L[2] > 0.f ? 1.0f / a.L[2] : 0.f;
-    w.ring = (uint16_t *)my;
-    w.stage = (float4 *)(my + CFI_QN * 2u);
+    {
+        const bool z = has_z(KIND);
+        unsigned char *q = my;
+        w.buf = (float *)q;
+        w.bufz = (float *)(q + SLOTS_PER_BLOCK * 32u * 4u);
+        q += warp_buf_bytes(KIND);
+        w.ring_d = (uint32_t *)q;
+        w.ring_z = (uint32_t *)(q + CFI_QN * 4u);
+        w.ring_c = (uint16_t *)(q + CFI_QN * (z ? 8u : 4u));
+        q += warp_ring_bytes(KIND);
+        w.stage_w = (float *)q;
+    }
     w.h_cnt = (uint32_t *)(my + hoff);
     if (KIND == KIND_RPPI) {
         uint32_t o = ((uint32_t)a.nslot * 4u + 7u) & ~7u;

@@ -157,13 +157,16 @@ bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint32_t> &wo
     if (segs.size() < 2) return false;
     uint32_t lo = segs[1].start;                  // first class change
     uint32_t hi = segs.back().start;              // last class change
-    for (int s = 23; s >= 0; s--) {
+    // the finest cell width whose table holds <= CFI_LUT_TARGET cells: cells that contain an
+    // edge need the fine entry, so narrow cells keep that slower path rare
+    int s0 = 0;
+    while (s0 < 23 && ((((uint64_t)hi - (((uint64_t)lo >> s0) << s0)) >> s0) + 2) > (uint64_t)CFI_LUT_TARGET) s0++;
+    for (int s = s0; s >= 0; s--) {
         uint64_t w = 1ull << s;
         uint64_t base = ((uint64_t)lo >> s) << s;
         base = base >= w ? base - w : 0;
         uint64_t last = ((uint64_t)hi - base) >> s;
         if (last + 1 > (uint64_t)CFI_LUT_MAX) return false;
-        if (last + 1 < 64 && s > 0) continue;     // too coarse to be useful; refine
         std::vector<uint32_t> cw(last + 1);
         std::vector<CfFine> fw;
         bool ok = true;
@@ -201,6 +204,7 @@ bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint32_t> &wo
         L.last = (uint32_t)last;
         L.coff = (uint32_t)words.size();
         L.foff = 0;
+        L.tail = segs.back().start;
         words.insert(words.end(), cw.begin(), cw.end());
         fine.insert(fine.end(), fw.begin(), fw.end());
         return true;
@@ -337,30 +341,6 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
         for (int m = 0; m <= p->npibins; m++)
             H.band_p[m] = SAFETY * (H.theta_rel * D.pe[m] + H.delta[2] + 4 * U64 * D.pe[m]);
     }
-    // Candidate cut of the pair kernel's first phase, which forms the squared separation without
-    // the low-order shift and cell residual terms (the first-order "non-precise" model): twice
-    // that model's band above the last edge, so every pair the second phase could bin or send to
-    // the FP64 recheck passes the cut.
-    {
-        double dnp[3];
-        for (int a = 0; a < 3; a++) {
-            double amax = std::max(std::fabs(G.lo[a]), std::fabs(G.lo[a] + extent[a]));
-            double Q = ulp32_of_magnitude(std::max(amax, 1e-300));
-            double epsX = f64 ? (u * (G.width[a] + 2 * Q) + 2 * U64 * amax) : 0.0;
-            double wrapterm = G.wrap[a] ? u * G.L[a] : 0.0;
-            dnp[a] = 2 * u * H.M[a] + 2 * epsX + wrapterm + 2 * U64 * (H.M[a] + G.L[a] + amax);
-        }
-        double Emax = D.e2[D.nb];
-        double cut = Emax + 2 * band_sq(Emax, naxes, u, dnp) + H.band_r[D.nb];
-        D.cut_r = std::nextafter((float)cut, INFINITY);
-        if (rppi_like) {
-            double cp = p->pimax + 2 * SAFETY * (u * p->pimax + dnp[2]) + H.band_p[p->npibins];
-            D.cut_p = std::nextafter((float)cp, INFINITY);
-        } else {
-            D.cut_p = INFINITY;
-        }
-    }
-
     // ---- lookup tables ----
     {
         auto segs = make_segments(D.e2, H.band_r, D.nb);
@@ -379,6 +359,16 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
             err = "pi bins too narrow for the FP32 lookup table";
             return CF_ERR_ARG;
         }
+    }
+    // candidate cuts of the pair kernel's first phase: the FP32 value at which the final
+    // "outside every bin" segment of each table starts
+    {
+        float f;
+        std::memcpy(&f, &D.lr.tail, 4);
+        D.cut_r = f;
+        if (rppi_like) std::memcpy(&f, &D.lp.tail, 4);
+        else f = INFINITY;
+        D.cut_p = f;
     }
     D.nlut_words = (int)H.lut.size();
     D.nfine = (int)H.fine.size();

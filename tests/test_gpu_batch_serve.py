@@ -47,6 +47,7 @@ def _params(cf, weighted=False):
 
 def test_graph_capture_replay(cf, cats):
     import torch
+    cats = list(cats)                       # the new-data replay below must not change the fixture
     ctx = cf.cf_create(0, torch.cuda.current_stream())
     try:
         p = _params(cf)
