@@ -204,6 +204,30 @@ cf_status cf_server_cancel(void *server, uint64_t ticket);
 cf_status cf_server_stop(void *server);
 const char *cf_server_last_error(const void *server);
 
+/* ---- allocation-free count (the paper has no counterpart) ----
+ * For callers that cannot allocate device memory: code running inside another framework's memory
+ * pool (every byte must come from that pool), plugins where allocation is forbidden, and programs
+ * that must not allocate after start-up because an allocation can synchronise the device.
+ * cf_count_noalloc allocates nothing (no cudaMalloc, cudaFree, pinned memory or allocating
+ * library call).  Inputs and outputs are the caller's DEVICE arrays: d1 (and d2 for a cross
+ * count) with on_device = 1; npairs / wsum / ravg of nbins * (npibins for CF_DD_RPPI) entries (any
+ * may be NULL).  Results follow the definition at the top of this file (counts exact, sums
+ * within 1e-6 relative).  The work is enqueued on `cuda_stream` and the function returns without
+ * waiting; the outputs are ready when the stream reaches that point.
+ * It evaluates every pair in FP64 without a cell list, so it suits small inputs (cost ~ N1*N2).
+ * Its only scratch is a fixed array of CF_NOALLOC_SCRATCH_BYTES in the library image, present on
+ * every device that loads the library until the process exits; histograms are limited to
+ * CF_NOALLOC_MAX_SLOTS slots (nbins, or nbins*npibins for rp-pi): larger requests return
+ * CF_ERR_ARG.  The first call on a device looks up the array's device address with that device
+ * current: make that first call before any stream capture.  All calls share the array and each
+ * call clears it first, so calls whose GPU work overlaps (other streams, or unordered host
+ * threads) race and must not be issued.  Status: CF_ERR_ARG for invalid or oversized input,
+ * CF_ERR_CUDA for a failed launch or no current device. */
+#define CF_NOALLOC_MAX_SLOTS 2048
+#define CF_NOALLOC_SCRATCH_BYTES 65536
+cf_status cf_count_noalloc(const cf_params *params, const cf_points *d1, const cf_points *d2, uint64_t *npairs,
+                           double *wsum, double *ravg, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -264,3 +264,12 @@ def cf_plan_probe(p: Params, bbox, npoints: int, any_f64: bool = False, which: i
     out["bands_p"] = bp[: p.c.npibins + 1] if p.kind in (CF_DD_RPPI, CF_WP) else np.zeros(0)
     out["classes"] = cls
     return out
+
+
+def cf_count_noalloc(p: Params, d1: Points, d2: Optional[Points], npairs, wsum=None, ravg=None, stream=None) -> None:
+    """Allocation-free count into caller-owned device tensors (see include/cf.h): for callers that
+    cannot allocate device memory.  Enqueued on `stream`; returns without waiting."""
+    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    rc = _capi.lib().cf_count_noalloc(ctypes.byref(p.c), ctypes.byref(d1.c), ctypes.byref(d2.c) if d2 else None,
+                                      ptr(npairs), ptr(wsum), ptr(ravg), _stream_handle(stream))
+    _check(rc)

@@ -119,6 +119,8 @@ _PROTOS = {
     "cf_server_cancel": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "cf_server_stop": (ctypes.c_int, [_P]),
     "cf_server_last_error": (ctypes.c_char_p, [_P]),
+    "cf_count_noalloc": (ctypes.c_int, [ctypes.POINTER(cf_params), ctypes.POINTER(cf_points), ctypes.POINTER(cf_points),
+                                        _P, _P, _P, _P]),
     "cf_plan_probe": (ctypes.c_int, [ctypes.POINTER(cf_params), ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                      ctypes.c_int, ctypes.POINTER(cf_plan_info), ctypes.POINTER(ctypes.c_double),
                                      ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.POINTER(ctypes.c_float),
