@@ -332,6 +332,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.cfg.nslot = D.nslot;
     R.cfg.warps = (int)C->opt[CF_OPT_WARPS];
     R.cfg.ctas_per_sm = (int)C->opt[CF_OPT_CTAS_PER_SM];
+    R.cfg.variant = C->opt[CF_OPT_VARIANT] == 2 ? 2 : 1;
     R.items_cap = 0;
     return CF_OK;
 }
@@ -495,7 +496,7 @@ int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
         C->stats.refine[a] = D.g.k[a];
     }
     C->stats.ncat = R.njobs;
-    C->stats.variant = C->last_warps;
+    C->stats.variant = R.cfg.variant;
     C->stats.kernel_launches = C->launches;
     return CF_OK;
 }

@@ -58,8 +58,9 @@ __host__ __device__ __forceinline__ bool has_z(int kind) { return kind == KIND_R
 __host__ __device__ __forceinline__ uint32_t warp_buf_bytes(int kind) { return SLOTS_PER_BLOCK * 32u * 4u * (has_z(kind) ? 2u : 1u); }
 __host__ __device__ __forceinline__ uint32_t warp_ring_bytes(int kind) { return CFI_QN * (has_z(kind) ? 10u : 6u); }
 __host__ __device__ __forceinline__ uint32_t warp_stage_bytes(bool W) { return W ? 128u * 4u : 0u; }
-__host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, int nslot)
+__host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, int nslot, bool direct)
 {
+    if (direct) return warp_hist_bytes(kind, W, R, nslot);
     return warp_buf_bytes(kind) + warp_ring_bytes(kind) + warp_stage_bytes(W) + warp_hist_bytes(kind, W, R, nslot);
 }
 
@@ -364,6 +365,130 @@ struct Warp {
         if (tail != head) drain<1>(tail - head);
     }
 
+    // ---- direct variant: every pair is binned where it is formed (no compaction) ----
+    template <bool DIAG>
+    __device__ __forceinline__ void bin_direct(uint32_t vb, uint32_t zb, float wp, uint32_t il, uint32_t j)
+    {
+        const bool live = (!DIAG || j > il) && (!WRAP || il < icnt);
+        if (KIND == KIND_R || KIND == KIND_THETA) {
+            const uint32_t c = lut_class(lr, fine, vb);
+            if (c < (uint32_t)nb) {
+                if (live) acc_lp(c, __uint_as_float(vb), wp);
+            } else if (c == CFI_CLS_AMB) {
+                if (live) push(ibeg + il, jbeg + j);
+            }
+        } else {
+            const uint32_t cz = lut_class(lp, fine, zb);
+            if (cz == CFI_CLS_OUT) return;
+            const uint32_t cr = lut_class(lr, fine, vb);
+            if (cr < (uint32_t)nb && cz < CFI_CLS_OUT) {
+                if (live) {
+                    if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, __uint_as_float(vb), wp);
+                    else acc_lp(cr, __uint_as_float(vb), wp);
+                }
+            } else if (cr != CFI_CLS_OUT) {
+                if (live) push(ibeg + il, jbeg + j);
+            }
+        }
+    }
+
+    template <int P, bool DIAG>
+    __device__ __forceinline__ void run_direct(const CfItem &it)
+    {
+        icnt = it.cnt & 0xFFFFu;
+        const uint32_t jcnt = it.cnt >> 16;
+        ibeg = it.ibeg;
+        jbeg = it.jbeg;
+        job = it.meta & CFI_ITEM_JOBMASK;
+        u64 sx[P], sy[P], sz[P], ex[P], ey[P], ez[P], wi[P];
+#pragma unroll
+        for (int p = 0; p < P; p++) {
+            float vs[3][2], ve[3][2], vw[2];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                const uint32_t il = lane + 32u * (2 * p + h);
+                vw[h] = 0.f;
+#pragma unroll
+                for (int d = 0; d < 3; d++) { vs[d][h] = 1e18f; ve[d][h] = 0.f; }
+                // empty slots sit far outside every bin (1e18^2 < FLT_MAX); in wrap mode the
+                // minimum image would fold them back, so there they are also masked by icnt
+                if (il < icnt) {
+                    const ulonglong2 A = a.pa[ibeg + il], B = a.pb[ibeg + il];
+                    const float X[3] = {-f2_lo(A.x), -f2_lo(A.y), -f2_lo(B.x)};
+                    float XL[3] = {0.f, 0.f, 0.f};
+                    if (LO) {
+                        const ulonglong2 C = a.plo[2 * (size_t)(ibeg + il)], D = a.plo[2 * (size_t)(ibeg + il) + 1];
+                        XL[0] = -f2_lo(C.x);
+                        XL[1] = -f2_lo(C.y);
+                        XL[2] = -f2_lo(D.x);
+                    }
+#pragma unroll
+                    for (int d = 0; d < 3; d++) {
+                        if (R) {
+                            float s, e;
+                            two_sum(X[d], it.s[d], s, e);
+                            vs[d][h] = s;
+                            ve[d][h] = (e + it.slo[d]) + XL[d];
+                        } else {
+                            vs[d][h] = X[d] + it.s[d];
+                        }
+                    }
+                    vw[h] = f2_lo(B.y);
+                }
+            }
+            sx[p] = f2_pack(vs[0][0], vs[0][1]);
+            sy[p] = f2_pack(vs[1][0], vs[1][1]);
+            sz[p] = f2_pack(vs[2][0], vs[2][1]);
+            ex[p] = f2_pack(ve[0][0], ve[0][1]);
+            ey[p] = f2_pack(ve[1][0], ve[1][1]);
+            ez[p] = f2_pack(ve[2][0], ve[2][1]);
+            wi[p] = f2_pack(vw[0], vw[1]);
+        }
+        const ulonglong2 *__restrict__ pa = a.pa + jbeg;
+        const ulonglong2 *__restrict__ pb = a.pb + jbeg;
+#pragma unroll 2
+        for (uint32_t j = 0; j < jcnt; j++) {
+            const ulonglong2 A = __ldg(pa + j), B = __ldg(pb + j);
+            u64 lx = 0, ly = 0, lz = 0;
+            if (LO) {
+                const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(jbeg + j));
+                const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(jbeg + j) + 1);
+                lx = C.x;
+                ly = C.y;
+                lz = D.x;
+            }
+#pragma unroll
+            for (int p = 0; p < P; p++) {
+                u64 dx = f2_add(sx[p], A.x), dy = f2_add(sy[p], A.y), dz = f2_add(sz[p], B.x);
+                if (R) {
+                    dx = f2_add(dx, LO ? f2_add(ex[p], lx) : ex[p]);
+                    dy = f2_add(dy, LO ? f2_add(ey[p], ly) : ey[p]);
+                    dz = f2_add(dz, LO ? f2_add(ez[p], lz) : ez[p]);
+                }
+                if (WRAP) {
+                    if (Lx > 0.f) dx = wrap2(dx, Lx, iLx);
+                    if (Ly > 0.f) dy = wrap2(dy, Ly, iLy);
+                    if (Lz > 0.f) dz = wrap2(dz, Lz, iLz);
+                }
+                const u64 wp = W ? f2_mul(wi[p], B.y) : 0ull;
+                const uint32_t il0 = lane + 64u * p, il1 = il0 + 32u;
+                if (KIND == KIND_R || KIND == KIND_THETA) {
+                    u64 d2 = f2_mul(dx, dx);
+                    d2 = f2_fma(dy, dy, d2);
+                    d2 = f2_fma(dz, dz, d2);
+                    bin_direct<DIAG>(f2_lo_bits(d2), 0u, f2_lo(wp), il0, j);
+                    bin_direct<DIAG>(f2_hi_bits(d2), 0u, f2_hi(wp), il1, j);
+                } else {
+                    u64 rp2 = f2_mul(dx, dx);
+                    rp2 = f2_fma(dy, dy, rp2);
+                    const u64 adz = dz & 0x7FFFFFFF7FFFFFFFull;
+                    bin_direct<DIAG>(f2_lo_bits(rp2), f2_lo_bits(adz), f2_lo(wp), il0, j);
+                    bin_direct<DIAG>(f2_hi_bits(rp2), f2_hi_bits(adz), f2_hi(wp), il1, j);
+                }
+            }
+        }
+    }
+
     __device__ void flush(uint32_t jb)
     {
         __syncwarp();
@@ -401,7 +526,7 @@ struct Warp {
     }
 };
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO>
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool DIRECT>
 __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -412,8 +537,8 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
     unsigned char *wbase = (unsigned char *)(s_fine + nf);
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
-    const uint32_t wb = warp_bytes(KIND, W, R, a.nslot);
-    const uint32_t hoff = warp_buf_bytes(KIND) + warp_ring_bytes(KIND) + warp_stage_bytes(W);
+    const uint32_t wb = warp_bytes(KIND, W, R, a.nslot, DIRECT);
+    const uint32_t hoff = DIRECT ? 0u : warp_buf_bytes(KIND) + warp_ring_bytes(KIND) + warp_stage_bytes(W);
     unsigned char *my = wbase + (size_t)(threadIdx.x >> 5) * wb;
     {
         // zero this warp's histogram (the buffers need no initial value)
@@ -476,7 +601,15 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
             cur = job;
         }
         const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
-        if (it.meta & CFI_ITEM_P2) {
+        if (DIRECT) {
+            if (it.meta & CFI_ITEM_P2) {
+                if (diag) w.template run_direct<2, true>(it);
+                else w.template run_direct<2, false>(it);
+            } else {
+                if (diag) w.template run_direct<1, true>(it);
+                else w.template run_direct<1, false>(it);
+            }
+        } else if (it.meta & CFI_ITEM_P2) {
             if (diag) w.template run<2, true>(it);
             else w.template run<2, false>(it);
         } else {
@@ -487,11 +620,11 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
     if (cur >= 0) w.flush((uint32_t)cur);
 }
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO>
-cudaError_t launch_one(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
-                       int *warps_out)
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool DIRECT>
+cudaError_t launch_variant(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
+                           int *warps_out)
 {
-    auto k = pair_kernel<KIND, W, R, WRAP, LO>;
+    auto k = pair_kernel<KIND, W, R, WRAP, LO, DIRECT>;
     int dev;
     cudaGetDevice(&dev);
     int maxsm = 0;
@@ -516,6 +649,15 @@ cudaError_t launch_one(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cud
     if (grid_out) *grid_out = grid;
     if (warps_out) *warps_out = warps;
     return cudaGetLastError();
+}
+
+// variant 1 = direct, 2 = compacting (0 picks one per kind: see cfp_default_variant)
+template <int KIND, bool W, bool R, bool WRAP, bool LO>
+cudaError_t launch_one(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
+                       int *warps_out)
+{
+    if (c.variant == 2) return launch_variant<KIND, W, R, WRAP, LO, false>(c, a, num_sms, st, grid_out, warps_out);
+    return launch_variant<KIND, W, R, WRAP, LO, true>(c, a, num_sms, st, grid_out, warps_out);
 }
 
 }  // namespace cfpair

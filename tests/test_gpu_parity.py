@@ -220,7 +220,7 @@ def test_options_do_not_change_results(ctx):
     kw = dict(autocorr=True, periodic=True, box=40.0, weighted=True, ravg=True)
     exp = oracle.count("r", edges, d, **kw)
     for opt, val in ((cf.CF_OPT_TILE, 64), (cf.CF_OPT_JCHUNK, 37), (cf.CF_OPT_WARPS, 2), (cf.CF_OPT_CTAS_PER_SM, 1),
-                     (cf.CF_OPT_QUEUE, 1)):
+                     (cf.CF_OPT_QUEUE, 1), (cf.CF_OPT_VARIANT, 2), (cf.CF_OPT_VARIANT, 1)):
         cf.cf_set_option(ctx, opt, val)
         try:
             got = gpu_count(ctx, "r", edges, d, **kw)
@@ -276,3 +276,14 @@ def test_errors_leave_context_usable(ctx):
     good = gen.uniform_box(2000, 10.0, 4)
     got, exp = both(ctx, "r", edges, good, autocorr=True, periodic=True, box=10.0)
     assert_match(got, exp)
+
+
+@pytest.mark.parametrize("kind,autocorr,periodic,weighted,ravg", CASES[::3])
+def test_compacting_variant_parity(ctx, kind, autocorr, periodic, weighted, ravg):
+    """The two-phase compacting pair kernel (variant 2) gives the same results."""
+    import paper_1911_03545_gb300 as cf
+    cf.cf_set_option(ctx, cf.CF_OPT_VARIANT, 2)
+    try:
+        test_random_parity(ctx, kind, autocorr, periodic, weighted, ravg)
+    finally:
+        cf.cf_set_option(ctx, cf.CF_OPT_VARIANT, 0)
