@@ -282,6 +282,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.self_pairs = p->edges[0] == 0.0;
 
     // ---- device buffers (allocated here so that the device phases never allocate) ----
+    CF_TRY(C->ensure(B_ORIGIN, sizeof(double) * H.origin.size()));
+    D.origin = (const double *)C->buf[B_ORIGIN].p;
     CF_TRY(C->ensure(B_PLAN, sizeof(CfDevPlan)));
     CF_TRY(C->ensure(B_LUT, 4 * H.lut.size()));
     CF_TRY(C->ensure(B_FINE, sizeof(CfFine) * std::max<size_t>(1, H.fine.size())));
@@ -307,6 +309,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_QUEUE, 16 * (size_t)R.qcap));
     CF_TRY(C->ensure_host(readback_bytes(R)));
 
+    CF_CU(cudaMemcpyAsync(C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size(), cudaMemcpyHostToDevice,
+                          st), "origins");
     CF_CU(cudaMemcpyAsync(C->buf[B_PLAN].p, &D, sizeof(CfDevPlan), cudaMemcpyHostToDevice, st), "plan");
     CF_CU(cudaMemcpyAsync(C->buf[B_LUT].p, H.lut.data(), 4 * H.lut.size(), cudaMemcpyHostToDevice, st), "lut");
     if (!H.fine.empty())

@@ -34,13 +34,41 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         }
         bad += __shfl_xor_sync(CF_FULL, bad, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        unsigned long long *o = out + blockIdx.y * 8;
+    // block reduction through shared memory, then one atomic per block and value
+    __shared__ unsigned long long red[7][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) {
         for (int a = 0; a < 3; a++) {
-            atomicMin(o + a, mn[a]);
-            atomicMax(o + 3 + a, mx[a]);
+            red[a][w] = mn[a];
+            red[3 + a][w] = mx[a];
         }
-        if (bad) atomicAdd(o + 6, bad);
+        red[6][w] = bad;
+    }
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long v[7];
+        for (int a = 0; a < 3; a++) {
+            v[a] = lane < nw ? red[a][lane] : ~0ull;
+            v[3 + a] = lane < nw ? red[3 + a][lane] : 0ull;
+        }
+        v[6] = lane < nw ? red[6][lane] : 0ull;
+        for (int o = 16; o; o >>= 1) {
+            for (int a = 0; a < 3; a++) {
+                unsigned long long t = __shfl_xor_sync(CF_FULL, v[a], o);
+                v[a] = t < v[a] ? t : v[a];
+                t = __shfl_xor_sync(CF_FULL, v[3 + a], o);
+                v[3 + a] = t > v[3 + a] ? t : v[3 + a];
+            }
+            v[6] += __shfl_xor_sync(CF_FULL, v[6], o);
+        }
+        if (lane == 0) {
+            unsigned long long *o = out + blockIdx.y * 8;
+            for (int a = 0; a < 3; a++) {
+                atomicMin(o + a, v[a]);
+                atomicMax(o + 3 + a, v[3 + a]);
+            }
+            if (v[6]) atomicAdd(o + 6, v[6]);
+        }
     }
 }
 
@@ -172,9 +200,9 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
         int iy = (c / g.n[2]) % g.n[1];
         int ix = c / (g.n[2] * g.n[1]);
         int64_t dst = cell_start[S.cbeg + c] + slot[p];
-        double X = cf_load(S.x, S.dtype, i) - cf_origin(g, 0, ix);
-        double Y = cf_load(S.y, S.dtype, i) - cf_origin(g, 1, iy);
-        double Z = cf_load(S.z, S.dtype, i) - cf_origin(g, 2, iz);
+        double X = cf_load(S.x, S.dtype, i) - cf_origin(plan, 0, ix);
+        double Y = cf_load(S.y, S.dtype, i) - cf_origin(plan, 1, iy);
+        double Z = cf_load(S.z, S.dtype, i) - cf_origin(plan, 2, iz);
         float xf = (float)X, yf = (float)Y, zf = (float)Z;
         float w = S.w ? (float)cf_load(S.w, S.dtype, i) : 1.0f;
         pa[dst] = make_float4(-xf, -xf, -yf, -yf);
@@ -239,7 +267,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                 ok = false;
             }
             tj[a] = v;
-            if (ok) shift[a] = cf_origin(g, a, ci[a]) - cf_origin(g, a, v) - delta;
+            if (ok && mode == 1) shift[a] = cf_origin(plan, a, ci[a]) - cf_origin(plan, a, v) - delta;
         }
         uint32_t cnt = 0;
         if (ok) {

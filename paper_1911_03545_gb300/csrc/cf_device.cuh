@@ -47,21 +47,8 @@ __device__ __forceinline__ float f_sqrt_approx(float x)
     return r;
 }
 
-// ---- cell origin (FP64).  For float32 coordinates x in the cell, x - origin is exact in
-// float32: the origin is a multiple of the float32 spacing at the cell's largest magnitude and
-// lies between 0 and every x of the cell (0 itself for a cell that straddles 0). ----
-__device__ __forceinline__ double cf_origin(const CfGrid &g, int a, int i)
-{
-    double lo = g.lo[a] + (double)i * g.width[a];
-    double hi = lo + g.width[a];
-    if (lo <= 0.0 && hi >= 0.0) return 0.0;
-    double m = fmax(fabs(lo), fabs(hi)) * (1.0 + 1.0 / 1048576.0);
-    int e;
-    frexp(m, &e);
-    double q = ldexp(1.0, e - 24);
-    if (lo > 0.0) return floor(lo / q) * q;
-    return ceil(hi / q) * q;
-}
+// ---- cell origin: precomputed on the host (cfp_origin in cf_plan.cpp) ----
+__device__ __forceinline__ double cf_origin(const CfDevPlan *plan, int a, int i) { return plan->origin[plan->ooff[a] + i]; }
 
 __device__ __forceinline__ int cf_cell_axis(const CfGrid &g, int a, double x)
 {

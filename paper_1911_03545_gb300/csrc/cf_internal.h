@@ -109,6 +109,8 @@ struct CfDevPlan {
     int nlut_words;        // coarse words (both LUTs)
     int nfine;             // fine entries (both LUTs)
     double pimax;
+    const double *origin;  // device table of cell origins: axis a, index i at origin[ooff[a] + i]
+    int ooff[3];
     float cut_r;           // candidate cut on the FP32 squared separation (above the last band)
     float cut_p;           // candidate cut on the FP32 |dz| (rp-pi / wp)
     double e2[CF_MAX_BINS + 1];     // squared edges (FP64, host-computed)

@@ -36,6 +36,19 @@ bool all_finite(const double *v, int n)
 
 }  // namespace
 
+double cfp_origin(double lo_axis, double width, int i)
+{
+    double lo = lo_axis + (double)i * width;
+    double hi = lo + width;
+    if (lo <= 0.0 && hi >= 0.0) return 0.0;
+    double m = std::max(std::fabs(lo), std::fabs(hi)) * (1.0 + 1.0 / 1048576.0);
+    int e;
+    std::frexp(m, &e);
+    double q = std::ldexp(1.0, e - 24);
+    if (lo > 0.0) return std::floor(lo / q) * q;
+    return std::ceil(hi / q) * q;
+}
+
 uint32_t cfp_float_ceil_bits(double v)
 {
     if (!(v > 0)) return 0u;
@@ -274,10 +287,13 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
         G.n[a] = std::max(G.k[a], (int)(G.n[a] * 0.8));
     }
     G.ncell = G.n[0] * G.n[1] * G.n[2];
+    H.origin.clear();
     for (int a = 0; a < 3; a++) {
         G.width[a] = extent[a] / G.n[a];
         G.inv[a] = G.n[a] / extent[a];
         G.wrap[a] = (p->periodic && G.n[a] < 2 * G.k[a] + 1) ? 1 : 0;
+        D.ooff[a] = (int)H.origin.size();
+        for (int i = 0; i < G.n[a]; i++) H.origin.push_back(cfp_origin(G.lo[a], G.width[a], i));
     }
 
     // ---- stencil, Sec. 4.2-4.3 ----

@@ -10,6 +10,7 @@ struct CfHostPlan {
     std::vector<uint32_t> lut;         // coarse LUT words: r-like LUT then pi LUT
     std::vector<CfFine> fine;          // fine LUT entries (both LUTs)
     std::vector<CfStencil> stencil;    // neighbour offsets after pruning
+    std::vector<double> origin;        // cell origins per axis (see cfp_origin), n0 + n1 + n2 values
     double W[3];                       // largest separation a counted pair can have, per axis
     double band_r[CF_MAX_BINS + 1];    // FP32 error band of each squared edge
     double band_p[CF_MAX_PIBINS + 1];  // FP32 error band of each pi edge
@@ -27,6 +28,12 @@ void cfp_edges(const cf_params *p, double *e2, double *pe);
 // (0 = automatic); tile = max i tile (64 or 128); jchunk = max j range per work item.
 int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int f64,
                   const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err);
+
+// Origin of cell i on an axis starting at lo with cell width w.  For float32 coordinates x in
+// the cell, x - origin is exact in float32: the origin is a multiple of the float32 spacing at
+// the cell's largest magnitude and lies between 0 and every x of the cell (0 itself for a cell
+// that straddles 0).
+double cfp_origin(double lo, double width, int i);
 
 // Bits of the smallest float >= v (v >= 0), and of the smallest float > v.
 uint32_t cfp_float_ceil_bits(double v);
