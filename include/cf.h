@@ -173,6 +173,8 @@ cf_status cf_get_stats(const void *ctx, cf_stats *out);
  * an FP32 value within a band of an edge is re-evaluated in FP64.  With nv > 0, `values` are
  * classified through the same lookup table the pair kernel uses (which = 0: squared r / rp /
  * chord; which = 1: |dz|): classes[i] = bin index, 0xFE outside every bin, 0xFF within a band.
+ * which = 2 / 3 classify the same way as the direct pair kernel does (an FP32 cut at the table's
+ * tail, then the lookup without its upper clamp); 0xFD there would mean an index past the table. 
  * Grid and refinement: Sec. 4.1-4.2; bins in squared space: Sec. 4.7. */
 typedef struct {
     int grid[3];

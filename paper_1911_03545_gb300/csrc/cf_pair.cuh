@@ -58,9 +58,11 @@ __host__ __device__ __forceinline__ bool has_z(int kind) { return kind == KIND_R
 __host__ __device__ __forceinline__ uint32_t warp_buf_bytes(int kind) { return SLOTS_PER_BLOCK * 32u * 4u * (has_z(kind) ? 2u : 1u); }
 __host__ __device__ __forceinline__ uint32_t warp_ring_bytes(int kind) { return CFI_QN * (has_z(kind) ? 10u : 6u); }
 __host__ __device__ __forceinline__ uint32_t warp_stage_bytes(bool W) { return W ? 128u * 4u : 0u; }
+constexpr uint32_t JSTAGE = 32;    // j points per staged chunk of the direct variant
+__host__ __device__ __forceinline__ uint32_t warp_jbuf_bytes() { return 2u * JSTAGE * 32u; }   // 2 chunks x (pa, pb)
 __host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, int nslot, bool direct)
 {
-    if (direct) return warp_hist_bytes(kind, W, R, nslot);
+    if (direct) return warp_jbuf_bytes() + warp_hist_bytes(kind, W, R, nslot);
     return warp_buf_bytes(kind) + warp_ring_bytes(kind) + warp_stage_bytes(W) + warp_hist_bytes(kind, W, R, nslot);
 }
 
@@ -85,6 +87,20 @@ __device__ __forceinline__ uint32_t lut_class(const Lut &L, const CfFine *__rest
     t = t > 0 ? t : 0;
     uint32_t idx = min((uint32_t)t >> L.shift, L.last);
     uint32_t c = L.words[idx];
+    if (c >= CFI_FINE_FLAG) {
+        const CfFine f = fine[c - CFI_FINE_FLAG];
+        uint32_t seg = (vb >= f.t1 ? 1u : 0u) + (vb >= f.t2 ? 1u : 0u);
+        c = (f.code >> (8u * seg)) & 0xFFu;
+    }
+    return c;
+}
+
+// lookup for a value known to lie below the table's tail (the start of its final "outside
+// every bin" segment): the index then never passes the last cell, so no upper clamp is needed
+__device__ __forceinline__ uint32_t lut_class_in(const Lut &L, const CfFine *__restrict__ fine, uint32_t vb)
+{
+    const uint32_t t = max(vb, L.base) - L.base;
+    uint32_t c = L.words[t >> L.shift];
     if (c >= CFI_FINE_FLAG) {
         const CfFine f = fine[c - CFI_FINE_FLAG];
         uint32_t seg = (vb >= f.t1 ? 1u : 0u) + (vb >= f.t2 ? 1u : 0u);
@@ -119,6 +135,7 @@ struct Warp {
     uint32_t *ring_d, *ring_z;
     uint16_t *ring_c;       // candidate code: (i slot << 9) | j
     float *stage_w;         // weights of the i tile
+    ulonglong2 *jbuf;       // direct variant: 2 chunks of JSTAGE j points, pa then pb per chunk
     int lane, nb, npi, nslot;
     uint32_t icnt, ibeg, jbeg, job, head, tail;
     float cut_r, cut_p;
@@ -366,28 +383,23 @@ struct Warp {
     }
 
     // ---- direct variant: every pair is binned where it is formed (no compaction) ----
-    template <bool DIAG>
-    __device__ __forceinline__ void bin_direct(uint32_t vb, uint32_t zb, float wp, uint32_t il, uint32_t j)
+    // Bin one pair that passed the FP32 cut (squared separation below cut_r and, for rp-pi and
+    // wp, |dz| below cut_p): both tables are then read without the upper clamp.
+    __device__ __forceinline__ void bin_in(uint32_t vb, uint32_t zb, float wp, uint32_t il, uint32_t j)
     {
-        const bool live = (!DIAG || j > il) && (!WRAP || il < icnt);
         if (KIND == KIND_R || KIND == KIND_THETA) {
-            const uint32_t c = lut_class(lr, fine, vb);
-            if (c < (uint32_t)nb) {
-                if (live) acc_lp(c, __uint_as_float(vb), wp);
-            } else if (c == CFI_CLS_AMB) {
-                if (live) push(ibeg + il, jbeg + j);
-            }
+            const uint32_t c = lut_class_in(lr, fine, vb);
+            if (c < (uint32_t)nb) acc_lp(c, __uint_as_float(vb), wp);
+            else if (c == CFI_CLS_AMB) push(ibeg + il, jbeg + j);
         } else {
-            const uint32_t cz = lut_class(lp, fine, zb);
-            if (cz == CFI_CLS_OUT) return;
-            const uint32_t cr = lut_class(lr, fine, vb);
-            if (cr < (uint32_t)nb && cz < CFI_CLS_OUT) {
-                if (live) {
-                    if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, __uint_as_float(vb), wp);
-                    else acc_lp(cr, __uint_as_float(vb), wp);
-                }
+            // the pi table starts at 0 with bin 0, so below cut_p it yields a bin or AMB
+            const uint32_t cr = lut_class_in(lr, fine, vb);
+            const uint32_t cz = lut_class_in(lp, fine, zb);
+            if (max(cr, cz) < CFI_CLS_OUT) {
+                if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, __uint_as_float(vb), wp);
+                else acc_lp(cr, __uint_as_float(vb), wp);
             } else if (cr != CFI_CLS_OUT) {
-                if (live) push(ibeg + il, jbeg + j);
+                push(ibeg + il, jbeg + j);
             }
         }
     }
@@ -444,49 +456,93 @@ struct Warp {
             ez[p] = f2_pack(ve[2][0], ve[2][1]);
             wi[p] = f2_pack(vw[0], vw[1]);
         }
+        // j points stream through a double-buffered shared-memory stage: chunk c+1 is copied
+        // asynchronously while chunk c is evaluated from broadcast shared loads
         const ulonglong2 *__restrict__ pa = a.pa + jbeg;
         const ulonglong2 *__restrict__ pb = a.pb + jbeg;
-#pragma unroll 2
-        for (uint32_t j = 0; j < jcnt; j++) {
-            const ulonglong2 A = __ldg(pa + j), B = __ldg(pb + j);
-            u64 lx = 0, ly = 0, lz = 0;
-            if (LO) {
-                const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(jbeg + j));
-                const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(jbeg + j) + 1);
-                lx = C.x;
-                ly = C.y;
-                lz = D.x;
-            }
-#pragma unroll
-            for (int p = 0; p < P; p++) {
-                u64 dx = f2_add(sx[p], A.x), dy = f2_add(sy[p], A.y), dz = f2_add(sz[p], B.x);
-                if (R) {
-                    dx = f2_add(dx, LO ? f2_add(ex[p], lx) : ex[p]);
-                    dy = f2_add(dy, LO ? f2_add(ey[p], ly) : ey[p]);
-                    dz = f2_add(dz, LO ? f2_add(ez[p], lz) : ez[p]);
-                }
-                if (WRAP) {
-                    if (Lx > 0.f) dx = wrap2(dx, Lx, iLx);
-                    if (Ly > 0.f) dy = wrap2(dy, Ly, iLy);
-                    if (Lz > 0.f) dz = wrap2(dz, Lz, iLz);
-                }
-                const u64 wp = W ? f2_mul(wi[p], B.y) : 0ull;
-                const uint32_t il0 = lane + 64u * p, il1 = il0 + 32u;
-                if (KIND == KIND_R || KIND == KIND_THETA) {
-                    u64 d2 = f2_mul(dx, dx);
-                    d2 = f2_fma(dy, dy, d2);
-                    d2 = f2_fma(dz, dz, d2);
-                    bin_direct<DIAG>(f2_lo_bits(d2), 0u, f2_lo(wp), il0, j);
-                    bin_direct<DIAG>(f2_hi_bits(d2), 0u, f2_hi(wp), il1, j);
-                } else {
-                    u64 rp2 = f2_mul(dx, dx);
-                    rp2 = f2_fma(dy, dy, rp2);
-                    const u64 adz = dz & 0x7FFFFFFF7FFFFFFFull;
-                    bin_direct<DIAG>(f2_lo_bits(rp2), f2_lo_bits(adz), f2_lo(wp), il0, j);
-                    bin_direct<DIAG>(f2_hi_bits(rp2), f2_hi_bits(adz), f2_hi(wp), il1, j);
-                }
-            }
+        const uint32_t nchunk = (jcnt + JSTAGE - 1) / JSTAGE;
+        if (lane < jcnt) {
+            cp_async16(jbuf + lane, pa + lane);
+            cp_async16(jbuf + JSTAGE + lane, pb + lane);
         }
+        cp_async_commit();
+        for (uint32_t c = 0; c < nchunk; c++) {
+            const uint32_t j0 = c * JSTAGE;
+            if (c + 1 < nchunk) {
+                ulonglong2 *nb2 = jbuf + ((c + 1) & 1) * 2 * JSTAGE;
+                const uint32_t jn = j0 + JSTAGE + lane;
+                if (jn < jcnt) {
+                    cp_async16(nb2 + lane, pa + jn);
+                    cp_async16(nb2 + JSTAGE + lane, pb + jn);
+                }
+            }
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncwarp();
+            const ulonglong2 *ca = jbuf + (c & 1) * 2 * JSTAGE;
+            const uint32_t n = min(JSTAGE, jcnt - j0);
+#pragma unroll 2
+            for (uint32_t jj = 0; jj < n; jj++) {
+                const uint32_t j = j0 + jj;
+                const ulonglong2 A = ca[jj], B = ca[JSTAGE + jj];
+                u64 lx = 0, ly = 0, lz = 0;
+                if (LO) {
+                    const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(jbeg + j));
+                    const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(jbeg + j) + 1);
+                    lx = C.x;
+                    ly = C.y;
+                    lz = D.x;
+                }
+#pragma unroll
+                for (int p = 0; p < P; p++) {
+                    u64 dx = f2_add(sx[p], A.x), dy = f2_add(sy[p], A.y), dz = f2_add(sz[p], B.x);
+                    if (R) {
+                        dx = f2_add(dx, LO ? f2_add(ex[p], lx) : ex[p]);
+                        dy = f2_add(dy, LO ? f2_add(ey[p], ly) : ey[p]);
+                        dz = f2_add(dz, LO ? f2_add(ez[p], lz) : ez[p]);
+                    }
+                    if (WRAP) {
+                        if (Lx > 0.f) dx = wrap2(dx, Lx, iLx);
+                        if (Ly > 0.f) dy = wrap2(dy, Ly, iLy);
+                        if (Lz > 0.f) dz = wrap2(dz, Lz, iLz);
+                    }
+                    const uint32_t il0 = lane + 64u * p, il1 = il0 + 32u;
+                    u64 v2, az = 0ull;
+                    bool in0, in1;
+                    if (KIND == KIND_R || KIND == KIND_THETA) {
+                        v2 = f2_mul(dx, dx);
+                        v2 = f2_fma(dy, dy, v2);
+                        v2 = f2_fma(dz, dz, v2);
+                        in0 = f2_lo(v2) < cut_r;
+                        in1 = f2_hi(v2) < cut_r;
+                    } else {
+                        v2 = f2_mul(dx, dx);
+                        v2 = f2_fma(dy, dy, v2);
+                        az = dz & 0x7FFFFFFF7FFFFFFFull;
+                        in0 = f2_lo(v2) < cut_r && f2_lo(az) < cut_p;
+                        in1 = f2_hi(v2) < cut_r && f2_hi(az) < cut_p;
+                    }
+                    // within a cell paired with itself only j > i counts; in wrap mode the
+                    // minimum image folds the far-away empty slots back, so mask them here
+                    if (DIAG) {
+                        in0 = in0 && j > il0;
+                        in1 = in1 && j > il1;
+                    }
+                    if (WRAP) {
+                        in0 = in0 && il0 < icnt;
+                        in1 = in1 && il1 < icnt;
+                    }
+                    if (in0 || in1) {
+                        const u64 wp = W ? f2_mul(wi[p], B.y) : 0ull;
+                        if (in0) bin_in(f2_lo_bits(v2), f2_lo_bits(az), f2_lo(wp), il0, j);
+                        if (in1) bin_in(f2_hi_bits(v2), f2_hi_bits(az), f2_hi(wp), il1, j);
+                    }
+                }
+            }
+            __syncwarp();       // the chunk buffer is refilled two chunks later
+        }
+        cp_async_wait<0>();
+        __syncwarp();
     }
 
     __device__ void flush(uint32_t jb)
@@ -526,8 +582,12 @@ struct Warp {
     }
 };
 
+// resident CTAs (of 256 threads) the register budget is sized for: the compacting form is held
+// to one CTA per SM by its shared memory; the direct form keeps 2 (weights / ravg) or 3 CTAs
+__host__ __device__ constexpr int pair_min_blocks(bool W, bool R, bool DIRECT) { return !DIRECT ? 1 : ((W || R) ? 2 : 3); }
+
 template <int KIND, bool W, bool R, bool WRAP, bool LO, bool DIRECT>
-__global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
+__global__ void __launch_bounds__(256, pair_min_blocks(W, R, DIRECT)) pair_kernel(const CfPairArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const CfDevPlan *__restrict__ P = a.plan;
@@ -538,7 +598,7 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
     const uint32_t wb = warp_bytes(KIND, W, R, a.nslot, DIRECT);
-    const uint32_t hoff = DIRECT ? 0u : warp_buf_bytes(KIND) + warp_ring_bytes(KIND) + warp_stage_bytes(W);
+    const uint32_t hoff = DIRECT ? warp_jbuf_bytes() : warp_buf_bytes(KIND) + warp_ring_bytes(KIND) + warp_stage_bytes(W);
     unsigned char *my = wbase + (size_t)(threadIdx.x >> 5) * wb;
     {
         // zero this warp's histogram (the buffers need no initial value)
@@ -573,6 +633,7 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
         w.ring_c = (uint16_t *)(q + CFI_QN * (z ? 8u : 4u));
         q += warp_ring_bytes(KIND);
         w.stage_w = (float *)q;
+        w.jbuf = (ulonglong2 *)my;
     }
     w.h_cnt = (uint32_t *)(my + hoff);
     if (KIND == KIND_RPPI) {
@@ -589,12 +650,19 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
 
     const uint32_t nitems = min(*a.nitems_dev, a.items_cap);
     int cur = -1;
+    // the next item's index and descriptor are fetched before the current item is processed
+    uint32_t t = 0;
+    if (w.lane == 0) t = atomicAdd(a.cursor, 1u);
+    t = __shfl_sync(CF_FULL, t, 0);
+    CfItem it;
+    if (t < nitems) it = a.items[t];
     for (;;) {
-        uint32_t t = 0;
-        if (w.lane == 0) t = atomicAdd(a.cursor, 1u);
-        t = __shfl_sync(CF_FULL, t, 0);
         if (t >= nitems) break;
-        const CfItem it = a.items[t];
+        uint32_t tn = 0;
+        if (w.lane == 0) tn = atomicAdd(a.cursor, 1u);
+        tn = __shfl_sync(CF_FULL, tn, 0);
+        CfItem nx;
+        if (tn < nitems) nx = a.items[tn];
         const int job = (int)(it.meta & CFI_ITEM_JOBMASK);
         if (job != cur) {
             if (cur >= 0) w.flush((uint32_t)cur);
@@ -616,6 +684,8 @@ __global__ void __launch_bounds__(256) pair_kernel(const CfPairArgs a)
             if (diag) w.template run<1, true>(it);
             else w.template run<1, false>(it);
         }
+        t = tn;
+        it = nx;
     }
     if (cur >= 0) w.flush((uint32_t)cur);
 }

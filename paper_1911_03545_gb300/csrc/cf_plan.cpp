@@ -394,7 +394,21 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
 // Host emulation of the kernel's table lookup (same arithmetic as lut_class in cf_pair.cuh).
 uint32_t cfp_lut_class(const CfHostPlan &H, int which, uint32_t vb)
 {
-    const CfLut &L = which ? H.d.lp : H.d.lr;
+    const CfLut &L = (which & 1) ? H.d.lp : H.d.lr;
+    if (which & 2) {
+        // the direct pair kernel: an FP32 cut at the tail, then the lookup without upper clamp
+        // (lut_class_in in cf_pair.cuh); 0xFD flags an index past the table
+        if (vb >= L.tail) return CFI_CLS_OUT;
+        const uint32_t idx = (std::max(vb, L.base) - L.base) >> L.shift;
+        if (idx > L.last) return 0xFDu;
+        uint32_t c = H.lut[L.coff + idx];
+        if (c >= CFI_FINE_FLAG) {
+            const CfFine &f = H.fine[c - CFI_FINE_FLAG];
+            uint32_t seg = (vb >= f.t1 ? 1u : 0u) + (vb >= f.t2 ? 1u : 0u);
+            c = (f.code >> (8u * seg)) & 0xFFu;
+        }
+        return c;
+    }
     int t = (int)(vb - L.base);
     t = t > 0 ? t : 0;
     uint32_t idx = std::min((uint32_t)t >> L.shift, L.last);
@@ -415,7 +429,7 @@ extern "C" cf_status cf_plan_probe(const cf_params *params, const double bbox[6]
     std::string err;
     if (cfp_check_params(params, err) != CF_OK) return CF_ERR_ARG;
     const bool rppi_like = params->kind == CF_DD_RPPI || params->kind == CF_WP;
-    if (which == 1 && !rppi_like && nv > 0) return CF_ERR_ARG;
+    if (which < 0 || which > 3 || ((which & 1) && !rppi_like && nv > 0)) return CF_ERR_ARG;
     CfHostPlan *H = new CfHostPlan();
     int refine[3];
     for (int a = 0; a < 3; a++) refine[a] = params->refine[a] > 0 ? params->refine[a] : 1;

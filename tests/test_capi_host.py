@@ -137,8 +137,9 @@ def _check_classes(vals, cls, E, B, nbins_out):
     assert cls.max() <= 0xFF and np.all((cls < nbins_out) | (cls >= 0xFE))
 
 
+@pytest.mark.parametrize("cut", [0, 2], ids=["clamped", "cut"])
 @pytest.mark.parametrize("name", ["clustered_r", "uniform_f64", "theta", "zero_first", "dense_edges"])
-def test_lut_matches_band_definition(cf, name):
+def test_lut_matches_band_definition(cf, name, cut):
     import oracle
     box, f64, bbox = 420.0, False, [0, 0, 0, 420, 420, 420]
     if name == "clustered_r":
@@ -154,18 +155,24 @@ def test_lut_matches_band_definition(cf, name):
     p = cf.params(kind=kind, edges=edges, autocorr=True, periodic=kind != "theta", box=box)
     E = oracle.squared_edges(kind, edges)
     vals = _values_near(E)
-    out = cf.cf_plan_probe(p, bbox, 10 ** 6, f64, which=0, values=vals)
+    out = cf.cf_plan_probe(p, bbox, 10 ** 6, f64, which=cut, values=vals)
     _check_classes(vals, out["classes"], E, out["bands_r"], len(edges) - 1)
 
 
-def test_pi_lut_matches_band_definition(cf):
-    p = cf.params(kind="rppi", edges=gen.log_edges(0.1, 25.0, 14), autocorr=True, periodic=True, box=1000.0,
+@pytest.mark.parametrize("cut", [0, 2], ids=["clamped", "cut"])
+@pytest.mark.parametrize("kind", ["rppi", "wp"])
+def test_pi_lut_matches_band_definition(cf, kind, cut):
+    p = cf.params(kind=kind, edges=gen.log_edges(0.1, 25.0, 14), autocorr=True, periodic=True, box=1000.0,
                   pimax=40.0, npibins=40)
     pe = np.arange(41, dtype=np.float64)
     vals = _values_near(pe[1:])
     vals = np.concatenate([vals, np.float32([0.0, 1e-30, 0.5])])
-    out = cf.cf_plan_probe(p, [0, 0, 0, 1000, 1000, 1000], 2 * 10 ** 6, which=1, values=vals)
-    _check_classes(vals, out["classes"], pe, out["bands_p"], 40)
+    out = cf.cf_plan_probe(p, [0, 0, 0, 1000, 1000, 1000], 2 * 10 ** 6, which=1 + cut, values=vals)
+    if kind == "rppi":
+        _check_classes(vals, out["classes"], pe, out["bands_p"], 40)
+    else:
+        # wp integrates over 0 <= |dz| < pimax: one pi class, banded at pimax only
+        _check_classes(vals, out["classes"], pe[[0, 40]], out["bands_p"][[0, 40]], 1)
 
 
 def _fma32(a, b, c):
