@@ -63,6 +63,17 @@ def _peaks():
         return {}
 
 
+def _parse_config(text: str) -> dict:
+    from paper_1911_03545_gb300 import tune
+    cfg = {}
+    for part in filter(None, text.split(",")):
+        k, v = part.split("=")
+        if k not in tune.OPT:
+            raise SystemExit(f"unknown knob {k!r}; knobs: {sorted(tune.OPT)}")
+        cfg[k] = int(v)
+    return cfg
+
+
 def _kernel_sha() -> str:
     h = hashlib.sha256()
     for name in ("cf_pair.cuh", "cf_device.cuh", "cf_internal.h"):
@@ -277,10 +288,15 @@ def run_gpu(args, wl, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     from paper_1911_03545_gb300 import tune
     npts = wl.d1.n + (0 if wl.autocorr else wl.d2.n)
-    tuned = tune.tune(ctx, p, d1, d2, device_name=torch.cuda.get_device_name(dev), npoints=npts,
-                      use_cache=not args.no_tune_cache) if not args.no_tune else dict(tune.DEFAULT)
-    if args.no_tune:
+    if args.config:
+        tuned = dict(tune.DEFAULT, **_parse_config(args.config))
         tune.apply(ctx, tuned)
+    elif args.no_tune:
+        tuned = dict(tune.DEFAULT)
+        tune.apply(ctx, tuned)
+    else:
+        tuned = tune.tune(ctx, p, d1, d2, device_name=torch.cuda.get_device_name(dev), npoints=npts,
+                          use_cache=not args.no_tune_cache)
 
     for _ in range(args.warmup):
         cf.cf_count(ctx, p, d1, d2)
@@ -572,6 +588,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-tune-cache", action="store_true")
+    ap.add_argument("--config", default="", help="pin the launch configuration instead of tuning, "
+                    "e.g. variant=2,warps=8 (knobs of paper_1911_03545_gb300.tune)")
     ap.add_argument("--ncat", type=int, default=256)
     ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--serve-requests", type=int, default=1024)

@@ -143,7 +143,8 @@ typedef enum {
     CF_OPT_CTAS_PER_SM = 6,
     CF_OPT_AUDIT = 7,
     CF_OPT_ITER_LIMIT = 8,
-    CF_OPT_WARPS = 9,        /* warps per CTA of the pair kernel (1..8) */
+    CF_OPT_WARPS = 9,        /* warps per CTA of the pair kernel: up to 16 for the direct form with
+                                weights or ravg, up to 8 otherwise (0 = as many as fit) */
     CF_OPT_REFINE = 10,      /* refinement factor used when params.refine is 0 */
     CF_OPT_COUNT_ = 11
 } cf_option;

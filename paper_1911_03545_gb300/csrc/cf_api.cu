@@ -285,7 +285,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_ORIGIN, sizeof(double) * H.origin.size()));
     D.origin = (const double *)C->buf[B_ORIGIN].p;
     CF_TRY(C->ensure(B_PLAN, sizeof(CfDevPlan)));
-    CF_TRY(C->ensure(B_LUT, 4 * H.lut.size()));
+    CF_TRY(C->ensure(B_LUT, sizeof(uint16_t) * H.lut.size()));
     CF_TRY(C->ensure(B_FINE, sizeof(CfFine) * std::max<size_t>(1, H.fine.size())));
     CF_TRY(C->ensure(B_STENCIL, sizeof(CfStencil) * H.stencil.size()));
     CF_TRY(C->ensure(B_JOBS, sizeof(CfJobDesc) * njobs));
@@ -312,7 +312,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_CU(cudaMemcpyAsync(C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size(), cudaMemcpyHostToDevice,
                           st), "origins");
     CF_CU(cudaMemcpyAsync(C->buf[B_PLAN].p, &D, sizeof(CfDevPlan), cudaMemcpyHostToDevice, st), "plan");
-    CF_CU(cudaMemcpyAsync(C->buf[B_LUT].p, H.lut.data(), 4 * H.lut.size(), cudaMemcpyHostToDevice, st), "lut");
+    CF_CU(cudaMemcpyAsync(C->buf[B_LUT].p, H.lut.data(), sizeof(uint16_t) * H.lut.size(), cudaMemcpyHostToDevice, st),
+          "lut");
     if (!H.fine.empty())
         CF_CU(cudaMemcpyAsync(C->buf[B_FINE].p, H.fine.data(), sizeof(CfFine) * H.fine.size(), cudaMemcpyHostToDevice, st),
               "fine");
@@ -394,7 +395,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     CfPairArgs &A = R.args;
     std::memset(&A, 0, sizeof(A));
     A.plan = dplan;
-    A.lut = (const uint32_t *)C->buf[B_LUT].p;
+    A.lut = (const uint16_t *)C->buf[B_LUT].p;
     A.fine = (const CfFine *)C->buf[B_FINE].p;
     A.items = (const CfItem *)C->buf[B_ITEMS].p;
     A.nitems_dev = ioff + R.nthr;

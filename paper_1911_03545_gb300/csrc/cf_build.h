@@ -21,7 +21,7 @@ cudaError_t cfb_wsq(const CfSetDesc *sets, int nsets, int64_t nmax, double *out,
 // ---- pair counting ----
 struct CfPairArgs {
     const CfDevPlan *plan;
-    const uint32_t *lut;         // coarse LUT words (global copy; staged into shared memory)
+    const uint16_t *lut;         // coarse LUT entries (global copy; staged into shared memory)
     const CfFine *fine;          // fine LUT entries
     const CfItem *items;
     const uint32_t *nitems_dev;  // item count written by the work-list scan

@@ -39,11 +39,16 @@ __device__ __forceinline__ float f2_hi(u64 v) { return __uint_as_float((uint32_t
 __device__ __forceinline__ uint32_t f2_lo_bits(u64 v) { return (uint32_t)v; }
 __device__ __forceinline__ uint32_t f2_hi_bits(u64 v) { return (uint32_t)(v >> 32); }
 
-// ---- asynchronous global -> shared copies (16 bytes per lane), grouped and awaited by group ----
+// ---- asynchronous global -> shared copies (16 or 4 bytes per lane), grouped and awaited by group ----
 __device__ __forceinline__ void cp_async16(void *smem_dst, const void *gmem_src)
 {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>

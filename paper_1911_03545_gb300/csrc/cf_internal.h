@@ -18,7 +18,7 @@
 
 #define CFI_MAX_SETS 4096
 #define CFI_MAX_STENCIL 4096
-#define CFI_LUT_MAX 8192          // coarse LUT cells (4 B each)
+#define CFI_LUT_MAX 8192          // coarse LUT cells (2 B each)
 #define CFI_LUT_TARGET 4096       // preferred coarse cells per table
 #define CFI_FINE_MAX 1024         // fine LUT entries (16 B each)
 #define CFI_CLS_OUT 0xFEu         // class: outside every bin

@@ -1,24 +1,28 @@
 // cf_pair.cuh -- the persistent pair kernel (template; instantiated per kind in cf_pair_*.cu).
 //
 // Sec. 4.3-4.7 on a GPU.  Every warp repeatedly takes one work item -- an i tile of one cell
-// (<= 128 points, four per lane as two packed pairs) against a j range (<= 512 points) of a
-// neighbour cell -- from a global atomic cursor.  The i points sit in registers already
-// translated by the cell-pair shift (Sec. 4.4, Code corrfunc_pbc: the shift is added once per
-// i, not per pair).  Each j point is a broadcast load.
+// (<= 128 points) against a j range (<= 512 points) of a neighbour cell -- from a global atomic
+// cursor.  Lane l holds the i points l + 32 q (q < Q; Q = 1, 2 or 4 by the tile's size) in
+// registers, already translated by the cell-pair shift (Sec. 4.4, Code corrfunc_pbc: the shift
+// is added once per i, not per pair), each duplicated into both halves of a packed FP32 pair.
+// The j points stream through a double-buffered shared-memory stage (cp.async) as float arrays
+// and are read two at a time by broadcast 8-byte loads: one packed add forms the separations of
+// an i point from two j points.
 //
-// Phase A (every pair): the separations and squared distance of two pairs at a time are formed
-// by packed FP32x2 add / mul / fma on cell-relative coordinates -- with the shift's low part and
-// the TwoSum residual of the i translation when ravg needs relative accuracy -- and each pair is
-// tested against one cut: the FP32 value above which every value lies outside all bins (Sec.
-// 4.7: squared space, no sqrt).  A lane keeps the values of a block of 16 pairs (4 j points x 4
-// i points) in a lane-private buffer and their outcome in a bit mask.
-// Compaction: the warp scans the mask counts and appends each candidate -- its FP32 value (and
-// |dz| for rp-pi / wp) and a 16-bit code (i slot, j) -- to a per-warp ring in shared memory.
-// Phase B (candidates only, 32 or 64 per pass, all lanes busy): the bin of the stored value is
-// looked up on its FP32 bit pattern through a coarse table (cells holding an edge resolve
-// through a fine entry of <= 2 thresholds).  A value within the proven FP32 error band of an
-// edge is not binned: the pair goes to a global queue and is re-evaluated in FP64 by the
-// recheck kernel, so counts equal the FP64 result.
+// Per pair: the separation and squared distance by packed FP32x2 add / mul / fma on
+// cell-relative coordinates -- with the shift's low part and the TwoSum residual of the i
+// translation when ravg needs relative accuracy -- and one cut: the FP32 value from which on
+// every value lies outside all bins (Sec. 4.7: squared space, no sqrt; rp-pi and wp also cut
+// |dz|).  A pair below the cut is binned on its FP32 bit pattern through a coarse table (cells
+// holding an edge resolve through a fine entry of <= 2 thresholds).  A value within the proven
+// FP32 error band of an edge is not binned: the pair goes to a global queue and is re-evaluated
+// in FP64 by the recheck kernel, so counts equal the FP64 result.
+//
+// Two forms of that binning step, with identical results:
+//   direct     (variant 1): each lane bins its own pairs below the cut where they are formed;
+//   compacting (variant 2): the warp appends its pairs below the cut (value bits, |dz| bits,
+//              i/j code, weight product) to a per-warp ring in shared memory at offsets from a
+//              ballot prefix sum, and bins them 32 at a time with every lane busy.
 //
 // Histograms live in shared memory per warp (Sec. 4.8: private histograms, merged once): for
 // r / theta / wp one private copy per lane (no bank conflicts, no contention; weighted sums
@@ -32,15 +36,17 @@
 namespace cfpair {
 
 constexpr int KIND_R = 0, KIND_RPPI = 1, KIND_WP = 2, KIND_THETA = 3;
-constexpr uint32_t QM = CFI_QN - 1;
 
 __host__ __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
-// per-warp shared memory: block buffer | candidate ring | i weights | histogram
-//   block buffer: the FP32 values phase A formed for one block of 16 pair slots per lane,
-//                 [j][lane][slot] (and the same for |dz| in rp-pi and wp)
-//   ring:         CFI_QN candidates: value bits (u32) [, |dz| bits (u32)], code (u16)
-constexpr uint32_t SLOTS_PER_BLOCK = 16;
+// per-warp shared memory: j stage | candidate ring (compacting form) | histogram
+//   j stage: 2 chunks x up to 7 float arrays (x, y, z, w, lo parts of x, y, z) of JSTAGE points
+//   ring:    RING candidates as arrays: value bits, |dz| bits (rp-pi, wp), weight product (W),
+//            code (u16: i slot | j << 7)
+constexpr uint32_t JSTAGE = 32;
+constexpr uint32_t RING = 512;
+constexpr uint32_t RM = RING - 1;
+static_assert(CFI_JMAX <= 512, "a ring code holds a 7-bit i slot and a 9-bit j");
 __host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int kind, bool W, bool R, int nslot)
 {
     if (kind == KIND_RPPI) {
@@ -55,15 +61,14 @@ __host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int kind, bool W, b
     return b;
 }
 __host__ __device__ __forceinline__ bool has_z(int kind) { return kind == KIND_RPPI || kind == KIND_WP; }
-__host__ __device__ __forceinline__ uint32_t warp_buf_bytes(int kind) { return SLOTS_PER_BLOCK * 32u * 4u * (has_z(kind) ? 2u : 1u); }
-__host__ __device__ __forceinline__ uint32_t warp_ring_bytes(int kind) { return CFI_QN * (has_z(kind) ? 10u : 6u); }
-__host__ __device__ __forceinline__ uint32_t warp_stage_bytes(bool W) { return W ? 128u * 4u : 0u; }
-constexpr uint32_t JSTAGE = 32;    // j points per staged chunk of the direct variant
-__host__ __device__ __forceinline__ uint32_t warp_jbuf_bytes() { return 2u * JSTAGE * 32u; }   // 2 chunks x (pa, pb)
-__host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, int nslot, bool direct)
+__host__ __device__ __forceinline__ uint32_t warp_jbuf_bytes() { return 2u * 8u * JSTAGE * 4u; }
+__host__ __device__ __forceinline__ uint32_t warp_ring_bytes(int kind, bool W)
 {
-    if (direct) return warp_jbuf_bytes() + warp_hist_bytes(kind, W, R, nslot);
-    return warp_buf_bytes(kind) + warp_ring_bytes(kind) + warp_stage_bytes(W) + warp_hist_bytes(kind, W, R, nslot);
+    return RING * (4u + (has_z(kind) ? 4u : 0u) + (W ? 4u : 0u) + 2u);
+}
+__host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, int nslot, bool compact)
+{
+    return warp_jbuf_bytes() + (compact ? warp_ring_bytes(kind, W) : 0u) + warp_hist_bytes(kind, W, R, nslot);
 }
 
 __device__ __forceinline__ void kahan_add(float2 *p, float v)
@@ -78,7 +83,7 @@ __device__ __forceinline__ void kahan_add(float2 *p, float v)
 
 struct Lut {
     uint32_t base, shift, last;
-    const uint32_t *words;   // shared
+    const uint16_t *words;   // shared
 };
 
 __device__ __forceinline__ uint32_t lut_class(const Lut &L, const CfFine *__restrict__ fine, uint32_t vb)
@@ -95,12 +100,15 @@ __device__ __forceinline__ uint32_t lut_class(const Lut &L, const CfFine *__rest
     return c;
 }
 
-// lookup for a value known to lie below the table's tail (the start of its final "outside
-// every bin" segment): the index then never passes the last cell, so no upper clamp is needed
-__device__ __forceinline__ uint32_t lut_class_in(const Lut &L, const CfFine *__restrict__ fine, uint32_t vb)
+// Lookup for a value known to lie below the table's tail (the start of its final "outside
+// every bin" segment): the index then never passes the last cell, so no upper clamp is needed.
+// Split in two so that several lookups can issue their table reads before any fine resolution.
+__device__ __forceinline__ uint32_t lut_raw_in(const Lut &L, uint32_t vb)
 {
-    const uint32_t t = max(vb, L.base) - L.base;
-    uint32_t c = L.words[t >> L.shift];
+    return L.words[(max(vb, L.base) - L.base) >> L.shift];
+}
+__device__ __forceinline__ uint32_t lut_fine(const CfFine *__restrict__ fine, uint32_t c, uint32_t vb)
+{
     if (c >= CFI_FINE_FLAG) {
         const CfFine f = fine[c - CFI_FINE_FLAG];
         uint32_t seg = (vb >= f.t1 ? 1u : 0u) + (vb >= f.t2 ? 1u : 0u);
@@ -123,6 +131,13 @@ __device__ __forceinline__ u64 wrap2(u64 d, float L, float invL)
     return f2_pack(wrap1(f2_lo(d), L, invL), wrap1(f2_hi(d), L, invL));
 }
 
+// queue one pair for the FP64 recheck (rare: kept out of line so the pair loops stay small)
+static __device__ __noinline__ void push_recheck(const CfPairArgs &a, uint32_t ip, uint32_t jp, uint32_t job)
+{
+    uint32_t k = atomicAdd(a.qcount, 1u);
+    if (k < a.qcap) a.queue[k] = make_uint4(a.orig[ip], a.orig[jp], job, 0u);
+}
+
 template <int KIND, bool W, bool R, bool WRAP, bool LO>
 struct Warp {
     const CfPairArgs &a;
@@ -131,23 +146,18 @@ struct Warp {
     uint32_t *h_cnt;        // lane-private [nslot][32] or per-warp [nslot]
     float2 *h_w, *h_r;      // lane-private Kahan pairs
     double *h_wd, *h_rd;    // per-warp FP64 (rp-pi)
-    float *buf, *bufz;      // block buffer: [j][lane][slot]
-    uint32_t *ring_d, *ring_z;
-    uint16_t *ring_c;       // candidate code: (i slot << 9) | j
-    float *stage_w;         // weights of the i tile
-    ulonglong2 *jbuf;       // direct variant: 2 chunks of JSTAGE j points, pa then pb per chunk
+    float *jst;             // j stage
+    uint32_t *rv, *rz;      // ring: value bits, |dz| bits
+    float *rw;              // ring: weight product
+    uint16_t *rc;           // ring: code, i slot | j << 7
     int lane, nb, npi, nslot;
-    uint32_t icnt, ibeg, jbeg, job, head, tail;
+    uint32_t icnt, ibeg, jbeg, job, head, tail, ltmask;
     float cut_r, cut_p;
     float Lx, Ly, Lz, iLx, iLy, iLz;
 
     __device__ Warp(const CfPairArgs &args) : a(args) {}
 
-    __device__ __forceinline__ void push(uint32_t ip, uint32_t jp)
-    {
-        uint32_t k = atomicAdd(a.qcount, 1u);
-        if (k < a.qcap) a.queue[k] = make_uint4(a.orig[ip], a.orig[jp], job, 0u);
-    }
+    __device__ __forceinline__ void push(uint32_t ip, uint32_t jp) { push_recheck(a, ip, jp, job); }
 
     __device__ __forceinline__ void acc_lp(uint32_t c, float d2, float wp)
     {
@@ -171,378 +181,289 @@ struct Warp {
         }
     }
 
-    __device__ __forceinline__ float weight(uint32_t il, uint32_t j) const
+    // Histogram slot of N pairs that passed the FP32 cut (squared separation below cut_r and,
+    // for rp-pi and wp, |dz| below cut_p), or K_AMB (re-evaluate in FP64) or K_OUT (outside
+    // every bin).  The table reads of all N are issued before any fine resolution.
+    static constexpr uint32_t K_AMB = 0xFFFFFFFFu, K_OUT = 0xFFFFFFFEu;
+    template <int N>
+    __device__ __forceinline__ void classify(const uint32_t (&vb)[N], const uint32_t (&zb)[N], uint32_t (&k)[N]) const
     {
-        return stage_w[il] * __ldg(reinterpret_cast<const float *>(a.pb + jbeg + j) + 2);
-    }
-
-    // Phase B for one candidate (valid == false: the lane only takes part in the warp's flow)
-    __device__ __forceinline__ void finish(uint32_t vb, uint32_t zb, uint32_t code, bool valid)
-    {
-        const uint32_t il = code >> 9, j = code & (CFI_JMAX - 1);
-        if (KIND == KIND_R || KIND == KIND_THETA) {
-            const uint32_t c = lut_class(lr, fine, vb);
-            if (valid && c < (uint32_t)nb) acc_lp(c, __uint_as_float(vb), W ? weight(il, j) : 0.f);
-            else if (valid && c == CFI_CLS_AMB) push(ibeg + il, jbeg + j);
-        } else {
-            const uint32_t cz = lut_class(lp, fine, zb);
-            const uint32_t cr = lut_class(lr, fine, vb);
-            if (valid && cz != CFI_CLS_OUT && cr != CFI_CLS_OUT) {
-                if (cr < (uint32_t)nb && cz < CFI_CLS_OUT) {
-                    const float wp = W ? weight(il, j) : 0.f;
-                    if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, __uint_as_float(vb), wp);
-                    else acc_lp(cr, __uint_as_float(vb), wp);
-                } else {
-                    push(ibeg + il, jbeg + j);
-                }
+        uint32_t cr[N], cz[N];
+#pragma unroll
+        for (int n = 0; n < N; n++) {
+            cr[n] = lut_raw_in(lr, vb[n]);
+            cz[n] = has_z(KIND) ? lut_raw_in(lp, zb[n]) : 0u;
+        }
+#pragma unroll
+        for (int n = 0; n < N; n++) {
+            cr[n] = lut_fine(fine, cr[n], vb[n]);
+            if (has_z(KIND)) cz[n] = lut_fine(fine, cz[n], zb[n]);
+            if (KIND == KIND_R || KIND == KIND_THETA) {
+                k[n] = cr[n] < (uint32_t)nb ? cr[n] : (cr[n] == CFI_CLS_AMB ? K_AMB : K_OUT);
+            } else {
+                // the pi table starts at 0 with bin 0, so below cut_p it yields a bin or AMB
+                if (max(cr[n], cz[n]) < CFI_CLS_OUT) k[n] = KIND == KIND_RPPI ? cr[n] * npi + cz[n] : cr[n];
+                else k[n] = cr[n] != CFI_CLS_OUT ? K_AMB : K_OUT;
             }
         }
     }
 
-    // drain K*32 candidates (or the `count` left at the end) from the ring
-    template <int K>
-    __device__ __forceinline__ void drain(uint32_t count)
+    __device__ __forceinline__ void finish(uint32_t k, uint32_t vb, float wp, uint32_t il, uint32_t j)
     {
-        uint32_t vb[K], zb[K], code[K];
-        bool v[K];
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            const uint32_t idx = lane + 32u * k;
-            const uint32_t e = (head + idx) & QM;
-            v[k] = idx < count;
-            vb[k] = ring_d[e];
-            zb[k] = has_z(KIND) ? ring_z[e] : 0u;
-            code[k] = ring_c[e];
+        if (k < K_OUT) {
+            if (KIND == KIND_RPPI) acc_sh(k, __uint_as_float(vb), wp);
+            else acc_lp(k, __uint_as_float(vb), wp);
+        } else if (k == K_AMB) {
+            push(ibeg + il, jbeg + j);
         }
-#pragma unroll
-        for (int k = 0; k < K; k++) finish(vb[k], zb[k], code[k], v[k]);
-        head += count;
-        __syncwarp();
     }
 
-    template <int P, bool DIAG>
-    __device__ __forceinline__ void run(const CfItem &it)
-    {
-        constexpr int SL = 2 * P;                           // pair slots per j per lane
-        constexpr int JB = SLOTS_PER_BLOCK / SL;            // j points per block
-        icnt = it.cnt & 0xFFFFu;
-        const uint32_t jcnt = it.cnt >> 16;
-        ibeg = it.ibeg;
-        jbeg = it.jbeg;
-        job = it.meta & CFI_ITEM_JOBMASK;
-        // ---- i tile: translate by the shift; with ravg keep the TwoSum residual too ----
-        u64 sx[P], sy[P], sz[P], ex[P], ey[P], ez[P];
-#pragma unroll
-        for (int p = 0; p < P; p++) {
-            float vs[3][2], ve[3][2];
-#pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint32_t il = lane + 32u * (2 * p + h);
-                float w = 0.f;
-#pragma unroll
-                for (int d = 0; d < 3; d++) { vs[d][h] = 1e18f; ve[d][h] = 0.f; }
-                // empty slots sit far outside every bin (1e18^2 < FLT_MAX); in wrap mode the
-                // minimum image would fold them back, so there they are also masked by icnt
-                if (il < icnt) {
-                    const ulonglong2 A = a.pa[ibeg + il], B = a.pb[ibeg + il];
-                    const float X[3] = {-f2_lo(A.x), -f2_lo(A.y), -f2_lo(B.x)};
-                    float XL[3] = {0.f, 0.f, 0.f};
-                    if (LO) {
-                        const ulonglong2 C = a.plo[2 * (size_t)(ibeg + il)], D = a.plo[2 * (size_t)(ibeg + il) + 1];
-                        XL[0] = -f2_lo(C.x);
-                        XL[1] = -f2_lo(C.y);
-                        XL[2] = -f2_lo(D.x);
-                    }
-#pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        if (R) {
-                            float s, e;
-                            two_sum(X[d], it.s[d], s, e);
-                            vs[d][h] = s;
-                            ve[d][h] = (e + it.slo[d]) + XL[d];
-                        } else {
-                            vs[d][h] = X[d] + it.s[d];
-                        }
-                    }
-                    w = f2_lo(B.y);
-                }
-                if (W) stage_w[il] = w;
-            }
-            sx[p] = f2_pack(vs[0][0], vs[0][1]);
-            sy[p] = f2_pack(vs[1][0], vs[1][1]);
-            sz[p] = f2_pack(vs[2][0], vs[2][1]);
-            ex[p] = f2_pack(ve[0][0], ve[0][1]);
-            ey[p] = f2_pack(ve[1][0], ve[1][1]);
-            ez[p] = f2_pack(ve[2][0], ve[2][1]);
-        }
-        __syncwarp();
-        head = tail = 0;
-        const ulonglong2 *__restrict__ pa = a.pa + jbeg;
-        const ulonglong2 *__restrict__ pb = a.pb + jbeg;
-        for (uint32_t j0 = 0; j0 < jcnt; j0 += JB) {
-            // ---- phase A: the exact FP32 value phase B will bin, one cut per pair ----
-            uint32_t mask = 0;
-#pragma unroll
-            for (int jj = 0; jj < JB; jj++) {
-                const uint32_t j = j0 + jj;
-                if (j < jcnt) {
-                    const ulonglong2 A = __ldg(pa + j), B = __ldg(pb + j);
-                    u64 lx = 0, ly = 0, lz = 0;
-                    if (LO) {
-                        const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(jbeg + j));
-                        const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(jbeg + j) + 1);
-                        lx = C.x;
-                        ly = C.y;
-                        lz = D.x;
-                    }
-                    float dv[SL], zv[SL];
-#pragma unroll
-                    for (int p = 0; p < P; p++) {
-                        u64 dx = f2_add(sx[p], A.x), dy = f2_add(sy[p], A.y), dz = f2_add(sz[p], B.x);
-                        if (R) {
-                            dx = f2_add(dx, LO ? f2_add(ex[p], lx) : ex[p]);
-                            dy = f2_add(dy, LO ? f2_add(ey[p], ly) : ey[p]);
-                            dz = f2_add(dz, LO ? f2_add(ez[p], lz) : ez[p]);
-                        }
-                        if (WRAP) {
-                            if (Lx > 0.f) dx = wrap2(dx, Lx, iLx);
-                            if (Ly > 0.f) dy = wrap2(dy, Ly, iLy);
-                            if (Lz > 0.f) dz = wrap2(dz, Lz, iLz);
-                        }
-                        bool c0, c1;
-                        if (KIND == KIND_R || KIND == KIND_THETA) {
-                            u64 d2 = f2_mul(dx, dx);
-                            d2 = f2_fma(dy, dy, d2);
-                            d2 = f2_fma(dz, dz, d2);
-                            dv[2 * p] = f2_lo(d2);
-                            dv[2 * p + 1] = f2_hi(d2);
-                            c0 = dv[2 * p] < cut_r;
-                            c1 = dv[2 * p + 1] < cut_r;
-                        } else {
-                            u64 rp2 = f2_mul(dx, dx);
-                            rp2 = f2_fma(dy, dy, rp2);
-                            const u64 adz = dz & 0x7FFFFFFF7FFFFFFFull;
-                            dv[2 * p] = f2_lo(rp2);
-                            dv[2 * p + 1] = f2_hi(rp2);
-                            zv[2 * p] = f2_lo(adz);
-                            zv[2 * p + 1] = f2_hi(adz);
-                            c0 = dv[2 * p] < cut_r && zv[2 * p] < cut_p;
-                            c1 = dv[2 * p + 1] < cut_r && zv[2 * p + 1] < cut_p;
-                        }
-                        const uint32_t il0 = lane + 64u * p, il1 = il0 + 32u;
-                        if (DIAG) {
-                            c0 = c0 && j > il0;
-                            c1 = c1 && j > il1;
-                        }
-                        if (WRAP) {
-                            c0 = c0 && il0 < icnt;
-                            c1 = c1 && il1 < icnt;
-                        }
-                        const int bit = jj * SL + 2 * p;
-                        mask |= (c0 ? 1u : 0u) << bit;
-                        mask |= (c1 ? 1u : 0u) << (bit + 1);
-                    }
-                    float *bp = buf + ((uint32_t)jj * 32u + lane) * SL;
-                    if (P == 2) *reinterpret_cast<float4 *>(bp) = make_float4(dv[0], dv[1], dv[2], dv[3]);
-                    else *reinterpret_cast<float2 *>(bp) = make_float2(dv[0], dv[1]);
-                    if (has_z(KIND)) {
-                        float *zp = bufz + ((uint32_t)jj * 32u + lane) * SL;
-                        if (P == 2) *reinterpret_cast<float4 *>(zp) = make_float4(zv[0], zv[1], zv[2], zv[3]);
-                        else *reinterpret_cast<float2 *>(zp) = make_float2(zv[0], zv[1]);
-                    }
-                }
-            }
-            // ---- compaction into the warp's ring ----
-            const uint32_t n = __popc(mask);
-            uint32_t pre = n;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t t = __shfl_up_sync(CF_FULL, pre, o);
-                if (lane >= o) pre += t;
-            }
-            const uint32_t tot = __shfl_sync(CF_FULL, pre, 31);
-            uint32_t pos = tail + pre - n;
-            while (mask) {
-                const uint32_t b = (uint32_t)(__ffs(mask) - 1);
-                mask &= mask - 1;
-                const uint32_t q = b % SL, jj = b / SL;
-                const uint32_t e = pos & QM;
-                const uint32_t o = (jj * 32u + lane) * SL + q;
-                ring_d[e] = __float_as_uint(buf[o]);
-                if (has_z(KIND)) ring_z[e] = __float_as_uint(bufz[o]);
-                ring_c[e] = (uint16_t)(((lane + 32u * q) << 9) | (j0 + jj));
-                pos++;
-            }
-            tail += tot;
-            __syncwarp();
-            // ---- phase B ----
-            while (tail - head >= 64) drain<2>(64);
-        }
-        while (tail - head >= 32) drain<1>(32);
-        if (tail != head) drain<1>(tail - head);
-    }
-
-    // ---- direct variant: every pair is binned where it is formed (no compaction) ----
-    // Bin one pair that passed the FP32 cut (squared separation below cut_r and, for rp-pi and
-    // wp, |dz| below cut_p): both tables are then read without the upper clamp.
     __device__ __forceinline__ void bin_in(uint32_t vb, uint32_t zb, float wp, uint32_t il, uint32_t j)
     {
-        if (KIND == KIND_R || KIND == KIND_THETA) {
-            const uint32_t c = lut_class_in(lr, fine, vb);
-            if (c < (uint32_t)nb) acc_lp(c, __uint_as_float(vb), wp);
-            else if (c == CFI_CLS_AMB) push(ibeg + il, jbeg + j);
-        } else {
-            // the pi table starts at 0 with bin 0, so below cut_p it yields a bin or AMB
-            const uint32_t cr = lut_class_in(lr, fine, vb);
-            const uint32_t cz = lut_class_in(lp, fine, zb);
-            if (max(cr, cz) < CFI_CLS_OUT) {
-                if (KIND == KIND_RPPI) acc_sh(cr * npi + cz, __uint_as_float(vb), wp);
-                else acc_lp(cr, __uint_as_float(vb), wp);
-            } else if (cr != CFI_CLS_OUT) {
-                push(ibeg + il, jbeg + j);
-            }
-        }
+        const uint32_t v[1] = {vb}, z[1] = {zb};
+        uint32_t k[1];
+        classify<1>(v, z, k);
+        finish(k[0], vb, wp, il, j);
     }
 
-    template <int P, bool DIAG>
-    __device__ __forceinline__ void run_direct(const CfItem &it)
+    // bin the ring's candidates with every lane busy: two per lane while 64 are queued, then
+    // 32 at a time; with all = true also the last, partial pass
+    __device__ __forceinline__ void drain(bool all)
+    {
+        __syncwarp();
+        while (tail - head >= 64u) {
+            const uint32_t e0 = (head + lane) & RM, e1 = (head + 32u + lane) & RM;
+            const uint32_t v[2] = {rv[e0], rv[e1]};
+            const uint32_t z[2] = {has_z(KIND) ? rz[e0] : 0u, has_z(KIND) ? rz[e1] : 0u};
+            const uint32_t c0 = rc[e0], c1 = rc[e1];
+            const float w0 = W ? rw[e0] : 0.f, w1 = W ? rw[e1] : 0.f;
+            uint32_t k[2];
+            classify<2>(v, z, k);
+            finish(k[0], v[0], w0, c0 & 0x7Fu, c0 >> 7);
+            finish(k[1], v[1], w1, c1 & 0x7Fu, c1 >> 7);
+            head += 64u;
+        }
+        for (;;) {
+            const uint32_t left = tail - head;
+            if (left == 0u || (!all && left < 32u)) break;
+            const uint32_t n = min(left, 32u);
+            if ((uint32_t)lane < n) {
+                const uint32_t e = (head + lane) & RM;
+                const uint32_t c = rc[e];
+                bin_in(rv[e], has_z(KIND) ? rz[e] : 0u, W ? rw[e] : 0.f, c & 0x7Fu, c >> 7);
+            }
+            head += n;
+        }
+        __syncwarp();
+    }
+
+    // One work item.  Q = i slots per lane; DIAG: the i tile and the j range are the same cell
+    // (only j > i counts); COMPACT selects the binning form.
+    template <int Q, bool DIAG, bool COMPACT>
+    __device__ __forceinline__ void run(const CfItem &it)
     {
         icnt = it.cnt & 0xFFFFu;
         const uint32_t jcnt = it.cnt >> 16;
         ibeg = it.ibeg;
         jbeg = it.jbeg;
         job = it.meta & CFI_ITEM_JOBMASK;
-        u64 sx[P], sy[P], sz[P], ex[P], ey[P], ez[P], wi[P];
+        u64 sx[Q], sy[Q], sz[Q], ex[Q], ey[Q], ez[Q], wi[Q];
 #pragma unroll
-        for (int p = 0; p < P; p++) {
-            float vs[3][2], ve[3][2], vw[2];
+        for (int q = 0; q < Q; q++) {
+            const uint32_t il = lane + 32u * q;
+            float vs[3], ve[3], vw = 0.f;
 #pragma unroll
-            for (int h = 0; h < 2; h++) {
-                const uint32_t il = lane + 32u * (2 * p + h);
-                vw[h] = 0.f;
-#pragma unroll
-                for (int d = 0; d < 3; d++) { vs[d][h] = 1e18f; ve[d][h] = 0.f; }
-                // empty slots sit far outside every bin (1e18^2 < FLT_MAX); in wrap mode the
-                // minimum image would fold them back, so there they are also masked by icnt
-                if (il < icnt) {
-                    const ulonglong2 A = a.pa[ibeg + il], B = a.pb[ibeg + il];
-                    const float X[3] = {-f2_lo(A.x), -f2_lo(A.y), -f2_lo(B.x)};
-                    float XL[3] = {0.f, 0.f, 0.f};
-                    if (LO) {
-                        const ulonglong2 C = a.plo[2 * (size_t)(ibeg + il)], D = a.plo[2 * (size_t)(ibeg + il) + 1];
-                        XL[0] = -f2_lo(C.x);
-                        XL[1] = -f2_lo(C.y);
-                        XL[2] = -f2_lo(D.x);
-                    }
-#pragma unroll
-                    for (int d = 0; d < 3; d++) {
-                        if (R) {
-                            float s, e;
-                            two_sum(X[d], it.s[d], s, e);
-                            vs[d][h] = s;
-                            ve[d][h] = (e + it.slo[d]) + XL[d];
-                        } else {
-                            vs[d][h] = X[d] + it.s[d];
-                        }
-                    }
-                    vw[h] = f2_lo(B.y);
+            for (int d = 0; d < 3; d++) { vs[d] = 1e18f; ve[d] = 0.f; }
+            // empty slots sit far outside every bin (1e18^2 < FLT_MAX); in wrap mode the
+            // minimum image would fold them back, so there they are also masked by icnt
+            if (il < icnt) {
+                const ulonglong2 A = a.pa[ibeg + il], B = a.pb[ibeg + il];
+                const float X[3] = {-f2_lo(A.x), -f2_lo(A.y), -f2_lo(B.x)};
+                float XL[3] = {0.f, 0.f, 0.f};
+                if (LO) {
+                    const ulonglong2 C = a.plo[2 * (size_t)(ibeg + il)], D = a.plo[2 * (size_t)(ibeg + il) + 1];
+                    XL[0] = -f2_lo(C.x);
+                    XL[1] = -f2_lo(C.y);
+                    XL[2] = -f2_lo(D.x);
                 }
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    if (R) {
+                        float s, e;
+                        two_sum(X[d], it.s[d], s, e);
+                        vs[d] = s;
+                        ve[d] = (e + it.slo[d]) + XL[d];
+                    } else {
+                        vs[d] = X[d] + it.s[d];
+                    }
+                }
+                vw = f2_lo(B.y);
             }
-            sx[p] = f2_pack(vs[0][0], vs[0][1]);
-            sy[p] = f2_pack(vs[1][0], vs[1][1]);
-            sz[p] = f2_pack(vs[2][0], vs[2][1]);
-            ex[p] = f2_pack(ve[0][0], ve[0][1]);
-            ey[p] = f2_pack(ve[1][0], ve[1][1]);
-            ez[p] = f2_pack(ve[2][0], ve[2][1]);
-            wi[p] = f2_pack(vw[0], vw[1]);
+            sx[q] = f2_pack(vs[0], vs[0]);
+            sy[q] = f2_pack(vs[1], vs[1]);
+            sz[q] = f2_pack(vs[2], vs[2]);
+            ex[q] = f2_pack(ve[0], ve[0]);
+            ey[q] = f2_pack(ve[1], ve[1]);
+            ez[q] = f2_pack(ve[2], ve[2]);
+            wi[q] = f2_pack(vw, vw);
         }
-        // j points stream through a double-buffered shared-memory stage: chunk c+1 is copied
-        // asynchronously while chunk c is evaluated from broadcast shared loads
-        const ulonglong2 *__restrict__ pa = a.pa + jbeg;
-        const ulonglong2 *__restrict__ pb = a.pb + jbeg;
+        // stage arrays of one chunk: 0 x, 1 y, 2 z, 3 w, 4-6 lo parts of x, y, z (all negated
+        // as stored); a j past the end of the range reads the far-away sentinel
+        constexpr uint32_t NA = LO ? 7u : 4u;
+        auto issue = [&](uint32_t c) {
+            float *bs = jst + (c & 1u) * NA * JSTAGE;
+            const uint32_t j = c * JSTAGE + lane;
+            if (j < jcnt) {
+                const float *fa = reinterpret_cast<const float *>(a.pa + jbeg + j);
+                const float *fb = reinterpret_cast<const float *>(a.pb + jbeg + j);
+                cp_async4(bs + lane, fa);
+                cp_async4(bs + JSTAGE + lane, fa + 2);
+                cp_async4(bs + 2 * JSTAGE + lane, fb);
+                if (W) cp_async4(bs + 3 * JSTAGE + lane, fb + 2);
+                if (LO) {
+                    const float *fl = reinterpret_cast<const float *>(a.plo + 2 * (size_t)(jbeg + j));
+                    cp_async4(bs + 4 * JSTAGE + lane, fl);
+                    cp_async4(bs + 5 * JSTAGE + lane, fl + 2);
+                    cp_async4(bs + 6 * JSTAGE + lane, fl + 4);
+                }
+            } else {
+                bs[lane] = 1e18f;
+                bs[JSTAGE + lane] = 1e18f;
+                bs[2 * JSTAGE + lane] = 1e18f;
+                if (W) bs[3 * JSTAGE + lane] = 0.f;
+                if (LO) bs[4 * JSTAGE + lane] = bs[5 * JSTAGE + lane] = bs[6 * JSTAGE + lane] = 0.f;
+            }
+        };
         const uint32_t nchunk = (jcnt + JSTAGE - 1) / JSTAGE;
-        if (lane < jcnt) {
-            cp_async16(jbuf + lane, pa + lane);
-            cp_async16(jbuf + JSTAGE + lane, pb + lane);
-        }
+        issue(0);
         cp_async_commit();
         for (uint32_t c = 0; c < nchunk; c++) {
-            const uint32_t j0 = c * JSTAGE;
-            if (c + 1 < nchunk) {
-                ulonglong2 *nb2 = jbuf + ((c + 1) & 1) * 2 * JSTAGE;
-                const uint32_t jn = j0 + JSTAGE + lane;
-                if (jn < jcnt) {
-                    cp_async16(nb2 + lane, pa + jn);
-                    cp_async16(nb2 + JSTAGE + lane, pb + jn);
-                }
-            }
+            if (c + 1 < nchunk) issue(c + 1);
             cp_async_commit();
             cp_async_wait<1>();
             __syncwarp();
-            const ulonglong2 *ca = jbuf + (c & 1) * 2 * JSTAGE;
+            const float *bs = jst + (c & 1u) * NA * JSTAGE;
+            const uint32_t j0 = c * JSTAGE;
             const uint32_t n = min(JSTAGE, jcnt - j0);
-#pragma unroll 2
-            for (uint32_t jj = 0; jj < n; jj++) {
+            // within a cell paired with itself, slot q (i >= 32 q) has a live pair in this
+            // chunk (j <= 32 c + 31) only if q <= c
+            const int nq = DIAG ? min(Q, (int)c + 1) : Q;
+#pragma unroll 1
+            for (uint32_t jj = 0; jj < n; jj += 2) {
                 const uint32_t j = j0 + jj;
-                const ulonglong2 A = ca[jj], B = ca[JSTAGE + jj];
+                const u64 xj = *reinterpret_cast<const u64 *>(bs + jj);
+                const u64 yj = *reinterpret_cast<const u64 *>(bs + JSTAGE + jj);
+                const u64 zj = *reinterpret_cast<const u64 *>(bs + 2 * JSTAGE + jj);
                 u64 lx = 0, ly = 0, lz = 0;
                 if (LO) {
-                    const ulonglong2 C = __ldg(a.plo + 2 * (size_t)(jbeg + j));
-                    const ulonglong2 D = __ldg(a.plo + 2 * (size_t)(jbeg + j) + 1);
-                    lx = C.x;
-                    ly = C.y;
-                    lz = D.x;
+                    lx = *reinterpret_cast<const u64 *>(bs + 4 * JSTAGE + jj);
+                    ly = *reinterpret_cast<const u64 *>(bs + 5 * JSTAGE + jj);
+                    lz = *reinterpret_cast<const u64 *>(bs + 6 * JSTAGE + jj);
                 }
+                // compacting form: the distances of every slot first (independent chains), then
+                // the append; bits 2q and 2q + 1 of m: slot q's pair with j and with j + 1 is
+                // below the cut
+                u64 v2[Q], az[Q];
+                uint32_t m = 0;
 #pragma unroll
-                for (int p = 0; p < P; p++) {
-                    u64 dx = f2_add(sx[p], A.x), dy = f2_add(sy[p], A.y), dz = f2_add(sz[p], B.x);
+                for (int q = 0; q < Q; q++) {
+                    v2[q] = az[q] = 0ull;
+                    if (DIAG && q >= nq) continue;
+                    u64 dx = f2_add(sx[q], xj), dy = f2_add(sy[q], yj), dz = f2_add(sz[q], zj);
                     if (R) {
-                        dx = f2_add(dx, LO ? f2_add(ex[p], lx) : ex[p]);
-                        dy = f2_add(dy, LO ? f2_add(ey[p], ly) : ey[p]);
-                        dz = f2_add(dz, LO ? f2_add(ez[p], lz) : ez[p]);
+                        dx = f2_add(dx, LO ? f2_add(ex[q], lx) : ex[q]);
+                        dy = f2_add(dy, LO ? f2_add(ey[q], ly) : ey[q]);
+                        dz = f2_add(dz, LO ? f2_add(ez[q], lz) : ez[q]);
                     }
                     if (WRAP) {
                         if (Lx > 0.f) dx = wrap2(dx, Lx, iLx);
                         if (Ly > 0.f) dy = wrap2(dy, Ly, iLy);
                         if (Lz > 0.f) dz = wrap2(dz, Lz, iLz);
                     }
-                    const uint32_t il0 = lane + 64u * p, il1 = il0 + 32u;
-                    u64 v2, az = 0ull;
+                    const uint32_t il = lane + 32u * q;
                     bool in0, in1;
+                    v2[q] = f2_mul(dx, dx);
+                    v2[q] = f2_fma(dy, dy, v2[q]);
                     if (KIND == KIND_R || KIND == KIND_THETA) {
-                        v2 = f2_mul(dx, dx);
-                        v2 = f2_fma(dy, dy, v2);
-                        v2 = f2_fma(dz, dz, v2);
-                        in0 = f2_lo(v2) < cut_r;
-                        in1 = f2_hi(v2) < cut_r;
+                        v2[q] = f2_fma(dz, dz, v2[q]);
+                        in0 = f2_lo(v2[q]) < cut_r;
+                        in1 = f2_hi(v2[q]) < cut_r;
                     } else {
-                        v2 = f2_mul(dx, dx);
-                        v2 = f2_fma(dy, dy, v2);
-                        az = dz & 0x7FFFFFFF7FFFFFFFull;
-                        in0 = f2_lo(v2) < cut_r && f2_lo(az) < cut_p;
-                        in1 = f2_hi(v2) < cut_r && f2_hi(az) < cut_p;
+                        az[q] = dz & 0x7FFFFFFF7FFFFFFFull;
+                        in0 = f2_lo(v2[q]) < cut_r && f2_lo(az[q]) < cut_p;
+                        in1 = f2_hi(v2[q]) < cut_r && f2_hi(az[q]) < cut_p;
                     }
                     // within a cell paired with itself only j > i counts; in wrap mode the
-                    // minimum image folds the far-away empty slots back, so mask them here
+                    // minimum image folds the far-away sentinels back, so mask them here
                     if (DIAG) {
-                        in0 = in0 && j > il0;
-                        in1 = in1 && j > il1;
+                        in0 = in0 && j > il;
+                        in1 = in1 && j + 1 > il;
                     }
                     if (WRAP) {
-                        in0 = in0 && il0 < icnt;
-                        in1 = in1 && il1 < icnt;
+                        const bool li = il < icnt;
+                        in0 = in0 && li;
+                        in1 = in1 && li && j + 1 < jcnt;
                     }
-                    if (in0 || in1) {
-                        const u64 wp = W ? f2_mul(wi[p], B.y) : 0ull;
-                        if (in0) bin_in(f2_lo_bits(v2), f2_lo_bits(az), f2_lo(wp), il0, j);
-                        if (in1) bin_in(f2_hi_bits(v2), f2_hi_bits(az), f2_hi(wp), il1, j);
+                    if (!COMPACT) {
+                        // direct form: bin where formed
+                        if (in0 || in1) {
+                            const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
+                            const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
+                            if (in0) bin_in(f2_lo_bits(v2[q]), f2_lo_bits(az[q]), f2_lo(wp), il, j);
+                            if (in1) bin_in(f2_hi_bits(v2[q]), f2_hi_bits(az[q]), f2_hi(wp), il, j + 1);
+                        }
+                    } else {
+                        m |= (in0 ? 1u : 0u) << (2 * q);
+                        m |= (in1 ? 2u : 0u) << (2 * q);
                     }
+                }
+                if (COMPACT && __any_sync(CF_FULL, m != 0u)) {
+                    // offsets of this lane's candidates: a prefix sum of the per-lane counts
+                    // (<= 2Q) from one ballot per bit of the count
+                    const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
+                    const uint32_t cnt = __popc(m);
+                    constexpr int CB = Q == 1 ? 2 : (Q == 2 ? 3 : 4);
+                    uint32_t pre = 0, tot = 0;
+#pragma unroll
+                    for (int b = 0; b < CB; b++) {
+                        const uint32_t bal = __ballot_sync(CF_FULL, (cnt >> b) & 1u);
+                        pre += (uint32_t)__popc(bal & ltmask) << b;
+                        tot += (uint32_t)__popc(bal) << b;
+                    }
+                    uint32_t pos = tail + pre;
+#pragma unroll
+                    for (int q = 0; q < Q; q++) {
+                        const uint32_t mq = (m >> (2 * q)) & 3u;
+                        if (!mq) continue;
+                        const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
+                        const uint32_t code = (lane + 32u * q) | (j << 7);
+                        if (mq & 1u) {
+                            const uint32_t e = pos & RM;
+                            rv[e] = f2_lo_bits(v2[q]);
+                            if (has_z(KIND)) rz[e] = f2_lo_bits(az[q]);
+                            rc[e] = (uint16_t)code;
+                            if (W) rw[e] = f2_lo(wp);
+                            pos++;
+                        }
+                        if (mq & 2u) {
+                            const uint32_t e = pos & RM;
+                            rv[e] = f2_hi_bits(v2[q]);
+                            if (has_z(KIND)) rz[e] = f2_hi_bits(az[q]);
+                            rc[e] = (uint16_t)(code + 128u);    // j + 1
+                            if (W) rw[e] = f2_hi(wp);
+                            pos++;
+                        }
+                    }
+                    // the ring held < 32 candidates and took <= 64 Q: at most 287 of RING
+                    tail += tot;
+                    if (tail - head >= 32u) drain(false);
                 }
             }
             __syncwarp();       // the chunk buffer is refilled two chunks later
         }
         cp_async_wait<0>();
         __syncwarp();
+        if (COMPACT) drain(true);
     }
 
     __device__ void flush(uint32_t jb)
@@ -582,23 +503,26 @@ struct Warp {
     }
 };
 
-// resident CTAs (of 256 threads) the register budget is sized for: the compacting form is held
-// to one CTA per SM by its shared memory; the direct form keeps 2 (weights / ravg) or 3 CTAs
-__host__ __device__ constexpr int pair_min_blocks(bool W, bool R, bool DIRECT) { return !DIRECT ? 1 : ((W || R) ? 2 : 3); }
+// CTA shape the register budget is sized for.  With weights or ravg the lane-private histograms
+// (about 13 KB per warp for 20 bins) hold an SM to one CTA, so it may take up to 16 warps (the
+// launcher takes as many as fit); count-only CTAs are small and run 3 per SM.
+__host__ __device__ constexpr int pair_max_threads(bool W, bool R) { return (W || R) ? 512 : 256; }
+__host__ __device__ constexpr int pair_min_blocks(bool W, bool R) { return (!W && !R) ? 3 : 1; }
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO, bool DIRECT>
-__global__ void __launch_bounds__(256, pair_min_blocks(W, R, DIRECT)) pair_kernel(const CfPairArgs a)
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT>
+__global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
+    pair_kernel(const CfPairArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const CfDevPlan *__restrict__ P = a.plan;
     const int nlw = P->nlut_words, nf = P->nfine;
-    uint32_t *s_lut = (uint32_t *)smem;
-    CfFine *s_fine = (CfFine *)(smem + align16(4u * nlw));
+    uint16_t *s_lut = (uint16_t *)smem;
+    CfFine *s_fine = (CfFine *)(smem + align16(2u * nlw));
     unsigned char *wbase = (unsigned char *)(s_fine + nf);
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
-    const uint32_t wb = warp_bytes(KIND, W, R, a.nslot, DIRECT);
-    const uint32_t hoff = DIRECT ? warp_jbuf_bytes() : warp_buf_bytes(KIND) + warp_ring_bytes(KIND) + warp_stage_bytes(W);
+    const uint32_t wb = warp_bytes(KIND, W, R, a.nslot, COMPACT);
+    const uint32_t hoff = warp_jbuf_bytes() + (COMPACT ? warp_ring_bytes(KIND, W) : 0u);
     unsigned char *my = wbase + (size_t)(threadIdx.x >> 5) * wb;
     {
         // zero this warp's histogram (the buffers need no initial value)
@@ -622,18 +546,18 @@ __global__ void __launch_bounds__(256, pair_min_blocks(W, R, DIRECT)) pair_kerne
     w.iLx = a.L[0] > 0.f ? 1.0f / a.L[0] : 0.f;
     w.iLy = a.L[1] > 0.f ? 1.0f / a.L[1] : 0.f;
     w.iLz = a.L[2] > 0.f ? 1.0f / a.L[2] : 0.f;
+    w.ltmask = (1u << w.lane) - 1u;
+    w.head = w.tail = 0u;
+    w.jst = (float *)my;
     {
-        const bool z = has_z(KIND);
-        unsigned char *q = my;
-        w.buf = (float *)q;
-        w.bufz = (float *)(q + SLOTS_PER_BLOCK * 32u * 4u);
-        q += warp_buf_bytes(KIND);
-        w.ring_d = (uint32_t *)q;
-        w.ring_z = (uint32_t *)(q + CFI_QN * 4u);
-        w.ring_c = (uint16_t *)(q + CFI_QN * (z ? 8u : 4u));
-        q += warp_ring_bytes(KIND);
-        w.stage_w = (float *)q;
-        w.jbuf = (ulonglong2 *)my;
+        unsigned char *q = my + warp_jbuf_bytes();
+        w.rv = (uint32_t *)q;
+        q += RING * 4u;
+        w.rz = has_z(KIND) ? (uint32_t *)q : nullptr;
+        q += has_z(KIND) ? RING * 4u : 0u;
+        w.rw = W ? (float *)q : nullptr;
+        q += W ? RING * 4u : 0u;
+        w.rc = (uint16_t *)q;
     }
     w.h_cnt = (uint32_t *)(my + hoff);
     if (KIND == KIND_RPPI) {
@@ -669,20 +593,16 @@ __global__ void __launch_bounds__(256, pair_min_blocks(W, R, DIRECT)) pair_kerne
             cur = job;
         }
         const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
-        if (DIRECT) {
-            if (it.meta & CFI_ITEM_P2) {
-                if (diag) w.template run_direct<2, true>(it);
-                else w.template run_direct<2, false>(it);
-            } else {
-                if (diag) w.template run_direct<1, true>(it);
-                else w.template run_direct<1, false>(it);
-            }
-        } else if (it.meta & CFI_ITEM_P2) {
-            if (diag) w.template run<2, true>(it);
-            else w.template run<2, false>(it);
+        const uint32_t ic = it.cnt & 0xFFFFu;
+        if (ic <= 32u) {
+            if (diag) w.template run<1, true, COMPACT>(it);
+            else w.template run<1, false, COMPACT>(it);
+        } else if (ic <= 64u) {
+            if (diag) w.template run<2, true, COMPACT>(it);
+            else w.template run<2, false, COMPACT>(it);
         } else {
-            if (diag) w.template run<1, true>(it);
-            else w.template run<1, false>(it);
+            if (diag) w.template run<4, true, COMPACT>(it);
+            else w.template run<4, false, COMPACT>(it);
         }
         t = tn;
         it = nx;
@@ -690,16 +610,17 @@ __global__ void __launch_bounds__(256, pair_min_blocks(W, R, DIRECT)) pair_kerne
     if (cur >= 0) w.flush((uint32_t)cur);
 }
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO, bool DIRECT>
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT>
 cudaError_t launch_variant(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
                            int *warps_out)
 {
-    auto k = pair_kernel<KIND, W, R, WRAP, LO, DIRECT>;
+    auto k = pair_kernel<KIND, W, R, WRAP, LO, COMPACT>;
     int dev;
     cudaGetDevice(&dev);
     int maxsm = 0;
     cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int warps = c.warps > 0 ? (c.warps > 8 ? 8 : c.warps) : 8;
+    const int maxw = pair_max_threads(W, R) / 32;
+    int warps = c.warps > 0 ? (c.warps > maxw ? maxw : c.warps) : maxw;
     size_t smem = 0;
     for (; warps >= 1; warps--) {
         smem = cfp_pair_smem(c, warps);
@@ -726,8 +647,8 @@ template <int KIND, bool W, bool R, bool WRAP, bool LO>
 cudaError_t launch_one(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
                        int *warps_out)
 {
-    if (c.variant == 2) return launch_variant<KIND, W, R, WRAP, LO, false>(c, a, num_sms, st, grid_out, warps_out);
-    return launch_variant<KIND, W, R, WRAP, LO, true>(c, a, num_sms, st, grid_out, warps_out);
+    if (c.variant == 2) return launch_variant<KIND, W, R, WRAP, LO, true>(c, a, num_sms, st, grid_out, warps_out);
+    return launch_variant<KIND, W, R, WRAP, LO, false>(c, a, num_sms, st, grid_out, warps_out);
 }
 
 }  // namespace cfpair

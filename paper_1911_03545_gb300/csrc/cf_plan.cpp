@@ -122,6 +122,7 @@ namespace {
 // Bin lookup tables
 // ---------------------------------------------------------------------------------------
 struct Seg { uint32_t start; uint32_t cls; };
+static_assert(CFI_FINE_FLAG + CFI_FINE_MAX <= 0x10000u, "coarse table entries are 16-bit");
 
 // Class function over float bit patterns for edges E[0..m] with bands B: half-open bins
 // [E_k, E_k+1) -> class k; below E_0 -> OUT (or bin 0 when E_0 == 0); at or above E_m -> OUT;
@@ -164,7 +165,7 @@ std::vector<Seg> make_segments(const double *E, const double *B, int m)
 
 // Build coarse + fine tables for the segment list.  Returns false if no cell width <= the
 // table limit separates the breakpoints into cells of at most three segments.
-bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint32_t> &words,
+bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint16_t> &words,
                std::vector<CfFine> &fine)
 {
     if (segs.size() < 2) return false;
@@ -180,7 +181,7 @@ bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint32_t> &wo
         base = base >= w ? base - w : 0;
         uint64_t last = ((uint64_t)hi - base) >> s;
         if (last + 1 > (uint64_t)CFI_LUT_MAX) return false;
-        std::vector<uint32_t> cw(last + 1);
+        std::vector<uint16_t> cw(last + 1);
         std::vector<CfFine> fw;
         bool ok = true;
         size_t si = 0;                            // segment containing the cell start
@@ -196,7 +197,7 @@ bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint32_t> &wo
                     if (segs[t].start >= c1) { ok = false; break; }
             }
             if (inside.empty()) {
-                cw[c] = segs[si].cls;
+                cw[c] = (uint16_t)segs[si].cls;
             } else if (inside.size() <= 2) {
                 CfFine f;
                 f.t1 = inside[0].start;
@@ -204,7 +205,7 @@ bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint32_t> &wo
                 uint32_t c2 = inside.size() > 1 ? inside[1].cls : inside[0].cls;
                 f.code = segs[si].cls | (inside[0].cls << 8) | (c2 << 16);
                 f.pad = 0;
-                cw[c] = CFI_FINE_FLAG | (uint32_t)(fine.size() + fw.size());
+                cw[c] = (uint16_t)(CFI_FINE_FLAG | (uint32_t)(fine.size() + fw.size()));
                 fw.push_back(f);
                 if (fine.size() + fw.size() > CFI_FINE_MAX) ok = false;
             } else {

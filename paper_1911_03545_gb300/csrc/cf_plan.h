@@ -7,7 +7,7 @@
 
 struct CfHostPlan {
     CfDevPlan d;                       // copied to device memory for the kernels
-    std::vector<uint32_t> lut;         // coarse LUT words: r-like LUT then pi LUT
+    std::vector<uint16_t> lut;         // coarse LUT entries (class or fine flag | index): r-like LUT then pi LUT
     std::vector<CfFine> fine;          // fine LUT entries (both LUTs)
     std::vector<CfStencil> stencil;    // neighbour offsets after pruning
     std::vector<double> origin;        // cell origins per axis (see cfp_origin), n0 + n1 + n2 values

@@ -5,7 +5,7 @@ Knobs (all results are identical across them; only speed changes):
           of each lane into a per-warp ring first
   refine  sub-cells per Rmax cell (Sec. 4.2): 1, 2, 3
   warps   warps per CTA of the persistent pair kernel (CTA shape; occupancy follows from the
-          shared-memory histograms): 4, 6, 8
+          shared-memory histograms): 0 (as many as fit), 12, 8, 6, 4
   tile    i-tile size (i points held in registers per warp item): 64, 128
   jchunk  j range per work item (staging depth of the j stream): 128, 256, 512
 
@@ -24,11 +24,11 @@ import time
 from . import (CF_OPT_JCHUNK, CF_OPT_REFINE, CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS, cf_count, cf_get_stats,
                cf_set_option)
 
-KNOBS = {"variant": [1, 2], "refine": [1, 2, 3], "warps": [8, 6, 4], "tile": [128, 64],
+KNOBS = {"variant": [1, 2], "refine": [1, 2, 3], "warps": [0, 12, 8, 6, 4], "tile": [128, 64],
          "jchunk": [512, 256, 128]}
 OPT = {"variant": CF_OPT_VARIANT, "refine": CF_OPT_REFINE, "warps": CF_OPT_WARPS, "tile": CF_OPT_TILE,
        "jchunk": CF_OPT_JCHUNK}
-DEFAULT = {"variant": 1, "refine": 1, "warps": 8, "tile": 128, "jchunk": 512}
+DEFAULT = {"variant": 1, "refine": 1, "warps": 0, "tile": 128, "jchunk": 512}
 
 
 def cache_path() -> str:
