@@ -258,7 +258,8 @@ struct Warp {
     }
 
     // One work item.  Q = i slots per lane; DIAG: the i tile and the j range are the same cell
-    // (only j > i counts); COMPACT selects the binning form.
+    // (only j > i counts; one instance with Q = 4 serves every tile size, the slots past the
+    // tile skipped at run time); COMPACT selects the binning form.
     template <int Q, bool DIAG, bool COMPACT>
     __device__ __forceinline__ void run(const CfItem &it)
     {
@@ -346,8 +347,8 @@ struct Warp {
             const uint32_t j0 = c * JSTAGE;
             const uint32_t n = min(JSTAGE, jcnt - j0);
             // within a cell paired with itself, slot q (i >= 32 q) has a live pair in this
-            // chunk (j <= 32 c + 31) only if q <= c
-            const int nq = DIAG ? min(Q, (int)c + 1) : Q;
+            // chunk (j <= 32 c + 31) only if q <= c, and none past the tile
+            const int nq = DIAG ? min((int)((icnt + 31u) >> 5), (int)c + 1) : Q;
 #pragma unroll 1
             for (uint32_t jj = 0; jj < n; jj += 2) {
                 const uint32_t j = j0 + jj;
@@ -594,16 +595,10 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
         }
         const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
         const uint32_t ic = it.cnt & 0xFFFFu;
-        if (ic <= 32u) {
-            if (diag) w.template run<1, true, COMPACT>(it);
-            else w.template run<1, false, COMPACT>(it);
-        } else if (ic <= 64u) {
-            if (diag) w.template run<2, true, COMPACT>(it);
-            else w.template run<2, false, COMPACT>(it);
-        } else {
-            if (diag) w.template run<4, true, COMPACT>(it);
-            else w.template run<4, false, COMPACT>(it);
-        }
+        if (diag) w.template run<4, true, COMPACT>(it);
+        else if (ic <= 32u) w.template run<1, false, COMPACT>(it);
+        else if (ic <= 64u) w.template run<2, false, COMPACT>(it);
+        else w.template run<4, false, COMPACT>(it);
         t = tn;
         it = nx;
     }
