@@ -50,7 +50,7 @@ struct CfPairCfg {
     int nlut_words, nfine, nslot;
     int warps;         // warps per CTA (0: automatic)
     int ctas_per_sm;   // 0: occupancy-derived
-    int variant;       // 1 direct binning, 2 compacting two-phase (resolved from 0 by the caller)
+    int variant;       // 1 direct binning, 2 compacting ring (resolved from 0 by the caller)
 };
 
 // Shared-memory bytes of one CTA with `warps` warps.

@@ -40,7 +40,7 @@ constexpr int KIND_R = 0, KIND_RPPI = 1, KIND_WP = 2, KIND_THETA = 3;
 __host__ __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
 // per-warp shared memory: j stage | candidate ring (compacting form) | histogram
-//   j stage: 2 chunks x up to 7 float arrays (x, y, z, w, lo parts of x, y, z) of JSTAGE points
+//   j stage: 2 chunks x 3-7 float arrays (x, y, z[, w][, lo parts of x, y, z]) of JSTAGE points
 //   ring:    RING candidates as arrays: value bits, |dz| bits (rp-pi, wp), weight product (W),
 //            code (u16: i slot | j << 7)
 constexpr uint32_t JSTAGE = 32;
@@ -61,23 +61,29 @@ __host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int kind, bool W, b
     return b;
 }
 __host__ __device__ __forceinline__ bool has_z(int kind) { return kind == KIND_RPPI || kind == KIND_WP; }
-__host__ __device__ __forceinline__ uint32_t warp_jbuf_bytes() { return 2u * 8u * JSTAGE * 4u; }
+__host__ __device__ constexpr uint32_t stage_arrays(bool W, bool LO) { return LO ? 7u : (W ? 4u : 3u); }
+__host__ __device__ constexpr uint32_t warp_jbuf_bytes(bool W, bool LO) { return 2u * stage_arrays(W, LO) * JSTAGE * 4u; }
 __host__ __device__ __forceinline__ uint32_t warp_ring_bytes(int kind, bool W)
 {
     return RING * (4u + (has_z(kind) ? 4u : 0u) + (W ? 4u : 0u) + 2u);
 }
-__host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, int nslot, bool compact)
+__host__ __device__ __forceinline__ uint32_t warp_bytes(int kind, bool W, bool R, bool LO, int nslot, bool compact)
 {
-    return warp_jbuf_bytes() + (compact ? warp_ring_bytes(kind, W) : 0u) + warp_hist_bytes(kind, W, R, nslot);
+    return warp_jbuf_bytes(W, LO) + (compact ? warp_ring_bytes(kind, W) : 0u) + warp_hist_bytes(kind, W, R, nslot);
 }
 
+// Kahan-compensated FP32 sum: s holds the sum, c the negated lost low part
+__device__ __forceinline__ void kahan_step(float &s, float &c, float v)
+{
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
 __device__ __forceinline__ void kahan_add(float2 *p, float v)
 {
     float2 sc = *p;
-    float y = v - sc.y;
-    float t = sc.x + y;
-    sc.y = (t - sc.x) - y;
-    sc.x = t;
+    kahan_step(sc.x, sc.y, v);
     *p = sc;
 }
 
@@ -144,7 +150,7 @@ struct Warp {
     Lut lr, lp;
     const CfFine *fine;
     uint32_t *h_cnt;        // lane-private [nslot][32] or per-warp [nslot]
-    float2 *h_w, *h_r;      // lane-private Kahan pairs
+    float2 *h_w, *h_r;      // lane-private Kahan pairs (interleaved when both are kept)
     double *h_wd, *h_rd;    // per-warp FP64 (rp-pi)
     float *jst;             // j stage
     uint32_t *rv, *rz;      // ring: value bits, |dz| bits
@@ -163,11 +169,21 @@ struct Warp {
     {
         uint32_t idx = c * 32u + lane;
         atomicAdd(h_cnt + idx, 1u);
-        if (W) kahan_add(h_w + idx, wp);
+        float r = 0.f;
         if (R) {
-            float r = f_sqrt_approx(d2);
+            r = f_sqrt_approx(d2);
             if (KIND == KIND_THETA) r = 2.0f * asinf(0.5f * r) * 57.29577951308232f;
-            kahan_add(h_r + idx, W ? wp * r : r);
+        }
+        if (W && R) {
+            // both sums of a lane's bin sit in one float4: one 16-byte load and store
+            float4 *p = reinterpret_cast<float4 *>(h_w) + idx;
+            float4 v = *p;
+            kahan_step(v.x, v.y, wp);
+            kahan_step(v.z, v.w, wp * r);
+            *p = v;
+        } else {
+            if (W) kahan_add(h_w + idx, wp);
+            if (R) kahan_add(h_r + idx, r);
         }
     }
 
@@ -310,7 +326,7 @@ struct Warp {
         }
         // stage arrays of one chunk: 0 x, 1 y, 2 z, 3 w, 4-6 lo parts of x, y, z (all negated
         // as stored); a j past the end of the range reads the far-away sentinel
-        constexpr uint32_t NA = LO ? 7u : 4u;
+        constexpr uint32_t NA = stage_arrays(W, LO);
         auto issue = [&](uint32_t c) {
             float *bs = jst + (c & 1u) * NA * JSTAGE;
             const uint32_t j = c * JSTAGE + lane;
@@ -480,19 +496,20 @@ struct Warp {
                 if (W) { ws = h_wd[sl]; h_wd[sl] = 0.0; }
                 if (R) { rs = h_rd[sl]; h_rd[sl] = 0.0; }
             } else {
+                constexpr int ST = (W && R) ? 2 : 1;     // float2 stride of the Kahan sums
                 for (int l = 0; l < 32; l++) {
                     int idx = sl * 32 + ((l + lane) & 31);
                     c += h_cnt[idx];
                     h_cnt[idx] = 0;
                     if (W) {
-                        float2 v = h_w[idx];
+                        float2 v = h_w[ST * idx];
                         ws += (double)v.x - (double)v.y;
-                        h_w[idx] = make_float2(0.f, 0.f);
+                        h_w[ST * idx] = make_float2(0.f, 0.f);
                     }
                     if (R) {
-                        float2 v = h_r[idx];
+                        float2 v = h_r[ST * idx];
                         rs += (double)v.x - (double)v.y;
-                        h_r[idx] = make_float2(0.f, 0.f);
+                        h_r[ST * idx] = make_float2(0.f, 0.f);
                     }
                 }
             }
@@ -522,8 +539,8 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     unsigned char *wbase = (unsigned char *)(s_fine + nf);
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
-    const uint32_t wb = warp_bytes(KIND, W, R, a.nslot, COMPACT);
-    const uint32_t hoff = warp_jbuf_bytes() + (COMPACT ? warp_ring_bytes(KIND, W) : 0u);
+    const uint32_t wb = warp_bytes(KIND, W, R, LO, a.nslot, COMPACT);
+    const uint32_t hoff = warp_jbuf_bytes(W, LO) + (COMPACT ? warp_ring_bytes(KIND, W) : 0u);
     unsigned char *my = wbase + (size_t)(threadIdx.x >> 5) * wb;
     {
         // zero this warp's histogram (the buffers need no initial value)
@@ -551,7 +568,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     w.head = w.tail = 0u;
     w.jst = (float *)my;
     {
-        unsigned char *q = my + warp_jbuf_bytes();
+        unsigned char *q = my + warp_jbuf_bytes(W, LO);
         w.rv = (uint32_t *)q;
         q += RING * 4u;
         w.rz = has_z(KIND) ? (uint32_t *)q : nullptr;
@@ -568,8 +585,9 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
         w.h_w = w.h_r = nullptr;
     } else {
         uint32_t o = a.nslot * 32u * 4u;
+        // with both sums they interleave (float4 per lane and bin: w, w-comp, r, r-comp)
         w.h_w = (float2 *)(my + hoff + o);
-        w.h_r = (float2 *)(my + hoff + o + (W ? a.nslot * 32u * 8u : 0u));
+        w.h_r = (W && R) ? w.h_w + 1 : (float2 *)(my + hoff + o + (W ? a.nslot * 32u * 8u : 0u));
         w.h_wd = w.h_rd = nullptr;
     }
 

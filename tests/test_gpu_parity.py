@@ -287,3 +287,29 @@ def test_compacting_variant_parity(ctx, kind, autocorr, periodic, weighted, ravg
         test_random_parity(ctx, kind, autocorr, periodic, weighted, ravg)
     finally:
         cf.cf_set_option(ctx, cf.CF_OPT_VARIANT, 0)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_tile_shapes_wrap_and_diagonal(ctx, variant):
+    """Ragged i tiles (1 to 4 slots of 32 points), odd j ranges, cells paired with themselves and the
+    explicit minimum image (Rmax = 5 in a box of 12: two cells per axis) together, against the
+    oracle, for several tile sizes and j range lengths."""
+    import paper_1911_03545_gb300 as cf
+    d = gen.clustered_box(30, 37, 0.8, 12.0, 91)
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 92)
+    edges = gen.log_edges(0.05, 5.0, 9)
+    kw_r = dict(autocorr=True, periodic=True, box=12.0, weighted=True, ravg=True)
+    kw_p = dict(autocorr=True, periodic=True, box=12.0, pimax=5.0, npibins=5)
+    exp_r = oracle.count("r", edges, d, **kw_r)
+    exp_p = oracle.count("rppi", edges, d, **kw_p)
+    cf.cf_set_option(ctx, cf.CF_OPT_VARIANT, variant)
+    try:
+        for tile in (32, 96, 128):
+            for jchunk in (31, 129, 512):
+                cf.cf_set_option(ctx, cf.CF_OPT_TILE, tile)
+                cf.cf_set_option(ctx, cf.CF_OPT_JCHUNK, jchunk)
+                assert_match(gpu_count(ctx, "r", edges, d, **kw_r), exp_r, True, True)
+                assert_match(gpu_count(ctx, "rppi", edges, d, **kw_p), exp_p)
+    finally:
+        for opt in (cf.CF_OPT_VARIANT, cf.CF_OPT_TILE, cf.CF_OPT_JCHUNK):
+            cf.cf_set_option(ctx, opt, 0)
