@@ -60,7 +60,7 @@ __host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int kind, bool W, b
     if (R) b += nslot * 32u * 8u;
     return b;
 }
-__host__ __device__ __forceinline__ bool has_z(int kind) { return kind == KIND_RPPI || kind == KIND_WP; }
+__host__ __device__ constexpr bool has_z(int kind) { return kind == KIND_RPPI || kind == KIND_WP; }
 __host__ __device__ constexpr uint32_t stage_arrays(bool W, bool LO) { return LO ? 7u : (W ? 4u : 3u); }
 __host__ __device__ constexpr uint32_t warp_jbuf_bytes(bool W, bool LO) { return 2u * stage_arrays(W, LO) * JSTAGE * 4u; }
 __host__ __device__ __forceinline__ uint32_t warp_ring_bytes(int kind, bool W)
@@ -279,6 +279,9 @@ struct Warp {
     template <int Q, bool DIAG, bool COMPACT>
     __device__ __forceinline__ void run(const CfItem &it)
     {
+        // direct form: r and theta issue the distances of all slots before binning any (more
+        // independent chains); rp-pi and wp, whose binning is larger, bin each slot right away
+        constexpr bool SPLIT = !has_z(KIND);
         icnt = it.cnt & 0xFFFFu;
         const uint32_t jcnt = it.cnt >> 16;
         ibeg = it.ibeg;
@@ -377,14 +380,16 @@ struct Warp {
                     ly = *reinterpret_cast<const u64 *>(bs + 5 * JSTAGE + jj);
                     lz = *reinterpret_cast<const u64 *>(bs + 6 * JSTAGE + jj);
                 }
-                // compacting form: the distances of every slot first (independent chains), then
-                // the append; bits 2q and 2q + 1 of m: slot q's pair with j and with j + 1 is
-                // below the cut
+                // the distances and cuts of every slot first (independent chains), then the
+                // binning; in the compacting form bits 2q and 2q + 1 of m: slot q's pair with j
+                // and with j + 1 is below the cut
                 u64 v2[Q], az[Q];
+                bool p0[Q], p1[Q];
                 uint32_t m = 0;
 #pragma unroll
                 for (int q = 0; q < Q; q++) {
                     v2[q] = az[q] = 0ull;
+                    p0[q] = p1[q] = false;
                     if (DIAG && q >= nq) continue;
                     u64 dx = f2_add(sx[q], xj), dy = f2_add(sy[q], yj), dz = f2_add(sz[q], zj);
                     if (R) {
@@ -421,17 +426,30 @@ struct Warp {
                         in0 = in0 && li;
                         in1 = in1 && li && j + 1 < jcnt;
                     }
-                    if (!COMPACT) {
-                        // direct form: bin where formed
-                        if (in0 || in1) {
-                            const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
-                            const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
-                            if (in0) bin_in(f2_lo_bits(v2[q]), f2_lo_bits(az[q]), f2_lo(wp), il, j);
-                            if (in1) bin_in(f2_hi_bits(v2[q]), f2_hi_bits(az[q]), f2_hi(wp), il, j + 1);
-                        }
-                    } else {
+                    p0[q] = in0;
+                    p1[q] = in1;
+                    if (COMPACT) {
                         m |= (in0 ? 1u : 0u) << (2 * q);
                         m |= (in1 ? 2u : 0u) << (2 * q);
+                    } else if (!SPLIT && (in0 || in1)) {
+                        // direct form, rp-pi / wp: bin where formed
+                        const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
+                        const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
+                        if (in0) bin_in(f2_lo_bits(v2[q]), f2_lo_bits(az[q]), f2_lo(wp), il, j);
+                        if (in1) bin_in(f2_hi_bits(v2[q]), f2_hi_bits(az[q]), f2_hi(wp), il, j + 1);
+                    }
+                }
+                if (!COMPACT && SPLIT) {
+                    // direct form, r / theta: bin after every slot's distances are issued
+#pragma unroll
+                    for (int q = 0; q < Q; q++) {
+                        if (p0[q] || p1[q]) {
+                            const uint32_t il = lane + 32u * q;
+                            const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
+                            const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
+                            if (p0[q]) bin_in(f2_lo_bits(v2[q]), f2_lo_bits(az[q]), f2_lo(wp), il, j);
+                            if (p1[q]) bin_in(f2_hi_bits(v2[q]), f2_hi_bits(az[q]), f2_hi(wp), il, j + 1);
+                        }
                     }
                 }
                 if (COMPACT && __any_sync(CF_FULL, m != 0u)) {
