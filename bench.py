@@ -577,13 +577,75 @@ def run_serve(args, world, rank, local):
     return 0
 
 
+def run_sweep(args, world, rank, local):
+    """Scaling with particle number and with Rmax, each for refinement factors k = 1, 2, 3 (Sec. 4.2
+    and the scaling study of Sec. 5): DD(r) auto on the clustered L=420 catalogue (random subsamples for
+    the N series, the full 1e6 points for the Rmax series), 20 log bins from 0.1 to Rmax."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import gen
+    import paper_1911_03545_gb300 as cf
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    ctx = cf.cf_create(local, torch.cuda.current_stream(dev))
+    wl = gen.workload("clustered_r_1m")
+    full, L = wl.d1, wl.box
+    perm = np.random.Generator(np.random.PCG64(77)).permutation(full.n)
+
+    def sub(n):
+        idx = np.sort(perm[:n])
+        return gen.Catalogue(full.x[idx], full.y[idx], full.z[idx])
+
+    rows, same = [], True
+
+    def measure(cat, rmax, series):
+        nonlocal same
+        edges = gen.log_edges(0.1, rmax, 20)
+        pts = _points(cat, False, cf, dev)
+        ref = None
+        for k in (1, 2, 3):
+            p = cf.params(kind="r", edges=edges, autocorr=True, periodic=True, box=L, refine=(k, k, k))
+            res = cf.cf_count(ctx, p, pts)
+            pair, tot = [], []
+            for _ in range(args.sweep_reps):
+                res = cf.cf_count(ctx, p, pts)
+                st = cf.cf_get_stats(ctx)
+                pair.append(st["ms_pair"])
+                tot.append(st["ms_build"] + st["ms_pair"] + st["ms_recheck"])
+            counts = np.asarray(res["npairs"])
+            if ref is None:
+                ref = counts
+            same = same and np.array_equal(ref, counts)
+            rows.append({"series": series, "n": int(cat.n), "rmax": rmax, "refine": k,
+                         "pair_ms": float(np.median(pair)), "device_ms": float(np.median(tot)),
+                         "evaluated_pairs": int(st["evaluated_pairs"]), "in_range_pairs": int(counts.sum()),
+                         "cells": int(st["cells"])})
+
+    for n in (10_000, 30_000, 100_000, 300_000, 1_000_000):
+        measure(sub(n) if n < full.n else full, 20.0, "N")
+    for rmax in (5.0, 10.0, 40.0, 80.0):
+        measure(full, rmax, "Rmax")
+    if rank == 0:
+        print(json.dumps({"metric": "scaling sweep", "workload": "clustered_r_1m recipe, DD(r) auto, periodic L=420, "
+                          "20 log bins 0.1-Rmax, float32, unweighted", "rows": rows,
+                          "counts_identical_across_refine": bool(same),
+                          "refine_model": "evaluated pairs relative to k=1: ((k+1)/(2k))^3 for cubic sub-cells"}),
+              flush=True)
+    cf.cf_destroy(ctx)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="clustered_r_1m", choices=sorted(WORKLOADS) + ["batch256", "serve"])
+    ap.add_argument("--workload", default="clustered_r_1m", choices=sorted(WORKLOADS) + ["batch256", "serve", "sweep"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
@@ -591,6 +653,7 @@ def main(argv=None):
     ap.add_argument("--config", default="", help="pin the launch configuration instead of tuning, "
                     "e.g. variant=2,warps=8 (knobs of paper_1911_03545_gb300.tune)")
     ap.add_argument("--ncat", type=int, default=256)
+    ap.add_argument("--sweep-reps", type=int, default=3)
     ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--serve-budget", type=int, default=16, help="GiB")
@@ -603,6 +666,8 @@ def main(argv=None):
         return run_batch(args, world, rank, local)
     if args.workload == "serve":
         return run_serve(args, world, rank, local)
+    if args.workload == "sweep":
+        return run_sweep(args, world, rank, local)
     import gen
     wl = gen.workload(args.workload)
     if args.impl == "reference":

@@ -274,8 +274,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.ncell_all = R.ncell * nsets;
     if (R.ncell_all >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "too many cells");
     R.nst = D.g.nstencil;
-    R.nthr = (int64_t)njobs * R.ncell * R.nst;
-    if (R.nthr >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "work list too large");
+    R.nunit = (int64_t)njobs * R.ncell;      // work-list units: one per (job, i cell)
+    if (R.nunit >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "work list too large");
     R.np = std::max<int64_t>(R.npts, 1);
     R.nslot = (size_t)D.nslot;
     R.hsz = R.nslot * njobs;
@@ -297,9 +297,9 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_PB, 16 * (size_t)R.np));
     CF_TRY(C->ensure(B_ORIG, 4 * (size_t)R.np));
     if (D.f64lo) CF_TRY(C->ensure(B_PLO, 32 * (size_t)R.np));
-    CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.ncell_all, R.nthr))));
-    CF_TRY(C->ensure(B_ICNT, 4 * (size_t)std::max<int64_t>(R.nthr, 1)));
-    CF_TRY(C->ensure(B_IOFF, 4 * (size_t)(R.nthr + 1)));
+    CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.ncell_all, R.nunit))));
+    CF_TRY(C->ensure(B_ICNT, 4 * (size_t)std::max<int64_t>(R.nunit, 1)));
+    CF_TRY(C->ensure(B_IOFF, 4 * (size_t)(R.nunit + 1)));
     CF_TRY(C->ensure(B_MISC, 4096));
     CF_TRY(C->ensure(B_HCNT, 8 * R.hsz));
     CF_TRY(C->ensure(B_HW, 8 * R.hsz));
@@ -363,10 +363,10 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
                       (uint32_t *)C->buf[B_ORIG].p, st),
           "scatter");
     uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
-    CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, cstart, R.nthr, 0, icnt, nullptr, nullptr,
+    CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, cstart, R.nunit, 0, icnt, nullptr, nullptr,
                     0, nullptr, st),
           "items count");
-    CF_CU(cfb_scan(icnt, ioff, R.nthr, (uint32_t *)C->buf[B_SCAN].p, st), "scan items");
+    CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, st), "scan items");
     C->launches += 9;   // assign, 3 scan, scatter, items count, 3 scan
     return CF_OK;
 }
@@ -385,7 +385,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     CF_CU(cudaMemsetAsync(misc, 0, 16, st), "memset");
     CF_CU(cudaMemsetAsync(evaluated, 0, 8, st), "memset");
     CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, (const uint32_t *)C->buf[B_CSTART].p,
-                    R.nthr, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated, st),
+                    R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated, st),
           "items emit");
     CF_CU(cudaMemsetAsync(C->buf[B_HCNT].p, 0, 8 * R.hsz, st), "memset");
     CF_CU(cudaMemsetAsync(C->buf[B_HW].p, 0, 8 * R.hsz, st), "memset");
@@ -398,7 +398,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     A.lut = (const uint16_t *)C->buf[B_LUT].p;
     A.fine = (const CfFine *)C->buf[B_FINE].p;
     A.items = (const CfItem *)C->buf[B_ITEMS].p;
-    A.nitems_dev = ioff + R.nthr;
+    A.nitems_dev = ioff + R.nunit;
     A.items_cap = R.items_cap;
     A.qcap = R.qcap;
     A.cursor = misc;
@@ -435,7 +435,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     char *h = (char *)C->hpin;
     const size_t hsz = R.hsz;
     CF_CU(cudaMemcpyAsync(h, misc, 8, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 8, ioff + R.nthr, 4, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 8, ioff + R.nunit, 4, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 16, evaluated, 8, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 64, C->buf[B_HCNT].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 64 + 8 * hsz, C->buf[B_HW].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
@@ -526,7 +526,7 @@ int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &p
     CF_CU(cudaEventRecord(C->ev[0], st), "event");
     CF_TRY(cf_enqueue_build(C, R));
     // size the work list from the device count (one small readback)
-    CF_CU(cudaMemcpyAsync(C->hpin, (uint32_t *)C->buf[B_IOFF].p + R.nthr, 4, cudaMemcpyDeviceToHost, st), "items total");
+    CF_CU(cudaMemcpyAsync(C->hpin, (uint32_t *)C->buf[B_IOFF].p + R.nunit, 4, cudaMemcpyDeviceToHost, st), "items total");
     CF_CU(cudaStreamSynchronize(st), "items sync");
     R.items_cap = *(const uint32_t *)C->hpin;
     CF_TRY(C->ensure(B_ITEMS, sizeof(CfItem) * std::max<size_t>(1, R.items_cap)));

@@ -45,7 +45,7 @@ struct CfRun {
     std::vector<CfJobDesc> jobs;
     CfHostPlan plan;
     int nsets = 0, njobs = 0;
-    int64_t npts = 0, nmax = 0, np = 1, ncell = 0, ncell_all = 0, nst = 0, nthr = 0;
+    int64_t npts = 0, nmax = 0, np = 1, ncell = 0, ncell_all = 0, nst = 0, nunit = 0;
     size_t nslot = 0, hsz = 0;
     bool self_pairs = false;
     uint32_t qcap = 0, items_cap = 0;

@@ -223,12 +223,11 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
 // i tile (<= tile points) by one j range (<= jchunk points; the i tiles themselves for the
 // diagonal of an auto-correlation).  mode 0 counts items per thread, mode 1 writes them.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ void cf_tiles(uint32_t n, uint32_t tmax, uint32_t &nt, uint32_t &ts)
-{
-    nt = (n + tmax - 1) / tmax;
-    ts = nt ? (n + nt - 1) / nt : 0;
-}
-
+// Work items, one warp per (job, i cell).  The lanes walk the cell's stencil (Sec. 4.3: neighbours
+// +-k per axis, periodic shift per cell pair, auto keeps cj >= ci), a warp prefix sum orders the
+// items of the cell, and an empty i cell costs one load.  i tiles are full (tile points) plus one
+// remainder tile, so a tile wastes at most 31 pair-kernel slots; j ranges split evenly (<= jchunk).
+// mode 0 writes the item count of each (job, cell); mode 1 writes the items at the scanned offsets.
 __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
                                 const uint32_t *__restrict__ cell_start, int mode,
@@ -238,82 +237,99 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
 {
     const CfGrid &g = plan->g;
     const int nst = g.nstencil;
-    const int64_t per_job = (int64_t)g.ncell * nst;
-    const int64_t total = per_job * plan->njobs;
+    const int64_t nunit = (int64_t)g.ncell * plan->njobs;
     const uint32_t tile = plan->tile, jchunk = plan->jchunk;
+    const uint32_t lane = threadIdx.x & 31u;
     unsigned long long ev = 0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        int job = (int)(t / per_job);
-        int64_t r = t - (int64_t)job * per_job;
-        int c = (int)(r / nst);
-        int s = (int)(r - (int64_t)c * nst);
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < nunit; u += wstride) {
+        const int job = (int)(u / g.ncell);
+        const int c = (int)(u - (int64_t)job * g.ncell);
         const CfJobDesc J = jobs[job];
         const CfSetDesc &A = sets[J.a];
         const CfSetDesc &B = sets[J.b];
-        int ci[3] = {c / (g.n[2] * g.n[1]), (c / g.n[2]) % g.n[1], c % g.n[2]};
-        int tj[3];
-        double shift[3];
-        bool ok = true;
-        for (int a = 0; a < 3; a++) {
-            int d = stencil[s].d[a];
-            int v = ci[a] + d;
-            double delta = 0.0;        // image of the j point: x_j + delta
-            if (g.wrap[a]) {
-                v %= g.n[a];
-            } else if (g.periodic) {
-                if (v < 0) { v += g.n[a]; delta = -g.L[a]; }
-                else if (v >= g.n[a]) { v -= g.n[a]; delta = g.L[a]; }
-            } else if (v < 0 || v >= g.n[a]) {
-                ok = false;
-            }
-            tj[a] = v;
-            if (ok && mode == 1) shift[a] = cf_origin(plan, a, ci[a]) - cf_origin(plan, a, v) - delta;
-        }
-        uint32_t cnt = 0;
-        if (ok) {
-            int ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
-            if (J.autoc && ct < c) ok = false;
-            if (ok) {
-                uint32_t ia = cell_start[A.cbeg + c], na = cell_start[A.cbeg + c + 1] - ia;
-                uint32_t jb = cell_start[B.cbeg + ct], nb = cell_start[B.cbeg + ct + 1] - jb;
-                if (na && nb) {
-                    uint32_t nti, tsi;
-                    cf_tiles(na, tile, nti, tsi);
-                    bool diag = J.autoc && ct == c;
-                    uint32_t ntj, tsj;
-                    if (diag) { ntj = nti; tsj = tsi; }
-                    else cf_tiles(nb, jchunk, ntj, tsj);
-                    cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
-                    if (mode == 1) {
-                        uint32_t o = offsets[t];
-                        float sh[3], sl[3];
-                        for (int a = 0; a < 3; a++) {
-                            sh[a] = (float)shift[a];
-                            sl[a] = (float)(shift[a] - (double)sh[a]);
+        const uint32_t ia = cell_start[A.cbeg + c], na = cell_start[A.cbeg + c + 1] - ia;
+        uint32_t total = 0;
+        if (na) {
+            const int ci[3] = {c / (g.n[2] * g.n[1]), (c / g.n[2]) % g.n[1], c % g.n[2]};
+            const uint32_t nti = (na + tile - 1) / tile;
+            const uint32_t base = mode == 1 ? offsets[u] : 0u;
+            for (int s0 = 0; s0 < nst; s0 += 32) {
+                const int s = s0 + (int)lane;
+                uint32_t cnt = 0, jb = 0, nb = 0, ntj = 0, tsj = 0;
+                bool diag = false;
+                double shift[3] = {0.0, 0.0, 0.0};
+                if (s < nst) {
+                    int tj[3];
+                    bool ok = true;
+                    for (int a = 0; a < 3; a++) {
+                        int v = ci[a] + stencil[s].d[a];
+                        double delta = 0.0;        // image of the j point: x_j + delta
+                        if (g.wrap[a]) {
+                            v %= g.n[a];
+                        } else if (g.periodic) {
+                            if (v < 0) { v += g.n[a]; delta = -g.L[a]; }
+                            else if (v >= g.n[a]) { v -= g.n[a]; delta = g.L[a]; }
+                        } else if (v < 0 || v >= g.n[a]) {
+                            ok = false;
                         }
-                        for (uint32_t a0 = 0; a0 < nti; a0++) {
-                            uint32_t i0 = a0 * tsi, ic = min(tsi, na - i0);
-                            uint32_t b0 = diag ? a0 : 0;
-                            for (uint32_t b = b0; b < ntj; b++) {
-                                uint32_t j0 = b * tsj, jc = min(tsj, nb - j0);
-                                CfItem it;
-                                it.ibeg = ia + i0;
-                                it.jbeg = jb + j0;
-                                it.cnt = ic | (jc << 16);
-                                it.meta = (uint32_t)job | ((diag && b == a0) ? CFI_ITEM_DIAG : 0u) |
-                                          (ic > 64 ? CFI_ITEM_P2 : 0u);
-                                it.s[0] = sh[0]; it.s[1] = sh[1]; it.s[2] = sh[2]; it.pad0 = 0.f;
-                                it.slo[0] = sl[0]; it.slo[1] = sl[1]; it.slo[2] = sl[2]; it.pad1 = 0.f;
-                                if (o < items_cap) items[o] = it;
-                                o++;
-                                ev += (unsigned long long)ic * jc;
+                        tj[a] = v;
+                        if (ok && mode == 1) shift[a] = cf_origin(plan, a, ci[a]) - cf_origin(plan, a, v) - delta;
+                    }
+                    if (ok) {
+                        const int ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
+                        if (!(J.autoc && ct < c)) {
+                            jb = cell_start[B.cbeg + ct];
+                            nb = cell_start[B.cbeg + ct + 1] - jb;
+                            if (nb) {
+                                diag = J.autoc && ct == c;
+                                if (diag) {
+                                    ntj = nti;
+                                    tsj = tile;
+                                } else {
+                                    ntj = (nb + jchunk - 1) / jchunk;
+                                    tsj = (nb + ntj - 1) / ntj;
+                                }
+                                cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
                             }
                         }
                     }
                 }
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t v = __shfl_up_sync(CF_FULL, incl, o);
+                    if ((int)lane >= o) incl += v;
+                }
+                if (mode == 1 && cnt) {
+                    uint32_t o = base + total + (incl - cnt);
+                    float sh[3], sl[3];
+                    for (int a = 0; a < 3; a++) {
+                        sh[a] = (float)shift[a];
+                        sl[a] = (float)(shift[a] - (double)sh[a]);
+                    }
+                    for (uint32_t a0 = 0; a0 < nti; a0++) {
+                        const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
+                        for (uint32_t b = diag ? a0 : 0; b < ntj; b++) {
+                            const uint32_t j0 = b * tsj, jc = min(tsj, nb - j0);
+                            CfItem it;
+                            it.ibeg = ia + i0;
+                            it.jbeg = jb + j0;
+                            it.cnt = ic | (jc << 16);
+                            it.meta = (uint32_t)job | ((diag && b == a0) ? CFI_ITEM_DIAG : 0u) |
+                                      (ic > 64 ? CFI_ITEM_P2 : 0u);
+                            it.s[0] = sh[0]; it.s[1] = sh[1]; it.s[2] = sh[2]; it.pad0 = 0.f;
+                            it.slo[0] = sl[0]; it.slo[1] = sl[1]; it.slo[2] = sl[2]; it.pad1 = 0.f;
+                            if (o < items_cap) items[o] = it;
+                            o++;
+                            ev += (unsigned long long)ic * jc;
+                        }
+                    }
+                }
+                total += __shfl_sync(CF_FULL, incl, 31);
             }
         }
-        if (mode == 0) counts[t] = cnt;
+        if (mode == 0 && lane == 0) counts[u] = total;
     }
     if (mode == 1) {
         for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(CF_FULL, ev, o);
@@ -384,12 +400,12 @@ cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets,
 }
 
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
-                      const uint32_t *cell_start, int64_t nthreads, int mode, uint32_t *counts,
+                      const uint32_t *cell_start, int64_t nunits, int mode, uint32_t *counts,
                       const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
                       cudaStream_t st)
 {
-    cf_items_kernel<<<blocks_for(nthreads, 256, 8192), 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, mode,
-                                                                    counts, offsets, items, items_cap, evaluated);
+    cf_items_kernel<<<blocks_for(nunits * 32, 256, 8192), 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, mode,
+                                                                       counts, offsets, items, items_cap, evaluated);
     return cudaGetLastError();
 }
 

@@ -13,7 +13,7 @@ cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets,
                         const uint32_t *cell_start, const uint32_t *cellid, const uint32_t *slot, float4 *pa,
                         float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st);
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
-                      const uint32_t *cell_start, int64_t nthreads, int mode, uint32_t *counts,
+                      const uint32_t *cell_start, int64_t nunits, int mode, uint32_t *counts,
                       const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
                       cudaStream_t st);
 cudaError_t cfb_wsq(const CfSetDesc *sets, int nsets, int64_t nmax, double *out, cudaStream_t st);
