@@ -146,7 +146,10 @@ typedef enum {
     CF_OPT_WARPS = 9,        /* warps per CTA of the pair kernel: up to 16 for the direct form with
                                 weights or ravg, up to 8 otherwise (0 = as many as fit) */
     CF_OPT_REFINE = 10,      /* refinement factor used when params.refine is 0 */
-    CF_OPT_COUNT_ = 11
+    CF_OPT_CELL_PRUNE = 11,  /* 0 (default): skip cell pairs whose points' bounding boxes lie farther
+                                apart than the largest edge (and pimax along z for rp-pi / wp);
+                                1: visit every stencil neighbour.  Results are the same either way */
+    CF_OPT_COUNT_ = 12
 } cf_option;
 cf_status cf_set_option(void *ctx, int option, int64_t value);
 

@@ -296,6 +296,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_PA, 16 * (size_t)R.np));
     CF_TRY(C->ensure(B_PB, 16 * (size_t)R.np));
     CF_TRY(C->ensure(B_ORIG, 4 * (size_t)R.np));
+    CF_TRY(C->ensure(B_CBOX, 24 * (size_t)R.ncell_all));
     if (D.f64lo) CF_TRY(C->ensure(B_PLO, 32 * (size_t)R.np));
     CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.ncell_all, R.nunit))));
     CF_TRY(C->ensure(B_ICNT, 4 * (size_t)std::max<int64_t>(R.nunit, 1)));
@@ -362,9 +363,18 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
                       (float4 *)C->buf[B_PA].p, (float4 *)C->buf[B_PB].p, (float4 *)C->buf[B_PLO].p,
                       (uint32_t *)C->buf[B_ORIG].p, st),
           "scatter");
+    const float *cbox = nullptr;
+    if (C->opt[CF_OPT_CELL_PRUNE] == 0) {
+        CF_CU(cfb_cellbox(cstart, R.ncell_all, (const float4 *)C->buf[B_PA].p, (const float4 *)C->buf[B_PB].p,
+                          (float *)C->buf[B_CBOX].p, st),
+              "cell boxes");
+        cbox = (const float *)C->buf[B_CBOX].p;
+        C->launches += 1;
+    }
+    R.cbox = cbox;
     uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
-    CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, cstart, R.nunit, 0, icnt, nullptr, nullptr,
-                    0, nullptr, st),
+    CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, cstart, cbox, R.nunit, 0, icnt, nullptr,
+                    nullptr, 0, nullptr, st),
           "items count");
     CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, st), "scan items");
     C->launches += 9;   // assign, 3 scan, scatter, items count, 3 scan
@@ -385,7 +395,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     CF_CU(cudaMemsetAsync(misc, 0, 16, st), "memset");
     CF_CU(cudaMemsetAsync(evaluated, 0, 8, st), "memset");
     CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, (const uint32_t *)C->buf[B_CSTART].p,
-                    R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated, st),
+                    R.cbox, R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated, st),
           "items emit");
     CF_CU(cudaMemsetAsync(C->buf[B_HCNT].p, 0, 8 * R.hsz, st), "memset");
     CF_CU(cudaMemsetAsync(C->buf[B_HW].p, 0, 8 * R.hsz, st), "memset");

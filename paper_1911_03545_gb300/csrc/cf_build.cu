@@ -217,12 +217,37 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
 }
 
 // ---------------------------------------------------------------------------------------------
-// Work list (Sec. 4.2-4.3).  One thread per (job, cell of set a, stencil entry): the target cell
-// of set b, the shift that brings the target's points next to the source cell (Sec. 4.4), the
-// auto-correlation rule target >= source (Sec. 4.3), then the cell pair is cut into items of one
-// i tile (<= tile points) by one j range (<= jchunk points; the i tiles themselves for the
-// diagonal of an auto-correlation).  mode 0 counts items per thread, mode 1 writes them.
+// Tight bounding box of each cell's points in the cell-relative float32 coordinates of the pair
+// kernel (x - origin; lo then hi per axis, 6 floats per cell of every point set).  One warp per
+// cell; an empty cell keeps (+inf, -inf).  The work list uses it to skip cell pairs whose points
+// are all farther apart than the largest edge: the paper's late entry / early exit (Sec. 4.5) at
+// the granularity of cells.
 // ---------------------------------------------------------------------------------------------
+__global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64_t ncell_all,
+                                  const float4 *__restrict__ pa, const float4 *__restrict__ pb, float *__restrict__ box)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncell_all; c += wstride) {
+        const uint32_t b = cell_start[c], e = cell_start[c + 1];
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (uint32_t p = b + lane; p < e; p += 32u) {
+            const float4 A = pa[p], B = pb[p];
+            const float v[3] = {-A.x, -A.z, -B.x};
+            for (int a = 0; a < 3; a++) {
+                lo[a] = fminf(lo[a], v[a]);
+                hi[a] = fmaxf(hi[a], v[a]);
+            }
+        }
+        for (int o = 16; o; o >>= 1)
+            for (int a = 0; a < 3; a++) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(CF_FULL, lo[a], o));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(CF_FULL, hi[a], o));
+            }
+        if (lane < 6u) box[6 * c + lane] = lane < 3u ? lo[lane] : hi[lane - 3u];
+    }
+}
+
 // Work items, one warp per (job, i cell).  The lanes walk the cell's stencil (Sec. 4.3: neighbours
 // +-k per axis, periodic shift per cell pair, auto keeps cj >= ci), a warp prefix sum orders the
 // items of the cell, and an empty i cell costs one load.  i tiles are full (tile points) plus one
@@ -230,13 +255,17 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
 // mode 0 writes the item count of each (job, cell); mode 1 writes the items at the scanned offsets.
 __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
-                                const uint32_t *__restrict__ cell_start, int mode,
+                                const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox, int mode,
                                 uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets,
                                 CfItem *__restrict__ items, uint32_t items_cap,
                                 unsigned long long *__restrict__ evaluated)
 {
     const CfGrid &g = plan->g;
     const int nst = g.nstencil;
+    // box pruning needs the cell pair's own shift, which wrap axes (explicit minimum image) lack
+    const bool prune = cbox != nullptr && !g.wrap[0] && !g.wrap[1] && !g.wrap[2];
+    const bool zsep = plan->kind == CF_DD_RPPI || plan->kind == CF_WP;
+    const double e2max = plan->e2[plan->nb], zmax = zsep ? (double)plan->pimax : 0.0;
     const int64_t nunit = (int64_t)g.ncell * plan->njobs;
     const uint32_t tile = plan->tile, jchunk = plan->jchunk;
     const uint32_t lane = threadIdx.x & 31u;
@@ -274,13 +303,30 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                             ok = false;
                         }
                         tj[a] = v;
-                        if (ok && mode == 1) shift[a] = cf_origin(plan, a, ci[a]) - cf_origin(plan, a, v) - delta;
+                        if (ok && (mode == 1 || prune))
+                            shift[a] = cf_origin(plan, a, ci[a]) - cf_origin(plan, a, v) - delta;
                     }
                     if (ok) {
                         const int ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
                         if (!(J.autoc && ct < c)) {
                             jb = cell_start[B.cbeg + ct];
                             nb = cell_start[B.cbeg + ct + 1] - jb;
+                            if (nb && prune) {
+                                // separation range of the two boxes per axis under this shift; each
+                                // gap is shrunk by a margin far above the rounding of the cell-relative
+                                // coordinates, so a skipped pair is out of every bin in FP64 as well
+                                const float *bi = cbox + 6 * (A.cbeg + c), *bj = cbox + 6 * (B.cbeg + ct);
+                                double s2 = 0.0, gz = 0.0;
+                                for (int a = 0; a < 3; a++) {
+                                    const double lo = (double)bi[a] + shift[a] - (double)bj[3 + a];
+                                    const double hi = (double)bi[3 + a] + shift[a] - (double)bj[a];
+                                    double gap = lo > 0.0 ? lo : (hi < 0.0 ? -hi : 0.0);
+                                    gap = fmax(0.0, gap - 1e-5 * g.width[a]);
+                                    if (zsep && a == 2) gz = gap;
+                                    else s2 += gap * gap;
+                                }
+                                if (s2 >= e2max || (zsep && gz >= zmax)) nb = 0;
+                            }
                             if (nb) {
                                 diag = J.autoc && ct == c;
                                 if (diag) {
@@ -399,13 +445,21 @@ cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets,
     return cudaGetLastError();
 }
 
+cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const float4 *pa, const float4 *pb, float *box,
+                        cudaStream_t st)
+{
+    cf_cellbox_kernel<<<blocks_for(ncell_all * 32, 256, 8192), 256, 0, st>>>(cell_start, ncell_all, pa, pb, box);
+    return cudaGetLastError();
+}
+
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
-                      const uint32_t *cell_start, int64_t nunits, int mode, uint32_t *counts,
+                      const uint32_t *cell_start, const float *cbox, int64_t nunits, int mode, uint32_t *counts,
                       const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
                       cudaStream_t st)
 {
-    cf_items_kernel<<<blocks_for(nunits * 32, 256, 8192), 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, mode,
-                                                                       counts, offsets, items, items_cap, evaluated);
+    cf_items_kernel<<<blocks_for(nunits * 32, 256, 8192), 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox,
+                                                                       mode, counts, offsets, items, items_cap,
+                                                                       evaluated);
     return cudaGetLastError();
 }
 

@@ -12,8 +12,12 @@ cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp
 cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax,
                         const uint32_t *cell_start, const uint32_t *cellid, const uint32_t *slot, float4 *pa,
                         float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st);
+// tight point bounding box per cell (6 floats: lo xyz, hi xyz, cell-relative), for cell-pair pruning
+cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const float4 *pa, const float4 *pb, float *box,
+                        cudaStream_t st);
+// cbox: the boxes above, or nullptr to visit every stencil neighbour
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
-                      const uint32_t *cell_start, int64_t nunits, int mode, uint32_t *counts,
+                      const uint32_t *cell_start, const float *cbox, int64_t nunits, int mode, uint32_t *counts,
                       const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
                       cudaStream_t st);
 cudaError_t cfb_wsq(const CfSetDesc *sets, int nsets, int64_t nmax, double *out, cudaStream_t st);

@@ -8,6 +8,8 @@ Knobs (all results are identical across them; only speed changes):
           shared-memory histograms): 0 (as many as fit), 12, 8, 6, 4
   tile    i-tile size (i points held in registers per warp item): 64, 128
   jchunk  j range per work item (staging depth of the j stream): 128, 256, 512
+  noprune 1 visits every stencil neighbour; 0 skips cell pairs whose points' bounding boxes are
+          farther apart than the largest edge (costs one pass over the points)
 
 The tuner times `cf_count` on the caller's own catalogue with each candidate (a coordinate
 descent from the default), keeps the fastest, and caches it in a JSON file keyed by device name,
@@ -21,14 +23,14 @@ import math
 import os
 import time
 
-from . import (CF_OPT_JCHUNK, CF_OPT_REFINE, CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS, cf_count, cf_get_stats,
-               cf_set_option)
+from . import (CF_OPT_CELL_PRUNE, CF_OPT_JCHUNK, CF_OPT_REFINE, CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS, cf_count,
+               cf_get_stats, cf_set_option)
 
 KNOBS = {"variant": [1, 2], "refine": [1, 2, 3], "warps": [0, 12, 8, 6, 4], "tile": [128, 64],
-         "jchunk": [512, 256, 128]}
+         "jchunk": [512, 256, 128], "noprune": [0, 1]}
 OPT = {"variant": CF_OPT_VARIANT, "refine": CF_OPT_REFINE, "warps": CF_OPT_WARPS, "tile": CF_OPT_TILE,
-       "jchunk": CF_OPT_JCHUNK}
-DEFAULT = {"variant": 1, "refine": 1, "warps": 0, "tile": 128, "jchunk": 512}
+       "jchunk": CF_OPT_JCHUNK, "noprune": CF_OPT_CELL_PRUNE}
+DEFAULT = {"variant": 1, "refine": 1, "warps": 0, "tile": 128, "jchunk": 512, "noprune": 0}
 
 
 def cache_path() -> str:

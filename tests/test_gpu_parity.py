@@ -313,3 +313,47 @@ def test_tile_shapes_wrap_and_diagonal(ctx, variant):
     finally:
         for opt in (cf.CF_OPT_VARIANT, cf.CF_OPT_TILE, cf.CF_OPT_JCHUNK):
             cf.cf_set_option(ctx, opt, 0)
+
+
+def test_cell_pruning_keeps_results(ctx):
+    """Skipping cell pairs by their points' bounding boxes (the default) changes neither counts nor
+    sums, and on clustered data it removes evaluated pairs."""
+    import paper_1911_03545_gb300 as cf
+    d = gen.clustered_box(120, 40, 0.7, 60.0, 93)
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 94)
+    edges = gen.log_edges(0.05, 6.0, 10)
+    kw_r = dict(autocorr=True, periodic=True, box=60.0, weighted=True, ravg=True)
+    kw_p = dict(autocorr=True, periodic=True, box=60.0, pimax=8.0, npibins=8)
+    exp_r = oracle.count("r", edges, d, **kw_r)
+    exp_p = oracle.count("rppi", edges, d, **kw_p)
+    exp_w = oracle.count("wp", edges, d, **kw_p)
+    evaluated = {}
+    for prune in (0, 1):
+        cf.cf_set_option(ctx, cf.CF_OPT_CELL_PRUNE, prune)
+        try:
+            assert_match(gpu_count(ctx, "r", edges, d, **kw_r), exp_r, True, True)
+            evaluated[prune] = cf.cf_get_stats(ctx)["evaluated_pairs"]
+            assert_match(gpu_count(ctx, "rppi", edges, d, **kw_p), exp_p)
+            assert_match(gpu_count(ctx, "wp", edges, d, **kw_p), exp_w)
+        finally:
+            cf.cf_set_option(ctx, cf.CF_OPT_CELL_PRUNE, 0)
+    assert evaluated[0] < evaluated[1]
+
+
+def test_cell_pruning_at_the_largest_edge(ctx):
+    """Two tight groups in neighbouring cells at separations just below, at and just above the largest
+    edge (10): a pruned cell pair must never hold a pair the oracle counts."""
+    pts = []
+    for k, delta in enumerate([-1e-4, -1e-5, -2e-6, 0.0, 2e-6, 1e-5, 1e-4]):
+        y = 5.0 + 12.0 * k
+        for m in range(3):
+            pts.append((12.0, y + 0.01 * m, 50.0))
+            pts.append((22.0 + delta, y + 0.01 * m, 50.0))
+    a = np.array(pts, dtype=np.float64)
+    d = gen.Catalogue(a[:, 0].astype(np.float32), a[:, 1].astype(np.float32), a[:, 2].astype(np.float32))
+    edges = np.array([1.0, 5.0, 9.99, 10.0])
+    for kind, kw in (("r", {}), ("rppi", dict(pimax=10.0, npibins=10)), ("wp", dict(pimax=10.0, npibins=10))):
+        got, exp = both(ctx, kind, edges, d, autocorr=True, periodic=True, box=100.0, **kw)
+        assert_match(got, exp)
+        got, exp = both(ctx, kind, edges, d, d, autocorr=False, periodic=True, box=100.0, **kw)
+        assert_match(got, exp)
