@@ -149,7 +149,10 @@ typedef enum {
     CF_OPT_CELL_PRUNE = 11,  /* 0 (default): skip cell pairs whose points' bounding boxes lie farther
                                 apart than the largest edge (and pimax along z for rp-pi / wp);
                                 1: visit every stencil neighbour.  Results are the same either way */
-    CF_OPT_COUNT_ = 12
+    CF_OPT_CELL_ORDER = 12,  /* points inside a cell are ordered by Morton sub-cell: 0 (default) picks
+                                the sub-cells per axis (4, 2 or 1) from the cell count; 1, 2 or 4 pin
+                                it.  Results are the same for every order */
+    CF_OPT_COUNT_ = 13
 } cf_option;
 cf_status cf_set_option(void *ctx, int option, int64_t value);
 

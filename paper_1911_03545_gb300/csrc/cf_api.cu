@@ -274,6 +274,16 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.ncell_all = R.ncell * nsets;
     if (R.ncell_all >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "too many cells");
     R.nst = D.g.nstencil;
+    // points sort by (cell, Morton sub-cell): the finest order whose key array stays within about
+    // twice the points (and 1M keys)
+    {
+        const int64_t want = C->opt[CF_OPT_CELL_ORDER];
+        const int64_t lim = std::max<int64_t>(2 * R.npts, (int64_t)1 << 20);
+        if (want == 1 || want == 2 || want == 4) R.sub = (int)want;
+        else R.sub = R.ncell_all * 64 <= lim ? 4 : (R.ncell_all * 8 <= lim ? 2 : 1);
+        R.nfine = R.ncell_all * R.sub * R.sub * R.sub;
+        if (R.nfine >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "too many cells");
+    }
     R.nunit = (int64_t)njobs * R.ncell;      // work-list units: one per (job, i cell)
     if (R.nunit >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "work list too large");
     R.np = std::max<int64_t>(R.npts, 1);
@@ -289,7 +299,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_FINE, sizeof(CfFine) * std::max<size_t>(1, H.fine.size())));
     CF_TRY(C->ensure(B_STENCIL, sizeof(CfStencil) * H.stencil.size()));
     CF_TRY(C->ensure(B_JOBS, sizeof(CfJobDesc) * njobs));
-    CF_TRY(C->ensure(B_CNT, 4 * (size_t)(R.ncell_all + 1)));
+    CF_TRY(C->ensure(B_CNT, 4 * (size_t)(R.nfine + 1)));
+    CF_TRY(C->ensure(B_FSTART, 4 * (size_t)(R.nfine + 1)));
     CF_TRY(C->ensure(B_CSTART, 4 * (size_t)(R.ncell_all + 1)));
     CF_TRY(C->ensure(B_CELLID, 4 * (size_t)R.np));
     CF_TRY(C->ensure(B_SLOT, 4 * (size_t)R.np));
@@ -298,7 +309,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_ORIG, 4 * (size_t)R.np));
     CF_TRY(C->ensure(B_CBOX, 24 * (size_t)R.ncell_all));
     if (D.f64lo) CF_TRY(C->ensure(B_PLO, 32 * (size_t)R.np));
-    CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.ncell_all, R.nunit))));
+    CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.nfine, R.nunit))));
     CF_TRY(C->ensure(B_ICNT, 4 * (size_t)std::max<int64_t>(R.nunit, 1)));
     CF_TRY(C->ensure(B_IOFF, 4 * (size_t)(R.nunit + 1)));
     CF_TRY(C->ensure(B_MISC, 4096));
@@ -354,14 +365,17 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     const CfJobDesc *djobs = (const CfJobDesc *)C->buf[B_JOBS].p;
     uint32_t *cnt = (uint32_t *)C->buf[B_CNT].p, *cstart = (uint32_t *)C->buf[B_CSTART].p;
     uint32_t *misc = (uint32_t *)C->buf[B_MISC].p;
-    CF_CU(cudaMemsetAsync(cnt, 0, 4 * (size_t)R.ncell_all, st), "memset counts");
+    uint32_t *fstart = (uint32_t *)C->buf[B_FSTART].p;
+    CF_CU(cudaMemsetAsync(cnt, 0, 4 * (size_t)R.nfine, st), "memset counts");
     CF_CU(cudaMemsetAsync(misc, 0, 4096, st), "memset misc");
-    CF_CU(cfb_assign(dplan, dsets, R.nsets, R.np, cnt, (uint32_t *)C->buf[B_CELLID].p, (uint32_t *)C->buf[B_SLOT].p, st),
+    CF_CU(cfb_assign(dplan, dsets, R.nsets, R.np, R.sub, cnt, (uint32_t *)C->buf[B_CELLID].p,
+                     (uint32_t *)C->buf[B_SLOT].p, st),
           "assign");
-    CF_CU(cfb_scan(cnt, cstart, R.ncell_all, (uint32_t *)C->buf[B_SCAN].p, st), "scan cells");
-    CF_CU(cfb_scatter(dplan, dsets, R.nsets, R.np, cstart, (uint32_t *)C->buf[B_CELLID].p, (uint32_t *)C->buf[B_SLOT].p,
-                      (float4 *)C->buf[B_PA].p, (float4 *)C->buf[B_PB].p, (float4 *)C->buf[B_PLO].p,
-                      (uint32_t *)C->buf[B_ORIG].p, st),
+    CF_CU(cfb_scan(cnt, fstart, R.nfine, (uint32_t *)C->buf[B_SCAN].p, st), "scan cells");
+    CF_CU(cfb_cell_starts(fstart, R.ncell_all, R.sub, cstart, st), "cell starts");
+    CF_CU(cfb_scatter(dplan, dsets, R.nsets, R.np, R.sub, fstart, (uint32_t *)C->buf[B_CELLID].p,
+                      (uint32_t *)C->buf[B_SLOT].p, (float4 *)C->buf[B_PA].p, (float4 *)C->buf[B_PB].p,
+                      (float4 *)C->buf[B_PLO].p, (uint32_t *)C->buf[B_ORIG].p, st),
           "scatter");
     const float *cbox = nullptr;
     if (C->opt[CF_OPT_CELL_PRUNE] == 0) {
@@ -377,7 +391,7 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
                     nullptr, 0, nullptr, st),
           "items count");
     CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, st), "scan items");
-    C->launches += 9;   // assign, 3 scan, scatter, items count, 3 scan
+    C->launches += 10;   // assign, 3 scan, cell starts, scatter, items count, 3 scan
     return CF_OK;
 }
 
@@ -395,7 +409,8 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     CF_CU(cudaMemsetAsync(misc, 0, 16, st), "memset");
     CF_CU(cudaMemsetAsync(evaluated, 0, 8, st), "memset");
     CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, (const uint32_t *)C->buf[B_CSTART].p,
-                    R.cbox, R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated, st),
+                    R.cbox, R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap,
+                    evaluated, st),
           "items emit");
     CF_CU(cudaMemsetAsync(C->buf[B_HCNT].p, 0, 8 * R.hsz, st), "memset");
     CF_CU(cudaMemsetAsync(C->buf[B_HW].p, 0, 8 * R.hsz, st), "memset");

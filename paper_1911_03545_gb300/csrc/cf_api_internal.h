@@ -12,7 +12,7 @@
 enum CfBuf {
     B_IN, B_SETS, B_BBOX, B_PLAN, B_LUT, B_FINE, B_STENCIL, B_JOBS, B_CNT, B_CSTART, B_CELLID, B_SLOT,
     B_PA, B_PB, B_PLO, B_ORIG, B_SCAN, B_ICNT, B_IOFF, B_ITEMS, B_HCNT, B_HW, B_HR, B_QUEUE, B_WSQ, B_MISC, B_ORIGIN,
-    B_CBOX, B_COUNT_
+    B_CBOX, B_FSTART, B_COUNT_
 };
 
 struct DeviceGuard {
@@ -47,6 +47,8 @@ struct CfRun {
     int nsets = 0, njobs = 0;
     int64_t npts = 0, nmax = 0, np = 1, ncell = 0, ncell_all = 0, nst = 0, nunit = 0;
     const float *cbox = nullptr;   // cell boxes for pruning (nullptr: every stencil neighbour)
+    int sub = 1;                   // Morton sub-cells per axis inside a cell (1, 2, 4)
+    int64_t nfine = 0;             // ncell_all * sub^3 counting-sort keys
     size_t nslot = 0, hsz = 0;
     bool self_pairs = false;
     uint32_t qcap = 0, items_cap = 0;

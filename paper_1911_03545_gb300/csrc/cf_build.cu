@@ -73,24 +73,53 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
 }
 
 // ---------------------------------------------------------------------------------------------
-// Cell assignment (Sec. 4.1, Eq. 3): cell = (ix*ny + iy)*nz + iz; the rank within the cell comes
-// from an atomic counter.
+// Cell assignment (Sec. 4.1, Eq. 3): cell = (ix*ny + iy)*nz + iz.  Inside its cell a point also
+// gets one of sub^3 sub-cells (sub = 1, 2 or 4 per axis) in Morton order, and the counting sort
+// runs on the key cell * sub^3 + sub-cell: every cell stays contiguous and its points come out in
+// spatial order, so 32 consecutive points of a cell are spatially compact.  The rank within the
+// key comes from an atomic counter.
 // ---------------------------------------------------------------------------------------------
-__global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
-                                 uint32_t *__restrict__ count, uint32_t *__restrict__ cellid,
+__device__ __forceinline__ uint32_t cf_morton3(uint32_t x, uint32_t y, uint32_t z, int sub)
+{
+    if (sub == 2) return (x << 2) | (y << 1) | z;
+    // sub == 4: interleave two bits per axis, high bits first
+    return (((x >> 1) & 1u) << 5) | (((y >> 1) & 1u) << 4) | (((z >> 1) & 1u) << 3) | ((x & 1u) << 2) |
+           ((y & 1u) << 1) | (z & 1u);
+}
+
+__global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets, int sub,
+                                 uint32_t *__restrict__ count, uint32_t *__restrict__ key,
                                  uint32_t *__restrict__ slot)
 {
     const CfSetDesc S = sets[blockIdx.y];
     const CfGrid &g = plan->g;
+    const uint32_t ns = (uint32_t)(sub * sub * sub);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
-        int ix = cf_cell_axis(g, 0, cf_load(S.x, S.dtype, i));
-        int iy = cf_cell_axis(g, 1, cf_load(S.y, S.dtype, i));
-        int iz = cf_cell_axis(g, 2, cf_load(S.z, S.dtype, i));
-        uint32_t c = (uint32_t)((ix * g.n[1] + iy) * g.n[2] + iz);
+        const double x[3] = {cf_load(S.x, S.dtype, i), cf_load(S.y, S.dtype, i), cf_load(S.z, S.dtype, i)};
+        int ia[3];
+        uint32_t sa[3];
+        for (int a = 0; a < 3; a++) {
+            const double t = (x[a] - g.lo[a]) * g.inv[a];
+            int c = (int)floor(t);
+            c = c < 0 ? 0 : (c > g.n[a] - 1 ? g.n[a] - 1 : c);
+            ia[a] = c;
+            int s = (int)((t - (double)c) * sub);
+            sa[a] = (uint32_t)(s < 0 ? 0 : (s > sub - 1 ? sub - 1 : s));
+        }
+        const uint32_t c = (uint32_t)((ia[0] * g.n[1] + ia[1]) * g.n[2] + ia[2]);
+        const uint32_t k = ((uint32_t)S.cbeg + c) * ns + (sub > 1 ? cf_morton3(sa[0], sa[1], sa[2], sub) : 0u);
         int64_t p = S.pbeg + i;
-        cellid[p] = c;
-        slot[p] = atomicAdd(count + S.cbeg + c, 1u);
+        key[p] = k;
+        slot[p] = atomicAdd(count + k, 1u);
     }
+}
+
+// cell start of every cell from the start of its first sub-cell (and the total at the end)
+__global__ void cf_cell_starts_kernel(const uint32_t *__restrict__ fstart, int64_t ncell_all, uint32_t ns,
+                                      uint32_t *__restrict__ cell_start)
+{
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ncell_all; c += (int64_t)gridDim.x * blockDim.x)
+        cell_start[c] = fstart[c * ns];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -185,7 +214,7 @@ __global__ void cf_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_
 // negated, duplicated), the FP64 residual plo when requested, and the original index.
 // ---------------------------------------------------------------------------------------------
 __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
-                                  const uint32_t *__restrict__ cell_start, const uint32_t *__restrict__ cellid,
+                                  uint32_t ns, const uint32_t *__restrict__ fstart, const uint32_t *__restrict__ key,
                                   const uint32_t *__restrict__ slot, float4 *__restrict__ pa,
                                   float4 *__restrict__ pb, float4 *__restrict__ plo,
                                   uint32_t *__restrict__ orig)
@@ -195,11 +224,12 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
     const int lo = plan->f64lo;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t p = S.pbeg + i;
-        uint32_t c = cellid[p];
+        const uint32_t k = key[p];
+        const uint32_t c = k / ns - (uint32_t)S.cbeg;
         int iz = c % g.n[2];
         int iy = (c / g.n[2]) % g.n[1];
         int ix = c / (g.n[2] * g.n[1]);
-        int64_t dst = cell_start[S.cbeg + c] + slot[p];
+        int64_t dst = fstart[k] + slot[p];
         double X = cf_load(S.x, S.dtype, i) - cf_origin(plan, 0, ix);
         double Y = cf_load(S.y, S.dtype, i) - cf_origin(plan, 1, iy);
         double Z = cf_load(S.z, S.dtype, i) - cf_origin(plan, 2, iz);
@@ -377,7 +407,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
         }
         if (mode == 0 && lane == 0) counts[u] = total;
     }
-    if (mode == 1) {
+    if (mode == 1 && evaluated) {
         for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(CF_FULL, ev, o);
         if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evaluated, ev);
     }
@@ -415,11 +445,18 @@ cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned lo
     return cudaGetLastError();
 }
 
-cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, uint32_t *count,
-                       uint32_t *cellid, uint32_t *slot, cudaStream_t st)
+cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
+                       uint32_t *count, uint32_t *key, uint32_t *slot, cudaStream_t st)
 {
     dim3 grid(blocks_for(nmax, 256, 4096), nsets);
-    cf_assign_kernel<<<grid, 256, 0, st>>>(plan, sets, count, cellid, slot);
+    cf_assign_kernel<<<grid, 256, 0, st>>>(plan, sets, sub, count, key, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t cfb_cell_starts(const uint32_t *fstart, int64_t ncell_all, int sub, uint32_t *cell_start, cudaStream_t st)
+{
+    cf_cell_starts_kernel<<<blocks_for(ncell_all + 1, 256, 4096), 256, 0, st>>>(fstart, ncell_all,
+                                                                               (uint32_t)(sub * sub * sub), cell_start);
     return cudaGetLastError();
 }
 
@@ -436,12 +473,13 @@ cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp
     return cudaGetLastError();
 }
 
-cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax,
-                        const uint32_t *cell_start, const uint32_t *cellid, const uint32_t *slot, float4 *pa,
+cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
+                        const uint32_t *fstart, const uint32_t *key, const uint32_t *slot, float4 *pa,
                         float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st)
 {
     dim3 grid(blocks_for(nmax, 256, 4096), nsets);
-    cf_scatter_kernel<<<grid, 256, 0, st>>>(plan, sets, cell_start, cellid, slot, pa, pb, plo, orig);
+    cf_scatter_kernel<<<grid, 256, 0, st>>>(plan, sets, (uint32_t)(sub * sub * sub), fstart, key, slot, pa, pb, plo,
+                                            orig);
     return cudaGetLastError();
 }
 

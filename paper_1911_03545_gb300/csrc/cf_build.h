@@ -5,12 +5,15 @@
 #include "cf_internal.h"
 
 cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st);
-cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, uint32_t *count,
-                       uint32_t *cellid, uint32_t *slot, cudaStream_t st);
+// key = cell * sub^3 + Morton sub-cell (sub = 1, 2, 4): the counting-sort key of every point
+cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
+                       uint32_t *count, uint32_t *key, uint32_t *slot, cudaStream_t st);
+// cell_start[c] = fstart[c * sub^3] for c in [0, ncell_all]
+cudaError_t cfb_cell_starts(const uint32_t *fstart, int64_t ncell_all, int sub, uint32_t *cell_start, cudaStream_t st);
 int64_t cfb_scan_tmp_words(int64_t n);
 cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st);
-cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax,
-                        const uint32_t *cell_start, const uint32_t *cellid, const uint32_t *slot, float4 *pa,
+cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
+                        const uint32_t *fstart, const uint32_t *key, const uint32_t *slot, float4 *pa,
                         float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st);
 // tight point bounding box per cell (6 floats: lo xyz, hi xyz, cell-relative), for cell-pair pruning
 cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const float4 *pa, const float4 *pb, float *box,

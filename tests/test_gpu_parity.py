@@ -220,7 +220,8 @@ def test_options_do_not_change_results(ctx):
     kw = dict(autocorr=True, periodic=True, box=40.0, weighted=True, ravg=True)
     exp = oracle.count("r", edges, d, **kw)
     for opt, val in ((cf.CF_OPT_TILE, 64), (cf.CF_OPT_JCHUNK, 37), (cf.CF_OPT_WARPS, 2), (cf.CF_OPT_CTAS_PER_SM, 1),
-                     (cf.CF_OPT_QUEUE, 1), (cf.CF_OPT_VARIANT, 2), (cf.CF_OPT_VARIANT, 1)):
+                     (cf.CF_OPT_QUEUE, 1), (cf.CF_OPT_VARIANT, 2), (cf.CF_OPT_VARIANT, 1), (cf.CF_OPT_CELL_ORDER, 1),
+                     (cf.CF_OPT_CELL_ORDER, 2), (cf.CF_OPT_CELL_ORDER, 4), (cf.CF_OPT_CELL_PRUNE, 1)):
         cf.cf_set_option(ctx, opt, val)
         try:
             got = gpu_count(ctx, "r", edges, d, **kw)
