@@ -11,8 +11,9 @@ Knobs (all results are identical across them; only speed changes):
   noprune 1 visits every stencil neighbour; 0 skips cell pairs whose points' bounding boxes are
           farther apart than the largest edge (costs one pass over the points)
 
-The tuner times `cf_count` on the caller's own catalogue with each candidate (a coordinate
-descent from the default), keeps the fastest, and caches it in a JSON file keyed by device name,
+The tuner times `cf_count` on the caller's own catalogue with each candidate (coordinate descent
+from the default, best of 3 runs per candidate, repeated while a pass still improves, at most
+twice), keeps the fastest, and caches it in a JSON file keyed by device name,
 kind, options and an occupancy class (log2 of the mean number of points per Rmax cell).  The cache
 path is $CF_TUNE_CACHE, else ~/.cache/cf_gb300_tune.json.
 """
@@ -73,8 +74,8 @@ def _time(ctx, p, d1, d2, reps: int) -> float:
     return best
 
 
-def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, reps: int = 2,
-         use_cache: bool = True, log=None) -> dict:
+def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, reps: int = 3,
+         passes: int = 2, use_cache: bool = True, log=None) -> dict:
     """Return the best configuration for this workload (and leave it applied on ctx)."""
     key = _key(device_name, p, npoints or 1)
     path = cache_path()
@@ -94,19 +95,24 @@ def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, rep
     _time(ctx, p, d1, d2, 1)                      # warm up
     best_t = _time(ctx, p, d1, d2, reps)
     trials = [(dict(cfg), best_t)]
-    for knob, values in KNOBS.items():
-        for v in values:
-            if v == cfg[knob]:
-                continue
-            cand = dict(cfg)
-            cand[knob] = v
-            apply(ctx, cand)
-            t = _time(ctx, p, d1, d2, reps)
-            trials.append((dict(cand), t))
-            if log:
-                log(f"tune {cand} {t * 1e3:.3f} ms")
-            if t < best_t:
-                best_t, cfg = t, cand
+    # coordinate descent, repeated: a knob's best value can change once later knobs have moved
+    for _ in range(passes):
+        moved = False
+        for knob, values in KNOBS.items():
+            for v in values:
+                if v == cfg[knob]:
+                    continue
+                cand = dict(cfg)
+                cand[knob] = v
+                apply(ctx, cand)
+                t = _time(ctx, p, d1, d2, reps)
+                trials.append((dict(cand), t))
+                if log:
+                    log(f"tune {cand} {t * 1e3:.3f} ms")
+                if t < best_t:
+                    best_t, cfg, moved = t, cand, True
+        if not moved:
+            break
     apply(ctx, cfg)
     if use_cache:
         cache[key] = {"cfg": cfg, "ms": best_t * 1e3,
