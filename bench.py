@@ -45,6 +45,8 @@ WORKLOADS = {
                          "14 log rp bins 0.1-25, pimax=40 with 40 pi bins",
     "sphere_theta_1m": "DD(theta) auto, non-periodic, N=1,000,000 unit vectors (RA 0-90, DEC -10..30 deg) float32, "
                        "20 log bins 0.001-1 deg",
+    "polar_theta_1m": "DD(theta) auto, non-periodic, N=1,000,000 unit vectors uniform on the polar cap DEC 60..90 deg "
+                      "float32, 20 log bins 0.001-1 deg",
 }
 
 

@@ -165,6 +165,10 @@ def workload(name: str, scale: float = 1.0) -> Workload:
                             pimax=40.0, npibins=40)
         return Workload(name, kind, True, True, L, log_edges(0.1, 25.0, 14), d,
                         pimax=40.0, npibins=40)
+    if name == "polar_theta_1m":
+        n = max(8, int(1000000 * scale))
+        return Workload(name, "theta", True, False, 0.0, log_edges(0.001, 1.0, 20),
+                        sphere_patch(n, 0.0, 360.0, 60.0, 90.0, 1006))
     if name == "sphere_theta_1m":
         n = max(8, int(1000000 * scale))
         return Workload(name, "theta", True, False, 0.0, log_edges(0.001, 1.0, 20),

@@ -152,7 +152,10 @@ typedef enum {
     CF_OPT_CELL_ORDER = 12,  /* points inside a cell are ordered by Morton sub-cell: 0 (default) picks
                                 the sub-cells per axis (4, 2 or 1) from the cell count; 1, 2 or 4 pin
                                 it.  Results are the same for every order */
-    CF_OPT_COUNT_ = 13
+    CF_OPT_THETA_GRID = 13,  /* DD(theta) cell list: 0 (default) a 3-D grid over the unit vectors,
+                                1 declination bands x right-ascension cells (Sec. 4.1.2), for wide or
+                                near-polar footprints.  Results are the same for both */
+    CF_OPT_COUNT_ = 14
 } cf_option;
 cf_status cf_set_option(void *ctx, int option, int64_t value);
 

@@ -239,11 +239,15 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_CU(cudaMemcpyAsync(C->hpin, C->buf[B_BBOX].p, 64 * (size_t)nsets, cudaMemcpyDeviceToHost, st), "bbox readback");
     CF_CU(cudaStreamSynchronize(st), "bbox sync");
     double bbox[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    double norm_dev = 0.0;   // largest | |v|^2 - 1 | over the points
     {
         const unsigned long long *bb = (const unsigned long long *)C->hpin;
         for (int s = 0; s < nsets; s++) {
             if (R.sets[s].n == 0) continue;
             if (bb[8 * s + 6]) return C->fail(CF_ERR_ARG, "non-finite coordinate or weight");
+            double nd;
+            std::memcpy(&nd, &bb[8 * s + 7], 8);
+            norm_dev = std::max(norm_dev, nd);
             for (int a = 0; a < 3; a++) {
                 double lo = dkey_to_double(bb[8 * s + a]), hi = dkey_to_double(bb[8 * s + 3 + a]);
                 if (p->periodic && (lo < 0.0 || hi > p->box[a]))
@@ -258,13 +262,16 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     }
 
     // ---- plan ----
+    const bool angular = p->kind == CF_DD_THETA && C->opt[CF_OPT_THETA_GRID] == 1;
+    if (angular && norm_dev > 2e-3)
+        return C->fail(CF_ERR_ARG, "the angular grid needs unit vectors (|v| within 1e-3 of 1)");
     CfHostPlan &H = R.plan;
     int refine[3];
     for (int a = 0; a < 3; a++)
         refine[a] = p->refine[a] > 0 ? p->refine[a] : (C->opt[CF_OPT_REFINE] > 0 ? (int)C->opt[CF_OPT_REFINE] : 1);
     int tile = C->opt[CF_OPT_TILE] > 0 ? (int)std::min<int64_t>(128, std::max<int64_t>(32, C->opt[CF_OPT_TILE])) : 128;
     int jchunk = C->opt[CF_OPT_JCHUNK] > 0 ? (int)std::min<int64_t>(CFI_JMAX, C->opt[CF_OPT_JCHUNK]) : CFI_JMAX;
-    rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err);
+    rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err, angular ? 1 : 0);
     if (rc) return C->fail(rc, err);
     CfDevPlan &D = H.d;
     D.nsets = nsets;
@@ -294,6 +301,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     // ---- device buffers (allocated here so that the device phases never allocate) ----
     CF_TRY(C->ensure(B_ORIGIN, sizeof(double) * H.origin.size()));
     D.origin = (const double *)C->buf[B_ORIGIN].p;
+    CF_TRY(C->ensure(B_BANDS, sizeof(CfBand) * std::max<size_t>(1, H.bands.size())));
+    D.band = (const CfBand *)C->buf[B_BANDS].p;
     CF_TRY(C->ensure(B_PLAN, sizeof(CfDevPlan)));
     CF_TRY(C->ensure(B_LUT, sizeof(uint16_t) * H.lut.size()));
     CF_TRY(C->ensure(B_FINE, sizeof(CfFine) * std::max<size_t>(1, H.fine.size())));
@@ -323,6 +332,10 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
 
     CF_CU(cudaMemcpyAsync(C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size(), cudaMemcpyHostToDevice,
                           st), "origins");
+    if (!H.bands.empty())
+        CF_CU(cudaMemcpyAsync(C->buf[B_BANDS].p, H.bands.data(), sizeof(CfBand) * H.bands.size(),
+                              cudaMemcpyHostToDevice, st),
+              "bands");
     CF_CU(cudaMemcpyAsync(C->buf[B_PLAN].p, &D, sizeof(CfDevPlan), cudaMemcpyHostToDevice, st), "plan");
     CF_CU(cudaMemcpyAsync(C->buf[B_LUT].p, H.lut.data(), sizeof(uint16_t) * H.lut.size(), cudaMemcpyHostToDevice, st),
           "lut");

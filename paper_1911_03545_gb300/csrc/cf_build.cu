@@ -10,16 +10,22 @@
 __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long long *__restrict__ out)
 {
     const CfSetDesc S = sets[blockIdx.y];
-    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0}, bad = 0;
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0}, bad = 0, nrm = 0;
     const void *P[3] = {S.x, S.y, S.z};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+        double r2 = 0.0;
         for (int a = 0; a < 3; a++) {
             double v = cf_load(P[a], S.dtype, i);
             if (!isfinite(v)) { bad++; continue; }
+            r2 += v * v;
             unsigned long long k = cf_dkey(v);
             mn[a] = k < mn[a] ? k : mn[a];
             mx[a] = k > mx[a] ? k : mx[a];
         }
+        // largest | |v|^2 - 1 | (unit vectors for the angular grid of DD(theta)); a non-negative
+        // double's bits order like the value
+        const unsigned long long d = (unsigned long long)__double_as_longlong(fabs(r2 - 1.0));
+        nrm = d > nrm ? d : nrm;
         if (S.w) {
             double w = cf_load(S.w, S.dtype, i);
             if (!isfinite(w)) bad++;
@@ -33,9 +39,11 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
             mx[a] = t > mx[a] ? t : mx[a];
         }
         bad += __shfl_xor_sync(CF_FULL, bad, o);
+        const unsigned long long t = __shfl_xor_sync(CF_FULL, nrm, o);
+        nrm = t > nrm ? t : nrm;
     }
     // block reduction through shared memory, then one atomic per block and value
-    __shared__ unsigned long long red[7][32];
+    __shared__ unsigned long long red[8][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) {
         for (int a = 0; a < 3; a++) {
@@ -43,15 +51,17 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
             red[3 + a][w] = mx[a];
         }
         red[6][w] = bad;
+        red[7][w] = nrm;
     }
     __syncthreads();
     if (w == 0) {
-        unsigned long long v[7];
+        unsigned long long v[8];
         for (int a = 0; a < 3; a++) {
             v[a] = lane < nw ? red[a][lane] : ~0ull;
             v[3 + a] = lane < nw ? red[3 + a][lane] : 0ull;
         }
         v[6] = lane < nw ? red[6][lane] : 0ull;
+        v[7] = lane < nw ? red[7][lane] : 0ull;
         for (int o = 16; o; o >>= 1) {
             for (int a = 0; a < 3; a++) {
                 unsigned long long t = __shfl_xor_sync(CF_FULL, v[a], o);
@@ -60,6 +70,8 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
                 v[3 + a] = t > v[3 + a] ? t : v[3 + a];
             }
             v[6] += __shfl_xor_sync(CF_FULL, v[6], o);
+            const unsigned long long t = __shfl_xor_sync(CF_FULL, v[7], o);
+            v[7] = t > v[7] ? t : v[7];
         }
         if (lane == 0) {
             unsigned long long *o = out + blockIdx.y * 8;
@@ -68,6 +80,7 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
                 atomicMax(o + 3 + a, v[3 + a]);
             }
             if (v[6]) atomicAdd(o + 6, v[6]);
+            atomicMax(o + 7, v[7]);
         }
     }
 }
@@ -96,17 +109,39 @@ __global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSet
     const uint32_t ns = (uint32_t)(sub * sub * sub);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
         const double x[3] = {cf_load(S.x, S.dtype, i), cf_load(S.y, S.dtype, i), cf_load(S.z, S.dtype, i)};
-        int ia[3];
-        uint32_t sa[3];
-        for (int a = 0; a < 3; a++) {
-            const double t = (x[a] - g.lo[a]) * g.inv[a];
-            int c = (int)floor(t);
-            c = c < 0 ? 0 : (c > g.n[a] - 1 ? g.n[a] - 1 : c);
-            ia[a] = c;
-            int s = (int)((t - (double)c) * sub);
-            sa[a] = (uint32_t)(s < 0 ? 0 : (s > sub - 1 ? sub - 1 : s));
+        uint32_t sa[3] = {0u, 0u, 0u};
+        uint32_t c;
+        if (plan->ang) {
+            // angular grid: declination band of the normalised vector (a vector off unit length then
+            // stays within its cell's box scaled by |v|), then right-ascension cell in [0, 2 pi)
+            const double nv = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+            const double dec = nv > 0.0 ? asin(fmin(1.0, fmax(-1.0, x[2] / nv))) : 0.0;
+            double ra = atan2(x[1], x[0]);
+            if (ra < 0.0) ra += 2.0 * M_PI;
+            int b = (int)floor((dec - plan->adlo) / plan->ah);
+            b = b < 0 ? 0 : (b > plan->nband - 1 ? plan->nband - 1 : b);
+            const CfBand B = plan->band[b];
+            const double tr = ra / B.w;
+            int r = (int)floor(tr);
+            r = r < 0 ? 0 : (r > B.nra - 1 ? B.nra - 1 : r);
+            c = (uint32_t)(B.base + r);
+            const double fr[2] = {(dec - B.dlo) / (B.dhi - B.dlo), tr - (double)r};
+            for (int a = 0; a < 2; a++) {
+                const int s = (int)(fr[a] * sub);
+                sa[a] = (uint32_t)(s < 0 ? 0 : (s > sub - 1 ? sub - 1 : s));
+            }
+        } else {
+            int ia[3];
+            for (int a = 0; a < 3; a++) {
+                const double t = (x[a] - g.lo[a]) * g.inv[a];
+                int cc = (int)floor(t);
+                cc = cc < 0 ? 0 : (cc > g.n[a] - 1 ? g.n[a] - 1 : cc);
+                ia[a] = cc;
+                const int s = (int)((t - (double)cc) * sub);
+                sa[a] = (uint32_t)(s < 0 ? 0 : (s > sub - 1 ? sub - 1 : s));
+            }
+            c = (uint32_t)((ia[0] * g.n[1] + ia[1]) * g.n[2] + ia[2]);
         }
-        const uint32_t c = (uint32_t)((ia[0] * g.n[1] + ia[1]) * g.n[2] + ia[2]);
         const uint32_t k = ((uint32_t)S.cbeg + c) * ns + (sub > 1 ? cf_morton3(sa[0], sa[1], sa[2], sub) : 0u);
         int64_t p = S.pbeg + i;
         key[p] = k;
@@ -230,9 +265,9 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
         int iy = (c / g.n[2]) % g.n[1];
         int ix = c / (g.n[2] * g.n[1]);
         int64_t dst = fstart[k] + slot[p];
-        double X = cf_load(S.x, S.dtype, i) - cf_origin(plan, 0, ix);
-        double Y = cf_load(S.y, S.dtype, i) - cf_origin(plan, 1, iy);
-        double Z = cf_load(S.z, S.dtype, i) - cf_origin(plan, 2, iz);
+        double X = cf_load(S.x, S.dtype, i) - cf_cell_origin(plan, 0, (int)c, ix);
+        double Y = cf_load(S.y, S.dtype, i) - cf_cell_origin(plan, 1, (int)c, iy);
+        double Z = cf_load(S.z, S.dtype, i) - cf_cell_origin(plan, 2, (int)c, iz);
         float xf = (float)X, yf = (float)Y, zf = (float)Z;
         float w = S.w ? (float)cf_load(S.w, S.dtype, i) : 1.0f;
         pa[dst] = make_float4(-xf, -xf, -yf, -yf);
@@ -313,31 +348,72 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
             const int ci[3] = {c / (g.n[2] * g.n[1]), (c / g.n[2]) % g.n[1], c % g.n[2]};
             const uint32_t nti = (na + tile - 1) / tile;
             const uint32_t base = mode == 1 ? offsets[u] : 0u;
-            for (int s0 = 0; s0 < nst; s0 += 32) {
+            // target cells: the 3-D stencil, or for the angular grid the RA cells of the bands
+            // within k of this one whose RA range comes within the search angle: two points at
+            // declinations up to dm apart by an angle <= t differ in RA by at most
+            // 2 asin(sin(t / 2) / cos dm) (from the haversine formula)
+            int ncand = nst, bsel[2 * CFI_MAX_ANG_K + 1], blo[2 * CFI_MAX_ANG_K + 1], bn[2 * CFI_MAX_ANG_K + 1], nbs = 0;
+            if (plan->ang) {
+                const int ab = cf_band_of(plan, c);
+                const CfBand Bi = plan->band[ab];
+                const int ar = c - Bi.base, k = g.k[0];
+                const double sh = sin(0.5 * plan->tsearch);
+                ncand = 0;
+                for (int b2 = max(0, ab - k); b2 <= min(plan->nband - 1, ab + k); b2++) {
+                    const CfBand Bj = plan->band[b2];
+                    const double dm = fmax(fmax(fabs(Bi.dlo), fabs(Bi.dhi)), fmax(fabs(Bj.dlo), fabs(Bj.dhi)));
+                    const double cm = cos(fmin(dm, 0.5 * M_PI));
+                    int lo = 0, n = Bj.nra;
+                    if (sh < cm) {
+                        const double da = 2.0 * asin(sh / cm) * (1.0 + 1e-9) + 1e-12;
+                        lo = (int)floor((ar * Bi.w - da) / Bj.w);
+                        n = (int)floor(((ar + 1) * Bi.w + da) / Bj.w) - lo + 1;
+                        if (n >= Bj.nra) { lo = 0; n = Bj.nra; }
+                    }
+                    bsel[nbs] = b2;
+                    blo[nbs] = lo;
+                    bn[nbs] = n;
+                    nbs++;
+                    ncand += n;
+                }
+            }
+            for (int s0 = 0; s0 < ncand; s0 += 32) {
                 const int s = s0 + (int)lane;
                 uint32_t cnt = 0, jb = 0, nb = 0, ntj = 0, tsj = 0;
                 bool diag = false;
                 double shift[3] = {0.0, 0.0, 0.0};
-                if (s < nst) {
-                    int tj[3];
+                if (s < ncand) {
+                    int ct = 0;
                     bool ok = true;
-                    for (int a = 0; a < 3; a++) {
-                        int v = ci[a] + stencil[s].d[a];
-                        double delta = 0.0;        // image of the j point: x_j + delta
-                        if (g.wrap[a]) {
-                            v %= g.n[a];
-                        } else if (g.periodic) {
-                            if (v < 0) { v += g.n[a]; delta = -g.L[a]; }
-                            else if (v >= g.n[a]) { v -= g.n[a]; delta = g.L[a]; }
-                        } else if (v < 0 || v >= g.n[a]) {
-                            ok = false;
+                    if (plan->ang) {
+                        int q = 0, off = s;
+                        while (off >= bn[q]) { off -= bn[q]; q++; }
+                        const CfBand Bj = plan->band[bsel[q]];
+                        int rr = (blo[q] + off) % Bj.nra;
+                        if (rr < 0) rr += Bj.nra;
+                        ct = Bj.base + rr;
+                        if (mode == 1 || prune)
+                            for (int a = 0; a < 3; a++) shift[a] = plan->origin[3 * c + a] - plan->origin[3 * ct + a];
+                    } else {
+                        int tj[3];
+                        for (int a = 0; a < 3; a++) {
+                            int v = ci[a] + stencil[s].d[a];
+                            double delta = 0.0;        // image of the j point: x_j + delta
+                            if (g.wrap[a]) {
+                                v %= g.n[a];
+                            } else if (g.periodic) {
+                                if (v < 0) { v += g.n[a]; delta = -g.L[a]; }
+                                else if (v >= g.n[a]) { v -= g.n[a]; delta = g.L[a]; }
+                            } else if (v < 0 || v >= g.n[a]) {
+                                ok = false;
+                            }
+                            tj[a] = v;
+                            if (ok && (mode == 1 || prune))
+                                shift[a] = cf_origin(plan, a, ci[a]) - cf_origin(plan, a, v) - delta;
                         }
-                        tj[a] = v;
-                        if (ok && (mode == 1 || prune))
-                            shift[a] = cf_origin(plan, a, ci[a]) - cf_origin(plan, a, v) - delta;
+                        ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
                     }
                     if (ok) {
-                        const int ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
                         if (!(J.autoc && ct < c)) {
                             jb = cell_start[B.cbeg + ct];
                             nb = cell_start[B.cbeg + ct + 1] - jb;

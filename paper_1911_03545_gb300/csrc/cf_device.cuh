@@ -64,6 +64,22 @@ __device__ __forceinline__ float f_sqrt_approx(float x)
 
 // ---- cell origin: precomputed on the host (cfp_origin in cf_plan.cpp) ----
 __device__ __forceinline__ double cf_origin(const CfDevPlan *plan, int a, int i) { return plan->origin[plan->ooff[a] + i]; }
+// origin of cell c on axis a: the 3-D grid's per-axis table (index ia), or the angular grid's per-cell one
+__device__ __forceinline__ double cf_cell_origin(const CfDevPlan *plan, int a, int c, int ia)
+{
+    return plan->ang ? plan->origin[3 * c + a] : plan->origin[plan->ooff[a] + ia];
+}
+// band of a cell of the angular grid (binary search over the band bases)
+__device__ __forceinline__ int cf_band_of(const CfDevPlan *plan, int c)
+{
+    int lo = 0, hi = plan->nband - 1;
+    while (lo < hi) {
+        const int m = (lo + hi + 1) >> 1;
+        if (plan->band[m].base <= c) lo = m;
+        else hi = m - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ int cf_cell_axis(const CfGrid &g, int a, double x)
 {

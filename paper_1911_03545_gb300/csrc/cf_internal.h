@@ -94,6 +94,15 @@ struct CfStencil {         // neighbour offset per axis; wrap axes enumerate tar
     int pad;
 };
 
+#define CFI_MAX_ANG_K 4           // refinement of the angular grid (bands searched: 2k + 1)
+
+// One DEC band of the angular grid (DD(theta) alternative cell list): DEC in [dlo, dhi),
+// nra RA cells of width w (radians) over [0, 2 pi), cells base .. base + nra - 1
+struct CfBand {
+    double dlo, dhi, w;
+    int nra, base;
+};
+
 // Everything the kernels need for one call
 struct CfDevPlan {
     CfGrid g;
@@ -110,7 +119,13 @@ struct CfDevPlan {
     int nfine;             // fine entries (both LUTs)
     double pimax;
     const double *origin;  // device table of cell origins: axis a, index i at origin[ooff[a] + i]
+                           // (angular grid: cell c at origin[3 c + a])
     int ooff[3];
+    int ang;               // 1: angular grid (theta): DEC bands x RA cells instead of the 3-D grid
+    int nband;
+    const CfBand *band;    // device table of the bands
+    double adlo, ah;       // lowest band edge and band height (radians)
+    double tsearch;        // neighbour-search angle (radians): the largest edge, widened
     float cut_r;           // candidate cut on the FP32 squared separation (above the last band)
     float cut_p;           // candidate cut on the FP32 |dz| (rp-pi / wp)
     double e2[CF_MAX_BINS + 1];     // squared edges (FP64, host-computed)

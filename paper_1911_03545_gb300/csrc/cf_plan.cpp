@@ -228,8 +228,38 @@ bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint16_t> &wo
 
 }  // namespace
 
+namespace {
+
+// Origin of an interval [lo, hi] of values (largest magnitude m): 0 if it holds 0, else the multiple of
+// the float32 spacing at m nearest to 0 that still lies between 0 and every value.  x - origin is then
+// exact in float32 for every float32 x of the interval (same rule as cfp_origin).
+double origin_of_interval(double lo, double hi)
+{
+    if (lo <= 0.0 && hi >= 0.0) return 0.0;
+    const double m = std::max(std::fabs(lo), std::fabs(hi));
+    const double sp = ulp32_of_magnitude(m);
+    return lo > 0.0 ? std::floor(lo / sp) * sp : std::ceil(hi / sp) * sp;
+}
+
+// range of cos (c = 1) or sin (c = 0) over the angle interval [a0, a1] (a1 - a0 <= 2 pi)
+void trig_range(double a0, double a1, int c, double &mn, double &mx)
+{
+    auto f = [&](double a) { return c ? std::cos(a) : std::sin(a); };
+    mn = std::min(f(a0), f(a1));
+    mx = std::max(f(a0), f(a1));
+    // extrema at multiples of pi / 2 inside the interval
+    const double q = M_PI / 2;
+    for (double k = std::ceil(a0 / q); k * q <= a1; k += 1.0) {
+        const double v = f(k * q);
+        mn = std::min(mn, v);
+        mx = std::max(mx, v);
+    }
+}
+
+}  // namespace
+
 int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int f64,
-                  const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err)
+                  const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err, int angular)
 {
     CfHostPlan &H = *out;
     std::memset(&H.d, 0, sizeof(H.d));
@@ -321,15 +351,104 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
     if ((int)H.stencil.size() > CFI_MAX_STENCIL) { err = "stencil too large"; return CF_ERR_ARG; }
     G.nstencil = (int)H.stencil.size();
 
+    // ---- angular grid for DD(theta) (Sec. 4.1.2: declination bands, right-ascension cells) ----
+    // Bands of height >= tmax / k over the data's declinations; in each band RA cells at least
+    // tmax / k wide at the band's edge nearest a pole.  Each cell's origin comes from the analytic
+    // box of its (RA, DEC) patch on the unit sphere, widened for unit vectors stored in float32.
+    double Mang[3] = {0.0, 0.0, 0.0};
+    H.bands.clear();
+    D.ang = (angular && p->kind == CF_DD_THETA) ? 1 : 0;
+    if (D.ang) {
+        const double t = p->edges[p->nbins] * (M_PI / 180.0);
+        // chords are taken between the given vectors: with |v| up to 1e-3 off unit length a pair a
+        // little beyond t in angle can still be below the largest chord edge
+        const double tw = t * (1.0 + 2e-3) + 1e-9;
+        const int k = std::min(G.k[0], CFI_MAX_ANG_K);
+        G.k[0] = G.k[1] = G.k[2] = k;
+        // declinations of the normalised vectors: z / |v| differs from z by <= 1.5e-3 |z|
+        const double zlo = std::max(-1.0, bbox[2] - 2e-3 * std::fabs(bbox[2]) - 1e-6);
+        const double zhi = std::min(1.0, bbox[5] + 2e-3 * std::fabs(bbox[5]) + 1e-6);
+        const double dlo = std::asin(zlo), dhi = std::asin(zhi);
+        int nband = (int)std::floor((dhi - dlo) / tw);
+        nband = std::max(1, std::min(nband, 100000)) * k;
+        const double h = (dhi - dlo) / nband;
+        double cap = std::max(1048576.0, 8.0 * (double)npoints);
+        // RA cells of a band: at least tw / k wide where the band is narrowest (its poleward edge)
+        auto nra_of = [&](double blo, double bhi, double scale) {
+            const double dm = std::max(std::fabs(blo), std::fabs(bhi));
+            double n = std::floor(2 * M_PI * std::cos(std::min(dm, M_PI / 2)) / tw * scale);
+            return (int)std::max(1.0, std::min(n, 1e6)) * k;
+        };
+        double scale = 1.0;
+        for (int it = 0; it < 64; it++) {
+            double tot = 0;
+            for (int b = 0; b < nband; b++) tot += nra_of(dlo + b * h, dlo + (b + 1) * h, scale);
+            if (tot <= cap) break;
+            scale *= 0.8;
+        }
+        int base = 0;
+        H.origin.clear();
+        double ext[3] = {0.0, 0.0, 0.0};
+        for (int b = 0; b < nband; b++) {
+            CfBand B;
+            B.dlo = dlo + b * h;
+            B.dhi = (b == nband - 1) ? dhi : dlo + (b + 1) * h;
+            B.nra = nra_of(B.dlo, B.dhi, scale);
+            B.w = 2 * M_PI / B.nra;
+            B.base = base;
+            base += B.nra;
+            H.bands.push_back(B);
+            double cmin, cmax, zmn, zmx;
+            trig_range(B.dlo, B.dhi, 1, cmin, cmax);
+            trig_range(B.dlo, B.dhi, 0, zmn, zmx);
+            cmin = std::max(cmin, 0.0);
+            for (int r = 0; r < B.nra; r++) {
+                double ca0, ca1, sa0, sa1;
+                trig_range(r * B.w, (r + 1) * B.w, 1, ca0, ca1);
+                trig_range(r * B.w, (r + 1) * B.w, 0, sa0, sa1);
+                // x = cos(dec) cos(ra) with cos(dec) in [cmin, cmax] >= 0; likewise y with sin(ra)
+                const double lo[3] = {ca0 >= 0 ? cmin * ca0 : cmax * ca0, sa0 >= 0 ? cmin * sa0 : cmax * sa0, zmn};
+                const double hi[3] = {ca1 >= 0 ? cmax * ca1 : cmin * ca1, sa1 >= 0 ? cmax * sa1 : cmin * sa1, zmx};
+                for (int a = 0; a < 3; a++) {
+                    // widened for vectors up to 1e-3 off unit length (the library rejects more)
+                    const double l = lo[a] - 1e-3 * std::fabs(lo[a]) - 2e-6, u2 = hi[a] + 1e-3 * std::fabs(hi[a]) + 2e-6;
+                    const double o = origin_of_interval(l, u2);
+                    H.origin.push_back(o);
+                    ext[a] = std::max(ext[a], std::max(std::fabs(l - o), std::fabs(u2 - o)));
+                }
+            }
+        }
+        if (base <= 0 || (double)base > 2e9) { err = "angular grid too large"; return CF_ERR_ARG; }
+        D.nband = nband;
+        D.adlo = dlo;
+        D.ah = h;
+        D.tsearch = tw;
+        int maxra = 0;
+        for (auto &B : H.bands) maxra = std::max(maxra, B.nra);
+        G.n[0] = nband;
+        G.n[1] = maxra;
+        G.n[2] = 1;
+        G.ncell = base;
+        G.nstencil = 0;
+        H.stencil.clear();
+        for (int a = 0; a < 3; a++) {
+            G.wrap[a] = 0;
+            G.width[a] = ext[a];
+            D.ooff[a] = 0;
+            // |X_i + S| = |x_i - o_j| <= |x_i - x_j| + |x_j - o_j| for pairs near an edge
+            Mang[a] = ext[a] + 2.0 * std::sin(tw / 2) * 1.01;
+        }
+    }
+
     // ---- FP32 error model (derivation in the design doc) ----
     // stored cell-relative coordinates X are exact for float32 inputs (snapped origins);
     // float64 inputs round to float32 (epsX), or keep a lo part when ravg is requested.
     const double u = U32;
     const bool precise = D.ravg;
     for (int a = 0; a < 3; a++) {
-        double amax = std::max(std::fabs(G.lo[a]), std::fabs(G.lo[a] + extent[a]));
+        double amax = D.ang ? 1.01 : std::max(std::fabs(G.lo[a]), std::fabs(G.lo[a] + extent[a]));
         double Q = ulp32_of_magnitude(std::max(amax, 1e-300));
-        double M = G.wrap[a] ? (extent[a] + 2 * G.width[a]) : ((G.k[a] + 1) * G.width[a]);
+        double M = D.ang ? Mang[a] : (G.wrap[a] ? (extent[a] + 2 * G.width[a]) : ((G.k[a] + 1) * G.width[a]));
         M = M * 1.001 + 4 * Q;
         double epsX = 0;
         if (f64) epsX = D.f64lo ? (2 * U64 * 2 * amax + u * u * (G.width[a] + 2 * Q)) : (u * (G.width[a] + 2 * Q) + 2 * U64 * amax);

@@ -11,6 +11,8 @@ struct CfHostPlan {
     std::vector<CfFine> fine;          // fine LUT entries (both LUTs)
     std::vector<CfStencil> stencil;    // neighbour offsets after pruning
     std::vector<double> origin;        // cell origins per axis (see cfp_origin), n0 + n1 + n2 values
+                                       // (angular grid: 3 per cell)
+    std::vector<CfBand> bands;         // angular grid: the DEC bands
     double W[3];                       // largest separation a counted pair can have, per axis
     double band_r[CF_MAX_BINS + 1];    // FP32 error band of each squared edge
     double band_p[CF_MAX_PIBINS + 1];  // FP32 error band of each pi edge
@@ -26,8 +28,10 @@ void cfp_edges(const cf_params *p, double *e2, double *pe);
 // Build the plan.  bbox = {xlo, ylo, zlo, xhi, yhi, zhi} over every point set of the call;
 // npoints = total points (caps the grid); f64 = any float64 input; refine = requested factors
 // (0 = automatic); tile = max i tile (64 or 128); jchunk = max j range per work item.
+// angular = 1 (DD(theta) only): DEC bands x RA cells instead of the 3-D grid over unit vectors.
 int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int f64,
-                  const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err);
+                  const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err,
+                  int angular = 0);
 
 // Origin of cell i on an axis starting at lo with cell width w.  For float32 coordinates x in
 // the cell, x - origin is exact in float32: the origin is a multiple of the float32 spacing at
