@@ -184,7 +184,9 @@ cf_status cf_get_stats(const void *ctx, cf_stats *out);
  * classified through the same lookup table the pair kernel uses (which = 0: squared r / rp /
  * chord; which = 1: |dz|): classes[i] = bin index, 0xFE outside every bin, 0xFF within a band.
  * which = 2 / 3 classify the same way as the direct pair kernel does (an FP32 cut at the table's
- * tail, then the lookup without its upper clamp); 0xFD there would mean an index past the table. 
+ * tail, then the lookup without its upper clamp); 0xFD there would mean an index past the table.
+ * Adding 4 to `which` plans DD(theta) on the angular grid (CF_OPT_THETA_GRID = 1): grid[] then
+ * reports the bands, the most RA cells of a band, and 1. 
  * Grid and refinement: Sec. 4.1-4.2; bins in squared space: Sec. 4.7. */
 typedef struct {
     int grid[3];

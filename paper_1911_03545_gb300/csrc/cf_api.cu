@@ -299,7 +299,9 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.self_pairs = p->edges[0] == 0.0;
 
     // ---- device buffers (allocated here so that the device phases never allocate) ----
-    CF_TRY(C->ensure(B_ORIGIN, sizeof(double) * H.origin.size()));
+    // the angular grid's origins (3 per cell) are computed on the device by the build
+    const size_t norigin = D.ang ? 3 * (size_t)D.g.ncell : H.origin.size();
+    CF_TRY(C->ensure(B_ORIGIN, sizeof(double) * norigin));
     D.origin = (const double *)C->buf[B_ORIGIN].p;
     CF_TRY(C->ensure(B_BANDS, sizeof(CfBand) * std::max<size_t>(1, H.bands.size())));
     D.band = (const CfBand *)C->buf[B_BANDS].p;
@@ -330,7 +332,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_QUEUE, 16 * (size_t)R.qcap));
     CF_TRY(C->ensure_host(readback_bytes(R)));
 
-    CF_CU(cudaMemcpyAsync(C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size(), cudaMemcpyHostToDevice,
+    if (!H.origin.empty())
+        CF_CU(cudaMemcpyAsync(C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size(), cudaMemcpyHostToDevice,
                           st), "origins");
     if (!H.bands.empty())
         CF_CU(cudaMemcpyAsync(C->buf[B_BANDS].p, H.bands.data(), sizeof(CfBand) * H.bands.size(),
@@ -379,6 +382,10 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     uint32_t *cnt = (uint32_t *)C->buf[B_CNT].p, *cstart = (uint32_t *)C->buf[B_CSTART].p;
     uint32_t *misc = (uint32_t *)C->buf[B_MISC].p;
     uint32_t *fstart = (uint32_t *)C->buf[B_FSTART].p;
+    if (R.plan.d.ang) {
+        CF_CU(cfb_ang_origins(dplan, R.plan.d.g.ncell, (double *)C->buf[B_ORIGIN].p, st), "cell origins");
+        C->launches += 1;
+    }
     CF_CU(cudaMemsetAsync(cnt, 0, 4 * (size_t)R.nfine, st), "memset counts");
     CF_CU(cudaMemsetAsync(misc, 0, 4096, st), "memset misc");
     CF_CU(cfb_assign(dplan, dsets, R.nsets, R.np, R.sub, cnt, (uint32_t *)C->buf[B_CELLID].p,

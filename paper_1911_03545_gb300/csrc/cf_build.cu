@@ -112,16 +112,18 @@ __global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSet
         uint32_t sa[3] = {0u, 0u, 0u};
         uint32_t c;
         if (plan->ang) {
-            // angular grid: declination band of the normalised vector (a vector off unit length then
-            // stays within its cell's box scaled by |v|), then right-ascension cell in [0, 2 pi)
-            const double nv = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-            const double dec = nv > 0.0 ? asin(fmin(1.0, fmax(-1.0, x[2] / nv))) : 0.0;
-            double ra = atan2(x[1], x[0]);
+            // angular grid: declination band of the vector's direction (atan2 of z over the projected
+            // length: independent of |v| and well conditioned at the poles), then right-ascension
+            // cell in [0, 2 pi).  Float32 is enough: any cell choice is correct as long as the point
+            // lies in the cell's box, whose margin (2e-6) is far above these ~1e-7 errors.
+            const float xf = (float)x[0], yf = (float)x[1], zf = (float)x[2];
+            const double dec = (double)atan2f(zf, sqrtf(xf * xf + yf * yf));
+            double ra = (double)atan2f(yf, xf);
             if (ra < 0.0) ra += 2.0 * M_PI;
             int b = (int)floor((dec - plan->adlo) / plan->ah);
             b = b < 0 ? 0 : (b > plan->nband - 1 ? plan->nband - 1 : b);
-            const CfBand B = plan->band[b];
-            const double tr = ra / B.w;
+            const CfBand &B = plan->band[b];
+            const double tr = ra * B.inv_w;
             int r = (int)floor(tr);
             r = r < 0 ? 0 : (r > B.nra - 1 ? B.nra - 1 : r);
             c = (uint32_t)(B.base + r);
@@ -146,6 +148,55 @@ __global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSet
         int64_t p = S.pbeg + i;
         key[p] = k;
         slot[p] = atomicAdd(count + k, 1u);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Origins of the angular grid's cells (Sec. 4.1.2 cells on the unit sphere).  The box of a cell's
+// (RA, DEC) patch bounds x = cos(dec) cos(ra), y = cos(dec) sin(ra), z = sin(dec); widened by 0.1 %
+// + 2e-6 for float32 vectors up to 1e-3 off unit length.  Per axis the origin is 0 when the box
+// holds 0, else the multiple of the float32 spacing at the box's largest magnitude nearest to 0 that
+// still lies between 0 and every value: x - origin is then exact in float32 for every float32 x of
+// the cell (the 3-D grid's rule, cfp_origin).
+// ---------------------------------------------------------------------------------------------
+__device__ void cf_trig_range(double a0, double a1, int c, double &mn, double &mx)
+{
+    mn = c ? fmin(cos(a0), cos(a1)) : fmin(sin(a0), sin(a1));
+    mx = c ? fmax(cos(a0), cos(a1)) : fmax(sin(a0), sin(a1));
+    const double q = 0.5 * M_PI;
+    for (double k = ceil(a0 / q); k * q <= a1; k += 1.0) {
+        const int m = ((int)k % 4 + 4) % 4;   // multiples of pi / 2: cos 1, 0, -1, 0; sin 0, 1, 0, -1
+        const double v = c ? (m == 0 ? 1.0 : (m == 2 ? -1.0 : 0.0)) : (m == 1 ? 1.0 : (m == 3 ? -1.0 : 0.0));
+        mn = fmin(mn, v);
+        mx = fmax(mx, v);
+    }
+}
+
+__device__ double cf_origin_of_interval(double lo, double hi)
+{
+    if (lo <= 0.0 && hi >= 0.0) return 0.0;
+    int e;
+    frexp(fmax(fabs(lo), fabs(hi)) * (1.0 + 1.0 / 1048576.0), &e);
+    const double sp = ldexp(1.0, e - 24);
+    return lo > 0.0 ? floor(lo / sp) * sp : ceil(hi / sp) * sp;
+}
+
+__global__ void cf_ang_origin_kernel(const CfDevPlan *__restrict__ plan, int ncell, double *__restrict__ origin)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+        const int b = cf_band_of(plan, c);
+        const CfBand &B = plan->band[b];
+        const int r = c - B.base;
+        double cmin, cmax, zmn, zmx, ca0, ca1, sa0, sa1;
+        cf_trig_range(B.dlo, B.dhi, 1, cmin, cmax);
+        cf_trig_range(B.dlo, B.dhi, 0, zmn, zmx);
+        cmin = fmax(cmin, 0.0);
+        cf_trig_range(r * B.w, (r + 1) * B.w, 1, ca0, ca1);
+        cf_trig_range(r * B.w, (r + 1) * B.w, 0, sa0, sa1);
+        const double lo[3] = {ca0 >= 0 ? cmin * ca0 : cmax * ca0, sa0 >= 0 ? cmin * sa0 : cmax * sa0, zmn};
+        const double hi[3] = {ca1 >= 0 ? cmax * ca1 : cmin * ca1, sa1 >= 0 ? cmax * sa1 : cmin * sa1, zmx};
+        for (int a = 0; a < 3; a++)
+            origin[3 * c + a] = cf_origin_of_interval(lo[a] - 1e-3 * fabs(lo[a]) - 2e-6, hi[a] + 1e-3 * fabs(hi[a]) + 2e-6);
     }
 }
 
@@ -355,19 +406,16 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
             int ncand = nst, bsel[2 * CFI_MAX_ANG_K + 1], blo[2 * CFI_MAX_ANG_K + 1], bn[2 * CFI_MAX_ANG_K + 1], nbs = 0;
             if (plan->ang) {
                 const int ab = cf_band_of(plan, c);
-                const CfBand Bi = plan->band[ab];
+                const CfBand &Bi = plan->band[ab];
                 const int ar = c - Bi.base, k = g.k[0];
-                const double sh = sin(0.5 * plan->tsearch);
                 ncand = 0;
                 for (int b2 = max(0, ab - k); b2 <= min(plan->nband - 1, ab + k); b2++) {
-                    const CfBand Bj = plan->band[b2];
-                    const double dm = fmax(fmax(fabs(Bi.dlo), fabs(Bi.dhi)), fmax(fabs(Bj.dlo), fabs(Bj.dhi)));
-                    const double cm = cos(fmin(dm, 0.5 * M_PI));
+                    const CfBand &Bj = plan->band[b2];
+                    const double da = Bi.da[b2 - ab + k];
                     int lo = 0, n = Bj.nra;
-                    if (sh < cm) {
-                        const double da = 2.0 * asin(sh / cm) * (1.0 + 1e-9) + 1e-12;
-                        lo = (int)floor((ar * Bi.w - da) / Bj.w);
-                        n = (int)floor(((ar + 1) * Bi.w + da) / Bj.w) - lo + 1;
+                    if (da >= 0.0) {
+                        lo = (int)floor((ar * Bi.w - da) * Bj.inv_w);
+                        n = (int)floor(((ar + 1) * Bi.w + da) * Bj.inv_w) - lo + 1;
                         if (n >= Bj.nra) { lo = 0; n = Bj.nra; }
                     }
                     bsel[nbs] = b2;
@@ -388,7 +436,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                     if (plan->ang) {
                         int q = 0, off = s;
                         while (off >= bn[q]) { off -= bn[q]; q++; }
-                        const CfBand Bj = plan->band[bsel[q]];
+                        const CfBand &Bj = plan->band[bsel[q]];
                         int rr = (blo[q] + off) % Bj.nra;
                         if (rr < 0) rr += Bj.nra;
                         ct = Bj.base + rr;
@@ -526,6 +574,12 @@ cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, 
 {
     dim3 grid(blocks_for(nmax, 256, 4096), nsets);
     cf_assign_kernel<<<grid, 256, 0, st>>>(plan, sets, sub, count, key, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t cfb_ang_origins(const CfDevPlan *plan, int ncell, double *origin, cudaStream_t st)
+{
+    cf_ang_origin_kernel<<<blocks_for(ncell, 256, 4096), 256, 0, st>>>(plan, ncell, origin);
     return cudaGetLastError();
 }
 

@@ -97,9 +97,13 @@ struct CfStencil {         // neighbour offset per axis; wrap axes enumerate tar
 #define CFI_MAX_ANG_K 4           // refinement of the angular grid (bands searched: 2k + 1)
 
 // One DEC band of the angular grid (DD(theta) alternative cell list): DEC in [dlo, dhi),
-// nra RA cells of width w (radians) over [0, 2 pi), cells base .. base + nra - 1
+// nra RA cells of width w (radians) over [0, 2 pi), cells base .. base + nra - 1.  da[d] is the RA
+// half-width to search in band b + d - k: 2 asin(sin(t / 2) / cos dm) with dm the largest |DEC| of
+// both bands (haversine bound), or -1 when every RA cell is searched
 struct CfBand {
     double dlo, dhi, w;
+    double inv_w;                      // 1 / w
+    double da[2 * CFI_MAX_ANG_K + 1];  // RA half-width searched in band b + d - k (negative: every cell)
     int nra, base;
 };
 

@@ -230,17 +230,6 @@ bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint16_t> &wo
 
 namespace {
 
-// Origin of an interval [lo, hi] of values (largest magnitude m): 0 if it holds 0, else the multiple of
-// the float32 spacing at m nearest to 0 that still lies between 0 and every value.  x - origin is then
-// exact in float32 for every float32 x of the interval (same rule as cfp_origin).
-double origin_of_interval(double lo, double hi)
-{
-    if (lo <= 0.0 && hi >= 0.0) return 0.0;
-    const double m = std::max(std::fabs(lo), std::fabs(hi));
-    const double sp = ulp32_of_magnitude(m);
-    return lo > 0.0 ? std::floor(lo / sp) * sp : std::ceil(hi / sp) * sp;
-}
-
 // range of cos (c = 1) or sin (c = 0) over the angle interval [a0, a1] (a1 - a0 <= 2 pi)
 void trig_range(double a0, double a1, int c, double &mn, double &mx)
 {
@@ -386,11 +375,16 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
             if (tot <= cap) break;
             scale *= 0.8;
         }
+        // The cells' origins are computed on the device (cf_ang_origin_kernel) from the same
+        // boxes; here only a bound on how far a cell's points lie from its origin, per band: the
+        // box is at most (cos range) + cos_max * min(w, 2) wide in x and y (|d cos a| <= |d a|) and
+        // the z range of the band in z, widened like the boxes, plus one float32 spacing.
         int base = 0;
         H.origin.clear();
         double ext[3] = {0.0, 0.0, 0.0};
         for (int b = 0; b < nband; b++) {
             CfBand B;
+            std::memset(&B, 0, sizeof(B));
             B.dlo = dlo + b * h;
             B.dhi = (b == nband - 1) ? dhi : dlo + (b + 1) * h;
             B.nra = nra_of(B.dlo, B.dhi, scale);
@@ -402,23 +396,28 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
             trig_range(B.dlo, B.dhi, 1, cmin, cmax);
             trig_range(B.dlo, B.dhi, 0, zmn, zmx);
             cmin = std::max(cmin, 0.0);
-            for (int r = 0; r < B.nra; r++) {
-                double ca0, ca1, sa0, sa1;
-                trig_range(r * B.w, (r + 1) * B.w, 1, ca0, ca1);
-                trig_range(r * B.w, (r + 1) * B.w, 0, sa0, sa1);
-                // x = cos(dec) cos(ra) with cos(dec) in [cmin, cmax] >= 0; likewise y with sin(ra)
-                const double lo[3] = {ca0 >= 0 ? cmin * ca0 : cmax * ca0, sa0 >= 0 ? cmin * sa0 : cmax * sa0, zmn};
-                const double hi[3] = {ca1 >= 0 ? cmax * ca1 : cmin * ca1, sa1 >= 0 ? cmax * sa1 : cmin * sa1, zmx};
-                for (int a = 0; a < 3; a++) {
-                    // widened for vectors up to 1e-3 off unit length (the library rejects more)
-                    const double l = lo[a] - 1e-3 * std::fabs(lo[a]) - 2e-6, u2 = hi[a] + 1e-3 * std::fabs(hi[a]) + 2e-6;
-                    const double o = origin_of_interval(l, u2);
-                    H.origin.push_back(o);
-                    ext[a] = std::max(ext[a], std::max(std::fabs(l - o), std::fabs(u2 - o)));
-                }
-            }
+            const double wxy = (cmax - cmin) + cmax * std::min(B.w, 2.0);
+            const double widen = 2.0 * (1e-3 * 1.0 + 2e-6) + 1e-7;
+            ext[0] = std::max(ext[0], wxy + widen);
+            ext[1] = std::max(ext[1], wxy + widen);
+            ext[2] = std::max(ext[2], (zmx - zmn) + widen);
         }
         if (base <= 0 || (double)base > 2e9) { err = "angular grid too large"; return CF_ERR_ARG; }
+        const double sh = std::sin(0.5 * tw);
+        for (int b = 0; b < nband; b++) {
+            CfBand &B = H.bands[b];
+            B.inv_w = 1.0 / B.w;
+            for (int d = 0; d <= 2 * CFI_MAX_ANG_K; d++) {
+                const int b2 = b + d - k;
+                B.da[d] = -1.0;
+                if (d > 2 * k || b2 < 0 || b2 >= nband) continue;
+                const CfBand &O = H.bands[b2];
+                const double dm = std::max(std::max(std::fabs(B.dlo), std::fabs(B.dhi)),
+                                           std::max(std::fabs(O.dlo), std::fabs(O.dhi)));
+                const double cm = std::cos(std::min(dm, 0.5 * M_PI));
+                if (sh < cm) B.da[d] = 2.0 * std::asin(sh / cm) * (1.0 + 1e-9) + 1e-12;
+            }
+        }
         D.nband = nband;
         D.adlo = dlo;
         D.ah = h;
@@ -549,11 +548,14 @@ extern "C" cf_status cf_plan_probe(const cf_params *params, const double bbox[6]
     std::string err;
     if (cfp_check_params(params, err) != CF_OK) return CF_ERR_ARG;
     const bool rppi_like = params->kind == CF_DD_RPPI || params->kind == CF_WP;
-    if (which < 0 || which > 3 || ((which & 1) && !rppi_like && nv > 0)) return CF_ERR_ARG;
+    if (which < 0 || which > 7) return CF_ERR_ARG;
+    const int angular = (which & 4) ? 1 : 0;
+    which &= 3;
+    if ((which & 1) && !rppi_like && nv > 0) return CF_ERR_ARG;
     CfHostPlan *H = new CfHostPlan();
     int refine[3];
     for (int a = 0; a < 3; a++) refine[a] = params->refine[a] > 0 ? params->refine[a] : 1;
-    int rc = cfp_make_plan(params, bbox, npoints, any_f64, refine, 128, 512, H, err);
+    int rc = cfp_make_plan(params, bbox, npoints, any_f64, refine, 128, 512, H, err, angular);
     if (rc) {
         delete H;
         return (cf_status)rc;
