@@ -30,7 +30,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KINDS = {"r": 0, "rppi": 1, "wp": 2, "theta": 3}
+KINDS = {"r": 0, "rppi": 1, "wp": 2, "theta": 3, "mocks": 4}
 MODES = {"brute": 0, "zwin": 1, "rows": 2}
 
 
@@ -124,7 +124,7 @@ def count(kind: str, edges, d1, d2=None, *, autocorr: bool, periodic: bool, box=
         a2 = [_f64(getattr(d2, c)) for c in "xyz"]
         w2 = _f64(d2.w) if weighted and d2.w is not None else None
         n2 = len(a2[0])
-    nout = nb * (npibins if kind == "rppi" else 1)
+    nout = nb * (npibins if kind in ("rppi", "mocks") else 1)
     npairs = np.zeros(nout, dtype=np.uint64)
     wsum = np.zeros(nout)
     rsum = np.zeros(nout)
@@ -147,7 +147,7 @@ def count(kind: str, edges, d1, d2=None, *, autocorr: bool, periodic: bool, box=
         out["rsum"] = rsum
     if kind == "wp" and periodic and autocorr and rows is None:
         out["wp"] = wp_from_counts(npairs, e, len(a1[0]), b, pimax)
-    if kind == "rppi":
+    if kind in ("rppi", "mocks"):
         for k in list(out):
             out[k] = out[k].reshape(nb, npibins)
     return out

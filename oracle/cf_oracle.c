@@ -14,6 +14,9 @@
  *     [0, pimax] (Appendix A.1); wp counts include every pair with pi < pimax.
  *   - Appendix A.2.2 / Sec. 4.7: angular bins are compared in a monotone transform of theta
  *     instead of theta itself; here the chord length |v1 - v2| of the given unit vectors.
+ *   - Appendix A.2.1 (observed or mock galaxies, the line of sight of Fisher et al.): for
+ *     positions v1, v2 seen from an observer at the origin, s = v1 - v2, l = (v1 + v2) / 2,
+ *     pi = s.l / |l|, rp^2 = s.s - pi^2; rp bins from the edges, pi bins as above.
  *   - Sec. 4.4, Code "normal_pbc": periodic separations use the minimum image, subtracting
  *     first and then wrapping once in each direction.
  *   - Sec. 4.3 and Appendix B: auto-correlations count each unordered pair once and double
@@ -26,7 +29,11 @@
  *   - theta edges are in degrees; chord edge c = 2*sin(theta*(pi/360)), e2 = c*c;
  *   - pi edges p_m = m*(pimax/npibins) for m < npibins, p_npibins = pimax;
  *   - ravg sums sqrt(s) (weighted by w_i*w_j when weights are given); for theta it sums the
- *     angle in degrees, 2*asin(chord/2)*(180/pi).
+ *     angle in degrees, 2*asin(chord/2)*(180/pi);
+ *   - mocks: each dot product is ((a.x*b.x + a.y*b.y) + a.z*b.z); pi is compared in squared
+ *     space, pi^2 = (s.l * s.l) / (l.l) against the squared pi edges (0 when l = 0);
+ *     rp^2 = s.s - pi^2, taken as 0 when rounding makes it negative; positions are Cartesian
+ *     with the observer at the origin and never periodic.
  *
  * Modes:
  *   OR_BRUTE  every pair (i<j for auto), the definition;
@@ -52,6 +59,7 @@
 #define OR_RPPI 1
 #define OR_WP 2
 #define OR_THETA 3
+#define OR_MOCKS 4
 
 #define OR_BRUTE 0
 #define OR_ZWIN 1
@@ -75,10 +83,14 @@ typedef struct {
     double box[3];
     double e2[1025];     /* squared r / rp / chord edges */
     double pe[1025];     /* pi edges */
-    double pimax;
+    double pe2[1025];    /* squared pi edges (mocks) */
+    double pimax, pimax2;
 } or_plan;
 
-static int or_nout(const or_plan *p) { return p->kind == OR_RPPI ? p->nbins * p->npi : p->nbins; }
+static int or_nout(const or_plan *p)
+{
+    return (p->kind == OR_RPPI || p->kind == OR_MOCKS) ? p->nbins * p->npi : p->nbins;
+}
 
 /* Sec. 4.4, Code normal_pbc: subtract, then wrap once each way. */
 static double or_sep(double a, double b, int periodic, double L)
@@ -104,10 +116,29 @@ static int or_find(const double *e, int n, double s)
 static int or_bin_pair(const or_plan *p, double xi, double yi, double zi, double xj, double yj,
                        double zj, double *sep)
 {
+    int nb = p->nbins;
+    if (p->kind == OR_MOCKS) {
+        /* Appendix A.2.1: s = v1 - v2, l = (v1 + v2) / 2, pi = s.l / |l|, rp^2 = s.s - pi^2 */
+        double sx = xi - xj, sy = yi - yj, sz = zi - zj;
+        double lx = 0.5 * (xi + xj), ly = 0.5 * (yi + yj), lz = 0.5 * (zi + zj);
+        double sl = sx * lx + sy * ly;
+        sl = sl + sz * lz;
+        double ll = lx * lx + ly * ly;
+        ll = ll + lz * lz;
+        double ss = sx * sx + sy * sy;
+        ss = ss + sz * sz;
+        double pi2 = ll > 0.0 ? (sl * sl) / ll : 0.0;
+        double rp2 = ss - pi2;
+        if (rp2 < 0.0) rp2 = 0.0;
+        if (!(pi2 < p->pimax2)) return -1;
+        if (rp2 < p->e2[0] || rp2 >= p->e2[nb]) return -1;
+        int k = or_find(p->e2, nb, rp2);
+        if (p->ravg) *sep = sqrt(rp2);
+        return k * p->npi + or_find(p->pe2, p->npi, pi2);
+    }
     double dx = or_sep(xi, xj, p->periodic, p->box[0]);
     double dy = or_sep(yi, yj, p->periodic, p->box[1]);
     double dz = or_sep(zi, zj, p->periodic, p->box[2]);
-    int nb = p->nbins;
     if (p->kind == OR_R || p->kind == OR_THETA) {
         double s = dx * dx + dy * dy;
         s = s + dz * dz;
@@ -151,13 +182,16 @@ static int or_make_plan(const or_params *in, or_plan *p)
         }
     }
     p->npi = 1;
-    if (in->kind == OR_RPPI || in->kind == OR_WP) {
+    if (in->kind == OR_MOCKS && in->periodic) return -1;
+    if (in->kind == OR_RPPI || in->kind == OR_WP || in->kind == OR_MOCKS) {
         if (in->npibins < 1 || in->npibins > 1024 || !(in->pimax > 0)) return -1;
         p->npi = in->npibins;
         p->pimax = in->pimax;
+        p->pimax2 = in->pimax * in->pimax;
         double dpi = in->pimax / in->npibins;
         for (int m = 0; m < in->npibins; m++) p->pe[m] = (double)m * dpi;
         p->pe[in->npibins] = in->pimax;
+        for (int m = 0; m <= in->npibins; m++) p->pe2[m] = p->pe[m] * p->pe[m];
     }
     return 0;
 }
@@ -166,6 +200,9 @@ static int or_make_plan(const or_params *in, or_plan *p)
 static double or_zmax(const or_plan *p)
 {
     if (p->kind == OR_RPPI || p->kind == OR_WP) return p->pimax;
+    /* mocks: a pair with |dz| >= 1.001 Rsep (Rsep^2 = rmax^2 + pimax^2) has s.s >= 1.002 Rsep^2, so
+     * either pi^2 >= pimax^2 or rp^2 > rmax^2, with margins far above the rounding */
+    if (p->kind == OR_MOCKS) return 1.001 * sqrt(p->e2[p->nbins] + p->pimax2);
     return sqrt(p->e2[p->nbins]);
 }
 

@@ -14,9 +14,18 @@ import numpy as np
 import pytest
 
 import oracle
+from tests.test_oracle_mocks import MOCK_CHECKS
 from tests.test_oracle_pins import LATTICE, PERIODIC, RPPI, Cat
 
 MUTANTS = {
+    # observed / mock galaxies (Appendix A.2.1)
+    "mocks_los_from_difference": ("double lx = 0.5 * (xi + xj)", "double lx = 0.5 * (xi - xj)"),
+    "mocks_pi_not_normalised": ("double pi2 = ll > 0.0 ? (sl * sl) / ll : 0.0;",
+                                "double pi2 = ll > 0.0 ? (sl * sl) : 0.0;"),
+    "mocks_rp_adds_pi": ("double rp2 = ss - pi2;", "double rp2 = ss + pi2;"),
+    "mocks_pi_edges_unsquared": ("or_find(p->pe2, p->npi, pi2)", "or_find(p->pe, p->npi, pi2)"),
+    "mocks_drop_sz_term": ("ss = ss + sz * sz;", "ss = ss;"),
+    "mocks_pimax_inclusive": ("if (!(pi2 < p->pimax2)) return -1;", "if (!(pi2 <= p->pimax2)) return -1;"),
     "drop_dz_term": ("s = s + dz * dz;", "s = s;"),
     "wrap_wrong_sign": ("if (d > 0.5 * L) d -= L;", "if (d > 0.5 * L) d += L;"),
     "lower_edge_exclusive": ("if (s < p->e2[0] || s >= p->e2[nb]) return -1;\n        int k",
@@ -94,7 +103,13 @@ def _pin_checks(lib):
         t = cKDTree(a, boxsize=30.0)
         assert out["npairs"].astype(np.int64).tolist() == np.diff(t.count_neighbors(t, edges)).astype(np.int64).tolist()
 
-    return [lattice, lattice_w, periodic, rppi, theta, totals, ckdtree]
+    mocks = []
+    for chk in MOCK_CHECKS:
+        def run(chk=chk):
+            chk(lib)
+        run.__name__ = chk.__name__
+        mocks.append(run)
+    return [lattice, lattice_w, periodic, rppi, theta, totals, ckdtree] + mocks
 
 
 def _build_mutant(tmp_path, name, old, new):
