@@ -13,6 +13,7 @@ from .catalogs import (  # noqa: F401
     uniform_weights,
     sphere_patch,
     unit_sphere,
+    survey_cone,
     workload,
     batch_sizes,
     batch_catalogue,

@@ -14,6 +14,10 @@ Recipes (float32 unless stated):
   * weights ~ U[lo, hi) float32.
   * sphere patch: RA ~ U[ra0, ra1) deg, sin(DEC) ~ U[sin dec0, sin dec1), converted to a unit
     vector in float64, then each component rounded to float32.
+  * survey cone (observed galaxies, observer at the origin): RA ~ U[ra0, ra1) deg, sin(DEC) ~
+    U[sin dec0, sin dec1), comoving distance d with d^3 ~ U[d0^3, d1^3) (uniform in volume),
+    converted to Cartesian in float64; clustered: that recipe for the centres, each with
+    `members` points offset by isotropic N(0, sigma^2); every component rounded to float32.
   * edges: log-spaced in float64 with the end points set exactly.
 """
 from __future__ import annotations
@@ -95,6 +99,22 @@ def sphere_patch(n: int, ra0: float, ra1: float, dec0: float, dec1: float, seed:
                      sdec.astype(np.float32))
 
 
+def survey_cone(n: int, ra0: float, ra1: float, dec0: float, dec1: float, d0: float, d1: float, seed: int,
+                members: int = 1, sigma: float = 0.0) -> Catalogue:
+    """Positions of observed galaxies (or randoms with members = 1) in a survey cone seen from
+    the origin; n points in total (n // members centres, the remainder dropped)."""
+    r = _rng(seed)
+    nc = max(1, n // members)
+    ra = np.deg2rad(r.uniform(ra0, ra1, size=nc))
+    sdec = r.uniform(math.sin(math.radians(dec0)), math.sin(math.radians(dec1)), size=nc)
+    cdec = np.sqrt(np.maximum(0.0, 1.0 - sdec * sdec))
+    d = np.cbrt(r.uniform(d0 ** 3, d1 ** 3, size=nc))
+    c = np.stack([d * cdec * np.cos(ra), d * cdec * np.sin(ra), d * sdec], axis=1)
+    if members > 1:
+        c = (c[:, None, :] + r.normal(0.0, sigma, size=(nc, members, 3))).reshape(-1, 3)
+    return Catalogue(c[:, 0].astype(np.float32), c[:, 1].astype(np.float32), c[:, 2].astype(np.float32))
+
+
 def unit_sphere(n: int, seed: int) -> Catalogue:
     """Uniform on the full sphere (for the analytic angular pin)."""
     return sphere_patch(n, 0.0, 360.0, -90.0, 90.0, seed)
@@ -107,7 +127,7 @@ def unit_sphere(n: int, seed: int) -> Catalogue:
 @dataclasses.dataclass
 class Workload:
     name: str
-    kind: str                      # "r", "rppi", "wp", "theta"
+    kind: str                      # "r", "rppi", "wp", "theta", "mocks"
     autocorr: bool
     periodic: bool
     box: float
@@ -165,6 +185,15 @@ def workload(name: str, scale: float = 1.0) -> Workload:
                             pimax=40.0, npibins=40)
         return Workload(name, kind, True, True, L, log_edges(0.1, 25.0, 14), d,
                         pimax=40.0, npibins=40)
+    if name == "mock_dr_rppi":
+        # DR(rp, pi) of mock galaxies against randoms at 10x their density (the paper's mocks
+        # scaling workload, Sec. 5.2), in a 90 x 60 deg cone from 300 to 1000 Mpc/h
+        nd = max(8, int(200000 * scale))
+        d0, d1 = 300.0, 300.0 + 700.0 * (scale ** (1.0 / 3.0) if scale != 1.0 else 1.0)
+        d = survey_cone(nd, 0.0, 90.0, 0.0, 60.0, d0, d1, 1007, members=100, sigma=2.0)
+        rr = survey_cone(10 * nd, 0.0, 90.0, 0.0, 60.0, d0, d1, 1008)
+        return Workload(name, "mocks", False, False, 0.0, log_edges(0.5, 42.0, 14), d, rr,
+                        pimax=42.0, npibins=42)
     if name == "polar_theta_1m":
         n = max(8, int(1000000 * scale))
         return Workload(name, "theta", True, False, 0.0, log_edges(0.001, 1.0, 20),

@@ -4,7 +4,8 @@
  * Method: Sinha & Garrison, "Corrfunc -- a suite of blazing fast correlation functions on the
  * CPU" (arXiv:1911.03545).  The library counts pairs of points binned by separation over a
  * cell-list grid (Sec. 4.1-4.3), for the four pair counters of Table 1's theory rows plus the
- * angular counter: DD(r), DD(rp, pi), wp(rp) and DD(theta); auto or cross; periodic or not;
+ * angular counter and DD(rp, pi) of observed positions: DD(r), DD(rp, pi), wp(rp), DD(theta) and
+ * DDrppi_mocks (Appendix A.2.1); auto or cross; periodic or not (mocks: not);
  * optionally with pair-product weights (Sec. 2.1, weight_func) and the mean separation per
  * bin ("ravg", Sec. 6.5).
  *
@@ -18,6 +19,11 @@
  *     if d <= -L/2: d += L (Sec. 4.4, Code normal_pbc);
  *   - pi bins have width pimax/npibins on [0, pimax) (Appendix A.1 uses width 1); pairs with
  *     pi >= pimax are excluded; wp counts are the sum over pi bins (Appendix A.1);
+ *   - mocks (Appendix A.2.1): s = v1 - v2, l = 0.5*(v1 + v2) per axis, then s.l, l.l and s.s as
+ *     ((x + y) + z) sums of products, pi^2 = (s.l)^2 / l.l (0 when l.l = 0), rp^2 = s.s - pi^2
+ *     (clamped at 0); a pair counts when pi^2 < pimax^2 and e0^2 <= rp^2 < e_n^2, in the rp bin
+ *     of rp^2 and the pi bin of pi^2 against the squared pi edges (m * pimax/npibins)^2; ravg
+ *     sums sqrt(rp^2);
  *   - theta edges are in degrees; a pair of unit vectors is binned by its chord |v1 - v2|
  *     against c = 2*sin(theta*(pi/360)), squared in FP64 (Appendix A.2.2, Sec. 4.7);
  *   - auto-correlations return ordered counts: every unordered pair counted twice, plus the N
@@ -57,7 +63,12 @@ typedef enum {
     CF_ERR_INTERNAL = -7    /* an internal consistency check failed */
 } cf_status;
 
-typedef enum { CF_DD_R = 0, CF_DD_RPPI = 1, CF_WP = 2, CF_DD_THETA = 3 } cf_kind;
+/* CF_DD_RPPI_MOCKS: DD(rp, pi) of observed positions (Appendix A.2.1, the line of sight of Fisher
+ * et al. 1994): for points v1, v2 seen from an observer at the origin, s = v1 - v2,
+ * l = (v1 + v2) / 2, pi = |s.l| / |l|, rp^2 = s.s - pi^2; pi bins of width pimax / npibins on
+ * 0 <= pi < pimax, rp bins from `edges`.  Cartesian inputs (convert RA, DEC, comoving distance
+ * beforehand), non-periodic only. */
+typedef enum { CF_DD_R = 0, CF_DD_RPPI = 1, CF_WP = 2, CF_DD_THETA = 3, CF_DD_RPPI_MOCKS = 4 } cf_kind;
 typedef enum { CF_F32 = 0, CF_F64 = 1 } cf_dtype;
 typedef enum { CF_W_NONE = 0, CF_W_PAIR_PRODUCT = 1 } cf_weight;
 
@@ -73,8 +84,9 @@ typedef struct {
     const double *edges; /* host array of nbins+1 strictly increasing edges >= 0: r, rp, or theta in
                             degrees (<= 180) */
     int nbins;           /* 1 .. CF_MAX_BINS */
-    double pimax;        /* CF_DD_RPPI / CF_WP: pi cut (> 0) */
-    int npibins;         /* CF_DD_RPPI / CF_WP: number of pi bins of width pimax/npibins */
+    double pimax;        /* CF_DD_RPPI / CF_WP / CF_DD_RPPI_MOCKS: pi cut (> 0) */
+    int npibins;         /* CF_DD_RPPI / CF_WP / CF_DD_RPPI_MOCKS: number of pi bins of width
+                            pimax/npibins */
     int refine[3];       /* refinement factor per axis (Sec. 4.2, 1..4); 0 = automatic */
     int output_ravg;     /* 1: compute ravg (Sec. 6.5) */
     int weight;          /* cf_weight; CF_W_PAIR_PRODUCT needs w in every point set */
@@ -91,7 +103,8 @@ typedef struct {
     int on_device;       /* 1: device pointers on the context's device; 0: host pointers */
 } cf_points;
 
-/* Caller-owned host outputs of length nout = nbins * (kind == CF_DD_RPPI ? npibins : 1),
+/* Caller-owned host outputs of length
+ * nout = nbins * (kind == CF_DD_RPPI || kind == CF_DD_RPPI_MOCKS ? npibins : 1),
  * row-major (rp bin, pi bin).  Any pointer may be NULL to skip that output. */
 typedef struct {
     uint64_t *npairs;
@@ -179,10 +192,11 @@ cf_status cf_get_stats(const void *ctx, cf_stats *out);
 /* Host-only planning probe (needs no GPU): builds the plan that cf_count would use for
  * `params` over the bounding box bbox = {xlo, ylo, zlo, xhi, yhi, zhi} of `npoints` points
  * (any_f64 = 1 if any input is float64) and reports it.  bands_r (nbins+1 values) and bands_p
- * (npibins+1 values, rp-pi / wp) receive the FP32 error band of each squared edge / pi edge:
+ * (npibins+1 values, rp-pi / wp / mocks) receive the FP32 error band of each squared edge / pi
+ * edge (mocks: of each squared pi edge):
  * an FP32 value within a band of an edge is re-evaluated in FP64.  With nv > 0, `values` are
  * classified through the same lookup table the pair kernel uses (which = 0: squared r / rp /
- * chord; which = 1: |dz|): classes[i] = bin index, 0xFE outside every bin, 0xFF within a band.
+ * chord; which = 1: |dz|, or pi^2 for mocks): classes[i] = bin index, 0xFE outside every bin, 0xFF within a band.
  * which = 2 / 3 classify the same way as the direct pair kernel does (an FP32 cut at the table's
  * tail, then the lookup without its upper clamp); 0xFD there would mean an index past the table.
  * Adding 4 to `which` plans DD(theta) on the angular grid (CF_OPT_THETA_GRID = 1): grid[] then
@@ -224,14 +238,15 @@ const char *cf_server_last_error(const void *server);
  * that must not allocate after start-up because an allocation can synchronise the device.
  * cf_count_noalloc allocates nothing (no cudaMalloc, cudaFree, pinned memory or allocating
  * library call).  Inputs and outputs are the caller's DEVICE arrays: d1 (and d2 for a cross
- * count) with on_device = 1; npairs / wsum / ravg of nbins * (npibins for CF_DD_RPPI) entries (any
+ * count) with on_device = 1; npairs / wsum / ravg of nbins * (npibins for CF_DD_RPPI and
+ * CF_DD_RPPI_MOCKS) entries (any
  * may be NULL).  Results follow the definition at the top of this file (counts exact, sums
  * within 1e-6 relative).  The work is enqueued on `cuda_stream` and the function returns without
  * waiting; the outputs are ready when the stream reaches that point.
  * It evaluates every pair in FP64 without a cell list, so it suits small inputs (cost ~ N1*N2).
  * Its only scratch is a fixed array of CF_NOALLOC_SCRATCH_BYTES in the library image, present on
  * every device that loads the library until the process exits; histograms are limited to
- * CF_NOALLOC_MAX_SLOTS slots (nbins, or nbins*npibins for rp-pi): larger requests return
+ * CF_NOALLOC_MAX_SLOTS slots (nbins, or nbins*npibins for rp-pi and mocks): larger requests return
  * CF_ERR_ARG.  The first call on a device looks up the array's device address with that device
  * current: make that first call before any stream capture.  All calls share the array and each
  * call clears it first, so calls whose GPU work overlaps (other streams, or unordered host

@@ -19,12 +19,12 @@ import numpy as np
 
 from . import _capi
 from ._capi import (  # noqa: F401
-    CF_DD_R, CF_DD_RPPI, CF_DD_THETA, CF_F32, CF_F64, CF_OK, CF_OPT_AUDIT, CF_OPT_CTAS_PER_SM, CF_OPT_ITER_LIMIT,
+    CF_DD_R, CF_DD_RPPI, CF_DD_RPPI_MOCKS, CF_DD_THETA, CF_F32, CF_F64, CF_OK, CF_OPT_AUDIT, CF_OPT_CTAS_PER_SM, CF_OPT_ITER_LIMIT,
     CF_OPT_CELL_ORDER, CF_OPT_CELL_PRUNE, CF_OPT_JCHUNK, CF_OPT_MEM_CAP, CF_OPT_QUEUE, CF_OPT_REFINE, CF_OPT_THETA_GRID, CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS,
     CF_W_NONE, CF_W_PAIR_PRODUCT, CF_WP, STATUS_NAMES,
 )
 
-KINDS = {"r": CF_DD_R, "rppi": CF_DD_RPPI, "wp": CF_WP, "theta": CF_DD_THETA}
+KINDS = {"r": CF_DD_R, "rppi": CF_DD_RPPI, "wp": CF_WP, "theta": CF_DD_THETA, "mocks": CF_DD_RPPI_MOCKS}
 
 
 class CfError(RuntimeError):
@@ -61,7 +61,7 @@ class Params:
     @property
     def nout(self) -> int:
         nb = len(self.edges) - 1
-        return nb * (self.c.npibins if self.kind == CF_DD_RPPI else 1)
+        return nb * (self.c.npibins if self.kind in (CF_DD_RPPI, CF_DD_RPPI_MOCKS) else 1)
 
 
 def params(**kw) -> Params:
@@ -123,7 +123,7 @@ class _Out:
             d["ravg"] = self.ravg
         if p.kind == CF_WP:
             d["wp"] = self.wp
-        if p.kind == CF_DD_RPPI:
+        if p.kind in (CF_DD_RPPI, CF_DD_RPPI_MOCKS):
             nb = len(p.edges) - 1
             for k in ("npairs", "wsum", "ravg"):
                 if k in d:
@@ -261,7 +261,7 @@ def cf_plan_probe(p: Params, bbox, npoints: int, any_f64: bool = False, which: i
     out = {f: (list(getattr(info, f)) if hasattr(getattr(info, f), "__len__") else getattr(info, f))
            for f, _ in info._fields_}
     out["bands_r"] = br
-    out["bands_p"] = bp[: p.c.npibins + 1] if p.kind in (CF_DD_RPPI, CF_WP) else np.zeros(0)
+    out["bands_p"] = bp[: p.c.npibins + 1] if p.kind in (CF_DD_RPPI, CF_WP, CF_DD_RPPI_MOCKS) else np.zeros(0)
     out["classes"] = cls
     return out
 

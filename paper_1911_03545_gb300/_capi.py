@@ -16,7 +16,7 @@ HEADER = os.path.join(ROOT, "include", "cf.h")
 
 CF_OK, CF_ERR_ARG, CF_ERR_OOM, CF_ERR_CUDA, CF_ERR_TIMEOUT, CF_ERR_BUSY, CF_ERR_CANCELLED, CF_ERR_INTERNAL = (
     0, -1, -2, -3, -4, -5, -6, -7)
-CF_DD_R, CF_DD_RPPI, CF_WP, CF_DD_THETA = 0, 1, 2, 3
+CF_DD_R, CF_DD_RPPI, CF_WP, CF_DD_THETA, CF_DD_RPPI_MOCKS = 0, 1, 2, 3, 4
 CF_F32, CF_F64 = 0, 1
 CF_W_NONE, CF_W_PAIR_PRODUCT = 0, 1
 CF_MAX_BINS = 252

@@ -20,7 +20,7 @@ LIB = os.path.join(HERE, "libcfgb300.so")
 
 SOURCES = [
     "cf_api.cu", "cf_build.cu", "cf_recheck.cu", "cf_batch.cu", "cf_server.cpp",
-    "cf_pair_r.cu", "cf_pair_rppi.cu", "cf_pair_wp.cu", "cf_pair_theta.cu",
+    "cf_pair_r.cu", "cf_pair_rppi.cu", "cf_pair_wp.cu", "cf_pair_theta.cu", "cf_pair_mocks.cu",
     "cf_plan.cpp", "cf_noalloc.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -223,33 +223,40 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
 
     // ---- bbox + validation (Sec. 4.1: the grid covers every data set of the call) ----
     CF_TRY(C->ensure(B_SETS, sizeof(CfSetDesc) * nsets));
-    CF_TRY(C->ensure(B_BBOX, 64 * (size_t)nsets));
-    CF_TRY(C->ensure_host(std::max<size_t>(64 * (size_t)nsets, 4096)));
+    const size_t bbw = CFB_BBOX_WORDS;
+    CF_TRY(C->ensure(B_BBOX, 8 * bbw * (size_t)nsets));
+    CF_TRY(C->ensure_host(std::max<size_t>(8 * bbw * (size_t)nsets, 4096)));
     CF_CU(cudaMemcpyAsync(C->buf[B_SETS].p, R.sets.data(), sizeof(CfSetDesc) * nsets, cudaMemcpyHostToDevice, st),
           "sets upload");
     {
         unsigned long long *init = (unsigned long long *)C->hpin;
         for (int s = 0; s < nsets; s++)
-            for (int a = 0; a < 8; a++) init[8 * s + a] = a < 3 ? ~0ull : 0ull;
-        CF_CU(cudaMemcpyAsync(C->buf[B_BBOX].p, init, 64 * (size_t)nsets, cudaMemcpyHostToDevice, st), "bbox init");
+            for (size_t a = 0; a < bbw; a++) init[bbw * s + a] = (a < 3 || a == 8) ? ~0ull : 0ull;
+        CF_CU(cudaMemcpyAsync(C->buf[B_BBOX].p, init, 8 * bbw * (size_t)nsets, cudaMemcpyHostToDevice, st),
+              "bbox init");
     }
     CF_CU(cfb_bbox((const CfSetDesc *)C->buf[B_SETS].p, nsets, std::max<int64_t>(R.nmax, 1),
                    (unsigned long long *)C->buf[B_BBOX].p, st), "bbox kernel");
     C->launches = 1;
-    CF_CU(cudaMemcpyAsync(C->hpin, C->buf[B_BBOX].p, 64 * (size_t)nsets, cudaMemcpyDeviceToHost, st), "bbox readback");
+    CF_CU(cudaMemcpyAsync(C->hpin, C->buf[B_BBOX].p, 8 * bbw * (size_t)nsets, cudaMemcpyDeviceToHost, st),
+          "bbox readback");
     CF_CU(cudaStreamSynchronize(st), "bbox sync");
     double bbox[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     double norm_dev = 0.0;   // largest | |v|^2 - 1 | over the points
+    double vmin2 = INFINITY;  // smallest |v|^2 over the points
     {
         const unsigned long long *bb = (const unsigned long long *)C->hpin;
         for (int s = 0; s < nsets; s++) {
             if (R.sets[s].n == 0) continue;
-            if (bb[8 * s + 6]) return C->fail(CF_ERR_ARG, "non-finite coordinate or weight");
-            double nd;
-            std::memcpy(&nd, &bb[8 * s + 7], 8);
+            const unsigned long long *b = bb + bbw * s;
+            if (b[6]) return C->fail(CF_ERR_ARG, "non-finite coordinate or weight");
+            double nd, r2;
+            std::memcpy(&nd, &b[7], 8);
+            std::memcpy(&r2, &b[8], 8);
             norm_dev = std::max(norm_dev, nd);
+            vmin2 = std::min(vmin2, r2);
             for (int a = 0; a < 3; a++) {
-                double lo = dkey_to_double(bb[8 * s + a]), hi = dkey_to_double(bb[8 * s + 3 + a]);
+                double lo = dkey_to_double(b[a]), hi = dkey_to_double(b[3 + a]);
                 if (p->periodic && (lo < 0.0 || hi > p->box[a]))
                     return C->fail(CF_ERR_ARG,
                                    "periodic positions must lie in [0, box] (axis " + std::to_string(a) + ")");
@@ -271,7 +278,9 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
         refine[a] = p->refine[a] > 0 ? p->refine[a] : (C->opt[CF_OPT_REFINE] > 0 ? (int)C->opt[CF_OPT_REFINE] : 1);
     int tile = C->opt[CF_OPT_TILE] > 0 ? (int)std::min<int64_t>(128, std::max<int64_t>(32, C->opt[CF_OPT_TILE])) : 128;
     int jchunk = C->opt[CF_OPT_JCHUNK] > 0 ? (int)std::min<int64_t>(CFI_JMAX, C->opt[CF_OPT_JCHUNK]) : CFI_JMAX;
-    rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err, angular ? 1 : 0);
+    // |v| of the point nearest the observer (its FP64 square may be one rounding low or high)
+    const double vmin = std::isfinite(vmin2) ? std::sqrt(vmin2) * (1.0 - 1e-12) : 0.0;
+    rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err, angular ? 1 : 0, vmin);
     if (rc) return C->fail(rc, err);
     CfDevPlan &D = H.d;
     D.nsets = nsets;
@@ -365,7 +374,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.cfg.nslot = D.nslot;
     R.cfg.warps = (int)C->opt[CF_OPT_WARPS];
     R.cfg.ctas_per_sm = (int)C->opt[CF_OPT_CTAS_PER_SM];
-    R.cfg.variant = C->opt[CF_OPT_VARIANT] == 2 ? 2 : 1;
+    // the mocks kind has the direct form only (its candidates need more than one value each)
+    R.cfg.variant = (C->opt[CF_OPT_VARIANT] == 2 && D.kind != CF_DD_RPPI_MOCKS) ? 2 : 1;
     R.items_cap = 0;
     return CF_OK;
 }

@@ -5,12 +5,14 @@
 
 // ---------------------------------------------------------------------------------------------
 // Bounding box and validity of every point set: min / max per axis, count of non-finite values.
-// grid = (blocks, nsets); out[s*8 + 0..5] = key(min x,y,z), key(max x,y,z); out[s*8+6] = bad.
+// grid = (blocks, nsets); out[s*W + 0..5] = key(min x,y,z), key(max x,y,z); out[s*W+6] = bad;
+// out[s*W+7] = bits of the largest | |v|^2 - 1 |; out[s*W+8] = bits of the smallest |v|^2
+// (W = CFB_BBOX_WORDS; a non-negative double's bits order like its value).
 // ---------------------------------------------------------------------------------------------
 __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long long *__restrict__ out)
 {
     const CfSetDesc S = sets[blockIdx.y];
-    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0}, bad = 0, nrm = 0;
+    unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0}, bad = 0, nrm = 0, rmin = ~0ull;
     const void *P[3] = {S.x, S.y, S.z};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
         double r2 = 0.0;
@@ -26,6 +28,9 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         // double's bits order like the value
         const unsigned long long d = (unsigned long long)__double_as_longlong(fabs(r2 - 1.0));
         nrm = d > nrm ? d : nrm;
+        // smallest |v|^2 (distance from the observer at the origin, for mocks)
+        const unsigned long long r2b = (unsigned long long)__double_as_longlong(r2);
+        rmin = r2b < rmin ? r2b : rmin;
         if (S.w) {
             double w = cf_load(S.w, S.dtype, i);
             if (!isfinite(w)) bad++;
@@ -41,9 +46,11 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         bad += __shfl_xor_sync(CF_FULL, bad, o);
         const unsigned long long t = __shfl_xor_sync(CF_FULL, nrm, o);
         nrm = t > nrm ? t : nrm;
+        const unsigned long long t2 = __shfl_xor_sync(CF_FULL, rmin, o);
+        rmin = t2 < rmin ? t2 : rmin;
     }
     // block reduction through shared memory, then one atomic per block and value
-    __shared__ unsigned long long red[8][32];
+    __shared__ unsigned long long red[CFB_BBOX_WORDS][32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if (lane == 0) {
         for (int a = 0; a < 3; a++) {
@@ -52,16 +59,18 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         }
         red[6][w] = bad;
         red[7][w] = nrm;
+        red[8][w] = rmin;
     }
     __syncthreads();
     if (w == 0) {
-        unsigned long long v[8];
+        unsigned long long v[CFB_BBOX_WORDS];
         for (int a = 0; a < 3; a++) {
             v[a] = lane < nw ? red[a][lane] : ~0ull;
             v[3 + a] = lane < nw ? red[3 + a][lane] : 0ull;
         }
         v[6] = lane < nw ? red[6][lane] : 0ull;
         v[7] = lane < nw ? red[7][lane] : 0ull;
+        v[8] = lane < nw ? red[8][lane] : ~0ull;
         for (int o = 16; o; o >>= 1) {
             for (int a = 0; a < 3; a++) {
                 unsigned long long t = __shfl_xor_sync(CF_FULL, v[a], o);
@@ -72,15 +81,18 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
             v[6] += __shfl_xor_sync(CF_FULL, v[6], o);
             const unsigned long long t = __shfl_xor_sync(CF_FULL, v[7], o);
             v[7] = t > v[7] ? t : v[7];
+            const unsigned long long t2 = __shfl_xor_sync(CF_FULL, v[8], o);
+            v[8] = t2 < v[8] ? t2 : v[8];
         }
         if (lane == 0) {
-            unsigned long long *o = out + blockIdx.y * 8;
+            unsigned long long *o = out + blockIdx.y * CFB_BBOX_WORDS;
             for (int a = 0; a < 3; a++) {
                 atomicMin(o + a, v[a]);
                 atomicMax(o + 3 + a, v[3 + a]);
             }
             if (v[6]) atomicAdd(o + 6, v[6]);
             atomicMax(o + 7, v[7]);
+            atomicMin(o + 8, v[8]);
         }
     }
 }
@@ -316,17 +328,24 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
         int iy = (c / g.n[2]) % g.n[1];
         int ix = c / (g.n[2] * g.n[1]);
         int64_t dst = fstart[k] + slot[p];
-        double X = cf_load(S.x, S.dtype, i) - cf_cell_origin(plan, 0, (int)c, ix);
-        double Y = cf_load(S.y, S.dtype, i) - cf_cell_origin(plan, 1, (int)c, iy);
-        double Z = cf_load(S.z, S.dtype, i) - cf_cell_origin(plan, 2, (int)c, iz);
+        const double vx = cf_load(S.x, S.dtype, i), vy = cf_load(S.y, S.dtype, i), vz = cf_load(S.z, S.dtype, i);
+        double X = vx - cf_cell_origin(plan, 0, (int)c, ix);
+        double Y = vy - cf_cell_origin(plan, 1, (int)c, iy);
+        double Z = vz - cf_cell_origin(plan, 2, (int)c, iz);
         float xf = (float)X, yf = (float)Y, zf = (float)Z;
         float w = S.w ? (float)cf_load(S.w, S.dtype, i) : 1.0f;
-        pa[dst] = make_float4(-xf, -xf, -yf, -yf);
-        pb[dst] = make_float4(-zf, -zf, w, w);
+        // second copies: X again, or for mocks the absolute position (its line of sight)
+        const bool mocks = plan->kind == CF_DD_RPPI_MOCKS;
+        const float ax = mocks ? (float)vx : -xf, ay = mocks ? (float)vy : -yf, az = mocks ? (float)vz : -zf;
+        pa[dst] = make_float4(-xf, ax, -yf, ay);
+        pb[dst] = make_float4(-zf, az, w, w);
         if (lo) {
             float xl = (float)(X - (double)xf), yl = (float)(Y - (double)yf), zl = (float)(Z - (double)zf);
-            plo[2 * dst] = make_float4(-xl, -xl, -yl, -yl);
-            plo[2 * dst + 1] = make_float4(-zl, -zl, 0.f, 0.f);
+            const float axl = mocks ? (float)(vx - (double)ax) : -xl;
+            const float ayl = mocks ? (float)(vy - (double)ay) : -yl;
+            const float azl = mocks ? (float)(vz - (double)az) : -zl;
+            plo[2 * dst] = make_float4(-xl, axl, -yl, ayl);
+            plo[2 * dst + 1] = make_float4(-zl, azl, 0.f, 0.f);
         }
         orig[dst] = (uint32_t)i;
     }
@@ -381,7 +400,9 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
     // box pruning needs the cell pair's own shift, which wrap axes (explicit minimum image) lack
     const bool prune = cbox != nullptr && !g.wrap[0] && !g.wrap[1] && !g.wrap[2];
     const bool zsep = plan->kind == CF_DD_RPPI || plan->kind == CF_WP;
-    const double e2max = plan->e2[plan->nb], zmax = zsep ? (double)plan->pimax : 0.0;
+    // mocks: the line of sight varies, so only |s| < sqrt(rmax^2 + pimax^2) bounds a counted pair
+    const double e2max = plan->kind == CF_DD_RPPI_MOCKS ? plan->smax2 : plan->e2[plan->nb];
+    const double zmax = zsep ? (double)plan->pimax : 0.0;
     const int64_t nunit = (int64_t)g.ncell * plan->njobs;
     const uint32_t tile = plan->tile, jchunk = plan->jchunk;
     const uint32_t lane = threadIdx.x & 31u;

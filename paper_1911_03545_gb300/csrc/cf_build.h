@@ -4,6 +4,7 @@
 
 #include "cf_internal.h"
 
+#define CFB_BBOX_WORDS 9     // per point set: 3 min keys, 3 max keys, bad, norm deviation, min |v|^2
 cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st);
 // key = cell * sub^3 + Morton sub-cell (sub = 1, 2, 4): the counting-sort key of every point
 cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,

@@ -101,3 +101,22 @@ __device__ __forceinline__ unsigned long long cf_dkey(double v)
     unsigned long long b = (unsigned long long)__double_as_longlong(v);
     return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
 }
+
+// DD(rp, pi) of observed positions in FP64, as the result definition states it (Appendix A.2.1,
+// the line of sight of Fisher et al.): s = a - b, l = 0.5 (a + b) per axis; s.l, l.l and s.s as
+// ((x + y) + z) sums of products; pi^2 = (s.l)^2 / l.l (0 when l.l = 0); rp^2 = s.s - pi^2,
+// clamped at 0.  Explicit round-to-nearest operations, no fused multiply-add.
+__device__ __forceinline__ void cf_mocks64(double ax, double ay, double az, double bx, double by, double bz,
+                                           double &rp2, double &pi2)
+{
+    const double sx = __dsub_rn(ax, bx), sy = __dsub_rn(ay, by), sz = __dsub_rn(az, bz);
+    const double lx = __dmul_rn(0.5, __dadd_rn(ax, bx));
+    const double ly = __dmul_rn(0.5, __dadd_rn(ay, by));
+    const double lz = __dmul_rn(0.5, __dadd_rn(az, bz));
+    const double sl = __dadd_rn(__dadd_rn(__dmul_rn(sx, lx), __dmul_rn(sy, ly)), __dmul_rn(sz, lz));
+    const double ll = __dadd_rn(__dadd_rn(__dmul_rn(lx, lx), __dmul_rn(ly, ly)), __dmul_rn(lz, lz));
+    const double ss = __dadd_rn(__dadd_rn(__dmul_rn(sx, sx), __dmul_rn(sy, sy)), __dmul_rn(sz, sz));
+    pi2 = ll > 0.0 ? __ddiv_rn(__dmul_rn(sl, sl), ll) : 0.0;
+    rp2 = __dsub_rn(ss, pi2);
+    if (rp2 < 0.0) rp2 = 0.0;
+}

@@ -7,7 +7,11 @@
 //     pa[p] = float4(-X, -X, -Y, -Y)   pb[p] = float4(-Z, -Z, w, w)
 //   where X = x - o(cell) is the cell-relative coordinate (Sec. 4.4's shift trick applied per
 //   cell), stored negated and duplicated so that one packed f32x2 add forms two separations.
-//     plo[p] = float4(-Xlo, -Ylo, -Zlo, 0)  (float64 inputs with ravg only: x - o = X + Xlo)
+//   For mocks the second copies hold the absolute position instead: pa = (-X, x, -Y, y),
+//   pb = (-Z, z, w, w) with x, y, z rounded to float32.
+//     plo[2p] = float4(-Xlo, -Xlo, -Ylo, -Ylo), plo[2p+1] = float4(-Zlo, -Zlo, 0, 0)
+//   (float64 inputs with ravg only: x - o = X + Xlo; for mocks the second copies hold the low
+//   parts of the absolute position, x = float(x) + xlo)
 //     orig[p] = index of the point in its input arrays
 //   cell_start[set cell offset + c] .. [c+1] delimit a cell's points.
 //   A work item is one (i tile, j range, shift) triple of a cell pair (Sec. 4.3).
@@ -110,10 +114,10 @@ struct CfBand {
 // Everything the kernels need for one call
 struct CfDevPlan {
     CfGrid g;
-    int kind;              // 0 r, 1 rppi, 2 wp, 3 theta
+    int kind;              // 0 r, 1 rppi, 2 wp, 3 theta, 4 mocks (rp-pi of observed positions)
     int nb;                // r / rp / theta bins
     int npi;               // pi bins (1 for r, theta, wp)
-    int nslot;             // nb * npi for rppi, nb otherwise
+    int nslot;             // nb * npi for rppi and mocks, nb otherwise
     int weighted, ravg, f64lo;
     int nsets, njobs;
     int tile;              // max i tile (64 or 128)
@@ -130,8 +134,14 @@ struct CfDevPlan {
     const CfBand *band;    // device table of the bands
     double adlo, ah;       // lowest band edge and band height (radians)
     double tsearch;        // neighbour-search angle (radians): the largest edge, widened
-    float cut_r;           // candidate cut on the FP32 squared separation (above the last band)
-    float cut_p;           // candidate cut on the FP32 |dz| (rp-pi / wp)
+    float cut_r;           // candidate cut on the FP32 squared separation (above the last band);
+                           // mocks: on rp^2 in the form (s.s - cut_r) l.l < (s.l)^2
+    float cut_p;           // candidate cut on the FP32 |dz| (rp-pi / wp); mocks: on pi^2 in the
+                           // form (s.l)^2 < cut_p l.l
+    float near2;           // mocks: a candidate whose FP32 l.l is below this goes to the FP64
+                           // recheck when its s.s - cut_r is below cut_su (0: no candidate can be)
+    float cut_su;
+    double smax2;          // mocks: largest |s|^2 of a counted pair (rmax^2 + pimax^2, widened)
     double e2[CF_MAX_BINS + 1];     // squared edges (FP64, host-computed)
-    double pe[CF_MAX_PIBINS + 1];   // pi edges
+    double pe[CF_MAX_PIBINS + 1];   // pi edges (mocks: squared pi edges)
 };

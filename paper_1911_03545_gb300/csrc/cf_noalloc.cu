@@ -96,6 +96,19 @@ __global__ void na_pairs(const NaParams P, CfSetDesc A, CfSetDesc B, unsigned ch
         const double wi = P.weighted ? cf_load(A.w, A.dtype, i) : 1.0;
         if (P.self_pairs) wsq += __dmul_rn(wi, wi);
         for (int64_t j = P.autoc ? i + 1 : 0; j < B.n; j++) {
+            if (P.kind == 4) {
+                // mocks (Appendix A.2.1): squared pi edges in pe
+                double rp2, pi2;
+                cf_mocks64(xi, yi, zi, cf_load(B.x, B.dtype, j), cf_load(B.y, B.dtype, j), cf_load(B.z, B.dtype, j),
+                           rp2, pi2);
+                if (!(pi2 < P.pe[P.npi]) || rp2 < P.e2[0] || rp2 >= P.e2[P.nb]) continue;
+                const int slot = na_find(P.e2, P.nb, rp2) * P.npi + na_find(P.pe, P.npi, pi2);
+                const double ww = P.weighted ? __dmul_rn(wi, cf_load(B.w, B.dtype, j)) : 1.0;
+                atomicAdd(sc + slot, 1ull);
+                if (P.weighted) atomicAdd(sw + slot, ww);
+                if (P.ravg) atomicAdd(sr + slot, __dmul_rn(ww, sqrt(rp2)));
+                continue;
+            }
             const double dx = na_sep(xi, cf_load(B.x, B.dtype, j), P.L[0]);
             const double dy = na_sep(yi, cf_load(B.y, B.dtype, j), P.L[1]);
             const double dz = na_sep(zi, cf_load(B.z, B.dtype, j), P.L[2]);
@@ -201,7 +214,7 @@ extern "C" cf_status cf_count_noalloc(const cf_params *params, const cf_points *
     std::memset(&P, 0, sizeof(P));
     P.kind = params->kind;
     P.nb = params->nbins;
-    P.npi = params->kind == CF_DD_RPPI ? params->npibins : 1;
+    P.npi = (params->kind == CF_DD_RPPI || params->kind == CF_DD_RPPI_MOCKS) ? params->npibins : 1;
     P.nslot = P.nb * P.npi;
     if (P.nslot > CF_NOALLOC_MAX_SLOTS) {
         g_err = "more than " + std::to_string(CF_NOALLOC_MAX_SLOTS) + " histogram slots (the scratch limit)";

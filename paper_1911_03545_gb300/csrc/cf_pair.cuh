@@ -35,7 +35,10 @@
 
 namespace cfpair {
 
-constexpr int KIND_R = 0, KIND_RPPI = 1, KIND_WP = 2, KIND_THETA = 3;
+constexpr int KIND_R = 0, KIND_RPPI = 1, KIND_WP = 2, KIND_THETA = 3, KIND_MOCKS = 4;
+
+// rp-pi kinds keep one histogram per warp updated by shared atomics (nb * npi slots)
+__host__ __device__ constexpr bool warp_hist(int kind) { return kind == KIND_RPPI || kind == KIND_MOCKS; }
 
 __host__ __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
@@ -49,7 +52,7 @@ constexpr uint32_t RM = RING - 1;
 static_assert(CFI_JMAX <= 512, "a ring code holds a 7-bit i slot and a 9-bit j");
 __host__ __device__ __forceinline__ uint32_t warp_hist_bytes(int kind, bool W, bool R, int nslot)
 {
-    if (kind == KIND_RPPI) {
+    if (warp_hist(kind)) {
         uint32_t b = ((uint32_t)nslot * 4u + 7u) & ~7u;
         if (W) b += nslot * 8u;
         if (R) b += nslot * 8u;
@@ -144,6 +147,56 @@ static __device__ __noinline__ void push_recheck(const CfPairArgs &a, uint32_t i
     if (k < a.qcap) a.queue[k] = make_uint4(a.orig[ip], a.orig[jp], job, 0u);
 }
 
+// rp of a counted pair of the mocks kind, for ravg (Appendix A.2.1).  rp^2 = |s x l|^2 / |l|^2,
+// and s x l = s x v_i because l = v_i - s / 2: the cancellation that makes s.s - pi^2 inaccurate
+// for rp << pi moves into one cross product of exactly known numbers (s as a hi + lo pair from
+// the cell-relative coordinates, v_i as float32 plus its lo part), taken by Kahan's difference of
+// products (error <= 2u of each component).  ip: the i point; bs, jl: the stage buffer and the j
+// point's index in it; sh / sl: the item's shift, hi and lo.  Rare (counted pairs with ravg
+// only), so kept out of line.
+template <bool LO>
+static __device__ __noinline__ float mocks_rp(const CfPairArgs &a, uint32_t ip, const float *bs, uint32_t jl,
+                                              float shx, float shy, float shz, float slx, float sly, float slz)
+{
+    const float4 A = reinterpret_cast<const float4 *>(a.pa)[ip];
+    const float4 B = reinterpret_cast<const float4 *>(a.pb)[ip];
+    const float X[3] = {-A.x, -A.z, -B.x}, Ah[3] = {A.y, A.w, B.y};
+    const float ish[3] = {shx, shy, shz}, isl[3] = {slx, sly, slz};
+    float XL[3] = {0.f, 0.f, 0.f}, AL[3] = {0.f, 0.f, 0.f}, XJL[3] = {0.f, 0.f, 0.f};
+    if (LO) {
+        const float4 C = reinterpret_cast<const float4 *>(a.plo)[2 * (size_t)ip];
+        const float4 D = reinterpret_cast<const float4 *>(a.plo)[2 * (size_t)ip + 1];
+        XL[0] = -C.x; XL[1] = -C.z; XL[2] = -D.x;
+        AL[0] = C.y; AL[1] = C.w; AL[2] = D.y;
+        XJL[0] = bs[4 * JSTAGE + jl]; XJL[1] = bs[5 * JSTAGE + jl]; XJL[2] = bs[6 * JSTAGE + jl];
+    }
+    const float XJ[3] = {bs[jl], bs[JSTAGE + jl], bs[2 * JSTAGE + jl]};   // -X_j
+    float sh[3], sl[3], l[3];
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        float h, e, h2, e2;
+        two_sum(X[d], ish[d], h, e);          // X_i + shift hi, exactly h + e
+        two_sum(h, XJ[d], h2, e2);            // - X_j, exactly h2 + e2
+        sh[d] = h2;
+        sl[d] = ((e + e2) + isl[d]) + (XL[d] + XJL[d]);
+        l[d] = fmaf(-0.5f, sh[d], Ah[d]) + (AL[d] - 0.5f * sl[d]);
+    }
+    float c2 = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; d++) {
+        const int p = (d + 1) % 3, q = (d + 2) % 3;
+        // component d of s x A: s_p A_q - s_q A_p
+        const float w = sh[q] * Ah[p];
+        const float err = fmaf(sh[q], Ah[p], -w);
+        const float f = fmaf(sh[p], Ah[q], -w);
+        const float corr = (sh[p] * AL[q] - sh[q] * AL[p]) + (sl[p] * Ah[q] - sl[q] * Ah[p]);
+        const float c = (f - err) + corr;
+        c2 = fmaf(c, c, c2);
+    }
+    const float ll = fmaf(l[2], l[2], fmaf(l[1], l[1], l[0] * l[0]));
+    return sqrtf(__fdiv_rn(c2, ll));
+}
+
 template <int KIND, bool W, bool R, bool WRAP, bool LO>
 struct Warp {
     const CfPairArgs &a;
@@ -160,6 +213,8 @@ struct Warp {
     uint32_t icnt, ibeg, jbeg, job, head, tail, ltmask;
     float cut_r, cut_p;
     float Lx, Ly, Lz, iLx, iLy, iLz;
+    float near2, cut_su;    // mocks: the near-observer test (near2 = 0: off)
+    float ish[3], isl[3];   // mocks with ravg: the item's shift, hi and lo
 
     __device__ Warp(const CfPairArgs &args) : a(args) {}
 
@@ -227,7 +282,7 @@ struct Warp {
     __device__ __forceinline__ void finish(uint32_t k, uint32_t vb, float wp, uint32_t il, uint32_t j)
     {
         if (k < K_OUT) {
-            if (KIND == KIND_RPPI) acc_sh(k, __uint_as_float(vb), wp);
+            if (warp_hist(KIND)) acc_sh(k, __uint_as_float(vb), wp);
             else acc_lp(k, __uint_as_float(vb), wp);
         } else if (k == K_AMB) {
             push(ibeg + il, jbeg + j);
@@ -271,6 +326,35 @@ struct Warp {
             head += n;
         }
         __syncwarp();
+    }
+
+    // Stage chunk c of the j range into its buffer: arrays 0 x, 1 y, 2 z, 3 w, 4-6 lo parts of
+    // x, y, z (all negated as stored); a j past the end of the range reads the far-away sentinel
+    __device__ __forceinline__ void stage(uint32_t c, uint32_t jcnt)
+    {
+        constexpr uint32_t NA = stage_arrays(W, LO);
+        float *bs = jst + (c & 1u) * NA * JSTAGE;
+        const uint32_t j = c * JSTAGE + lane;
+        if (j < jcnt) {
+            const float *fa = reinterpret_cast<const float *>(a.pa + jbeg + j);
+            const float *fb = reinterpret_cast<const float *>(a.pb + jbeg + j);
+            cp_async4(bs + lane, fa);
+            cp_async4(bs + JSTAGE + lane, fa + 2);
+            cp_async4(bs + 2 * JSTAGE + lane, fb);
+            if (W) cp_async4(bs + 3 * JSTAGE + lane, fb + 2);
+            if (LO) {
+                const float *fl = reinterpret_cast<const float *>(a.plo + 2 * (size_t)(jbeg + j));
+                cp_async4(bs + 4 * JSTAGE + lane, fl);
+                cp_async4(bs + 5 * JSTAGE + lane, fl + 2);
+                cp_async4(bs + 6 * JSTAGE + lane, fl + 4);
+            }
+        } else {
+            bs[lane] = 1e18f;
+            bs[JSTAGE + lane] = 1e18f;
+            bs[2 * JSTAGE + lane] = 1e18f;
+            if (W) bs[3 * JSTAGE + lane] = 0.f;
+            if (LO) bs[4 * JSTAGE + lane] = bs[5 * JSTAGE + lane] = bs[6 * JSTAGE + lane] = 0.f;
+        }
     }
 
     // One work item.  Q = i slots per lane; DIAG: the i tile and the j range are the same cell
@@ -327,38 +411,12 @@ struct Warp {
             ez[q] = f2_pack(ve[2], ve[2]);
             wi[q] = f2_pack(vw, vw);
         }
-        // stage arrays of one chunk: 0 x, 1 y, 2 z, 3 w, 4-6 lo parts of x, y, z (all negated
-        // as stored); a j past the end of the range reads the far-away sentinel
         constexpr uint32_t NA = stage_arrays(W, LO);
-        auto issue = [&](uint32_t c) {
-            float *bs = jst + (c & 1u) * NA * JSTAGE;
-            const uint32_t j = c * JSTAGE + lane;
-            if (j < jcnt) {
-                const float *fa = reinterpret_cast<const float *>(a.pa + jbeg + j);
-                const float *fb = reinterpret_cast<const float *>(a.pb + jbeg + j);
-                cp_async4(bs + lane, fa);
-                cp_async4(bs + JSTAGE + lane, fa + 2);
-                cp_async4(bs + 2 * JSTAGE + lane, fb);
-                if (W) cp_async4(bs + 3 * JSTAGE + lane, fb + 2);
-                if (LO) {
-                    const float *fl = reinterpret_cast<const float *>(a.plo + 2 * (size_t)(jbeg + j));
-                    cp_async4(bs + 4 * JSTAGE + lane, fl);
-                    cp_async4(bs + 5 * JSTAGE + lane, fl + 2);
-                    cp_async4(bs + 6 * JSTAGE + lane, fl + 4);
-                }
-            } else {
-                bs[lane] = 1e18f;
-                bs[JSTAGE + lane] = 1e18f;
-                bs[2 * JSTAGE + lane] = 1e18f;
-                if (W) bs[3 * JSTAGE + lane] = 0.f;
-                if (LO) bs[4 * JSTAGE + lane] = bs[5 * JSTAGE + lane] = bs[6 * JSTAGE + lane] = 0.f;
-            }
-        };
         const uint32_t nchunk = (jcnt + JSTAGE - 1) / JSTAGE;
-        issue(0);
+        stage(0, jcnt);
         cp_async_commit();
         for (uint32_t c = 0; c < nchunk; c++) {
-            if (c + 1 < nchunk) issue(c + 1);
+            if (c + 1 < nchunk) stage(c + 1, jcnt);
             cp_async_commit();
             cp_async_wait<1>();
             __syncwarp();
@@ -501,6 +559,184 @@ struct Warp {
         if (COMPACT) drain(true);
     }
 
+    // ---- DD(rp, pi) of observed positions (Appendix A.2.1) ----
+    // Bin one mocks candidate from its FP32 separation d = s, the i point's position A_i, (s.l)^2
+    // and l.l; jl: the j point's index in the stage.  pi^2 = (s.l)^2 / l.l; rp^2 = |s x A_i|^2 / l.l
+    // (s x A_i = s x l): its error scales with rp, where s.s - pi^2 would lose everything below
+    // the rounding of s.s when rp << pi.
+    __device__ __forceinline__ void bin_mocks(float dx, float dy, float dz, float Ax, float Ay, float Az, float sl2,
+                                              float ll, float wp, uint32_t il, uint32_t j, uint32_t jl,
+                                              const float *bs)
+    {
+        if (near2 > 0.f && ll < near2) {
+            push(ibeg + il, jbeg + j);        // midpoint near the observer: FP64
+            return;
+        }
+        const float qx = fmaf(dy, Az, -(dz * Ay)), qy = fmaf(dz, Ax, -(dx * Az)), qz = fmaf(dx, Ay, -(dy * Ax));
+        const float c2 = fmaf(qz, qz, fmaf(qy, qy, qx * qx));
+        const float pi2 = __fdividef(sl2, ll);
+        const float rp2 = __fdividef(c2, ll);
+        const uint32_t cr = lut_class(lr, fine, __float_as_uint(rp2));
+        const uint32_t cz = lut_class(lp, fine, __float_as_uint(pi2));
+        if (cr == CFI_CLS_OUT || cz == CFI_CLS_OUT) return;
+        if (max(cr, cz) == CFI_CLS_AMB) {
+            push(ibeg + il, jbeg + j);
+            return;
+        }
+        const uint32_t slot = cr * (uint32_t)npi + cz;
+        atomicAdd(h_cnt + slot, 1u);
+        if (W) atomicAdd(h_wd + slot, (double)wp);
+        if (R) {
+            const float r = mocks_rp<LO>(a, ibeg + il, bs, jl, ish[0], ish[1], ish[2], isl[0], isl[1], isl[2]);
+            atomicAdd(h_rd + slot, (double)(W ? wp * r : r));
+        }
+    }
+
+    // One work item of the mocks kind (the direct form; Q and DIAG as in run).  Per pair, packed
+    // FP32x2: s = v_i - v_j (cell-relative), l = A_i - s / 2, u = s.s - cut_r, s.l, l.l; the
+    // candidate cut needs no division: rp^2 = s.s - pi^2 < cut_r and pi^2 < cut_p become
+    // u l.l < (s.l)^2 < cut_p l.l (cut_r lies above the last edge by twice this form's error).
+    // Candidates are binned by bin_mocks.
+    template <int Q, bool DIAG>
+    __device__ __forceinline__ void run_mocks(const CfItem &it)
+    {
+        icnt = it.cnt & 0xFFFFu;
+        const uint32_t jcnt = it.cnt >> 16;
+        ibeg = it.ibeg;
+        jbeg = it.jbeg;
+        job = it.meta & CFI_ITEM_JOBMASK;
+        if (R) {
+#pragma unroll
+            for (int d = 0; d < 3; d++) { ish[d] = it.s[d]; isl[d] = it.slo[d]; }
+        }
+        u64 sx[Q], sy[Q], sz[Q], ex[Q], ey[Q], ez[Q], ax[Q], ay[Q], az[Q], wi[Q];
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            const uint32_t il = lane + 32u * q;
+            float vs[3], ve[3], va[3], vw = 0.f;
+#pragma unroll
+            for (int d = 0; d < 3; d++) { vs[d] = 1e18f; ve[d] = 0.f; va[d] = 0.f; }
+            if (il < icnt) {
+                const ulonglong2 A = a.pa[ibeg + il], B = a.pb[ibeg + il];
+                const float X[3] = {-f2_lo(A.x), -f2_lo(A.y), -f2_lo(B.x)};
+                va[0] = f2_hi(A.x);
+                va[1] = f2_hi(A.y);
+                va[2] = f2_hi(B.x);
+                float XL[3] = {0.f, 0.f, 0.f};
+                if (LO) {
+                    const ulonglong2 C = a.plo[2 * (size_t)(ibeg + il)], D = a.plo[2 * (size_t)(ibeg + il) + 1];
+                    XL[0] = -f2_lo(C.x);
+                    XL[1] = -f2_lo(C.y);
+                    XL[2] = -f2_lo(D.x);
+                }
+#pragma unroll
+                for (int d = 0; d < 3; d++) {
+                    if (R) {
+                        float t, e;
+                        two_sum(X[d], it.s[d], t, e);
+                        vs[d] = t;
+                        ve[d] = (e + it.slo[d]) + XL[d];
+                    } else {
+                        vs[d] = X[d] + it.s[d];
+                    }
+                }
+                vw = f2_lo(B.y);
+            }
+            sx[q] = f2_pack(vs[0], vs[0]);
+            sy[q] = f2_pack(vs[1], vs[1]);
+            sz[q] = f2_pack(vs[2], vs[2]);
+            ex[q] = f2_pack(ve[0], ve[0]);
+            ey[q] = f2_pack(ve[1], ve[1]);
+            ez[q] = f2_pack(ve[2], ve[2]);
+            ax[q] = f2_pack(va[0], va[0]);
+            ay[q] = f2_pack(va[1], va[1]);
+            az[q] = f2_pack(va[2], va[2]);
+            wi[q] = f2_pack(vw, vw);
+        }
+        const u64 NH = f2_pack(-0.5f, -0.5f), NCR = f2_pack(-cut_r, -cut_r), CP = f2_pack(cut_p, cut_p);
+        constexpr uint32_t NA = stage_arrays(W, LO);
+        const uint32_t nchunk = (jcnt + JSTAGE - 1) / JSTAGE;
+        stage(0, jcnt);
+        cp_async_commit();
+        for (uint32_t c = 0; c < nchunk; c++) {
+            if (c + 1 < nchunk) stage(c + 1, jcnt);
+            cp_async_commit();
+            cp_async_wait<1>();
+            __syncwarp();
+            const float *bs = jst + (c & 1u) * NA * JSTAGE;
+            const uint32_t j0 = c * JSTAGE;
+            const uint32_t n = min(JSTAGE, jcnt - j0);
+            const int nq = DIAG ? min((int)((icnt + 31u) >> 5), (int)c + 1) : Q;
+#pragma unroll 1
+            for (uint32_t jj = 0; jj < n; jj += 2) {
+                const uint32_t j = j0 + jj;
+                const u64 xj = *reinterpret_cast<const u64 *>(bs + jj);
+                const u64 yj = *reinterpret_cast<const u64 *>(bs + JSTAGE + jj);
+                const u64 zj = *reinterpret_cast<const u64 *>(bs + 2 * JSTAGE + jj);
+                u64 lxj = 0, lyj = 0, lzj = 0;
+                if (LO) {
+                    lxj = *reinterpret_cast<const u64 *>(bs + 4 * JSTAGE + jj);
+                    lyj = *reinterpret_cast<const u64 *>(bs + 5 * JSTAGE + jj);
+                    lzj = *reinterpret_cast<const u64 *>(bs + 6 * JSTAGE + jj);
+                }
+#pragma unroll
+                for (int q = 0; q < Q; q++) {
+                    if (DIAG && q >= nq) continue;
+                    u64 dx = f2_add(sx[q], xj), dy = f2_add(sy[q], yj), dz = f2_add(sz[q], zj);
+                    if (R) {
+                        dx = f2_add(dx, LO ? f2_add(ex[q], lxj) : ex[q]);
+                        dy = f2_add(dy, LO ? f2_add(ey[q], lyj) : ey[q]);
+                        dz = f2_add(dz, LO ? f2_add(ez[q], lzj) : ez[q]);
+                    }
+                    const u64 lx = f2_fma(dx, NH, ax[q]), ly = f2_fma(dy, NH, ay[q]), lz = f2_fma(dz, NH, az[q]);
+                    u64 uu = f2_fma(dx, dx, NCR);
+                    uu = f2_fma(dy, dy, uu);
+                    uu = f2_fma(dz, dz, uu);
+                    u64 sl = f2_mul(dx, lx);
+                    sl = f2_fma(dy, ly, sl);
+                    sl = f2_fma(dz, lz, sl);
+                    u64 ll = f2_mul(lx, lx);
+                    ll = f2_fma(ly, ly, ll);
+                    ll = f2_fma(lz, lz, ll);
+                    const u64 sl2 = f2_mul(sl, sl);
+                    const u64 m = f2_mul(uu, ll);
+                    const u64 cpl = f2_mul(CP, ll);
+                    bool in0 = f2_lo(m) < f2_lo(sl2) && f2_lo(sl2) < f2_lo(cpl);
+                    bool in1 = f2_hi(m) < f2_hi(sl2) && f2_hi(sl2) < f2_hi(cpl);
+                    if (near2 > 0.f) {
+                        // a midpoint near the observer makes the multiplied cut meaningless:
+                        // there only s.s decides, and the pair goes to FP64
+                        if (f2_lo(ll) < near2) in0 = f2_lo(uu) < cut_su;
+                        if (f2_hi(ll) < near2) in1 = f2_hi(uu) < cut_su;
+                    }
+                    const uint32_t il = lane + 32u * q;
+                    // empty slots and j past the range hold far-away sentinels whose products
+                    // overflow; mask them by index rather than rely on those comparisons
+                    in0 = in0 && il < icnt;
+                    in1 = in1 && il < icnt && j + 1 < jcnt;
+                    if (DIAG) {
+                        in0 = in0 && j > il;
+                        in1 = in1 && j + 1 > il;
+                    }
+                    if (in0 || in1) {
+                        const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
+                        const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
+                        const float Ax = f2_lo(ax[q]), Ay = f2_lo(ay[q]), Az = f2_lo(az[q]);
+                        if (in0)
+                            bin_mocks(f2_lo(dx), f2_lo(dy), f2_lo(dz), Ax, Ay, Az, f2_lo(sl2), f2_lo(ll), f2_lo(wp), il,
+                                      j, jj, bs);
+                        if (in1)
+                            bin_mocks(f2_hi(dx), f2_hi(dy), f2_hi(dz), Ax, Ay, Az, f2_hi(sl2), f2_hi(ll), f2_hi(wp), il,
+                                      j + 1, jj + 1, bs);
+                    }
+                }
+            }
+            __syncwarp();       // the chunk buffer is refilled two chunks later
+        }
+        cp_async_wait<0>();
+        __syncwarp();
+    }
+
     __device__ void flush(uint32_t jb)
     {
         __syncwarp();
@@ -508,7 +744,7 @@ struct Warp {
         for (int sl = lane; sl < nslot; sl += 32) {
             unsigned long long c = 0;
             double ws = 0.0, rs = 0.0;
-            if (KIND == KIND_RPPI) {
+            if (warp_hist(KIND)) {
                 c = h_cnt[sl];
                 h_cnt[sl] = 0;
                 if (W) { ws = h_wd[sl]; h_wd[sl] = 0.0; }
@@ -578,6 +814,8 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     w.lp = {P->lp.base, P->lp.shift, P->lp.last, s_lut + P->lp.coff};
     w.cut_r = P->cut_r;
     w.cut_p = P->cut_p;
+    w.near2 = P->near2;
+    w.cut_su = P->cut_su;
     w.Lx = a.L[0]; w.Ly = a.L[1]; w.Lz = a.L[2];
     w.iLx = a.L[0] > 0.f ? 1.0f / a.L[0] : 0.f;
     w.iLy = a.L[1] > 0.f ? 1.0f / a.L[1] : 0.f;
@@ -596,7 +834,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
         w.rc = (uint16_t *)q;
     }
     w.h_cnt = (uint32_t *)(my + hoff);
-    if (KIND == KIND_RPPI) {
+    if (warp_hist(KIND)) {
         uint32_t o = ((uint32_t)a.nslot * 4u + 7u) & ~7u;
         w.h_wd = (double *)(my + hoff + o);
         w.h_rd = (double *)(my + hoff + o + (W ? a.nslot * 8u : 0u));
@@ -631,10 +869,17 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
         }
         const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
         const uint32_t ic = it.cnt & 0xFFFFu;
-        if (diag) w.template run<4, true, COMPACT>(it);
-        else if (ic <= 32u) w.template run<1, false, COMPACT>(it);
-        else if (ic <= 64u) w.template run<2, false, COMPACT>(it);
-        else w.template run<4, false, COMPACT>(it);
+        if (KIND == KIND_MOCKS) {
+            if (diag) w.template run_mocks<4, true>(it);
+            else if (ic <= 32u) w.template run_mocks<1, false>(it);
+            else if (ic <= 64u) w.template run_mocks<2, false>(it);
+            else w.template run_mocks<4, false>(it);
+        } else {
+            if (diag) w.template run<4, true, COMPACT>(it);
+            else if (ic <= 32u) w.template run<1, false, COMPACT>(it);
+            else if (ic <= 64u) w.template run<2, false, COMPACT>(it);
+            else w.template run<4, false, COMPACT>(it);
+        }
         t = tn;
         it = nx;
     }

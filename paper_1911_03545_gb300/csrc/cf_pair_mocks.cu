@@ -1,0 +1,19 @@
+// cf_pair_mocks.cu -- instances of the pair kernel for DD(rp, pi) of observed positions
+// (Appendix A.2.1; see cf_pair.cuh).  Non-periodic only, direct form only.
+#include "cf_pair.cuh"
+
+using namespace cfpair;
+
+#define CF_L(W, R, LO) return launch_variant<KIND_MOCKS, W, R, false, LO, false>(c, a, num_sms, st, grid_out, warps_out)
+
+cudaError_t cfp_launch_mocks(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
+                             int *warps_out)
+{
+    if (c.wrap || c.variant == 2) return cudaErrorInvalidValue;
+    if (c.weighted) {
+        if (c.ravg) { if (c.lo) CF_L(true, true, true); else CF_L(true, true, false); }
+        CF_L(true, false, false);
+    }
+    if (c.ravg) { if (c.lo) CF_L(false, true, true); else CF_L(false, true, false); }
+    CF_L(false, false, false);
+}

@@ -72,7 +72,7 @@ uint32_t cfp_float_above_bits(double v)
 int cfp_check_params(const cf_params *p, std::string &err)
 {
     if (!p) { err = "params is NULL"; return CF_ERR_ARG; }
-    if (p->kind < CF_DD_R || p->kind > CF_DD_THETA) { err = "unknown kind"; return CF_ERR_ARG; }
+    if (p->kind < CF_DD_R || p->kind > CF_DD_RPPI_MOCKS) { err = "unknown kind"; return CF_ERR_ARG; }
     if (p->nbins < 1 || p->nbins > CF_MAX_BINS) { err = "nbins must be in [1, 252]"; return CF_ERR_ARG; }
     if (!p->edges) { err = "edges is NULL"; return CF_ERR_ARG; }
     if (!all_finite(p->edges, p->nbins + 1)) { err = "edges must be finite"; return CF_ERR_ARG; }
@@ -83,7 +83,8 @@ int cfp_check_params(const cf_params *p, std::string &err)
         if (p->periodic) { err = "DD(theta) is non-periodic"; return CF_ERR_ARG; }
         if (p->edges[p->nbins] > 180.0) { err = "theta edges must be <= 180 degrees"; return CF_ERR_ARG; }
     }
-    if (p->kind == CF_DD_RPPI || p->kind == CF_WP) {
+    if (p->kind == CF_DD_RPPI_MOCKS && p->periodic) { err = "DD(rp, pi) of mocks is non-periodic"; return CF_ERR_ARG; }
+    if (p->kind == CF_DD_RPPI || p->kind == CF_WP || p->kind == CF_DD_RPPI_MOCKS) {
         if (!(std::isfinite(p->pimax) && p->pimax > 0)) { err = "pimax must be finite and > 0"; return CF_ERR_ARG; }
         if (p->npibins < 1 || p->npibins > CF_MAX_PIBINS) { err = "npibins must be in [1, 252]"; return CF_ERR_ARG; }
     }
@@ -109,10 +110,13 @@ void cfp_edges(const cf_params *p, double *e2, double *pe)
             e2[k] = e * e;
         }
     }
-    if (p->kind == CF_DD_RPPI || p->kind == CF_WP) {
+    if (p->kind == CF_DD_RPPI || p->kind == CF_WP || p->kind == CF_DD_RPPI_MOCKS) {
         double dpi = p->pimax / p->npibins;
         for (int m = 0; m < p->npibins; m++) pe[m] = (double)m * dpi;
         pe[p->npibins] = p->pimax;
+        // mocks bin pi^2 against the squared edges (Appendix A.2.1 gives pi through s.l / |l|)
+        if (p->kind == CF_DD_RPPI_MOCKS)
+            for (int m = 0; m <= p->npibins; m++) pe[m] = pe[m] * pe[m];
     }
 }
 
@@ -248,7 +252,8 @@ void trig_range(double a0, double a1, int c, double &mn, double &mx)
 }  // namespace
 
 int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int f64,
-                  const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err, int angular)
+                  const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err, int angular,
+                  double vmin)
 {
     CfHostPlan &H = *out;
     std::memset(&H.d, 0, sizeof(H.d));
@@ -258,7 +263,7 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
     CfDevPlan &D = H.d;
     D.kind = p->kind;
     D.nb = p->nbins;
-    D.npi = p->kind == CF_DD_RPPI ? p->npibins : 1;
+    D.npi = (p->kind == CF_DD_RPPI || p->kind == CF_DD_RPPI_MOCKS) ? p->npibins : 1;
     D.nslot = D.nb * D.npi;
     D.weighted = p->weight == CF_W_PAIR_PRODUCT;
     D.ravg = p->output_ravg != 0;
@@ -268,9 +273,14 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
     D.pimax = p->pimax;
     cfp_edges(p, D.e2, D.pe);
     const bool rppi_like = p->kind == CF_DD_RPPI || p->kind == CF_WP;
+    const bool mocks = p->kind == CF_DD_RPPI_MOCKS;
+    // mocks: a counted pair has |s|^2 = rp^2 + pi^2 < rmax^2 + pimax^2 along no fixed axis
+    const double S2 = mocks ? D.e2[D.nb] + p->pimax * p->pimax : 0.0;
+    D.smax2 = S2 * (1.0 + 1e-6);
 
     // ---- largest separation per axis (cell width before refinement), Sec. 4.1 ----
     double rmax = std::sqrt(D.e2[D.nb]);      // r, rp or chord
+    if (mocks) rmax = std::sqrt(S2);
     H.W[0] = H.W[1] = rmax;
     H.W[2] = rppi_like ? p->pimax : rmax;
 
@@ -334,7 +344,7 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
                 double gx = gap(0, dx), gy = gap(1, dy), gz = gap(2, dz);
                 bool keep;
                 if (rppi_like) keep = (gx * gx + gy * gy < D.e2[D.nb] * (1 + 1e-6)) && (gz < p->pimax * (1 + 1e-6));
-                else keep = gx * gx + gy * gy + gz * gz < D.e2[D.nb] * (1 + 1e-6);
+                else keep = gx * gx + gy * gy + gz * gz < (mocks ? S2 : D.e2[D.nb]) * (1 + 1e-6);
                 if (keep) H.stencil.push_back({{dx, dy, dz}, 0});
             }
     if ((int)H.stencil.size() > CFI_MAX_STENCIL) { err = "stencil too large"; return CF_ERR_ARG; }
@@ -476,6 +486,96 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
         for (int m = 0; m <= p->npibins; m++)
             H.band_p[m] = SAFETY * (H.theta_rel * D.pe[m] + H.delta[2] + 4 * U64 * D.pe[m]);
     }
+    H.eta = 0.0;
+    D.near2 = 0.0f;
+    D.cut_su = 0.0f;
+    if (mocks) {
+        // Error model of the mocks kernel (Appendix A.2.1 evaluated in FP32; derivation in the
+        // design notes).  Per pair: s from the cell-relative coordinates (per-axis error <= delta,
+        // Dl2 its 2-norm), l = A_i - s/2 from the float32 absolute position A_i; the binned values
+        // are pi^2 = (s.l)^2 / l.l and rp^2 = |s x A_i|^2 / l.l (s x A_i = s x l exactly), the fast
+        // division (<= 2 ulp) for both.  A candidate with l.l below near2 = S^2 goes to the FP64
+        // recheck, so every other one has |l| >= 0.999 S and |A_i| <= 1.51 |l|.
+        double Dl = 0.0, Dl2 = 0.0;
+        for (int a = 0; a < 3; a++) {
+            Dl += H.delta[a];
+            Dl2 += H.delta[a] * H.delta[a];
+        }
+        Dl2 = std::sqrt(Dl2);
+        const double uA = f64 ? u : 0.0;
+        const double S = std::sqrt(S2);
+        const double lmin = 0.999 * S;
+        const double eta = (uA + u) + (0.5 * uA * S + 0.5 * Dl2) / lmin;   // |error of l| / |l|
+        if (!(eta < 1e-4)) {
+            err = "coordinates too large for the FP32 mocks kernel at these separations";
+            return CF_ERR_ARG;
+        }
+        H.eta = eta;
+        const double ell = (2 * eta + eta * eta + 3 * u) * 1.01;          // relative error of l.l
+        const double aA = 1.51;                                          // |A_i| / |l|
+        const double truth = 64 * U64;                    // the FP64 evaluation's own error / S^2
+        const double pm2 = p->pimax * p->pimax;
+        // |pi^2 - its FP32 value| for pi <= pimx, |s| <= Sx, rp <= rpx.  To first order the error
+        // of s enters as 2 pi (eps . l/|l|) and that of l as 2 pi (rp_vec . dl) / |l|; the dot
+        // product's rounding as 2 pi 3u |s|; l.l, the square and the division relatively.
+        auto epi = [&](double pimx, double Sx, double rpx) {
+            const double e1 = (Dl2 + rpx * eta + 3 * u * Sx) * 1.001;
+            const double e2nd = Dl2 + Sx * eta + 3 * u * Sx;
+            return (2 * pimx * e1 + e2nd * e2nd + pimx * pimx * ell) * (1 + 5 * u) + 5 * u * pimx * pimx;
+        };
+        // |rp^2 - its FP32 value| for rp <= rpx, |s| <= Sx: |c - its FP32 value| <= g |l| with
+        // c = s x A_i (input errors |eps||A| + |s||dA|, each component's fma rounding), then
+        // |c|^2's chain, l.l and the division relatively
+        auto erp = [&](double rpx, double Sx) {
+            const double g = aA * (Dl2 + Sx * uA + u * (Sx + Dl2) * 1.001) + u * rpx;
+            return 2 * rpx * g + g * g + rpx * rpx * (7 * u + ell);
+        };
+        for (int k = 0; k <= D.nb; k++) {
+            const double Sk = std::sqrt(D.e2[k] + pm2) * 1.001;
+            H.band_r[k] = SAFETY * erp(std::sqrt(D.e2[k]) * 1.0001, Sk) * 1.001 + truth * Sk * Sk;
+        }
+        const double rpm = std::sqrt(D.e2[D.nb] + H.band_r[D.nb]) * 1.001;
+        for (int m = 0; m <= p->npibins; m++) {
+            const double Sm = std::sqrt(rpm * rpm + D.pe[m]) * 1.001;
+            H.band_p[m] = SAFETY * epi(std::sqrt(D.pe[m]) * 1.0001 + 1e-300, Sm, rpm) + truth * Sm * Sm;
+        }
+        // Candidate cuts in the multiplied form (s.s - cut_r) l.l < (s.l)^2 < cut_p l.l, loose by
+        // twice the error of that form: s.s (input error, the chain from -cut_r), pi^2 as above
+        // with the full |s| in place of rp, and the form's own roundings.
+        const double Cbound = 1.1 * S2;
+        auto ess = [&](double Sx) {
+            const double a = Sx + Dl;
+            return 2 * Sx * Dl + Dl * Dl + 3 * u * (Cbound + a * a) + u * a * a;
+        };
+        const double Smax = S * 1.001;
+        const double ecut = ess(Smax) + epi(p->pimax * 1.001, Smax, Smax) + u * (D.e2[D.nb] + S2);
+        const double Cr = D.e2[D.nb] + 2 * SAFETY * ecut + 8 * u * S2;
+        const double Cp = pm2 + 2 * H.band_p[p->npibins] + 8 * u * pm2;
+        D.cut_r = (float)Cr;
+        if ((double)D.cut_r < Cr) D.cut_r = std::nextafter(D.cut_r, INFINITY);
+        D.cut_p = (float)Cp;
+        if ((double)D.cut_p < Cp) D.cut_p = std::nextafter(D.cut_p, INFINITY);
+        // Near the observer: a candidate with |s| up to the stencil's reach may have a midpoint
+        // within S of the origin unless every point is at least that far plus half the reach.
+        double reach = 0.0;
+        for (int a = 0; a < 3; a++) reach += ((G.k[a] + 1) * G.width[a]) * ((G.k[a] + 1) * G.width[a]);
+        reach = std::sqrt(reach) * 1.001;
+        if (vmin < 0.0) {
+            double g2 = 0.0;
+            for (int a = 0; a < 3; a++) {
+                const double gap = std::max(0.0, std::max(bbox[a], -bbox[3 + a]));
+                g2 += gap * gap;
+            }
+            vmin = std::sqrt(g2) * (1.0 - 1e-12);
+        }
+        if (!(vmin - 0.5 * reach >= 1.01 * S)) {
+            D.near2 = (float)S2;
+            // s.s - cut_r of a near candidate that may count: s.s <= S^2 (1 + 1e-4) + 2 ess(S)
+            const double su = S2 * (1 + 1e-4) + 2 * ess(S) - (double)D.cut_r;
+            D.cut_su = (float)su;
+            if ((double)D.cut_su < su) D.cut_su = std::nextafter(D.cut_su, INFINITY);
+        }
+    }
     // ---- lookup tables ----
     {
         auto segs = make_segments(D.e2, H.band_r, D.nb);
@@ -484,7 +584,7 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
             return CF_ERR_ARG;
         }
     }
-    if (rppi_like) {
+    if (rppi_like || mocks) {
         std::vector<double> pe(D.pe, D.pe + p->npibins + 1);
         std::vector<double> bp(H.band_p, H.band_p + p->npibins + 1);
         int m = p->npibins;
@@ -497,7 +597,7 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
     }
     // candidate cuts of the pair kernel's first phase: the FP32 value at which the final
     // "outside every bin" segment of each table starts
-    {
+    if (!mocks) {
         float f;
         std::memcpy(&f, &D.lr.tail, 4);
         D.cut_r = f;
@@ -547,7 +647,7 @@ extern "C" cf_status cf_plan_probe(const cf_params *params, const double bbox[6]
     if (!params || !bbox) return CF_ERR_ARG;
     std::string err;
     if (cfp_check_params(params, err) != CF_OK) return CF_ERR_ARG;
-    const bool rppi_like = params->kind == CF_DD_RPPI || params->kind == CF_WP;
+    const bool rppi_like = params->kind == CF_DD_RPPI || params->kind == CF_WP || params->kind == CF_DD_RPPI_MOCKS;
     if (which < 0 || which > 7) return CF_ERR_ARG;
     const int angular = (which & 4) ? 1 : 0;
     which &= 3;

@@ -17,6 +17,7 @@ struct CfHostPlan {
     double band_r[CF_MAX_BINS + 1];    // FP32 error band of each squared edge
     double band_p[CF_MAX_PIBINS + 1];  // FP32 error band of each pi edge
     double theta_rel, delta[3], M[3];  // error model terms (for diagnostics)
+    double eta;                        // mocks: bound on |error of l| / |l| (diagnostics)
 };
 
 // Validate the parameters alone (no point data).  Returns 0 or CF_ERR_ARG with a message.
@@ -29,9 +30,10 @@ void cfp_edges(const cf_params *p, double *e2, double *pe);
 // npoints = total points (caps the grid); f64 = any float64 input; refine = requested factors
 // (0 = automatic); tile = max i tile (64 or 128); jchunk = max j range per work item.
 // angular = 1 (DD(theta) only): DEC bands x RA cells instead of the 3-D grid over unit vectors.
+// vmin (mocks only): a lower bound on |v| over the points (negative: derived from bbox).
 int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int f64,
                   const int refine[3], int tile, int jchunk, CfHostPlan *out, std::string &err,
-                  int angular = 0);
+                  int angular = 0, double vmin = -1.0);
 
 // Origin of cell i on an axis starting at lo with cell width w.  For float32 coordinates x in
 // the cell, x - origin is exact in float32: the origin is a multiple of the float32 spacing at

@@ -5,6 +5,7 @@
 // Sec. 4.4 Code normal_pbc), evaluated on the original coordinates in FP64 with explicit
 // round-to-nearest operations and no fused multiply-add: d = a - b, wrapped once each way for a
 // periodic axis, s = (dx*dx + dy*dy) + dz*dz, bins half-open against the FP64 squared edges.
+// Mocks (Appendix A.2.1) take cf_mocks64: pi^2 and rp^2 from the pair's line of sight.
 #include "cf_build.h"
 #include "cf_device.cuh"
 #include "cf_pair.cuh"
@@ -43,11 +44,28 @@ __global__ void cf_recheck_kernel(const CfDevPlan *__restrict__ P, const CfSetDe
         const CfJobDesc J = jobs[e.z];
         const CfSetDesc &A = sets[J.a];
         const CfSetDesc &B = sets[J.b];
+        int slot;
+        double sep = 0.0;
+        if (kind == 4) {
+            // mocks (Appendix A.2.1): squared pi edges in pe, pimax^2 = pe[npi]
+            double rp2, pi2;
+            cf_mocks64(cf_load(A.x, A.dtype, e.x), cf_load(A.y, A.dtype, e.x), cf_load(A.z, A.dtype, e.x),
+                       cf_load(B.x, B.dtype, e.y), cf_load(B.y, B.dtype, e.y), cf_load(B.z, B.dtype, e.y), rp2, pi2);
+            if (!(pi2 < P->pe[npi])) continue;
+            if (rp2 < P->e2[0] || rp2 >= P->e2[nb]) continue;
+            slot = cf_find64(P->e2, nb, rp2) * npi + cf_find64(P->pe, npi, pi2);
+            if (P->ravg) sep = sqrt(rp2);
+            const size_t g = (size_t)e.z * nslot + slot;
+            atomicAdd(hcnt + g, 1ull);
+            double ww = 1.0;
+            if (P->weighted) ww = __dmul_rn(cf_load(A.w, A.dtype, e.x), cf_load(B.w, B.dtype, e.y));
+            if (P->weighted) atomicAdd(hw + g, ww);
+            if (P->ravg) atomicAdd(hr + g, __dmul_rn(ww, sep));
+            continue;
+        }
         double dx = cf_sep64(cf_load(A.x, A.dtype, e.x), cf_load(B.x, B.dtype, e.y), L0);
         double dy = cf_sep64(cf_load(A.y, A.dtype, e.x), cf_load(B.y, B.dtype, e.y), L1);
         double dz = cf_sep64(cf_load(A.z, A.dtype, e.x), cf_load(B.z, B.dtype, e.y), L2);
-        int slot;
-        double sep = 0.0;
         if (kind == 0 || kind == 3) {
             double s = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
             s = __dadd_rn(s, __dmul_rn(dz, dz));
@@ -88,6 +106,7 @@ cudaError_t cfp_launch_r(const CfPairCfg &, const CfPairArgs &, int, cudaStream_
 cudaError_t cfp_launch_rppi(const CfPairCfg &, const CfPairArgs &, int, cudaStream_t, int *, int *);
 cudaError_t cfp_launch_wp(const CfPairCfg &, const CfPairArgs &, int, cudaStream_t, int *, int *);
 cudaError_t cfp_launch_theta(const CfPairCfg &, const CfPairArgs &, int, cudaStream_t, int *, int *);
+cudaError_t cfp_launch_mocks(const CfPairCfg &, const CfPairArgs &, int, cudaStream_t, int *, int *);
 
 size_t cfp_pair_smem(const CfPairCfg &c, int warps)
 {
@@ -103,6 +122,7 @@ cudaError_t cfp_launch_pair(const CfPairCfg &c, const CfPairArgs &a, int num_sms
     case 1: return cfp_launch_rppi(c, a, num_sms, st, grid_out, warps_out);
     case 2: return cfp_launch_wp(c, a, num_sms, st, grid_out, warps_out);
     case 3: return cfp_launch_theta(c, a, num_sms, st, grid_out, warps_out);
+    case 4: return cfp_launch_mocks(c, a, num_sms, st, grid_out, warps_out);
     }
     return cudaErrorInvalidValue;
 }

@@ -31,6 +31,7 @@ CASES = [
     ("rppi", True, True, False, False),
     ("theta", True, False, False, True),
     ("wp", False, True, True, False),
+    ("mocks", False, False, True, True),
 ]
 
 
