@@ -32,6 +32,9 @@ if ROOT not in sys.path:
 METRIC = "pair-distance evals/s"
 UNIT = "pairs/s"
 FP32_INSTR_PER_PAIR = 6          # 3 FADD (dx, dy, dz) + 1 FMUL + 2 FFMA: the algorithmic minimum
+# the mocks kind's division-free candidate cut (Appendix A.2.1): s (3), s.s (3), s.A_i (3),
+# s.l = s.A_i - s.s/2 (1), l.l = A_i.A_i - s.A_i + s.s/4 (2), (s.l)^2 (1), the two cut products (2)
+FP32_INSTR_PER_PAIR_KIND = {"mocks": 15}
 L2_FLUSH_BYTES = 512 << 20       # > 129 MB L2
 
 WORKLOADS = {
@@ -47,6 +50,9 @@ WORKLOADS = {
                        "20 log bins 0.001-1 deg",
     "polar_theta_1m": "DD(theta) auto, non-periodic, N=1,000,000 unit vectors uniform on the polar cap DEC 60..90 deg "
                       "float32, 20 log bins 0.001-1 deg",
+    "mock_dr_rppi": "DR(rp,pi) of mocks (Fisher et al. line of sight), non-periodic, D=200,000 clustered (2,000 x 100, "
+                    "sigma=2) x R=2,000,000 uniform float32 in a cone RA 0-90, DEC 0-60 deg, 300-1000 Mpc/h from "
+                    "the observer, 14 log rp bins 0.5-42, pimax=42 with 42 pi bins",
 }
 
 
@@ -352,7 +358,8 @@ def run_gpu(args, wl, world, rank, local):
     peaks = _peaks()
     props = torch.cuda.get_device_properties(dev)
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = props.multi_processor_count * 128 * sm_max * 1e6 / FP32_INSTR_PER_PAIR
+    ipp = FP32_INSTR_PER_PAIR_KIND.get(wl.kind, FP32_INSTR_PER_PAIR)
+    peak = props.multi_processor_count * 128 * sm_max * 1e6 / ipp
     achieved = evaluated / (statistics.fmean(pair_ms) / 1e3)
     clocks = clk.summary()
 
@@ -370,7 +377,7 @@ def run_gpu(args, wl, world, rank, local):
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
                      "frac": achieved / peak, "traffic": _traffic(args.workload),
                      "peak_basis": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz / "
-                                   f"{FP32_INSTR_PER_PAIR} instr per pair"},
+                                   f"{ipp} instr per pair"},
         "clocks": clocks,
         "pair_kernel_ms": statistics.fmean(pair_ms),
         "evaluated_pairs_per_step": int(evaluated),

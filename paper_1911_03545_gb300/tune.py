@@ -25,14 +25,25 @@ import math
 import os
 import time
 
-from . import (CF_OPT_CELL_PRUNE, CF_OPT_JCHUNK, CF_OPT_REFINE, CF_OPT_THETA_GRID, CF_OPT_TILE, CF_OPT_VARIANT,
-               CF_OPT_WARPS, cf_count, cf_get_stats, cf_set_option)
+from . import (CF_DD_RPPI_MOCKS, CF_DD_THETA, CF_OPT_CELL_PRUNE, CF_OPT_JCHUNK, CF_OPT_REFINE, CF_OPT_THETA_GRID,
+               CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS, cf_count, cf_get_stats, cf_set_option)
 
 KNOBS = {"variant": [1, 2], "refine": [1, 2, 3], "warps": [0, 12, 8, 6, 4], "tile": [128, 64],
          "jchunk": [512, 256, 128], "noprune": [0, 1], "thetagrid": [0, 1]}
 OPT = {"variant": CF_OPT_VARIANT, "refine": CF_OPT_REFINE, "warps": CF_OPT_WARPS, "tile": CF_OPT_TILE,
        "jchunk": CF_OPT_JCHUNK, "noprune": CF_OPT_CELL_PRUNE, "thetagrid": CF_OPT_THETA_GRID}
 DEFAULT = {"variant": 1, "refine": 1, "warps": 0, "tile": 128, "jchunk": 512, "noprune": 0, "thetagrid": 0}
+
+
+def knobs_for(p) -> dict:
+    """The knobs that can change anything for this kind: the angular grid exists for DD(theta)
+    only, and the mocks kind has the direct form only."""
+    k = dict(KNOBS)
+    if p.kind != CF_DD_THETA:
+        k.pop("thetagrid")
+    if p.kind == CF_DD_RPPI_MOCKS:
+        k.pop("variant")
+    return k
 
 
 def cache_path() -> str:
@@ -99,7 +110,7 @@ def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, rep
     # coordinate descent, repeated: a knob's best value can change once later knobs have moved
     for _ in range(passes):
         moved = False
-        for knob, values in KNOBS.items():
+        for knob, values in knobs_for(p).items():
             for v in values:
                 if v == cfg[knob]:
                     continue
