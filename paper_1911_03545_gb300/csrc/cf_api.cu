@@ -374,7 +374,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.cfg.nslot = D.nslot;
     R.cfg.warps = (int)C->opt[CF_OPT_WARPS];
     R.cfg.ctas_per_sm = (int)C->opt[CF_OPT_CTAS_PER_SM];
-    // the mocks kind has the direct form only (its candidates need more than one value each)
+    // the mocks kind has the direct form only (a compacting form measured slower)
     R.cfg.variant = (C->opt[CF_OPT_VARIANT] == 2 && D.kind != CF_DD_RPPI_MOCKS) ? 2 : 1;
     R.items_cap = 0;
     return CF_OK;

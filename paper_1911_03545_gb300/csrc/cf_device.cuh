@@ -16,6 +16,12 @@ __device__ __forceinline__ u64 f2_add(u64 a, u64 b)
     asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
     return r;
 }
+__device__ __forceinline__ u64 f2_sub(u64 a, u64 b)
+{
+    u64 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ u64 f2_mul(u64 a, u64 b)
 {
     u64 r;

@@ -560,22 +560,19 @@ struct Warp {
     }
 
     // ---- DD(rp, pi) of observed positions (Appendix A.2.1) ----
-    // Bin one mocks candidate from its FP32 separation d = s, the i point's position A_i, (s.l)^2
-    // and l.l; jl: the j point's index in the stage.  pi^2 = (s.l)^2 / l.l; rp^2 = |s x A_i|^2 / l.l
-    // (s x A_i = s x l): its error scales with rp, where s.s - pi^2 would lose everything below
-    // the rounding of s.s when rp << pi.
-    __device__ __forceinline__ void bin_mocks(float dx, float dy, float dz, float Ax, float Ay, float Az, float sl2,
-                                              float ll, float wp, uint32_t il, uint32_t j, uint32_t jl,
-                                              const float *bs)
+    // Bin one mocks candidate from its FP32 |s x A_i|^2, (s.l)^2 and l.l: pi^2 = (s.l)^2 / l.l and
+    // rp^2 = |s x A_i|^2 / l.l (s x A_i = s x l), whose error scales with rp where s.s - pi^2 would
+    // lose everything below the rounding of s.s when rp << pi.  il, j: the pair within the item
+    // (j's chunk is the one staged now).
+    __device__ __forceinline__ void bin_mocks(float c2, float sl2, float ll, float wp, uint32_t il, uint32_t j)
     {
         if (near2 > 0.f && ll < near2) {
             push(ibeg + il, jbeg + j);        // midpoint near the observer: FP64
             return;
         }
-        const float qx = fmaf(dy, Az, -(dz * Ay)), qy = fmaf(dz, Ax, -(dx * Az)), qz = fmaf(dx, Ay, -(dy * Ax));
-        const float c2 = fmaf(qz, qz, fmaf(qy, qy, qx * qx));
-        const float pi2 = __fdividef(sl2, ll);
-        const float rp2 = __fdividef(c2, ll);
+        const float r = __fdividef(1.0f, ll);
+        const float pi2 = sl2 * r;
+        const float rp2 = c2 * r;
         const uint32_t cr = lut_class(lr, fine, __float_as_uint(rp2));
         const uint32_t cz = lut_class(lp, fine, __float_as_uint(pi2));
         if (cr == CFI_CLS_OUT || cz == CFI_CLS_OUT) return;
@@ -587,8 +584,12 @@ struct Warp {
         atomicAdd(h_cnt + slot, 1u);
         if (W) atomicAdd(h_wd + slot, (double)wp);
         if (R) {
-            const float r = mocks_rp<LO>(a, ibeg + il, bs, jl, ish[0], ish[1], ish[2], isl[0], isl[1], isl[2]);
-            atomicAdd(h_rd + slot, (double)(W ? wp * r : r));
+            // the j point is in the stage buffer of its chunk
+            constexpr uint32_t NA = stage_arrays(W, LO);
+            const float *bs = jst + ((j / JSTAGE) & 1u) * NA * JSTAGE;
+            const float rr = mocks_rp<LO>(a, ibeg + il, bs, j % JSTAGE, ish[0], ish[1], ish[2], isl[0], isl[1],
+                                          isl[2]);
+            atomicAdd(h_rd + slot, (double)(W ? wp * rr : rr));
         }
     }
 
@@ -596,7 +597,11 @@ struct Warp {
     // FP32x2: s = v_i - v_j (cell-relative), l = A_i - s / 2, u = s.s - cut_r, s.l, l.l; the
     // candidate cut needs no division: rp^2 = s.s - pi^2 < cut_r and pi^2 < cut_p become
     // u l.l < (s.l)^2 < cut_p l.l (cut_r lies above the last edge by twice this form's error).
-    // Candidates are binned by bin_mocks.
+    // When either pair of a slot passes, |s x A_i|^2 of both is formed packed and each passing
+    // pair is binned by bin_mocks where it was formed.  (A compacting form -- candidates to a
+    // per-warp ring by ballot prefix, binned 32 at a time -- was measured slower: 4.69 against
+    // 4.32 ms on the 200k x 2M survey cone, more warp instructions and full-width shared
+    // atomics on few slots.)
     template <int Q, bool DIAG>
     __device__ __forceinline__ void run_mocks(const CfItem &it)
     {
@@ -719,15 +724,15 @@ struct Warp {
                         in1 = in1 && j + 1 > il;
                     }
                     if (in0 || in1) {
+                        // |s x A_i|^2 of both pairs at once
+                        const u64 cx = f2_sub(f2_mul(dy, az[q]), f2_mul(dz, ay[q]));
+                        const u64 cy = f2_sub(f2_mul(dz, ax[q]), f2_mul(dx, az[q]));
+                        const u64 cz = f2_sub(f2_mul(dx, ay[q]), f2_mul(dy, ax[q]));
+                        const u64 c2 = f2_fma(cz, cz, f2_fma(cy, cy, f2_mul(cx, cx)));
                         const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
                         const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
-                        const float Ax = f2_lo(ax[q]), Ay = f2_lo(ay[q]), Az = f2_lo(az[q]);
-                        if (in0)
-                            bin_mocks(f2_lo(dx), f2_lo(dy), f2_lo(dz), Ax, Ay, Az, f2_lo(sl2), f2_lo(ll), f2_lo(wp), il,
-                                      j, jj, bs);
-                        if (in1)
-                            bin_mocks(f2_hi(dx), f2_hi(dy), f2_hi(dz), Ax, Ay, Az, f2_hi(sl2), f2_hi(ll), f2_hi(wp), il,
-                                      j + 1, jj + 1, bs);
+                        if (in0) bin_mocks(f2_lo(c2), f2_lo(sl2), f2_lo(ll), f2_lo(wp), il, j);
+                        if (in1) bin_mocks(f2_hi(c2), f2_hi(sl2), f2_hi(ll), f2_hi(wp), il, j + 1);
                     }
                 }
             }

@@ -1,5 +1,5 @@
 // cf_pair_mocks.cu -- instances of the pair kernel for DD(rp, pi) of observed positions
-// (Appendix A.2.1; see cf_pair.cuh).  Non-periodic only, direct form only.
+// (Appendix A.2.1; see cf_pair.cuh).  Non-periodic only, direct form only (run_mocks).
 #include "cf_pair.cuh"
 
 using namespace cfpair;

@@ -493,9 +493,9 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
         // Error model of the mocks kernel (Appendix A.2.1 evaluated in FP32; derivation in the
         // design notes).  Per pair: s from the cell-relative coordinates (per-axis error <= delta,
         // Dl2 its 2-norm), l = A_i - s/2 from the float32 absolute position A_i; the binned values
-        // are pi^2 = (s.l)^2 / l.l and rp^2 = |s x A_i|^2 / l.l (s x A_i = s x l exactly), the fast
-        // division (<= 2 ulp) for both.  A candidate with l.l below near2 = S^2 goes to the FP64
-        // recheck, so every other one has |l| >= 0.999 S and |A_i| <= 1.51 |l|.
+        // are pi^2 = (s.l)^2 / l.l and rp^2 = |s x A_i|^2 / l.l (s x A_i = s x l exactly).  A candidate with l.l below near2 = S^2 goes to the FP64
+        // recheck, so every other one has |l| >= 0.999 S and |A_i| <= 1.51 |l|.  Both values divide
+        // by l.l through one reciprocal (<= 2 ulp) and a product.
         double Dl = 0.0, Dl2 = 0.0;
         for (int a = 0; a < 3; a++) {
             Dl += H.delta[a];
@@ -521,14 +521,14 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
         auto epi = [&](double pimx, double Sx, double rpx) {
             const double e1 = (Dl2 + rpx * eta + 3 * u * Sx) * 1.001;
             const double e2nd = Dl2 + Sx * eta + 3 * u * Sx;
-            return (2 * pimx * e1 + e2nd * e2nd + pimx * pimx * ell) * (1 + 5 * u) + 5 * u * pimx * pimx;
+            return (2 * pimx * e1 + e2nd * e2nd + pimx * pimx * ell) * (1 + 6 * u) + 6 * u * pimx * pimx;
         };
         // |rp^2 - its FP32 value| for rp <= rpx, |s| <= Sx: |c - its FP32 value| <= g |l| with
-        // c = s x A_i (input errors |eps||A| + |s||dA|, each component's fma rounding), then
-        // |c|^2's chain, l.l and the division relatively
+        // c = s x A_i (input errors |eps||A| + |s||dA|; each component a difference of two rounded
+        // products, rounded), then |c|^2's chain (3u), the reciprocal (4u) and product (u), l.l
         auto erp = [&](double rpx, double Sx) {
-            const double g = aA * (Dl2 + Sx * uA + u * (Sx + Dl2) * 1.001) + u * rpx;
-            return 2 * rpx * g + g * g + rpx * rpx * (7 * u + ell);
+            const double g = aA * (Dl2 + Sx * uA + 2 * u * (Sx + Dl2) * 1.001) + u * rpx;
+            return 2 * rpx * g + g * g + rpx * rpx * (8 * u + ell);
         };
         for (int k = 0; k <= D.nb; k++) {
             const double Sk = std::sqrt(D.e2[k] + pm2) * 1.001;

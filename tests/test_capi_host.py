@@ -231,3 +231,101 @@ def test_bands_cover_actual_fp32_error(cf, precise):
 
 def out_band(info, k):
     return np.asarray(info["bands_r"])[k]
+
+
+MOCK_EDGES = gen.log_edges(0.1, 40.0, 14)
+MOCK_PIMAX, MOCK_NPI = 50.0, 25
+MOCK_BBOX = [0.0, 0.0, 0.0, 1100.0, 1100.0, 1100.0]
+
+
+@pytest.mark.parametrize("which", [0, 1], ids=["rp2", "pi2"])
+def test_mocks_luts_match_band_definition(cf, which):
+    """DD(rp, pi) of mocks (Appendix A.2.1) bins rp^2 against e^2 and pi^2 against the squared pi
+    edges; both tables must follow the band definition like the other kinds'."""
+    p = cf.params(kind="mocks", edges=MOCK_EDGES, autocorr=True, periodic=False, pimax=MOCK_PIMAX,
+                  npibins=MOCK_NPI)
+    if which == 0:
+        E = MOCK_EDGES ** 2
+        vals = _values_near(E)
+    else:
+        pe = np.arange(MOCK_NPI + 1, dtype=np.float64) * (MOCK_PIMAX / MOCK_NPI)
+        pe[-1] = MOCK_PIMAX
+        E = pe * pe
+        vals = np.concatenate([_values_near(E[1:]), np.float32([0.0, 1e-30, 0.5])])
+    out = cf.cf_plan_probe(p, MOCK_BBOX, 10 ** 6, which=which, values=vals)
+    B = out["bands_r"] if which == 0 else out["bands_p"]
+    _check_classes(vals, out["classes"], E, B, len(E) - 1)
+
+
+def test_mocks_bands_cover_actual_fp32_error(cf):
+    """Replay the mocks kernel's FP32 sequence on near-edge pairs of clustered points 300-1000 from
+    the observer and compare with the oracle's FP64 arithmetic: rp^2 = |s x A_i|^2 / l.l and
+    pi^2 = (s.l)^2 / l.l must stay within a quarter of the band of the nearest edge (the bands carry
+    a factor-4 margin).  The reciprocal is emulated correctly rounded; its 2-ulp allowance is added
+    to the measured error."""
+    p = cf.params(kind="mocks", edges=MOCK_EDGES, autocorr=True, periodic=False, pimax=MOCK_PIMAX,
+                  npibins=MOCK_NPI)
+    info = cf.cf_plan_probe(p, MOCK_BBOX, 10 ** 6)
+    assert min(info["width"]) >= 64.0          # the replay's cells below are no wider
+    rng = np.random.Generator(np.random.PCG64(5))
+    n = 300000
+    d = np.cbrt(rng.uniform(300.0 ** 3, 1000.0 ** 3, n))
+    u = rng.normal(size=(n, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    mid = np.abs(d[:, None] * u) + 100.0      # every coordinate positive: origins below stay exact
+    # pairs about the midpoint `mid` at rp and pi near the edges: s across and along its line of sight
+    los = mid / np.linalg.norm(mid, axis=1)[:, None]
+    perp = np.cross(los, rng.normal(size=(n, 3)))
+    perp /= np.linalg.norm(perp, axis=1)[:, None]
+    rp_t = rng.choice(MOCK_EDGES, n) * (1 + rng.uniform(-1e-3, 1e-3, n))
+    pi_t = rng.uniform(0, MOCK_PIMAX, n)
+    sv = perp * rp_t[:, None] + los * pi_t[:, None]
+    xi = (mid + 0.5 * sv).astype(np.float32)
+    xj = (mid - 0.5 * sv).astype(np.float32)
+    # cells of width 64 (origins multiples of 64: cell-relative coordinates exact in float32)
+    oi, oj = np.floor(xi / 64.0) * 64.0, np.floor(xj / 64.0) * 64.0
+    Xi = (xi.astype(np.float64) - oi).astype(np.float32)
+    Xj = (xj.astype(np.float64) - oj).astype(np.float32)
+    assert np.array_equal(Xi.astype(np.float64), xi.astype(np.float64) - oi)
+    Sh = (oi - oj).astype(np.float32)
+    f32 = np.float32
+    s = ((Xi + Sh).astype(f32) + (-Xj)).astype(f32)                   # s = v_i - v_j
+    A = xi
+    l = (s.astype(np.float64) * -0.5 + A.astype(np.float64)).astype(f32)
+    sl = (s[:, 0] * l[:, 0]).astype(f32)
+    sl = _fma32(s[:, 1], l[:, 1], sl)
+    sl = _fma32(s[:, 2], l[:, 2], sl)
+    ll = (l[:, 0] * l[:, 0]).astype(f32)
+    ll = _fma32(l[:, 1], l[:, 1], ll)
+    ll = _fma32(l[:, 2], l[:, 2], ll)
+    sl2 = (sl * sl).astype(f32)
+    c = np.stack([(s[:, 1] * A[:, 2]).astype(f32) - (s[:, 2] * A[:, 1]).astype(f32),
+                  (s[:, 2] * A[:, 0]).astype(f32) - (s[:, 0] * A[:, 2]).astype(f32),
+                  (s[:, 0] * A[:, 1]).astype(f32) - (s[:, 1] * A[:, 0]).astype(f32)], axis=1).astype(f32)
+    c2 = (c[:, 0] * c[:, 0]).astype(f32)
+    c2 = _fma32(c[:, 1], c[:, 1], c2)
+    c2 = _fma32(c[:, 2], c[:, 2], c2)
+    r = (1.0 / ll.astype(np.float64)).astype(f32)
+    pi2 = (sl2 * r).astype(f32).astype(np.float64)
+    rp2 = (c2 * r).astype(f32).astype(np.float64)
+    # the oracle's FP64 order
+    a, b = xi.astype(np.float64), xj.astype(np.float64)
+    S, L = a - b, 0.5 * (a + b)
+    dot = lambda x, y: (x[:, 0] * y[:, 0] + x[:, 1] * y[:, 1]) + x[:, 2] * y[:, 2]  # noqa: E731
+    pi2_64 = dot(S, L) ** 2 / dot(L, L)
+    rp2_64 = np.maximum(dot(S, S) - pi2_64, 0.0)
+    u = 2.0 ** -24
+    E = MOCK_EDGES ** 2
+    k = np.argmin(np.abs(rp2_64[:, None] - E[None, :]), axis=1)
+    near = np.abs(rp2_64 - E[k]) < 0.01 * E[k]
+    err = np.abs(rp2 - rp2_64) + 3 * u * rp2_64
+    assert near.sum() > 100000
+    band = np.asarray(info["bands_r"])[k]
+    assert np.all(err[near] <= band[near] / 4), float(np.max(err[near] / band[near]))
+    P = (np.arange(MOCK_NPI + 1) * (MOCK_PIMAX / MOCK_NPI)) ** 2
+    m = np.argmin(np.abs(pi2_64[:, None] - P[None, :]), axis=1)
+    okm = (m > 0) & (rp2_64 < E[-1] * 1.05)
+    err = np.abs(pi2 - pi2_64) + 3 * u * pi2_64
+    band = np.asarray(info["bands_p"])[m]
+    assert okm.sum() > 100000
+    assert np.all(err[okm] <= band[okm] / 4), float(np.max(err[okm] / band[okm]))

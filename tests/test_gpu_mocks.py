@@ -139,7 +139,7 @@ def test_host_inputs_and_refused_requests(ctx):
     kw = dict(pimax=wl.pimax, npibins=wl.npibins)
     host = _gpu(ctx, wl.edges, wl.d1, device=False, **kw)
     assert_match(host, _orc(wl.edges, wl.d1, **kw))
-    # the compacting form is not built for this kind: a request for it runs the direct form
+    # this kind has the direct form only: a request for the compacting form runs it anyway
     cf.cf_set_option(ctx, cf.CF_OPT_VARIANT, 2)
     try:
         again = _gpu(ctx, wl.edges, wl.d1, **kw)
