@@ -249,7 +249,7 @@ def _oracle_rows_rate(wl, seconds: float, seed: int = 0):
 def run_reference(args, wl, world, rank):
     if rank != 0:
         return 0
-    per_step = max(0.05, 150.0 / max(1, args.steps + args.warmup))
+    per_step = max(0.05, args.ref_seconds / max(1, args.steps + args.warmup))
     rates = []
     cores, sample = os.cpu_count() or 1, ""
     t_all = 0.0
@@ -656,6 +656,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="clustered_r_1m", choices=sorted(WORKLOADS) + ["batch256", "serve", "sweep"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="oracle time of the whole --impl reference run (split over its steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-tune-cache", action="store_true")

@@ -130,3 +130,39 @@ def test_server_budget_and_cancel(cf, cats):
     finally:
         cf.cf_server_stop(srv)
     assert done == len(tickets) - 1
+
+
+def test_mocks_batched_and_served(cf):
+    """DD(rp, pi) of mock catalogues (Appendix A.2.1) through the batched launch and the server:
+    each catalogue's result equals the oracle's, alone and in the mix."""
+    import torch
+    mcats = [gen.survey_cone(n, 0.0, 40.0, 10.0, 40.0, 100.0, 160.0, 700 + i, members=10, sigma=1.0)
+             for i, n in enumerate([800, 2000, 60, 1500])]
+    for i, c in enumerate(mcats):
+        c.w = gen.uniform_weights(c.n, 0.5, 1.5, 710 + i)
+    edges = gen.log_edges(0.2, 8.0, 8)
+    p = cf.params(kind="mocks", edges=edges, autocorr=True, periodic=False, pimax=8.0, npibins=8,
+                  weighted=True, ravg=True)
+    exp = [oracle.count("mocks", edges, c, autocorr=True, periodic=False, pimax=8.0, npibins=8, weighted=True,
+                        ravg=True) for c in mcats]
+    ctx = cf.cf_create(0, torch.cuda.current_stream())
+    try:
+        got = cf.cf_batch_count(ctx, p, [cf.points(*to_dev(c, "cuda:0", True)) for c in mcats])
+    finally:
+        cf.cf_destroy(ctx)
+    srv = cf.cf_server_start(0, p, 1 << 30, 16)
+    try:
+        tickets = [cf.cf_server_submit(srv, p, cf.points(c.x, c.y, c.z, c.w)) for c in mcats]
+        served = []
+        for t in tickets:
+            r = None
+            while r is None:
+                r = cf.cf_server_poll(srv, t, 1000)
+            served.append(r)
+    finally:
+        cf.cf_server_stop(srv)
+    for e, g, s in zip(exp, got, served):
+        for r in (g, s):
+            assert np.array_equal(np.asarray(r["npairs"]), e["npairs"])
+            np.testing.assert_allclose(r["wsum"], e["wsum"], rtol=TOL)
+            np.testing.assert_allclose(r["ravg"], e["ravg"], rtol=TOL)
