@@ -537,8 +537,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                             it.ibeg = ia + i0;
                             it.jbeg = jb + j0;
                             it.cnt = ic | (jc << 16);
-                            it.meta = (uint32_t)job | ((diag && b == a0) ? CFI_ITEM_DIAG : 0u) |
-                                      (ic > 64 ? CFI_ITEM_P2 : 0u);
+                            it.meta = (uint32_t)job | ((diag && b == a0) ? CFI_ITEM_DIAG : 0u);
                             it.s[0] = sh[0]; it.s[1] = sh[1]; it.s[2] = sh[2]; it.pad0 = 0.f;
                             it.slo[0] = sl[0]; it.slo[1] = sl[1]; it.slo[2] = sl[2]; it.pad1 = 0.f;
                             if (o < items_cap) items[o] = it;

@@ -28,7 +28,6 @@
 #define CFI_CLS_OUT 0xFEu         // class: outside every bin
 #define CFI_CLS_AMB 0xFFu         // class: within the FP32 error band of an edge
 #define CFI_FINE_FLAG 0x100u      // coarse entry >= this: index of a fine entry + flag
-#define CFI_QN 1024               // per-warp candidate ring entries
 #define CFI_JMAX 512              // longest j range of a work item (9-bit j in a candidate)
 
 // Pair-kernel item (48 bytes, three 16-byte loads)
@@ -36,14 +35,13 @@ struct CfItem {
     uint32_t ibeg;     // first i point (global sorted index)
     uint32_t jbeg;     // first j point
     uint32_t cnt;      // icnt (low 16) | jcnt (high 16)
-    uint32_t meta;     // job (low 20 bits) | diag (bit 30) | two packs (bit 29)
+    uint32_t meta;     // job (low 20 bits) | diag (bit 30)
     float s[3];        // shift hi:  x_i - x_j = (X_i + s + slo) - X_j
     float pad0;
     float slo[3];      // shift lo
     float pad1;
 };
 #define CFI_ITEM_DIAG (1u << 30)
-#define CFI_ITEM_P2 (1u << 29)
 #define CFI_ITEM_JOBMASK 0xFFFFFu
 
 // A point set (input view + where its sorted points and cells live)

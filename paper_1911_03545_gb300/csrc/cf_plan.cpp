@@ -95,7 +95,6 @@ int cfp_check_params(const cf_params *p, std::string &err)
     for (int a = 0; a < 3; a++)
         if (p->refine[a] < 0 || p->refine[a] > 4) { err = "refine factors must be in [0, 4]"; return CF_ERR_ARG; }
     if (p->weight != CF_W_NONE && p->weight != CF_W_PAIR_PRODUCT) { err = "unknown weight type"; return CF_ERR_ARG; }
-    if (p->kind == CF_WP && !p->autocorr && false) { err = ""; return CF_ERR_ARG; }
     return CF_OK;
 }
 
