@@ -54,3 +54,42 @@ def test_full_size_against_oracle(ctx, name):
         np.testing.assert_allclose(np.asarray(got["wsum"]).ravel(), gold["wsum"], rtol=TOL, atol=0)
     if wl.ravg:
         np.testing.assert_allclose(np.asarray(got["ravg"]).ravel(), gold["ravg"], rtol=TOL, atol=0)
+
+
+TUNED = ["clustered_r_1m", "clustered_rppi_2m", "sphere_theta_1m", "mock_dr_rppi"]
+
+
+@pytest.mark.parametrize("name", [n for n in TUNED if n in NAMES])
+def test_full_size_in_the_tuned_configuration(ctx, name):
+    """The launch configuration bench.py times is the tuner's pick: run the tuner on the workload
+    (no cache), then count in that configuration and compare with the oracle's histogram."""
+    import torch
+
+    import paper_1911_03545_gb300 as cf
+    from paper_1911_03545_gb300 import tune
+    with open(os.path.join(GOLDEN, f"full_{name}.json")) as f:
+        gold = json.load(f)
+    wl = workload(name)
+    if fingerprint(wl.d1, wl.d2) != gold["fingerprint"]:
+        pytest.skip("this machine's generator produced different inputs than the golden file's")
+    p = cf.params(kind=wl.kind, edges=wl.edges, autocorr=wl.autocorr, periodic=wl.periodic, box=wl.box,
+                  pimax=wl.pimax, npibins=wl.npibins, weighted=wl.weighted, ravg=wl.ravg)
+
+    def pts(c):
+        t = to_dev(c, "cuda:0", wl.weighted)
+        return cf.points(*t[:3], t[3] if wl.weighted else None)
+
+    d1 = pts(wl.d1)
+    d2 = None if wl.autocorr else pts(wl.d2)
+    cfg = tune.tune(ctx, p, d1, d2, device_name=torch.cuda.get_device_name(0),
+                    npoints=wl.d1.n + (0 if wl.autocorr else wl.d2.n), reps=1, passes=1, use_cache=False)
+    try:
+        got = cf.cf_count(ctx, p, d1, d2)
+    finally:
+        tune.reset(ctx)
+    n = np.asarray(got["npairs"]).ravel().astype(np.uint64)
+    assert np.array_equal(n, np.asarray(gold["npairs"], dtype=np.uint64)), (cfg, np.argwhere(n != gold["npairs"])[:10])
+    if wl.weighted:
+        np.testing.assert_allclose(np.asarray(got["wsum"]).ravel(), gold["wsum"], rtol=TOL, atol=0)
+    if wl.ravg:
+        np.testing.assert_allclose(np.asarray(got["ravg"]).ravel(), gold["ravg"], rtol=TOL, atol=0)
