@@ -470,6 +470,11 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     A.nb = D.nb;
     A.npi = D.npi;
     A.nslot = D.nslot;
+    // rp-pi / mocks keep one histogram per warp in shared memory; when even one warp's does not
+    // fit (many rp x pi slots, weights), they add straight into the global histograms instead
+    const bool per_warp = D.kind == CF_DD_RPPI || D.kind == CF_DD_RPPI_MOCKS;
+    if (per_warp && !R.cfg.ghist && cfp_pair_smem(R.cfg, 1) > (size_t)C->smem_optin) R.cfg.ghist = 1;
+    A.ghist = R.cfg.ghist;
     int grid = 0, warps = 0;
     if (R.items_cap > 0) {
         cudaError_t e = cfp_launch_pair(R.cfg, A, C->num_sms, st, &grid, &warps);
@@ -651,6 +656,7 @@ cf_status cf_create(void **ctx_out, int device, void *cuda_stream)
     C->device = device;
     C->stream = (cudaStream_t)cuda_stream;
     cudaDeviceGetAttribute(&C->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&C->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     for (auto &e : C->ev) {
         if (cudaEventCreate(&e) != cudaSuccess) {
             cudaGetLastError();

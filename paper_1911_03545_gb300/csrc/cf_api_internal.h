@@ -64,6 +64,7 @@ struct CfCtx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int num_sms = 1;
+    int smem_optin = 0;            // largest dynamic shared memory of one CTA (opt-in)
     std::string err;
     size_t mem_cap = 0, mem_used = 0;
     Buf buf[B_COUNT_];

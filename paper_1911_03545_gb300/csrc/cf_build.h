@@ -50,13 +50,16 @@ struct CfPairArgs {
     float L[3];                  // periodic sides (wrap axes)
     int nb, npi, nslot;
     int audit;
+    int ghist;                   // 1: rp-pi / mocks add straight into hcnt/hw/hr (global atomics):
+                                 // their per-warp histogram does not fit in shared memory
 };
 
 // Static configuration of a pair-kernel launch (selects the template instance and the shared
 // memory layout).
 struct CfPairCfg {
-    int kind;          // 0 r, 1 rppi, 2 wp, 3 theta
+    int kind;          // 0 r, 1 rppi, 2 wp, 3 theta, 4 mocks
     int weighted, ravg, wrap, lo;
+    int ghist;         // see CfPairArgs::ghist (no per-warp histogram in shared memory)
     int nlut_words, nfine, nslot;
     int warps;         // warps per CTA (0: automatic)
     int ctas_per_sm;   // 0: occupancy-derived

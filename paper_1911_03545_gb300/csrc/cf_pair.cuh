@@ -214,6 +214,7 @@ struct Warp {
     float cut_r, cut_p;
     float Lx, Ly, Lz, iLx, iLy, iLz;
     float near2, cut_su;    // mocks: the near-observer test (near2 = 0: off)
+    bool ghist;             // rp-pi / mocks: histograms in global memory (CfPairArgs::ghist)
     float ish[3], isl[3];   // mocks with ravg: the item's shift, hi and lo
 
     __device__ Warp(const CfPairArgs &args) : a(args) {}
@@ -244,6 +245,17 @@ struct Warp {
 
     __device__ __forceinline__ void acc_sh(uint32_t slot, float rp2, float wp)
     {
+        if (ghist) {
+            // no per-warp histogram: straight into the job's global one
+            const size_t g = (size_t)job * (uint32_t)nslot + slot;
+            atomicAdd(a.hcnt + g, 1ull);
+            if (W) atomicAdd(a.hw + g, (double)wp);
+            if (R) {
+                const float r = f_sqrt_approx(rp2);
+                atomicAdd(a.hr + g, (double)(W ? wp * r : r));
+            }
+            return;
+        }
         atomicAdd(h_cnt + slot, 1u);
         if (W) atomicAdd(h_wd + slot, (double)wp);
         if (R) {
@@ -581,6 +593,19 @@ struct Warp {
             return;
         }
         const uint32_t slot = cr * (uint32_t)npi + cz;
+        if (ghist) {
+            const size_t g = (size_t)job * (uint32_t)nslot + slot;
+            atomicAdd(a.hcnt + g, 1ull);
+            if (W) atomicAdd(a.hw + g, (double)wp);
+            if (R) {
+                constexpr uint32_t NA = stage_arrays(W, LO);
+                const float *bs = jst + ((j / JSTAGE) & 1u) * NA * JSTAGE;
+                const float rr = mocks_rp<LO>(a, ibeg + il, bs, j % JSTAGE, ish[0], ish[1], ish[2], isl[0], isl[1],
+                                              isl[2]);
+                atomicAdd(a.hr + g, (double)(W ? wp * rr : rr));
+            }
+            return;
+        }
         atomicAdd(h_cnt + slot, 1u);
         if (W) atomicAdd(h_wd + slot, (double)wp);
         if (R) {
@@ -744,6 +769,7 @@ struct Warp {
 
     __device__ void flush(uint32_t jb)
     {
+        if (ghist) return;      // nothing held per warp
         __syncwarp();
         const size_t g0 = (size_t)jb * nslot;
         for (int sl = lane; sl < nslot; sl += 32) {
@@ -798,13 +824,14 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     unsigned char *wbase = (unsigned char *)(s_fine + nf);
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
-    const uint32_t wb = warp_bytes(KIND, W, R, LO, a.nslot, COMPACT);
+    const int hslots = a.ghist ? 0 : a.nslot;   // slots of the per-warp histogram
+    const uint32_t wb = warp_bytes(KIND, W, R, LO, hslots, COMPACT);
     const uint32_t hoff = warp_jbuf_bytes(W, LO) + (COMPACT ? warp_ring_bytes(KIND, W) : 0u);
     unsigned char *my = wbase + (size_t)(threadIdx.x >> 5) * wb;
     {
         // zero this warp's histogram (the buffers need no initial value)
         uint32_t *h = (uint32_t *)(my + hoff);
-        const uint32_t words = warp_hist_bytes(KIND, W, R, a.nslot) / 4u;
+        const uint32_t words = warp_hist_bytes(KIND, W, R, hslots) / 4u;
         for (uint32_t i = threadIdx.x & 31; i < words; i += 32) h[i] = 0u;
     }
     __syncthreads();
@@ -821,6 +848,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     w.cut_p = P->cut_p;
     w.near2 = P->near2;
     w.cut_su = P->cut_su;
+    w.ghist = a.ghist != 0;
     w.Lx = a.L[0]; w.Ly = a.L[1]; w.Lz = a.L[2];
     w.iLx = a.L[0] > 0.f ? 1.0f / a.L[0] : 0.f;
     w.iLy = a.L[1] > 0.f ? 1.0f / a.L[1] : 0.f;
@@ -840,9 +868,9 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     }
     w.h_cnt = (uint32_t *)(my + hoff);
     if (warp_hist(KIND)) {
-        uint32_t o = ((uint32_t)a.nslot * 4u + 7u) & ~7u;
+        uint32_t o = ((uint32_t)hslots * 4u + 7u) & ~7u;
         w.h_wd = (double *)(my + hoff + o);
-        w.h_rd = (double *)(my + hoff + o + (W ? a.nslot * 8u : 0u));
+        w.h_rd = (double *)(my + hoff + o + (W ? hslots * 8u : 0u));
         w.h_w = w.h_r = nullptr;
     } else {
         uint32_t o = a.nslot * 32u * 4u;

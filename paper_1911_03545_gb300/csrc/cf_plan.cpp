@@ -208,7 +208,7 @@ bool build_lut(const std::vector<Seg> &segs, CfLut &L, std::vector<uint16_t> &wo
                 uint32_t c2 = inside.size() > 1 ? inside[1].cls : inside[0].cls;
                 f.code = segs[si].cls | (inside[0].cls << 8) | (c2 << 16);
                 f.pad = 0;
-                cw[c] = (uint16_t)(CFI_FINE_FLAG | (uint32_t)(fine.size() + fw.size()));
+                cw[c] = (uint16_t)(CFI_FINE_FLAG + (uint32_t)(fine.size() + fw.size()));
                 fw.push_back(f);
                 if (fine.size() + fw.size() > CFI_FINE_MAX) ok = false;
             } else {

@@ -329,3 +329,25 @@ def test_mocks_bands_cover_actual_fp32_error(cf):
     band = np.asarray(info["bands_p"])[m]
     assert okm.sum() > 100000
     assert np.all(err[okm] <= band[okm] / 4), float(np.max(err[okm] / band[okm]))
+
+
+@pytest.mark.parametrize("kind", ["rppi", "mocks"])
+def test_tables_at_the_largest_sizes(cf, kind):
+    """252 rp bins and 252 pi bins: the tables need several hundred fine entries, so a coarse
+    entry must address fine entries beyond the first 256 correctly."""
+    edges = gen.log_edges(0.05, 9.0, 252)
+    p = cf.params(kind=kind, edges=edges, autocorr=True, periodic=kind == "rppi", box=40.0, pimax=9.0, npibins=252)
+    bb = [0, 0, 0, 40, 40, 40] if kind == "rppi" else [30, 5, 15, 140, 90, 100]
+    E = edges ** 2
+    vals = _values_near(E, span=200)
+    for which in ((0, 2) if kind == "rppi" else (0,)):
+        out = cf.cf_plan_probe(p, bb, 1600, which=which, values=vals)
+        _check_classes(vals, out["classes"], E, out["bands_r"], 252)
+    assert out["fine_entries"] > 256
+    pe = np.arange(253) * (9.0 / 252)
+    pe[-1] = 9.0
+    P = pe if kind == "rppi" else pe * pe
+    vals = np.concatenate([_values_near(P[1:], span=200), np.float32([0.0, 1e-30, 0.01])])
+    for which in ((1, 3) if kind == "rppi" else (1,)):
+        out = cf.cf_plan_probe(p, bb, 1600, which=which, values=vals)
+        _check_classes(vals, out["classes"], P, out["bands_p"], 252)

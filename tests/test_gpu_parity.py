@@ -358,3 +358,22 @@ def test_cell_pruning_at_the_largest_edge(ctx):
         assert_match(got, exp)
         got, exp = both(ctx, kind, edges, d, d, autocorr=False, periodic=True, box=100.0, **kw)
         assert_match(got, exp)
+
+
+def test_maximum_bin_counts(ctx):
+    """The largest tables the ABI accepts (252 bins; 252 x 252 rp-pi slots).  An rp-pi or mocks
+    histogram that large does not fit in one warp's shared memory: those kinds then add straight
+    into the global histograms.  r keeps lane-private histograms (one warp per CTA with weights
+    and ravg)."""
+    d = gen.clustered_box(40, 40, 1.0, 40.0, 81)
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 82)
+    edges = gen.log_edges(0.05, 9.0, 252)
+    for weighted, ravg in ((False, False), (True, True)):
+        kw = dict(autocorr=True, periodic=True, box=40.0, pimax=9.0, npibins=252, weighted=weighted, ravg=ravg)
+        assert_match(gpu_count(ctx, "rppi", edges, d, **kw), oracle.count("rppi", edges, d, **kw), weighted, ravg)
+    kw = dict(autocorr=True, periodic=True, box=40.0, weighted=True, ravg=True)
+    assert_match(gpu_count(ctx, "r", edges, d, **kw), oracle.count("r", edges, d, **kw), True, True)
+    m = gen.survey_cone(3000, 0.0, 30.0, 10.0, 40.0, 100.0, 140.0, 83, members=30, sigma=1.0)
+    m.w = gen.uniform_weights(m.n, 0.5, 1.5, 84)
+    kw = dict(autocorr=True, periodic=False, pimax=9.0, npibins=252, weighted=True, ravg=True)
+    assert_match(gpu_count(ctx, "mocks", edges, m, **kw), oracle.count("mocks", edges, m, **kw), True, True)
