@@ -474,6 +474,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     // fit (many rp x pi slots, weights), they add straight into the global histograms instead
     const bool per_warp = D.kind == CF_DD_RPPI || D.kind == CF_DD_RPPI_MOCKS;
     if (per_warp && !R.cfg.ghist && cfp_pair_smem(R.cfg, 1) > (size_t)C->smem_optin) R.cfg.ghist = 1;
+    if (R.cfg.ghist) R.cfg.variant = 1;       // that form is built direct only
     A.ghist = R.cfg.ghist;
     int grid = 0, warps = 0;
     if (R.items_cap > 0) {

@@ -197,7 +197,9 @@ static __device__ __noinline__ float mocks_rp(const CfPairArgs &a, uint32_t ip, 
     return sqrtf(__fdiv_rn(c2, ll));
 }
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO>
+// GH (rp-pi and mocks only): no per-warp histogram; every pair adds straight into the job's global
+// histogram (CfPairArgs::ghist)
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool GH>
 struct Warp {
     const CfPairArgs &a;
     Lut lr, lp;
@@ -214,7 +216,6 @@ struct Warp {
     float cut_r, cut_p;
     float Lx, Ly, Lz, iLx, iLy, iLz;
     float near2, cut_su;    // mocks: the near-observer test (near2 = 0: off)
-    bool ghist;             // rp-pi / mocks: histograms in global memory (CfPairArgs::ghist)
     float ish[3], isl[3];   // mocks with ravg: the item's shift, hi and lo
 
     __device__ Warp(const CfPairArgs &args) : a(args) {}
@@ -245,7 +246,7 @@ struct Warp {
 
     __device__ __forceinline__ void acc_sh(uint32_t slot, float rp2, float wp)
     {
-        if (ghist) {
+        if (GH) {
             // no per-warp histogram: straight into the job's global one
             const size_t g = (size_t)job * (uint32_t)nslot + slot;
             atomicAdd(a.hcnt + g, 1ull);
@@ -593,7 +594,7 @@ struct Warp {
             return;
         }
         const uint32_t slot = cr * (uint32_t)npi + cz;
-        if (ghist) {
+        if (GH) {
             const size_t g = (size_t)job * (uint32_t)nslot + slot;
             atomicAdd(a.hcnt + g, 1ull);
             if (W) atomicAdd(a.hw + g, (double)wp);
@@ -769,7 +770,7 @@ struct Warp {
 
     __device__ void flush(uint32_t jb)
     {
-        if (ghist) return;      // nothing held per warp
+        if (GH) return;         // nothing held per warp
         __syncwarp();
         const size_t g0 = (size_t)jb * nslot;
         for (int sl = lane; sl < nslot; sl += 32) {
@@ -812,7 +813,7 @@ struct Warp {
 __host__ __device__ constexpr int pair_max_threads(bool W, bool R) { return (W || R) ? 512 : 256; }
 __host__ __device__ constexpr int pair_min_blocks(bool W, bool R) { return (!W && !R) ? 3 : 1; }
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT>
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT, bool GH>
 __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     pair_kernel(const CfPairArgs a)
 {
@@ -824,7 +825,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     unsigned char *wbase = (unsigned char *)(s_fine + nf);
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
-    const int hslots = a.ghist ? 0 : a.nslot;   // slots of the per-warp histogram
+    const int hslots = GH ? 0 : a.nslot;        // slots of the per-warp histogram
     const uint32_t wb = warp_bytes(KIND, W, R, LO, hslots, COMPACT);
     const uint32_t hoff = warp_jbuf_bytes(W, LO) + (COMPACT ? warp_ring_bytes(KIND, W) : 0u);
     unsigned char *my = wbase + (size_t)(threadIdx.x >> 5) * wb;
@@ -836,7 +837,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     }
     __syncthreads();
 
-    Warp<KIND, W, R, WRAP, LO> w(a);
+    Warp<KIND, W, R, WRAP, LO, GH> w(a);
     w.lane = threadIdx.x & 31;
     w.nb = a.nb;
     w.npi = a.npi;
@@ -848,7 +849,6 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     w.cut_p = P->cut_p;
     w.near2 = P->near2;
     w.cut_su = P->cut_su;
-    w.ghist = a.ghist != 0;
     w.Lx = a.L[0]; w.Ly = a.L[1]; w.Lz = a.L[2];
     w.iLx = a.L[0] > 0.f ? 1.0f / a.L[0] : 0.f;
     w.iLy = a.L[1] > 0.f ? 1.0f / a.L[1] : 0.f;
@@ -919,11 +919,11 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     if (cur >= 0) w.flush((uint32_t)cur);
 }
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT>
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT, bool GH = false>
 cudaError_t launch_variant(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
                            int *warps_out)
 {
-    auto k = pair_kernel<KIND, W, R, WRAP, LO, COMPACT>;
+    auto k = pair_kernel<KIND, W, R, WRAP, LO, COMPACT, GH>;
     int dev;
     cudaGetDevice(&dev);
     int maxsm = 0;
@@ -956,6 +956,9 @@ template <int KIND, bool W, bool R, bool WRAP, bool LO>
 cudaError_t launch_one(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
                        int *warps_out)
 {
+    // global histograms (rp-pi tables too large for shared memory): the direct form only
+    if constexpr (warp_hist(KIND))
+        if (c.ghist) return launch_variant<KIND, W, R, WRAP, LO, false, true>(c, a, num_sms, st, grid_out, warps_out);
     if (c.variant == 2) return launch_variant<KIND, W, R, WRAP, LO, true>(c, a, num_sms, st, grid_out, warps_out);
     return launch_variant<KIND, W, R, WRAP, LO, false>(c, a, num_sms, st, grid_out, warps_out);
 }

@@ -4,7 +4,9 @@
 
 using namespace cfpair;
 
-#define CF_L(W, R, LO) return launch_variant<KIND_MOCKS, W, R, false, LO, false>(c, a, num_sms, st, grid_out, warps_out)
+#define CF_L(W, R, LO)                                                                                         \
+    return c.ghist ? launch_variant<KIND_MOCKS, W, R, false, LO, false, true>(c, a, num_sms, st, grid_out, warps_out) \
+                   : launch_variant<KIND_MOCKS, W, R, false, LO, false, false>(c, a, num_sms, st, grid_out, warps_out)
 
 cudaError_t cfp_launch_mocks(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
                              int *warps_out)
