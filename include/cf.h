@@ -144,8 +144,12 @@ const char *cf_last_error(const void *ctx);
  * a request above it fails with CF_ERR_OOM instead of allocating; CF_OPT_VARIANT pins the
  * pair-kernel variant; CF_OPT_TILE pins the i-tile size (32..128); CF_OPT_JCHUNK pins the
  * j range length per work item; CF_OPT_QUEUE sets the FP64 recheck queue capacity;
- * CF_OPT_CTAS_PER_SM sets the persistent grid; CF_OPT_AUDIT = 1 re-evaluates every
- * in-range pair in FP64 (debug: the band audit); CF_OPT_ITER_LIMIT bounds device spin waits;
+ * CF_OPT_CTAS_PER_SM sets the persistent grid; CF_OPT_AUDIT = 1 sends every pair the pair
+ * kernel evaluates to the FP64 recheck instead of binning it in FP32, so the call returns the FP64
+ * result of every evaluated pair: equal counts with and without it show that the FP32 path
+ * misclassified nothing (the band audit; slow, and CF_ERR_ARG above 2^32 - 2^28 evaluated pairs,
+ * which the queue counts in 32 bits); CF_OPT_ITER_LIMIT is reserved and has no
+ * effect (no kernel of this library waits on a flag: every device loop is bounded by its data);
  * CF_OPT_WARPS and CF_OPT_REFINE are the autotuner's knobs. */
 typedef enum {
     CF_OPT_MEM_CAP = 1,

@@ -456,6 +456,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     A.nitems_dev = ioff + R.nunit;
     A.items_cap = R.items_cap;
     A.qcap = R.qcap;
+    A.audit = C->opt[CF_OPT_AUDIT] != 0 ? 1 : 0;
     A.cursor = misc;
     A.qcount = misc + 1;
     A.pa = (const ulonglong2 *)C->buf[B_PA].p;
@@ -513,6 +514,9 @@ int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
     const uint32_t qn = ((const uint32_t *)h)[1];
     const uint32_t nitems = ((const uint32_t *)h)[2];
     *retry = 0;
+    // the audit queues every evaluated pair under a 32-bit count
+    if (C->opt[CF_OPT_AUDIT] && *(const unsigned long long *)(h + 16) >= 0xF0000000ull)
+        return C->fail(CF_ERR_ARG, "CF_OPT_AUDIT needs fewer than 2^32 - 2^28 evaluated pairs");
     if (nitems > R.items_cap) {
         R.items_cap = nitems;
         *retry = 2;

@@ -93,3 +93,42 @@ def test_full_size_in_the_tuned_configuration(ctx, name):
         np.testing.assert_allclose(np.asarray(got["wsum"]).ravel(), gold["wsum"], rtol=TOL, atol=0)
     if wl.ravg:
         np.testing.assert_allclose(np.asarray(got["ravg"]).ravel(), gold["ravg"], rtol=TOL, atol=0)
+
+
+@pytest.mark.parametrize("name", [n for n in ("clustered_r_1m", "mock_dr_rppi") if n in NAMES])
+def test_full_size_band_audit(ctx, name):
+    """The band audit at full size: with CF_OPT_AUDIT every evaluated pair is binned by the FP64
+    recheck alone, and the result must equal the oracle's histogram (as the FP32 path's does)."""
+    import paper_1911_03545_gb300 as cf
+    with open(os.path.join(GOLDEN, f"full_{name}.json")) as f:
+        gold = json.load(f)
+    wl = workload(name)
+    if fingerprint(wl.d1, wl.d2) != gold["fingerprint"]:
+        pytest.skip("this machine's generator produced different inputs than the golden file's")
+    p = cf.params(kind=wl.kind, edges=wl.edges, autocorr=wl.autocorr, periodic=wl.periodic, box=wl.box,
+                  pimax=wl.pimax, npibins=wl.npibins, weighted=wl.weighted, ravg=wl.ravg)
+
+    def pts(c):
+        t = to_dev(c, "cuda:0", wl.weighted)
+        return cf.points(*t[:3], t[3] if wl.weighted else None)
+
+    cf.cf_set_option(ctx, cf.CF_OPT_AUDIT, 1)
+    # refinement 2 keeps the mocks workload's evaluated pairs (4e9 at refinement 1) within the
+    # audit's 32-bit queue count
+    cf.cf_set_option(ctx, cf.CF_OPT_REFINE, 2 if name == "mock_dr_rppi" else 0)
+    try:
+        got = cf.cf_count(ctx, p, pts(wl.d1), None if wl.autocorr else pts(wl.d2))
+        st = cf.cf_get_stats(ctx)
+    finally:
+        cf.cf_set_option(ctx, cf.CF_OPT_AUDIT, 0)
+        cf.cf_set_option(ctx, cf.CF_OPT_REFINE, 0)
+    # every evaluated pair went to FP64 (a cell's pairs with itself once, j > i)
+    assert 10 ** 9 < st["rechecked_pairs"] <= st["evaluated_pairs"]
+    if not wl.autocorr:
+        assert st["rechecked_pairs"] == st["evaluated_pairs"]
+    n = np.asarray(got["npairs"]).ravel().astype(np.uint64)
+    assert np.array_equal(n, np.asarray(gold["npairs"], dtype=np.uint64)), np.argwhere(n != gold["npairs"])[:10]
+    if wl.weighted:
+        np.testing.assert_allclose(np.asarray(got["wsum"]).ravel(), gold["wsum"], rtol=TOL, atol=0)
+    if wl.ravg:
+        np.testing.assert_allclose(np.asarray(got["ravg"]).ravel(), gold["ravg"], rtol=TOL, atol=0)

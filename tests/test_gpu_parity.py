@@ -377,3 +377,39 @@ def test_maximum_bin_counts(ctx):
     m.w = gen.uniform_weights(m.n, 0.5, 1.5, 84)
     kw = dict(autocorr=True, periodic=False, pimax=9.0, npibins=252, weighted=True, ravg=True)
     assert_match(gpu_count(ctx, "mocks", edges, m, **kw), oracle.count("mocks", edges, m, **kw), True, True)
+
+
+@pytest.mark.parametrize("kind", ["r", "rppi", "wp", "theta", "mocks"])
+def test_band_audit_agrees(ctx, kind):
+    """CF_OPT_AUDIT sends every evaluated pair to the FP64 recheck: its counts must equal the normal
+    FP32 path's bit for bit (the band audit) and the oracle's."""
+    import paper_1911_03545_gb300 as cf
+    if kind == "theta":
+        d = gen.sphere_patch(20000, 0.0, 40.0, -10.0, 30.0, 91)
+        edges = gen.log_edges(0.01, 2.0, 16)
+        kw = dict(autocorr=True, periodic=False)
+    elif kind == "mocks":
+        d = gen.survey_cone(20000, 0.0, 60.0, 0.0, 40.0, 100.0, 300.0, 92, members=50, sigma=1.5)
+        edges = gen.log_edges(0.2, 15.0, 12)
+        kw = dict(autocorr=True, periodic=False, pimax=15.0, npibins=15)
+    else:
+        d = gen.clustered_box(400, 50, 1.0, 100.0, 93)
+        edges = gen.log_edges(0.1, 10.0, 16)
+        kw = dict(autocorr=True, periodic=True, box=100.0)
+        if kind in ("rppi", "wp"):
+            kw.update(pimax=12.0, npibins=12)
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 94)
+    kw.update(weighted=True, ravg=True)
+    normal = gpu_count(ctx, kind, edges, d, **kw)
+    st = cf.cf_get_stats(ctx)
+    cf.cf_set_option(ctx, cf.CF_OPT_AUDIT, 1)
+    try:
+        audited = gpu_count(ctx, kind, edges, d, **kw)
+        sa = cf.cf_get_stats(ctx)
+    finally:
+        cf.cf_set_option(ctx, cf.CF_OPT_AUDIT, 0)
+    # every evaluated pair is queued: a cell's pairs with itself once (j > i), the rest i x j
+    assert sa["evaluated_pairs"] == st["evaluated_pairs"]
+    assert int(np.asarray(audited["npairs"]).sum()) // 2 <= sa["rechecked_pairs"] <= sa["evaluated_pairs"]
+    assert_match(normal, audited, True, True)
+    assert_match(audited, oracle.count(kind, edges, d, **kw), True, True)
