@@ -456,7 +456,6 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     A.nitems_dev = ioff + R.nunit;
     A.items_cap = R.items_cap;
     A.qcap = R.qcap;
-    A.audit = C->opt[CF_OPT_AUDIT] != 0 ? 1 : 0;
     A.cursor = misc;
     A.qcount = misc + 1;
     A.pa = (const ulonglong2 *)C->buf[B_PA].p;
@@ -478,7 +477,10 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     if (R.cfg.ghist) R.cfg.variant = 1;       // that form is built direct only
     A.ghist = R.cfg.ghist;
     int grid = 0, warps = 0;
-    if (R.items_cap > 0) {
+    if (R.items_cap > 0 && C->opt[CF_OPT_AUDIT]) {
+        CF_CU(cfp_launch_audit(A.items, A.nitems_dev, A.items_cap, A.orig, A.queue, A.qcount, A.qcap, C->num_sms,
+                               st), "audit");
+    } else if (R.items_cap > 0) {
         cudaError_t e = cfp_launch_pair(R.cfg, A, C->num_sms, st, &grid, &warps);
         if (e == cudaErrorInvalidValue) return C->fail(CF_ERR_ARG, "histogram does not fit in shared memory");
         CF_CU(e, "pair kernel");

@@ -49,7 +49,6 @@ struct CfPairArgs {
     uint32_t *qcount;
     float L[3];                  // periodic sides (wrap axes)
     int nb, npi, nslot;
-    int audit;
     int ghist;                   // 1: rp-pi / mocks add straight into hcnt/hw/hr (global atomics):
                                  // their per-warp histogram does not fit in shared memory
 };
@@ -73,6 +72,11 @@ size_t cfp_pair_smem(const CfPairCfg &c, int warps);
 // shared memory.  *grid_out receives the number of CTAs launched.
 cudaError_t cfp_launch_pair(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st,
                             int *grid_out, int *warps_out);
+// CF_OPT_AUDIT: queue every pair of every work item for the FP64 recheck (launched instead of the
+// pair kernel).
+cudaError_t cfp_launch_audit(const CfItem *items, const uint32_t *nitems_dev, uint32_t items_cap,
+                             const uint32_t *orig, uint4 *queue, uint32_t *qcount, uint32_t qcap, int num_sms,
+                             cudaStream_t st);
 cudaError_t cfp_launch_recheck(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs,
                                const uint4 *queue, const uint32_t *qcount, uint32_t qcap,
                                unsigned long long *hcnt, double *hw, double *hr, int num_sms, cudaStream_t st);

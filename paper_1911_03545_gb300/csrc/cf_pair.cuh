@@ -768,26 +768,6 @@ struct Warp {
         __syncwarp();
     }
 
-    // CF_OPT_AUDIT: every pair of the item goes to the FP64 recheck queue and nothing is binned in
-    // FP32, so the call returns the FP64 result of every evaluated pair; an i row reserves its
-    // entries with one atomic.  (Entries past the queue capacity are dropped; the host sees the
-    // count and repeats the call with a larger queue.)
-    __device__ void audit_item(const CfItem &it)
-    {
-        const uint32_t ic = it.cnt & 0xFFFFu, jc = it.cnt >> 16;
-        const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
-        const uint32_t jo = it.meta & CFI_ITEM_JOBMASK;
-        for (uint32_t il = lane; il < ic; il += 32u) {
-            const uint32_t j0 = diag ? il + 1u : 0u;      // within a cell paired with itself: j > i
-            if (j0 >= jc) continue;
-            const uint32_t n = jc - j0;
-            const uint32_t base = atomicAdd(a.qcount, n);
-            const uint32_t oi = a.orig[it.ibeg + il];
-            for (uint32_t t = 0; t < n; t++)
-                if (base + t < a.qcap) a.queue[base + t] = make_uint4(oi, a.orig[it.jbeg + j0 + t], jo, 0u);
-        }
-    }
-
     __device__ void flush(uint32_t jb)
     {
         if (GH) return;         // nothing held per warp
@@ -922,9 +902,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
         }
         const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
         const uint32_t ic = it.cnt & 0xFFFFu;
-        if (a.audit) {
-            w.audit_item(it);
-        } else if (KIND == KIND_MOCKS) {
+        if (KIND == KIND_MOCKS) {
             if (diag) w.template run_mocks<4, true>(it);
             else if (ic <= 32u) w.template run_mocks<1, false>(it);
             else if (ic <= 64u) w.template run_mocks<2, false>(it);

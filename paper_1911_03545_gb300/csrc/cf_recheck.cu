@@ -93,6 +93,43 @@ __global__ void cf_recheck_kernel(const CfDevPlan *__restrict__ P, const CfSetDe
     }
 }
 
+// CF_OPT_AUDIT, in place of the pair kernel: every pair of every work item goes to the FP64 recheck
+// queue and nothing is binned in FP32, so the call returns the FP64 result of every evaluated pair.
+// A warp takes items in turn; a lane takes i rows of the item and reserves each row's entries with
+// one atomic.  Entries past the queue capacity are dropped: the host sees the count and repeats the
+// call with a larger queue.
+__global__ void cf_audit_kernel(const CfItem *__restrict__ items, const uint32_t *__restrict__ nitems_dev,
+                                uint32_t items_cap, const uint32_t *__restrict__ orig, uint4 *__restrict__ queue,
+                                uint32_t *__restrict__ qcount, uint32_t qcap)
+{
+    const uint32_t n = min(*nitems_dev, items_cap);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n; t += nw) {
+        const CfItem it = items[t];
+        const uint32_t ic = it.cnt & 0xFFFFu, jc = it.cnt >> 16;
+        const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
+        const uint32_t jo = it.meta & CFI_ITEM_JOBMASK;
+        for (uint32_t il = lane; il < ic; il += 32u) {
+            const uint32_t j0 = diag ? il + 1u : 0u;      // within a cell paired with itself: j > i
+            if (j0 >= jc) continue;
+            const uint32_t cnt = jc - j0;
+            const uint32_t base = atomicAdd(qcount, cnt);
+            const uint32_t oi = orig[it.ibeg + il];
+            for (uint32_t k = 0; k < cnt; k++)
+                if (base + k < qcap) queue[base + k] = make_uint4(oi, orig[it.jbeg + j0 + k], jo, 0u);
+        }
+    }
+}
+
+cudaError_t cfp_launch_audit(const CfItem *items, const uint32_t *nitems_dev, uint32_t items_cap,
+                             const uint32_t *orig, uint4 *queue, uint32_t *qcount, uint32_t qcap, int num_sms,
+                             cudaStream_t st)
+{
+    cf_audit_kernel<<<num_sms * 4, 256, 0, st>>>(items, nitems_dev, items_cap, orig, queue, qcount, qcap);
+    return cudaGetLastError();
+}
+
 cudaError_t cfp_launch_recheck(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs,
                                const uint4 *queue, const uint32_t *qcount, uint32_t qcap,
                                unsigned long long *hcnt, double *hw, double *hr, int num_sms, cudaStream_t st)

@@ -12,9 +12,10 @@ Knobs (all results are identical across them; only speed changes):
           farther apart than the largest edge (costs one pass over the points)
   thetagrid DD(theta) only: 0 the 3-D grid over unit vectors, 1 declination bands x RA cells
 
-The tuner times `cf_count` on the caller's own catalogue with each candidate (coordinate descent
-from the default, best of 3 runs per candidate, repeated while a pass still improves, at most
-twice), keeps the fastest, and caches it in a JSON file keyed by device name,
+The tuner times `cf_count` on the caller's own catalogue (coordinate descent from the default,
+repeated while a pass still improves, at most twice). Each candidate runs alternately with the
+current best, 5 times each, and replaces it only if its median is more than 1 % faster. The
+result is cached in a JSON file keyed by device name,
 kind, options and an occupancy class (log2 of the mean number of points per Rmax cell).  The cache
 path is $CF_TUNE_CACHE, else ~/.cache/cf_gb300_tune.json.
 """
@@ -33,6 +34,7 @@ KNOBS = {"variant": [1, 2], "refine": [1, 2, 3], "warps": [0, 12, 8, 6, 4], "til
 OPT = {"variant": CF_OPT_VARIANT, "refine": CF_OPT_REFINE, "warps": CF_OPT_WARPS, "tile": CF_OPT_TILE,
        "jchunk": CF_OPT_JCHUNK, "noprune": CF_OPT_CELL_PRUNE, "thetagrid": CF_OPT_THETA_GRID}
 DEFAULT = {"variant": 1, "refine": 1, "warps": 0, "tile": 128, "jchunk": 512, "noprune": 0, "thetagrid": 0}
+MARGIN = 0.01
 
 
 def knobs_for(p) -> dict:
@@ -75,7 +77,9 @@ def reset(ctx) -> None:
     apply(ctx, {k: 0 for k in OPT})
 
 
-def _time(ctx, p, d1, d2, reps: int) -> float:
+def _time(ctx, p, d1, d2, reps: int, timer=None) -> float:
+    if timer is not None:
+        return min(timer() for _ in range(reps))
     best = float("inf")
     for _ in range(reps):
         t0 = time.perf_counter()
@@ -86,9 +90,24 @@ def _time(ctx, p, d1, d2, reps: int) -> float:
     return best
 
 
-def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, reps: int = 3,
-         passes: int = 2, use_cache: bool = True, log=None) -> dict:
-    """Return the best configuration for this workload (and leave it applied on ctx)."""
+def _duel(ctx, p, d1, d2, a: dict, b: dict, reps: int, timer=None):
+    """Median times of configurations a and b, measured alternately (a, b, a, b, ...) so that
+    drift and noise fall on both alike."""
+    ta, tb = [], []
+    for _ in range(reps):
+        apply(ctx, a)
+        ta.append(_time(ctx, p, d1, d2, 1, timer))
+        apply(ctx, b)
+        tb.append(_time(ctx, p, d1, d2, 1, timer))
+    return sorted(ta)[len(ta) // 2], sorted(tb)[len(tb) // 2]
+
+
+def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, reps: int = 5,
+         passes: int = 2, use_cache: bool = True, log=None, timer=None) -> dict:
+    """Return the best configuration for this workload (and leave it applied on ctx).  timer:
+    optional callable that runs one count on ctx and returns its time in seconds (so that the
+    tuner ranks configurations by the caller's own measurement); by default the library's event
+    times of build, pair kernel and recheck."""
     key = _key(device_name, p, npoints or 1)
     path = cache_path()
     cache = {}
@@ -104,8 +123,8 @@ def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, rep
         return cfg
     cfg = dict(DEFAULT)
     apply(ctx, cfg)
-    _time(ctx, p, d1, d2, 1)                      # warm up
-    best_t = _time(ctx, p, d1, d2, reps)
+    _time(ctx, p, d1, d2, 1, timer)               # warm up
+    best_t = _time(ctx, p, d1, d2, reps, timer)
     trials = [(dict(cfg), best_t)]
     # coordinate descent, repeated: a knob's best value can change once later knobs have moved
     for _ in range(passes):
@@ -116,13 +135,14 @@ def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, rep
                     continue
                 cand = dict(cfg)
                 cand[knob] = v
-                apply(ctx, cand)
-                t = _time(ctx, p, d1, d2, reps)
-                trials.append((dict(cand), t))
+                # the candidate against the current best, measured alternately; a move must win
+                # by a margin (a marginal win of a few repetitions is often noise)
+                tc, tb = _duel(ctx, p, d1, d2, cand, cfg, reps, timer)
+                trials.append((dict(cand), tc))
                 if log:
-                    log(f"tune {cand} {t * 1e3:.3f} ms")
-                if t < best_t:
-                    best_t, cfg, moved = t, cand, True
+                    log(f"tune {cand} {tc * 1e3:.3f} ms against {tb * 1e3:.3f} ms")
+                if tc < tb * (1.0 - MARGIN):
+                    best_t, cfg, moved = tc, cand, True
         if not moved:
             break
     apply(ctx, cfg)
