@@ -108,7 +108,7 @@ def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, rep
     optional callable that runs one count on ctx and returns its time in seconds (so that the
     tuner ranks configurations by the caller's own measurement); by default the library's event
     times of build, pair kernel and recheck."""
-    key = _key(device_name, p, npoints or 1)
+    key = _key(device_name, p, npoints or 1) if use_cache else ""
     path = cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
