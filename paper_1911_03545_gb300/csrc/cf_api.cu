@@ -278,8 +278,9 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
         refine[a] = p->refine[a] > 0 ? p->refine[a] : (C->opt[CF_OPT_REFINE] > 0 ? (int)C->opt[CF_OPT_REFINE] : 1);
     int tile = C->opt[CF_OPT_TILE] > 0 ? (int)std::min<int64_t>(128, std::max<int64_t>(32, C->opt[CF_OPT_TILE])) : 128;
     int jchunk = C->opt[CF_OPT_JCHUNK] > 0 ? (int)std::min<int64_t>(CFI_JMAX, C->opt[CF_OPT_JCHUNK]) : CFI_JMAX;
-    // |v| of the point nearest the observer (its FP64 square may be one rounding low or high)
-    const double vmin = std::isfinite(vmin2) ? std::sqrt(vmin2) * (1.0 - 1e-12) : 0.0;
+    // |v| of the point nearest the observer (its square was summed in float32 for float32 inputs:
+    // a few roundings high or low)
+    const double vmin = std::isfinite(vmin2) ? std::sqrt(vmin2) * (1.0 - 1e-6) : 0.0;
     rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err, angular ? 1 : 0, vmin);
     if (rc) return C->fail(rc, err);
     CfDevPlan &D = H.d;

@@ -14,7 +14,44 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
     const CfSetDesc S = sets[blockIdx.y];
     unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0}, bad = 0, nrm = 0, rmin = ~0ull;
     const void *P[3] = {S.x, S.y, S.z};
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (S.dtype == CF_F32) {
+        // float32 inputs: minima, maxima, |v|^2 and its deviation from 1 in float32 (the FP64 pipe
+        // runs at a small fraction of the FP32 rate); keys once per thread.  |v|^2 carries <= 3
+        // roundings here, which its users allow for.
+        const float *X = (const float *)S.x, *Y = (const float *)S.y, *Z = (const float *)S.z;
+        const float *Wt = (const float *)S.w;
+        float fmn[3] = {INFINITY, INFINITY, INFINITY}, fmx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        float fnrm = 0.f, frmin = INFINITY;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const float v[3] = {X[i], Y[i], Z[i]};
+            bool ok = true;
+            for (int a = 0; a < 3; a++) {
+                if (!isfinite(v[a])) {
+                    bad++;
+                    ok = false;
+                    continue;
+                }
+                fmn[a] = fminf(fmn[a], v[a]);
+                fmx[a] = fmaxf(fmx[a], v[a]);
+            }
+            if (ok) {
+                const float r2 = fmaf(v[2], v[2], fmaf(v[1], v[1], v[0] * v[0]));
+                fnrm = fmaxf(fnrm, fabsf(r2 - 1.0f));
+                frmin = fminf(frmin, r2);
+            }
+            if (Wt && !isfinite(Wt[i])) bad++;
+        }
+        for (int a = 0; a < 3; a++)
+            if (fmn[a] <= fmx[a]) {
+                mn[a] = cf_dkey((double)fmn[a]);
+                mx[a] = cf_dkey((double)fmx[a]);
+            }
+        nrm = (unsigned long long)__double_as_longlong((double)fnrm);
+        if (frmin < INFINITY) rmin = (unsigned long long)__double_as_longlong((double)frmin);
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; S.dtype != CF_F32 && i < S.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
         double r2 = 0.0;
         for (int a = 0; a < 3; a++) {
             double v = cf_load(P[a], S.dtype, i);
