@@ -11,6 +11,7 @@
 // into a CUDA graph and replay it.
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -281,8 +282,28 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     // |v| of the point nearest the observer (its square was summed in float32 for float32 inputs:
     // a few roundings high or low)
     const double vmin = std::isfinite(vmin2) ? std::sqrt(vmin2) * (1.0 - 1e-6) : 0.0;
-    rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err, angular ? 1 : 0, vmin);
-    if (rc) return C->fail(rc, err);
+    {
+        // the plan depends only on these: a repeated call on the same inputs reuses the previous
+        // one (planning takes ~0.1 ms of host time while the device waits)
+        std::string key;
+        auto put = [&key](const void *v, size_t n) { key.append((const char *)v, n); };
+        put(p, offsetof(cf_params, edges));
+        put(&p->nbins, sizeof(cf_params) - offsetof(cf_params, nbins));
+        put(p->edges, sizeof(double) * (size_t)(p->nbins + 1));
+        put(bbox, sizeof(bbox));
+        put(&R.npts, sizeof(R.npts));
+        const int ints[6] = {any_f64 ? 1 : 0, refine[0] * 16 + refine[1] * 4 + refine[2], tile, jchunk, angular ? 1 : 0,
+                             0};
+        put(ints, sizeof(ints));
+        put(&vmin, sizeof(vmin));
+        if (key != C->plan_key) {
+            C->plan_key.clear();
+            rc = cfp_make_plan(p, bbox, R.npts, any_f64 ? 1 : 0, refine, tile, jchunk, &H, err, angular ? 1 : 0,
+                               vmin);
+            if (rc) return C->fail(rc, err);
+            C->plan_key = key;
+        }
+    }
     CfDevPlan &D = H.d;
     D.nsets = nsets;
     D.njobs = njobs;

@@ -65,6 +65,7 @@ struct CfCtx {
     cudaStream_t stream = nullptr;
     int num_sms = 1;
     int smem_optin = 0;            // largest dynamic shared memory of one CTA (opt-in)
+    std::string plan_key;          // inputs of the plan held in run.plan (empty: none)
     std::string err;
     size_t mem_cap = 0, mem_used = 0;
     Buf buf[B_COUNT_];
