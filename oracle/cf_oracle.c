@@ -22,7 +22,7 @@
  *   - Sec. 4.3 and Appendix B: auto-correlations count each unordered pair once and double
  *     the totals; if the first bin starts at 0 the N self-pairs are added once.
  *
- * Arithmetic fixed here where the paper is silent (each reading is listed in the design doc):
+ * Arithmetic fixed here where the paper is silent:
  *   - bins are half-open, lo <= s < hi, compared in squared space against e2 = e*e (FP64);
  *   - the squared separation is evaluated as ((dx*dx + dy*dy) + dz*dz), no fused multiply-add
  *     (the file is compiled with -ffp-contract=off);

@@ -448,7 +448,7 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
         }
     }
 
-    // ---- FP32 error model (derivation in the design doc) ----
+    // ---- FP32 error model: a per-axis bound on the separation's error, then a band per edge ----
     // stored cell-relative coordinates X are exact for float32 inputs (snapped origins);
     // float64 inputs round to float32 (epsX), or keep a lo part when ravg is requested.
     const double u = U32;
@@ -489,11 +489,12 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
     D.near2 = 0.0f;
     D.cut_su = 0.0f;
     if (mocks) {
-        // Error model of the mocks kernel (Appendix A.2.1 evaluated in FP32; derivation in the
-        // design notes).  Per pair: s from the cell-relative coordinates (per-axis error <= delta,
-        // Dl2 its 2-norm), l = A_i - s/2 from the float32 absolute position A_i; the binned values
-        // are pi^2 = (s.l)^2 / l.l and rp^2 = |s x A_i|^2 / l.l (s x A_i = s x l exactly).  A candidate with l.l below near2 = S^2 goes to the FP64
-        // recheck, so every other one has |l| >= 0.999 S and |A_i| <= 1.51 |l|.  Both values divide
+        // Error model of the mocks kernel (Appendix A.2.1 evaluated in FP32).  Per pair: s from
+        // the cell-relative coordinates (per-axis error <= delta, Dl2 its 2-norm), l = A_i - s/2
+        // from the float32 absolute position A_i; the binned values are pi^2 = (s.l)^2 / l.l and
+        // rp^2 = |s x A_i|^2 / l.l (s x A_i = s x l exactly).  A candidate with l.l below
+        // near2 = S^2 goes to the FP64 recheck, so every other one has |l| >= 0.999 S and
+        // |A_i| <= 1.51 |l|.  Both values divide
         // by l.l through one reciprocal (<= 2 ulp) and a product.
         double Dl = 0.0, Dl2 = 0.0;
         for (int a = 0; a < 3; a++) {
