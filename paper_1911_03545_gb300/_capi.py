@@ -80,7 +80,7 @@ class cf_stats(ctypes.Structure):
         ("ms_recheck", ctypes.c_float),
         ("ms_total", ctypes.c_float),
         ("kernel_launches", ctypes.c_int),
-        ("pad", ctypes.c_int),
+        ("fixed_sums", ctypes.c_int),
     ]
 
 

@@ -232,7 +232,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     {
         unsigned long long *init = (unsigned long long *)C->hpin;
         for (int s = 0; s < nsets; s++)
-            for (size_t a = 0; a < bbw; a++) init[bbw * s + a] = (a < 3 || a == 8) ? ~0ull : 0ull;
+            for (size_t a = 0; a < bbw; a++) init[bbw * s + a] = (a < 3 || a == 8 || a == 9) ? ~0ull : 0ull;
         CF_CU(cudaMemcpyAsync(C->buf[B_BBOX].p, init, 8 * bbw * (size_t)nsets, cudaMemcpyHostToDevice, st),
               "bbox init");
     }
@@ -245,12 +245,20 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     double bbox[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     double norm_dev = 0.0;   // largest | |v|^2 - 1 | over the points
     double vmin2 = INFINITY;  // smallest |v|^2 over the points
+    R.wmin.assign(nsets, INFINITY);
+    R.wmax.assign(nsets, 0.0);
+    R.wneg = false;
     {
         const unsigned long long *bb = (const unsigned long long *)C->hpin;
         for (int s = 0; s < nsets; s++) {
             if (R.sets[s].n == 0) continue;
             const unsigned long long *b = bb + bbw * s;
             if (b[6]) return C->fail(CF_ERR_ARG, "non-finite coordinate or weight");
+            if (R.sets[s].w) {
+                if (b[9] != ~0ull) std::memcpy(&R.wmin[s], &b[9], 8);
+                std::memcpy(&R.wmax[s], &b[10], 8);
+                R.wneg = R.wneg || b[11] != 0;
+            }
             double nd, r2;
             std::memcpy(&nd, &b[7], 8);
             std::memcpy(&r2, &b[8], 8);
@@ -447,6 +455,53 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     return CF_OK;
 }
 
+// Power-of-two scale for fixed-point sums of terms in [tmin, tmax] (tmin > 0): tmax * scale < 2^35,
+// so that 2^28 terms (the most a warp holds between flushes) stay below 2^63, and tmin * scale >=
+// 2^22, so that rounding a term to an integer moves it by at most 2^-23 of itself.  0 (FP64 sums)
+// when no such scale exists or the terms are not normal float32 values.
+static float fixed_scale(double tmin, double tmax)
+{
+    if (!(tmin > 1e-30) || !(tmax >= tmin) || !(tmax < 1e30)) return 0.f;
+    int ex = 0;
+    std::frexp(tmax * (1.0 + 1.0 / 1024.0), &ex);   // the largest term, with margin for its FP32
+                                                    // rounding, is below 2^ex
+    const double s = std::ldexp(1.0, 35 - ex);
+    return tmin * s >= 4194304.0 ? (float)s : 0.f;
+}
+
+// Scales of the per-warp weight and ravg sums of rp-pi / mocks.  A term is w_i w_j (weights), rp
+// (ravg) or w_i w_j rp (both).  Weight products lie between the products of the sets' smallest
+// nonzero and largest |w| (zero products are exact); rp between the first and the last edge.
+// Negative weights (sums that may cancel) and, with ravg, a first edge of 0 keep FP64 for every
+// sum of the call.
+static void fixed_point_scales(const CfRun &R, bool weighted, bool ravg, CfPairArgs &A)
+{
+    A.fxw = A.fxr = 0.f;
+    A.ifxw = A.ifxr = 0.0;
+    double pmin = 1.0, pmax = 1.0;
+    if (weighted) {
+        if (R.wneg) return;
+        pmin = INFINITY;
+        pmax = 0.0;
+        for (const CfJobDesc &J : R.jobs) {
+            pmax = std::max(pmax, R.wmax[J.a] * R.wmax[J.b]);
+            const double lo = R.wmin[J.a] * R.wmin[J.b];
+            if (std::isfinite(lo)) pmin = std::min(pmin, lo);
+        }
+        if (!std::isfinite(pmin)) pmin = pmax = 1.0;   // every product is 0
+        A.fxw = fixed_scale(pmin, pmax);
+    }
+    if (ravg) {
+        const double e0 = R.edges.front(), e1 = R.edges.back();
+        // an FP32 rp of a pair in the first bin may sit a few roundings below its edge
+        A.fxr = fixed_scale(e0 * (1.0 - 1e-5) * pmin, e1 * pmax);
+    }
+    // one form for every sum the call keeps: fixed point only where all of them allow it
+    if ((weighted && A.fxw == 0.f) || (ravg && A.fxr == 0.f)) A.fxw = A.fxr = 0.f;
+    if (A.fxw != 0.f) A.ifxw = 1.0 / (double)A.fxw;
+    if (A.fxr != 0.f) A.ifxr = 1.0 / (double)A.fxr;
+}
+
 // work items -> pair kernel -> recheck -> readback (device only; records ev[1..3] when `timed`)
 int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
 {
@@ -498,6 +553,10 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     if (per_warp && !R.cfg.ghist && cfp_pair_smem(R.cfg, 1) > (size_t)C->smem_optin) R.cfg.ghist = 1;
     if (R.cfg.ghist) R.cfg.variant = 1;       // that form is built direct only
     A.ghist = R.cfg.ghist;
+    // their per-warp sums go to 64-bit fixed point when the terms' range allows it; never in a
+    // captured graph, whose replays bring new weights
+    if (per_warp && !A.ghist && !C->capturing) fixed_point_scales(R, D.weighted != 0, R.cfg.ravg != 0, A);
+    if (A.fxw != 0.f || A.fxr != 0.f) R.cfg.variant = 1;    // built direct only
     int grid = 0, warps = 0;
     if (R.items_cap > 0 && C->opt[CF_OPT_AUDIT]) {
         CF_CU(cfp_launch_audit(A.items, A.nitems_dev, A.items_cap, A.orig, A.queue, A.qcount, A.qcap, C->num_sms,
@@ -591,6 +650,7 @@ int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
     }
     C->stats.ncat = R.njobs;
     C->stats.variant = R.cfg.variant;
+    C->stats.fixed_sums = (R.args.fxw != 0.f ? 1 : 0) | (R.args.fxr != 0.f ? 2 : 0);
     C->stats.kernel_launches = C->launches;
     return CF_OK;
 }

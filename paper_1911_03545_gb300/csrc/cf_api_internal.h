@@ -51,6 +51,8 @@ struct CfRun {
     int64_t nfine = 0;             // ncell_all * sub^3 counting-sort keys
     size_t nslot = 0, hsz = 0;
     bool self_pairs = false;
+    std::vector<double> wmin, wmax;   // per point set: smallest nonzero |w| (inf: none), largest |w|
+    bool wneg = false;                // some weight is negative
     uint32_t qcap = 0, items_cap = 0;
     CfPairCfg cfg;
     CfPairArgs args;

@@ -6,13 +6,15 @@
 // ---------------------------------------------------------------------------------------------
 // Bounding box and validity of every point set: min / max per axis, count of non-finite values.
 // grid = (blocks, nsets); out[s*W + 0..5] = key(min x,y,z), key(max x,y,z); out[s*W+6] = bad;
-// out[s*W+7] = bits of the largest | |v|^2 - 1 |; out[s*W+8] = bits of the smallest |v|^2
-// (W = CFB_BBOX_WORDS; a non-negative double's bits order like its value).
+// out[s*W+7] = bits of the largest | |v|^2 - 1 |; out[s*W+8] = bits of the smallest |v|^2;
+// out[s*W+9], [10] = bits of the smallest nonzero and the largest |w|; out[s*W+11] = negative
+// weights (W = CFB_BBOX_WORDS; a non-negative double's bits order like its value).
 // ---------------------------------------------------------------------------------------------
 __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long long *__restrict__ out)
 {
     const CfSetDesc S = sets[blockIdx.y];
     unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0}, bad = 0, nrm = 0, rmin = ~0ull;
+    unsigned long long wmn = ~0ull, wmx = 0, wng = 0;    // |w| range (nonzero minimum), negatives
     const void *P[3] = {S.x, S.y, S.z};
     if (S.dtype == CF_F32) {
         // float32 inputs: minima, maxima, |v|^2 and its deviation from 1 in float32 (the FP64 pipe
@@ -21,7 +23,7 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         const float *X = (const float *)S.x, *Y = (const float *)S.y, *Z = (const float *)S.z;
         const float *Wt = (const float *)S.w;
         float fmn[3] = {INFINITY, INFINITY, INFINITY}, fmx[3] = {-INFINITY, -INFINITY, -INFINITY};
-        float fnrm = 0.f, frmin = INFINITY;
+        float fnrm = 0.f, frmin = INFINITY, fwmn = INFINITY, fwmx = 0.f;
         for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n;
              i += (int64_t)gridDim.x * blockDim.x) {
             const float v[3] = {X[i], Y[i], Z[i]};
@@ -40,7 +42,17 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
                 fnrm = fmaxf(fnrm, fabsf(r2 - 1.0f));
                 frmin = fminf(frmin, r2);
             }
-            if (Wt && !isfinite(Wt[i])) bad++;
+            if (Wt) {
+                const float w = Wt[i];
+                if (!isfinite(w)) {
+                    bad++;
+                } else {
+                    const float aw = fabsf(w);
+                    if (w < 0.f) wng++;
+                    if (aw > 0.f) fwmn = fminf(fwmn, aw);
+                    fwmx = fmaxf(fwmx, aw);
+                }
+            }
         }
         for (int a = 0; a < 3; a++)
             if (fmn[a] <= fmx[a]) {
@@ -49,6 +61,8 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
             }
         nrm = (unsigned long long)__double_as_longlong((double)fnrm);
         if (frmin < INFINITY) rmin = (unsigned long long)__double_as_longlong((double)frmin);
+        if (fwmn < INFINITY) wmn = (unsigned long long)__double_as_longlong((double)fwmn);
+        wmx = (unsigned long long)__double_as_longlong((double)fwmx);
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; S.dtype != CF_F32 && i < S.n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -70,7 +84,14 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         rmin = r2b < rmin ? r2b : rmin;
         if (S.w) {
             double w = cf_load(S.w, S.dtype, i);
-            if (!isfinite(w)) bad++;
+            if (!isfinite(w)) {
+                bad++;
+            } else {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(w));
+                if (w < 0.0) wng++;
+                if (b) wmn = b < wmn ? b : wmn;
+                wmx = b > wmx ? b : wmx;
+            }
         }
     }
     for (int o = 16; o; o >>= 1) {
@@ -85,6 +106,11 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         nrm = t > nrm ? t : nrm;
         const unsigned long long t2 = __shfl_xor_sync(CF_FULL, rmin, o);
         rmin = t2 < rmin ? t2 : rmin;
+        const unsigned long long t3 = __shfl_xor_sync(CF_FULL, wmn, o);
+        wmn = t3 < wmn ? t3 : wmn;
+        const unsigned long long t4 = __shfl_xor_sync(CF_FULL, wmx, o);
+        wmx = t4 > wmx ? t4 : wmx;
+        wng += __shfl_xor_sync(CF_FULL, wng, o);
     }
     // block reduction through shared memory, then one atomic per block and value
     __shared__ unsigned long long red[CFB_BBOX_WORDS][32];
@@ -97,6 +123,9 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         red[6][w] = bad;
         red[7][w] = nrm;
         red[8][w] = rmin;
+        red[9][w] = wmn;
+        red[10][w] = wmx;
+        red[11][w] = wng;
     }
     __syncthreads();
     if (w == 0) {
@@ -108,6 +137,9 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
         v[6] = lane < nw ? red[6][lane] : 0ull;
         v[7] = lane < nw ? red[7][lane] : 0ull;
         v[8] = lane < nw ? red[8][lane] : ~0ull;
+        v[9] = lane < nw ? red[9][lane] : ~0ull;
+        v[10] = lane < nw ? red[10][lane] : 0ull;
+        v[11] = lane < nw ? red[11][lane] : 0ull;
         for (int o = 16; o; o >>= 1) {
             for (int a = 0; a < 3; a++) {
                 unsigned long long t = __shfl_xor_sync(CF_FULL, v[a], o);
@@ -120,6 +152,11 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
             v[7] = t > v[7] ? t : v[7];
             const unsigned long long t2 = __shfl_xor_sync(CF_FULL, v[8], o);
             v[8] = t2 < v[8] ? t2 : v[8];
+            const unsigned long long t3 = __shfl_xor_sync(CF_FULL, v[9], o);
+            v[9] = t3 < v[9] ? t3 : v[9];
+            const unsigned long long t4 = __shfl_xor_sync(CF_FULL, v[10], o);
+            v[10] = t4 > v[10] ? t4 : v[10];
+            v[11] += __shfl_xor_sync(CF_FULL, v[11], o);
         }
         if (lane == 0) {
             unsigned long long *o = out + blockIdx.y * CFB_BBOX_WORDS;
@@ -130,6 +167,9 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
             if (v[6]) atomicAdd(o + 6, v[6]);
             atomicMax(o + 7, v[7]);
             atomicMin(o + 8, v[8]);
+            atomicMin(o + 9, v[9]);
+            atomicMax(o + 10, v[10]);
+            if (v[11]) atomicAdd(o + 11, v[11]);
         }
     }
 }

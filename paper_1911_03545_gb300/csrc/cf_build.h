@@ -4,7 +4,9 @@
 
 #include "cf_internal.h"
 
-#define CFB_BBOX_WORDS 9     // per point set: 3 min keys, 3 max keys, bad, norm deviation, min |v|^2
+// per point set: 3 min keys, 3 max keys, bad, norm deviation, min |v|^2, smallest nonzero |w|,
+// largest |w|, negative weights
+#define CFB_BBOX_WORDS 12
 cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st);
 // key = cell * sub^3 + Morton sub-cell (sub = 1, 2, 4): the counting-sort key of every point
 cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
@@ -51,6 +53,9 @@ struct CfPairArgs {
     int nb, npi, nslot;
     int ghist;                   // 1: rp-pi / mocks add straight into hcnt/hw/hr (global atomics):
                                  // their per-warp histogram does not fit in shared memory
+    float fxw, fxr;              // rp-pi / mocks per-warp weight / ravg sums: 64-bit fixed point at
+                                 // this power-of-two scale (0: FP64)
+    double ifxw, ifxr;           // 1 / fxw, 1 / fxr
 };
 
 // Static configuration of a pair-kernel launch (selects the template instance and the shared

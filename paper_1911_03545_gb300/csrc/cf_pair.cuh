@@ -26,9 +26,10 @@
 //
 // Histograms live in shared memory per warp (Sec. 4.8: private histograms, merged once): for
 // r / theta / wp one private copy per lane (no bank conflicts, no contention; weighted sums
-// Kahan-compensated in FP32), for rp-pi one copy per warp updated by shared atomics (FP64 for
-// weighted sums).  They are merged into the global histogram when a warp moves to another job
-// and at exit.
+// Kahan-compensated in FP32), for rp-pi one copy per warp updated by shared atomics (weight and
+// ravg sums in 64-bit fixed point where the host found a scale for the terms' range, else FP64).
+// They are merged into the global histogram when a warp moves to another job, after every 2^28
+// evaluated pairs, and at exit.
 #pragma once
 #include "cf_build.h"
 #include "cf_device.cuh"
@@ -46,6 +47,9 @@ __host__ __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 1
 //   j stage: 2 chunks x 3-7 float arrays (x, y, z[, w][, lo parts of x, y, z]) of JSTAGE points
 //   ring:    RING candidates as arrays: value bits, |dz| bits (rp-pi, wp), weight product (W),
 //            code (u16: i slot | j << 7)
+// a warp flushes its histograms once it has evaluated more than this many pairs of one job;
+// with the item in hand that keeps every flushed batch at <= 2^28 pairs (an item: <= 2^16)
+constexpr uint32_t CF_FLUSH_PAIRS = (1u << 28) - (1u << 16);
 constexpr uint32_t JSTAGE = 32;
 constexpr uint32_t RING = 512;
 constexpr uint32_t RM = RING - 1;
@@ -198,8 +202,9 @@ static __device__ __noinline__ float mocks_rp(const CfPairArgs &a, uint32_t ip, 
 }
 
 // GH (rp-pi and mocks only): no per-warp histogram; every pair adds straight into the job's global
-// histogram (CfPairArgs::ghist)
-template <int KIND, bool W, bool R, bool WRAP, bool LO, bool GH>
+// histogram (CfPairArgs::ghist).  FX (rp-pi and mocks, per-warp histogram): the weight and ravg sums
+// are 64-bit fixed point at the scales CfPairArgs::fxw / fxr, else FP64.
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool GH, bool FX>
 struct Warp {
     const CfPairArgs &a;
     Lut lr, lp;
@@ -258,11 +263,21 @@ struct Warp {
             return;
         }
         atomicAdd(h_cnt + slot, 1u);
-        if (W) atomicAdd(h_wd + slot, (double)wp);
+        if (W) add_sum(h_wd, slot, wp, a.fxw);
         if (R) {
             float r = f_sqrt_approx(rp2);
-            atomicAdd(h_rd + slot, (double)(W ? wp * r : r));
+            add_sum(h_rd, slot, W ? wp * r : r, a.fxr);
         }
+    }
+
+    // One term of a per-warp sum: with FX a 64-bit integer add of round(t * scale) (the scale is a
+    // power of two, so t * scale is exact; the host chose it so that every term is at least 2^22
+    // units, its rounding within 2^-23 of it, and flushes every 2^28 pairs keep the sum below
+    // 2^63), else an FP64 add.
+    static __device__ __forceinline__ void add_sum(double *h, uint32_t slot, float t, float scale)
+    {
+        if (FX) atomicAdd(reinterpret_cast<unsigned long long *>(h) + slot, __float2ull_rn(t * scale));
+        else atomicAdd(h + slot, (double)t);
     }
 
     // Histogram slot of N pairs that passed the FP32 cut (squared separation below cut_r and,
@@ -608,14 +623,14 @@ struct Warp {
             return;
         }
         atomicAdd(h_cnt + slot, 1u);
-        if (W) atomicAdd(h_wd + slot, (double)wp);
+        if (W) add_sum(h_wd, slot, wp, a.fxw);
         if (R) {
             // the j point is in the stage buffer of its chunk
             constexpr uint32_t NA = stage_arrays(W, LO);
             const float *bs = jst + ((j / JSTAGE) & 1u) * NA * JSTAGE;
             const float rr = mocks_rp<LO>(a, ibeg + il, bs, j % JSTAGE, ish[0], ish[1], ish[2], isl[0], isl[1],
                                           isl[2]);
-            atomicAdd(h_rd + slot, (double)(W ? wp * rr : rr));
+            add_sum(h_rd, slot, W ? wp * rr : rr, a.fxr);
         }
     }
 
@@ -779,8 +794,14 @@ struct Warp {
             if (warp_hist(KIND)) {
                 c = h_cnt[sl];
                 h_cnt[sl] = 0;
-                if (W) { ws = h_wd[sl]; h_wd[sl] = 0.0; }
-                if (R) { rs = h_rd[sl]; h_rd[sl] = 0.0; }
+                if (W) {
+                    ws = FX ? (double)reinterpret_cast<unsigned long long *>(h_wd)[sl] * a.ifxw : h_wd[sl];
+                    h_wd[sl] = 0.0;
+                }
+                if (R) {
+                    rs = FX ? (double)reinterpret_cast<unsigned long long *>(h_rd)[sl] * a.ifxr : h_rd[sl];
+                    h_rd[sl] = 0.0;
+                }
             } else {
                 constexpr int ST = (W && R) ? 2 : 1;     // float2 stride of the Kahan sums
                 for (int l = 0; l < 32; l++) {
@@ -813,7 +834,7 @@ struct Warp {
 __host__ __device__ constexpr int pair_max_threads(bool W, bool R) { return (W || R) ? 512 : 256; }
 __host__ __device__ constexpr int pair_min_blocks(bool W, bool R) { return (!W && !R) ? 3 : 1; }
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT, bool GH>
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT, bool GH, bool FX>
 __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     pair_kernel(const CfPairArgs a)
 {
@@ -837,7 +858,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     }
     __syncthreads();
 
-    Warp<KIND, W, R, WRAP, LO, GH> w(a);
+    Warp<KIND, W, R, WRAP, LO, GH, FX> w(a);
     w.lane = threadIdx.x & 31;
     w.nb = a.nb;
     w.npi = a.npi;
@@ -882,6 +903,9 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
 
     const uint32_t nitems = min(*a.nitems_dev, a.items_cap);
     int cur = -1;
+    // pairs evaluated since the last flush: a warp flushes at the latest every 2^28 (an item holds
+    // at most 128 x 512 = 2^16), so no 32-bit count and no fixed-point sum it holds can overflow
+    uint32_t pend = 0;
     // the next item's index and descriptor are fetched before the current item is processed
     uint32_t t = 0;
     if (w.lane == 0) t = atomicAdd(a.cursor, 1u);
@@ -896,12 +920,14 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
         CfItem nx;
         if (tn < nitems) nx = a.items[tn];
         const int job = (int)(it.meta & CFI_ITEM_JOBMASK);
-        if (job != cur) {
+        if (job != cur || pend > CF_FLUSH_PAIRS) {
             if (cur >= 0) w.flush((uint32_t)cur);
             cur = job;
+            pend = 0;
         }
         const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
         const uint32_t ic = it.cnt & 0xFFFFu;
+        pend += ic * (it.cnt >> 16);
         if (KIND == KIND_MOCKS) {
             if (diag) w.template run_mocks<4, true>(it);
             else if (ic <= 32u) w.template run_mocks<1, false>(it);
@@ -919,11 +945,11 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     if (cur >= 0) w.flush((uint32_t)cur);
 }
 
-template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT, bool GH = false>
+template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT, bool GH = false, bool FX = false>
 cudaError_t launch_variant(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
                            int *warps_out)
 {
-    auto k = pair_kernel<KIND, W, R, WRAP, LO, COMPACT, GH>;
+    auto k = pair_kernel<KIND, W, R, WRAP, LO, COMPACT, GH, FX>;
     int dev;
     cudaGetDevice(&dev);
     int maxsm = 0;
@@ -959,6 +985,10 @@ cudaError_t launch_one(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cud
     // global histograms (rp-pi tables too large for shared memory): the direct form only
     if constexpr (warp_hist(KIND))
         if (c.ghist) return launch_variant<KIND, W, R, WRAP, LO, false, true>(c, a, num_sms, st, grid_out, warps_out);
+    // fixed-point per-warp sums: the direct form only
+    if constexpr (warp_hist(KIND) && (W || R))
+        if (a.fxw != 0.f || a.fxr != 0.f)
+            return launch_variant<KIND, W, R, WRAP, LO, false, false, true>(c, a, num_sms, st, grid_out, warps_out);
     if (c.variant == 2) return launch_variant<KIND, W, R, WRAP, LO, true>(c, a, num_sms, st, grid_out, warps_out);
     return launch_variant<KIND, W, R, WRAP, LO, false>(c, a, num_sms, st, grid_out, warps_out);
 }

@@ -4,9 +4,20 @@
 
 using namespace cfpair;
 
-#define CF_L(W, R, LO)                                                                                         \
-    return c.ghist ? launch_variant<KIND_MOCKS, W, R, false, LO, false, true>(c, a, num_sms, st, grid_out, warps_out) \
-                   : launch_variant<KIND_MOCKS, W, R, false, LO, false, false>(c, a, num_sms, st, grid_out, warps_out)
+// global histograms, per-warp histograms with fixed-point sums, or per-warp with FP64 sums
+template <bool W, bool R, bool LO>
+static cudaError_t launch_mocks(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
+                                int *warps_out)
+{
+    if (c.ghist) return launch_variant<KIND_MOCKS, W, R, false, LO, false, true>(c, a, num_sms, st, grid_out, warps_out);
+    if constexpr (W || R)
+        if (a.fxw != 0.f || a.fxr != 0.f)
+            return launch_variant<KIND_MOCKS, W, R, false, LO, false, false, true>(c, a, num_sms, st, grid_out,
+                                                                               warps_out);
+    return launch_variant<KIND_MOCKS, W, R, false, LO, false, false>(c, a, num_sms, st, grid_out, warps_out);
+}
+
+#define CF_L(W, R, LO) return launch_mocks<W, R, LO>(c, a, num_sms, st, grid_out, warps_out)
 
 cudaError_t cfp_launch_mocks(const CfPairCfg &c, const CfPairArgs &a, int num_sms, cudaStream_t st, int *grid_out,
                              int *warps_out)
