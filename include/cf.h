@@ -185,8 +185,14 @@ cf_status cf_count(void *ctx, const cf_params *params, const cf_points *d1, cons
 
 /* Count `ncat` independent catalogues with the same params (autocorr only): one cell build
  * over all catalogues, one persistent pair-kernel launch over the concatenated work list.
- * outs[c] receives catalogue c's results.  With capture = 1 the device part is recorded into a
- * CUDA graph that cf_batch_replay re-launches on new data of the same sizes (same pointers). */
+ * outs[c] receives catalogue c's results.  cf_batch_capture counts once and records the device
+ * part into a CUDA graph that cf_batch_replay re-launches on new data of the same sizes (same
+ * pointers).  The graph re-runs the bounding-box pass: when the new data leave the box the
+ * capture was planned for (or, for DD(rp, pi) of observed positions, come nearer the observer),
+ * or the work list or recheck queue outgrow the captured capacity, the replay counts without
+ * the graph, with every check of cf_batch_count (so invalid data fail with CF_ERR_ARG), and
+ * drops the graph: the next replay then fails until the batch is captured again.  Weighted sums
+ * of a replay are FP64 (cf_stats.fixed_sums = 0). */
 cf_status cf_batch_count(void *ctx, const cf_params *params, const cf_points *cats, int ncat,
                          cf_result *outs);
 cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *cats, int ncat);

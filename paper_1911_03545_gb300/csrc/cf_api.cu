@@ -279,6 +279,9 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
 
     // ---- plan ----
     const bool angular = p->kind == CF_DD_THETA && C->opt[CF_OPT_THETA_GRID] == 1;
+    std::memcpy(R.bbox, bbox, sizeof(bbox));
+    R.vmin2 = vmin2;
+    R.angular = angular;
     if (angular && norm_dev > 2e-3)
         return C->fail(CF_ERR_ARG, "the angular grid needs unit vectors (|v| within 1e-3 of 1)");
     CfHostPlan &H = R.plan;
@@ -411,6 +414,39 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
 }
 
 size_t readback_bytes(const CfRun &R) { return 64 + 24 * R.hsz + 8 * (size_t)R.nsets; }
+
+// bbox pass of a captured graph: starting values, the pass, its readback at R.bb_off
+static int cf_enqueue_bbox(CfCtx *C, CfRun &R)
+{
+    cudaStream_t st = C->stream;
+    unsigned long long *bb = (unsigned long long *)C->buf[B_BBOX].p;
+    CF_CU(cfb_bbox_init(bb, R.nsets, st), "bbox init");
+    CF_CU(cfb_bbox((const CfSetDesc *)C->buf[B_SETS].p, R.nsets, std::max<int64_t>(R.nmax, 1), bb, st), "bbox kernel");
+    CF_CU(cudaMemcpyAsync((char *)C->hpin + R.bb_off, bb, 8 * CFB_BBOX_WORDS * (size_t)R.nsets, cudaMemcpyDeviceToHost,
+                          st), "bbox readback");
+    C->launches += 2;
+    return CF_OK;
+}
+
+// Whether new data of a replay still fits the captured plan: finite values, every set inside the
+// box the grid was made for (which for periodic sets lies in [0, box]), for mocks no point nearer
+// the observer than before, for the angular grid unit vectors.
+static bool bbox_within(const CfRun &R, const unsigned long long *bb)
+{
+    for (int s = 0; s < R.nsets; s++) {
+        if (R.sets[s].n == 0) continue;
+        const unsigned long long *b = bb + CFB_BBOX_WORDS * s;
+        if (b[6]) return false;
+        for (int a = 0; a < 3; a++)
+            if (!(dkey_to_double(b[a]) >= R.bbox[a] && dkey_to_double(b[3 + a]) <= R.bbox[3 + a])) return false;
+        double nd, r2;
+        std::memcpy(&nd, &b[7], 8);
+        std::memcpy(&r2, &b[8], 8);
+        if (R.p.kind == CF_DD_RPPI_MOCKS && !(r2 >= R.vmin2)) return false;
+        if (R.angular && !(nd <= 2e-3)) return false;
+    }
+    return true;
+}
 
 // cell build + work-list count and scan (device only)
 int cf_enqueue_build(CfCtx *C, CfRun &R)
@@ -864,6 +900,10 @@ cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *
     if ((rc = C->ensure(B_ITEMS, sizeof(CfItem) * (size_t)R.items_cap))) return (cf_status)rc;
     R.qcap = std::max(R.qcap, (uint32_t)(C->stats.rechecked_pairs * 2 + 4096));
     if ((rc = C->ensure(B_QUEUE, 16 * (size_t)R.qcap))) return (cf_status)rc;
+    // the graph also re-runs the bbox pass, read back past the results, so that a replay can
+    // check that its new data still fit the plan
+    R.bb_off = (readback_bytes(R) + 255) & ~(size_t)255;
+    if ((rc = C->ensure_host(R.bb_off + 8 * CFB_BBOX_WORDS * (size_t)R.nsets))) return (cf_status)rc;
     cudaStream_t user = C->stream;
     cudaStreamSynchronize(user);
     C->drop_graph();
@@ -875,7 +915,9 @@ cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *
     if ((rc = C->cuda(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture"))) return (cf_status)rc;
     C->capturing = true;
     C->stream = st;
-    int rc1 = cf_enqueue_build(C, R);
+    C->launches = 0;          // a replay reports the graph's own kernels
+    int rc0 = cf_enqueue_bbox(C, R);
+    int rc1 = rc0 ? rc0 : cf_enqueue_build(C, R);
     int rc2 = rc1 ? rc1 : cf_enqueue_count(C, R, true);
     C->stream = user;
     C->capturing = false;
@@ -915,10 +957,12 @@ cf_status cf_batch_replay(void *ctx, cf_result *outs, int ncat)
     CfRun &R = C->run;
     std::vector<CfJobResult> res;
     int retry = 0;
-    if ((rc = cf_finish(C, R, res, &retry))) return (cf_status)rc;
+    if (!bbox_within(R, (const unsigned long long *)((const char *)C->hpin + R.bb_off))) retry = 3;
+    else if ((rc = cf_finish(C, R, res, &retry))) return (cf_status)rc;
     if (retry) {
-        // the work list or the recheck queue outgrew the captured capacity: count without the
-        // graph (same inputs) and drop the graph so that the next capture sizes it again
+        // the new data left the captured plan's box (or are not finite), or the work list or the
+        // recheck queue outgrew the captured capacity: count without the graph (same inputs,
+        // checked and planned afresh) and drop the graph so that the next capture sizes it again
         std::vector<const cf_points *> pts;
         for (auto &q : R.pts) pts.push_back(&q);
         std::vector<CfJobDesc> jobs = R.jobs;

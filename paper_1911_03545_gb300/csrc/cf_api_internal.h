@@ -51,6 +51,10 @@ struct CfRun {
     int64_t nfine = 0;             // ncell_all * sub^3 counting-sort keys
     size_t nslot = 0, hsz = 0;
     bool self_pairs = false;
+    double bbox[6] = {0, 0, 0, 0, 0, 0};   // union of the sets' boxes the plan was made for
+    double vmin2 = 0.0;            // smallest |v|^2 over the points (mocks: the plan's near-observer test)
+    bool angular = false;          // DD(theta) on the angular grid (needs unit vectors)
+    size_t bb_off = 0;             // captured graph: offset of its bbox readback in pinned memory
     std::vector<double> wmin, wmax;   // per point set: smallest nonzero |w| (inf: none), largest |w|
     bool wneg = false;                // some weight is negative
     uint32_t qcap = 0, items_cap = 0;

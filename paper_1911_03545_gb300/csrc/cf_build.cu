@@ -659,6 +659,21 @@ static int blocks_for(int64_t n, int threads, int cap)
     return (int)b;
 }
 
+// the starting values of cf_bbox_kernel's reductions (minima at ~0, maxima and counters at 0)
+__global__ void cf_bbox_init_kernel(unsigned long long *__restrict__ out, int nsets)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nsets * CFB_BBOX_WORDS; i += gridDim.x * blockDim.x) {
+        const int a = i % CFB_BBOX_WORDS;
+        out[i] = (a < 3 || a == 8 || a == 9) ? ~0ull : 0ull;
+    }
+}
+
+cudaError_t cfb_bbox_init(unsigned long long *out, int nsets, cudaStream_t st)
+{
+    cf_bbox_init_kernel<<<blocks_for((int64_t)nsets * CFB_BBOX_WORDS, 256, 64), 256, 0, st>>>(out, nsets);
+    return cudaGetLastError();
+}
+
 cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st)
 {
     dim3 grid(blocks_for(nmax, 256, 1024), nsets);

@@ -8,6 +8,8 @@
 // largest |w|, negative weights
 #define CFB_BBOX_WORDS 12
 cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st);
+// fills out[nsets * CFB_BBOX_WORDS] with the starting values cfb_bbox reduces into
+cudaError_t cfb_bbox_init(unsigned long long *out, int nsets, cudaStream_t st);
 // key = cell * sub^3 + Morton sub-cell (sub = 1, 2, 4): the counting-sort key of every point
 cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
                        uint32_t *count, uint32_t *key, uint32_t *slot, cudaStream_t st);

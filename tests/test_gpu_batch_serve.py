@@ -73,6 +73,46 @@ def test_graph_capture_replay(cf, cats):
         cf.cf_destroy(ctx)
 
 
+def test_replay_checks_that_new_data_fit_the_plan(cf):
+    """A replay re-runs the bounding-box pass.  New data that left the captured box (the plan's grid
+    and FP32 error bands were made for it) are counted afresh without the graph, which is then
+    dropped; data that no call accepts (outside the periodic box, non-finite) are refused."""
+    import torch
+    ctx = cf.cf_create(0, torch.cuda.current_stream())
+    try:
+        kw = dict(autocorr=True, periodic=False, pimax=10.0, npibins=10)
+        p = cf.params(kind="rppi", edges=EDGES, **kw)
+        cs = [gen.batch_catalogue(40 + i, n, L=L, members=20) for i, n in enumerate((1200, 800))]
+        pts = [cf.points(*to_dev(c, "cuda:0", False)) for c in cs]
+        cf.cf_batch_capture(ctx, p, pts)
+        same = cf.cf_batch_replay(ctx, p, 2)
+        assert cf.cf_get_stats(ctx)["ms_build"] == 0          # the graph ran
+        for c, x in zip(cs, same):
+            assert np.array_equal(x["npairs"], oracle.count("rppi", EDGES, c, **kw)["npairs"])
+        big = gen.Catalogue(*(getattr(cs[1], ax) * np.float32(1.5) for ax in "xyz"))
+        for ax, t in zip("xyz", pts[1].keep[:3]):
+            t.copy_(torch.from_numpy(getattr(big, ax)).to(t.device))
+        moved = cf.cf_batch_replay(ctx, p, 2)
+        assert cf.cf_get_stats(ctx)["ms_build"] > 0           # counted afresh
+        for c, x in zip((cs[0], big), moved):
+            assert np.array_equal(x["npairs"], oracle.count("rppi", EDGES, c, **kw)["npairs"])
+        with pytest.raises(cf.CfError):
+            cf.cf_batch_replay(ctx, p, 2)                      # the graph was dropped
+
+        pp = cf.params(kind="rppi", edges=EDGES, autocorr=True, periodic=True, box=L, pimax=10.0, npibins=10)
+        pts = [cf.points(*to_dev(c, "cuda:0", False)) for c in cs]
+        for bad in (L + 5.0, float("nan")):
+            cf.cf_batch_capture(ctx, pp, pts)
+            keep = float(pts[0].keep[0][7])
+            pts[0].keep[0][7] = bad
+            with pytest.raises(cf.CfError) as ei:
+                cf.cf_batch_replay(ctx, pp, 2)
+            assert ei.value.status == -1
+            pts[0].keep[0][7] = keep
+    finally:
+        cf.cf_destroy(ctx)
+
+
 def test_server_alone_equals_mixed(cf, cats):
     p = _params(cf, weighted=True)
     srv = cf.cf_server_start(0, p, 1 << 30, 64)
