@@ -179,7 +179,8 @@ cf_status cf_set_option(void *ctx, int option, int64_t value);
 
 /* Count pairs of one point set (autocorr) or two (cross).  d2 must be NULL for autocorr.
  * Synchronous: returns after the outputs are written.  Sec. 4.1-4.7 (method), Sec. 2.1
- * (result). */
+ * (result).  Limits: fewer than 2^31 points per call; at most 2^32 - 1 work items (i tile x j
+ * range of a cell pair), counted in 64 bits and refused with CF_ERR_ARG beyond. */
 cf_status cf_count(void *ctx, const cf_params *params, const cf_points *d1, const cf_points *d2,
                    cf_result *out);
 

@@ -483,8 +483,11 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     }
     R.cbox = cbox;
     uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
+    // the work list's length in 64 bits, next to its 32-bit scan (checked in cf_finish)
+    unsigned long long *items64 = (unsigned long long *)(misc + 18);
+    CF_CU(cudaMemsetAsync(items64, 0, 8, st), "memset");
     CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, cstart, cbox, R.nunit, 0, icnt, nullptr,
-                    nullptr, 0, nullptr, st),
+                    nullptr, 0, items64, st),
           "items count");
     CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, st), "scan items");
     C->launches += 10;   // assign, 3 scan, cell starts, scatter, items count, 3 scan
@@ -612,12 +615,13 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     }
     C->launches += 2 + (R.items_cap > 0 ? 1 : 0);   // items emit, recheck, pair
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[3], st, C->capturing ? cudaEventRecordExternal : 0), "event");
-    // readback: [cursor, qcount, items total, pad] [evaluated] [hcnt] [hw] [hr] [wsq]
+    // readback: [cursor, qcount, items total, pad] [evaluated] [items total, 64-bit] [hcnt] [hw] [hr] [wsq]
     char *h = (char *)C->hpin;
     const size_t hsz = R.hsz;
     CF_CU(cudaMemcpyAsync(h, misc, 8, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 8, ioff + R.nunit, 4, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 16, evaluated, 8, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 24, misc + 18, 8, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 64, C->buf[B_HCNT].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 64 + 8 * hsz, C->buf[B_HW].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 64 + 16 * hsz, C->buf[B_HR].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
@@ -633,6 +637,9 @@ int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
     const uint32_t qn = ((const uint32_t *)h)[1];
     const uint32_t nitems = ((const uint32_t *)h)[2];
     *retry = 0;
+    // work items are indexed in 32 bits
+    if (*(const unsigned long long *)(h + 24) > 0xFFFFFFFFull)
+        return C->fail(CF_ERR_ARG, "the work list exceeds 2^32 - 1 items (fewer points per call, or a coarser grid)");
     // the audit queues every evaluated pair under a 32-bit count
     if (C->opt[CF_OPT_AUDIT] && *(const unsigned long long *)(h + 16) >= 0xF0000000ull)
         return C->fail(CF_ERR_ARG, "CF_OPT_AUDIT needs fewer than 2^32 - 2^28 evaluated pairs");

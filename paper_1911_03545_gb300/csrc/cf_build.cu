@@ -464,7 +464,9 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
 // +-k per axis, periodic shift per cell pair, auto keeps cj >= ci), a warp prefix sum orders the
 // items of the cell, and an empty i cell costs one load.  i tiles are full (tile points) plus one
 // remainder tile, so a tile wastes at most 31 pair-kernel slots; j ranges split evenly (<= jchunk).
-// mode 0 writes the item count of each (job, cell); mode 1 writes the items at the scanned offsets.
+// mode 0 writes the item count of each (job, cell) and adds the number of items, counted in 64 bits,
+// to *evaluated (the 32-bit scan of the counts would wrap silently past 2^32 items); mode 1 writes
+// the items at the scanned offsets and adds the pairs they hold to *evaluated.
 __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
                                 const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox, int mode,
@@ -589,6 +591,9 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                                     tsj = (nb + ntj - 1) / ntj;
                                 }
                                 cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
+                                if (mode == 0)
+                                    ev += diag ? (unsigned long long)nti * (nti + 1) / 2
+                                               : (unsigned long long)nti * ntj;
                             }
                         }
                     }
@@ -628,7 +633,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
         }
         if (mode == 0 && lane == 0) counts[u] = total;
     }
-    if (mode == 1 && evaluated) {
+    if (evaluated) {
         for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(CF_FULL, ev, o);
         if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evaluated, ev);
     }
