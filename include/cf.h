@@ -149,7 +149,7 @@ const char *cf_last_error(const void *ctx);
  * kernel evaluates to the FP64 recheck instead of binning it in FP32, so the call returns the FP64
  * result of every evaluated pair: equal counts with and without it show that the FP32 path
  * misclassified nothing (the band audit; slow, and CF_ERR_ARG above 2^32 - 2^28 evaluated pairs,
- * which the queue counts in 32 bits); CF_OPT_ITER_LIMIT is reserved and has no
+ * as the queue's entries are indexed in 32 bits); CF_OPT_ITER_LIMIT is reserved and has no
  * effect (no kernel of this library waits on a flag: every device loop is bounded by its data);
  * CF_OPT_WARPS and CF_OPT_REFINE are the autotuner's knobs. */
 typedef enum {
@@ -179,8 +179,9 @@ cf_status cf_set_option(void *ctx, int option, int64_t value);
 
 /* Count pairs of one point set (autocorr) or two (cross).  d2 must be NULL for autocorr.
  * Synchronous: returns after the outputs are written.  Sec. 4.1-4.7 (method), Sec. 2.1
- * (result).  Limits: fewer than 2^31 points per call; at most 2^32 - 1 work items (i tile x j
- * range of a cell pair), counted in 64 bits and refused with CF_ERR_ARG beyond. */
+ * (result).  Limits: fewer than 2^31 points per call; at most 2^32 - 2^20 work items (i tile x
+ * j range of a cell pair) and as many pairs within the FP32 error bands of the edges (the FP64
+ * recheck queue), both counted in 64 bits and refused with CF_ERR_ARG beyond. */
 cf_status cf_count(void *ctx, const cf_params *params, const cf_points *d1, const cf_points *d2,
                    cf_result *out);
 

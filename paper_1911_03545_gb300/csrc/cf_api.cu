@@ -370,7 +370,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_HW, 8 * R.hsz));
     CF_TRY(C->ensure(B_HR, 8 * R.hsz));
     CF_TRY(C->ensure(B_WSQ, 8 * (size_t)nsets));
-    R.qcap = C->opt[CF_OPT_QUEUE] > 0 ? (uint32_t)C->opt[CF_OPT_QUEUE] : C->qcap_default;
+    R.qcap = C->opt[CF_OPT_QUEUE] > 0 ? (uint32_t)std::min<int64_t>(CF_MAX_ENTRIES, C->opt[CF_OPT_QUEUE])
+                                      : C->qcap_default;
     CF_TRY(C->ensure(B_QUEUE, 16 * (size_t)R.qcap));
     CF_TRY(C->ensure_host(readback_bytes(R)));
 
@@ -554,6 +555,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     unsigned long long *evaluated = (unsigned long long *)(misc + 16);
     CF_CU(cudaMemsetAsync(misc, 0, 16, st), "memset");
     CF_CU(cudaMemsetAsync(evaluated, 0, 8, st), "memset");
+    CF_CU(cudaMemsetAsync(misc + 20, 0, 8, st), "memset");     // recheck queue count (64-bit)
     CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, (const uint32_t *)C->buf[B_CSTART].p,
                     R.cbox, R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap,
                     evaluated, st),
@@ -573,7 +575,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     A.items_cap = R.items_cap;
     A.qcap = R.qcap;
     A.cursor = misc;
-    A.qcount = misc + 1;
+    A.qcount = (unsigned long long *)(misc + 20);
     A.pa = (const ulonglong2 *)C->buf[B_PA].p;
     A.pb = (const ulonglong2 *)C->buf[B_PB].p;
     A.plo = (const ulonglong2 *)C->buf[B_PLO].p;
@@ -615,13 +617,15 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     }
     C->launches += 2 + (R.items_cap > 0 ? 1 : 0);   // items emit, recheck, pair
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[3], st, C->capturing ? cudaEventRecordExternal : 0), "event");
-    // readback: [cursor, qcount, items total, pad] [evaluated] [items total, 64-bit] [hcnt] [hw] [hr] [wsq]
+    // readback: [cursor, pad, items total, pad] [evaluated] [items total, 64-bit] [queued pairs, 64-bit]
+    // [hcnt] [hw] [hr] [wsq]
     char *h = (char *)C->hpin;
     const size_t hsz = R.hsz;
     CF_CU(cudaMemcpyAsync(h, misc, 8, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 8, ioff + R.nunit, 4, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 16, evaluated, 8, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 24, misc + 18, 8, cudaMemcpyDeviceToHost, st), "readback");
+    CF_CU(cudaMemcpyAsync(h + 32, misc + 20, 8, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 64, C->buf[B_HCNT].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 64 + 8 * hsz, C->buf[B_HW].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
     CF_CU(cudaMemcpyAsync(h + 64 + 16 * hsz, C->buf[B_HR].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
@@ -634,22 +638,26 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
 int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
 {
     const char *h = (const char *)C->hpin;
-    const uint32_t qn = ((const uint32_t *)h)[1];
+    const unsigned long long qn = *(const unsigned long long *)(h + 32);
     const uint32_t nitems = ((const uint32_t *)h)[2];
     *retry = 0;
-    // work items are indexed in 32 bits
-    if (*(const unsigned long long *)(h + 24) > 0xFFFFFFFFull)
-        return C->fail(CF_ERR_ARG, "the work list exceeds 2^32 - 1 items (fewer points per call, or a coarser grid)");
-    // the audit queues every evaluated pair under a 32-bit count
+    // work items and queue entries are indexed in 32 bits, with headroom for the grid-stride
+    // loops and the work cursor's overshoot
+    if (*(const unsigned long long *)(h + 24) > CF_MAX_ENTRIES)
+        return C->fail(CF_ERR_ARG, "the work list exceeds 2^32 - 2^20 items (fewer points per call, or a coarser grid)");
+    // the audit queues every evaluated pair
     if (C->opt[CF_OPT_AUDIT] && *(const unsigned long long *)(h + 16) >= 0xF0000000ull)
         return C->fail(CF_ERR_ARG, "CF_OPT_AUDIT needs fewer than 2^32 - 2^28 evaluated pairs");
+    if (qn > CF_MAX_ENTRIES)
+        return C->fail(CF_ERR_ARG, "more than 2^32 - 2^20 pairs lie within the FP32 error bands of the edges "
+                                   "(points on a lattice aligned with the edges?)");
     if (nitems > R.items_cap) {
         R.items_cap = nitems;
         *retry = 2;
         return CF_OK;
     }
     if (qn > R.qcap) {
-        R.qcap = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, (uint64_t)qn + qn / 4 + 1024);
+        R.qcap = (uint32_t)std::min<uint64_t>(CF_MAX_ENTRIES, qn + qn / 4 + 1024);
         C->qcap_default = std::max(C->qcap_default, R.qcap);
         *retry = 1;
         return CF_OK;
@@ -905,7 +913,7 @@ cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *
     CfRun &R = C->run;
     R.items_cap = R.items_cap + R.items_cap / 4 + 1024;
     if ((rc = C->ensure(B_ITEMS, sizeof(CfItem) * (size_t)R.items_cap))) return (cf_status)rc;
-    R.qcap = std::max(R.qcap, (uint32_t)(C->stats.rechecked_pairs * 2 + 4096));
+    R.qcap = std::max(R.qcap, (uint32_t)std::min<int64_t>(CF_MAX_ENTRIES, C->stats.rechecked_pairs * 2 + 4096));
     if ((rc = C->ensure(B_QUEUE, 16 * (size_t)R.qcap))) return (cf_status)rc;
     // the graph also re-runs the bbox pass, read back past the results, so that a replay can
     // check that its new data still fit the plan

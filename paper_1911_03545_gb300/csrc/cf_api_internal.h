@@ -36,6 +36,10 @@ struct CfJobResult {
     bool autoc = false;
 };
 
+// most work items and recheck-queue entries of one call: both are indexed in 32 bits, and the
+// grid-stride loops and the work cursor run a few thousand past the end
+constexpr uint64_t CF_MAX_ENTRIES = 0xFFF00000ull;   // 2^32 - 2^20
+
 // State of one call between its phases (kept in the context so a captured graph can be replayed)
 struct CfRun {
     cf_params p;

@@ -50,7 +50,7 @@ struct CfPairArgs {
     double *hw;                  // [njobs][nslot]
     double *hr;                  // [njobs][nslot]
     uint4 *queue;                // (orig i, orig j, job, 0)
-    uint32_t *qcount;
+    unsigned long long *qcount;  // queued pairs, 64-bit so that it cannot wrap (entries >= qcap are dropped)
     float L[3];                  // periodic sides (wrap axes)
     int nb, npi, nslot;
     int ghist;                   // 1: rp-pi / mocks add straight into hcnt/hw/hr (global atomics):
@@ -82,8 +82,8 @@ cudaError_t cfp_launch_pair(const CfPairCfg &c, const CfPairArgs &a, int num_sms
 // CF_OPT_AUDIT: queue every pair of every work item for the FP64 recheck (launched instead of the
 // pair kernel).
 cudaError_t cfp_launch_audit(const CfItem *items, const uint32_t *nitems_dev, uint32_t items_cap,
-                             const uint32_t *orig, uint4 *queue, uint32_t *qcount, uint32_t qcap, int num_sms,
+                             const uint32_t *orig, uint4 *queue, unsigned long long *qcount, uint32_t qcap, int num_sms,
                              cudaStream_t st);
 cudaError_t cfp_launch_recheck(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs,
-                               const uint4 *queue, const uint32_t *qcount, uint32_t qcap,
+                               const uint4 *queue, const unsigned long long *qcount, uint32_t qcap,
                                unsigned long long *hcnt, double *hw, double *hr, int num_sms, cudaStream_t st);

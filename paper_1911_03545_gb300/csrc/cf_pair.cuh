@@ -147,7 +147,7 @@ __device__ __forceinline__ u64 wrap2(u64 d, float L, float invL)
 // queue one pair for the FP64 recheck (rare: kept out of line so the pair loops stay small)
 static __device__ __noinline__ void push_recheck(const CfPairArgs &a, uint32_t ip, uint32_t jp, uint32_t job)
 {
-    uint32_t k = atomicAdd(a.qcount, 1u);
+    const unsigned long long k = atomicAdd(a.qcount, 1ull);
     if (k < a.qcap) a.queue[k] = make_uint4(a.orig[ip], a.orig[jp], job, 0u);
 }
 
@@ -211,7 +211,7 @@ struct Warp {
     const CfFine *fine;
     uint32_t *h_cnt;        // lane-private [nslot][32] or per-warp [nslot]
     float2 *h_w, *h_r;      // lane-private Kahan pairs (interleaved when both are kept)
-    double *h_wd, *h_rd;    // per-warp FP64 (rp-pi)
+    double *h_wd, *h_rd;    // per-warp sums (rp-pi, mocks): FP64, or 64-bit fixed point with FX
     float *jst;             // j stage
     uint32_t *rv, *rz;      // ring: value bits, |dz| bits
     float *rw;              // ring: weight product

@@ -30,11 +30,11 @@ __device__ __forceinline__ int cf_find64(const double *e, int n, double s)
 
 __global__ void cf_recheck_kernel(const CfDevPlan *__restrict__ P, const CfSetDesc *__restrict__ sets,
                                   const CfJobDesc *__restrict__ jobs, const uint4 *__restrict__ queue,
-                                  const uint32_t *__restrict__ qcount, uint32_t qcap,
+                                  const unsigned long long *__restrict__ qcount, uint32_t qcap,
                                   unsigned long long *__restrict__ hcnt, double *__restrict__ hw,
                                   double *__restrict__ hr)
 {
-    const uint32_t n = min(*qcount, qcap);
+    const uint32_t n = (uint32_t)min(*qcount, (unsigned long long)qcap);
     const int kind = P->kind, nb = P->nb, npi = P->npi, nslot = P->nslot;
     const double L0 = P->g.periodic ? P->g.L[0] : 0.0;
     const double L1 = P->g.periodic ? P->g.L[1] : 0.0;
@@ -100,7 +100,7 @@ __global__ void cf_recheck_kernel(const CfDevPlan *__restrict__ P, const CfSetDe
 // call with a larger queue.
 __global__ void cf_audit_kernel(const CfItem *__restrict__ items, const uint32_t *__restrict__ nitems_dev,
                                 uint32_t items_cap, const uint32_t *__restrict__ orig, uint4 *__restrict__ queue,
-                                uint32_t *__restrict__ qcount, uint32_t qcap)
+                                unsigned long long *__restrict__ qcount, uint32_t qcap)
 {
     const uint32_t n = min(*nitems_dev, items_cap);
     const uint32_t lane = threadIdx.x & 31u;
@@ -114,7 +114,7 @@ __global__ void cf_audit_kernel(const CfItem *__restrict__ items, const uint32_t
             const uint32_t j0 = diag ? il + 1u : 0u;      // within a cell paired with itself: j > i
             if (j0 >= jc) continue;
             const uint32_t cnt = jc - j0;
-            const uint32_t base = atomicAdd(qcount, cnt);
+            const unsigned long long base = atomicAdd(qcount, (unsigned long long)cnt);
             const uint32_t oi = orig[it.ibeg + il];
             for (uint32_t k = 0; k < cnt; k++)
                 if (base + k < qcap) queue[base + k] = make_uint4(oi, orig[it.jbeg + j0 + k], jo, 0u);
@@ -123,7 +123,7 @@ __global__ void cf_audit_kernel(const CfItem *__restrict__ items, const uint32_t
 }
 
 cudaError_t cfp_launch_audit(const CfItem *items, const uint32_t *nitems_dev, uint32_t items_cap,
-                             const uint32_t *orig, uint4 *queue, uint32_t *qcount, uint32_t qcap, int num_sms,
+                             const uint32_t *orig, uint4 *queue, unsigned long long *qcount, uint32_t qcap, int num_sms,
                              cudaStream_t st)
 {
     cf_audit_kernel<<<num_sms * 4, 256, 0, st>>>(items, nitems_dev, items_cap, orig, queue, qcount, qcap);
@@ -131,7 +131,7 @@ cudaError_t cfp_launch_audit(const CfItem *items, const uint32_t *nitems_dev, ui
 }
 
 cudaError_t cfp_launch_recheck(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs,
-                               const uint4 *queue, const uint32_t *qcount, uint32_t qcap,
+                               const uint4 *queue, const unsigned long long *qcount, uint32_t qcap,
                                unsigned long long *hcnt, double *hw, double *hr, int num_sms, cudaStream_t st)
 {
     cf_recheck_kernel<<<num_sms * 2, 256, 0, st>>>(plan, sets, jobs, queue, qcount, qcap, hcnt, hw, hr);

@@ -212,6 +212,27 @@ def test_host_inputs_equal_device_inputs(ctx):
     np.testing.assert_allclose(a["wsum"], b["wsum"], rtol=TOL)
 
 
+def test_lattice_on_the_edges(ctx):
+    """A 40^3 integer lattice in a periodic box with integer edges: about an eighth of the pairs
+    in range lie exactly on an edge (lattice vectors of integer length: axes, (2,2,1), (4,3,0),
+    (4,4,2)), so millions of pairs go to the FP64 recheck.  With the queue started at 4096 entries
+    it must grow; counts and sums still equal the oracle's."""
+    import paper_1911_03545_gb300 as cf
+    g = np.arange(40, dtype=np.float32)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    d = gen.Catalogue(X.ravel(), Y.ravel(), Z.ravel(), gen.uniform_weights(X.size, 0.5, 1.5, 71))
+    edges = np.arange(1.0, 7.0)
+    kw = dict(autocorr=True, periodic=True, box=40.0, weighted=True, ravg=True)
+    cf.cf_set_option(ctx, cf.CF_OPT_QUEUE, 4096)
+    try:
+        got = gpu_count(ctx, "r", edges, d, **kw)
+        st = cf.cf_get_stats(ctx)
+    finally:
+        cf.cf_set_option(ctx, cf.CF_OPT_QUEUE, 0)
+    assert st["rechecked_pairs"] > 1_000_000
+    assert_match(got, oracle.count("r", edges, d, **kw), True, True)
+
+
 def test_options_do_not_change_results(ctx):
     import paper_1911_03545_gb300 as cf
     d = _catalogue("r", 60, 41)
