@@ -43,6 +43,8 @@ WORKLOADS = {
     "uniform_r_20k": "DD(r) auto, periodic L=250, N=20,000 uniform float64, 20 log bins 0.1-25",
     "clustered_rppi_2m": "DD(rp,pi) auto, periodic L=1000, N=2,000,000 clustered float32 (20,000 x 100, "
                          "sigma=2), 14 log rp bins 0.1-25, pimax=40 with 40 pi bins",
+    "clustered_rppi_2m_wr": "DD(rp,pi) auto, the clustered_rppi_2m catalogue with pair-product weights U[0.5,1.5) "
+                            "+ ravg",
     "clustered_wp_2m": "wp(rp) auto, periodic L=1000, N=2,000,000 clustered float32, 14 log rp bins 0.1-25, pimax=40",
     "clustered_rppi_dr": "DR(rp,pi) cross, periodic L=1000, D=2,000,000 clustered x R=4,000,000 uniform float32, "
                          "14 log rp bins 0.1-25, pimax=40 with 40 pi bins",

@@ -173,11 +173,16 @@ def workload(name: str, scale: float = 1.0) -> Workload:
         d.w = uniform_weights(d.n, 0.5, 1.5, 1002)
         return Workload(name, "r", True, True, L, log_edges(0.1, 20.0, 20), d,
                         weighted=True, ravg=True)
-    if name in ("clustered_rppi_2m", "clustered_wp_2m", "clustered_rppi_dr"):
+    if name in ("clustered_rppi_2m", "clustered_wp_2m", "clustered_rppi_dr", "clustered_rppi_2m_wr"):
         nc = max(1, int(20000 * scale))
         L = 1000.0 * (nc / 20000) ** (1.0 / 3.0) if scale != 1.0 else 1000.0
         d = clustered_box(nc, 100, 2.0, L, 1003)
         kind = "wp" if name == "clustered_wp_2m" else "rppi"
+        if name == "clustered_rppi_2m_wr":
+            # the same catalogue with pair-product weights and ravg
+            d.w = uniform_weights(d.n, 0.5, 1.5, 1009)
+            return Workload(name, "rppi", True, True, L, log_edges(0.1, 25.0, 14), d,
+                            pimax=40.0, npibins=40, weighted=True, ravg=True)
         if name == "clustered_rppi_dr":
             rn = max(8, int(4000000 * scale))
             rr = uniform_box(rn, L, 1004)

@@ -78,7 +78,7 @@ def make(name: str) -> dict:
 def main(names):
     if not names:
         names = ["clustered_r_1m", "sphere_theta_1m", "clustered_rppi_2m", "clustered_wp_2m"] + batch_names() + \
-                ["clustered_rppi_dr", "mock_dr_rppi"]
+                ["clustered_rppi_dr", "mock_dr_rppi", "clustered_rppi_2m_wr"]
     for name in names:
         path = os.path.join(HERE, f"full_{name}.json")
         rec = make(name)

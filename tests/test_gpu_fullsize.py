@@ -47,6 +47,8 @@ def test_full_size_against_oracle(ctx, name):
         return cf.points(*t[:3], t[3] if wl.weighted else None)
 
     got = cf.cf_count(ctx, p, pts(wl.d1), None if wl.autocorr else pts(wl.d2))
+    if name == "clustered_rppi_2m_wr":
+        assert cf.cf_get_stats(ctx)["fixed_sums"] == 3     # weights in [0.5, 1.5): fixed-point sums
     n = np.asarray(got["npairs"]).ravel().astype(np.uint64)
     e = np.asarray(gold["npairs"], dtype=np.uint64)
     assert np.array_equal(n, e), np.argwhere(n != e)[:10]
@@ -56,7 +58,7 @@ def test_full_size_against_oracle(ctx, name):
         np.testing.assert_allclose(np.asarray(got["ravg"]).ravel(), gold["ravg"], rtol=TOL, atol=0)
 
 
-TUNED = ["clustered_r_1m", "clustered_rppi_2m", "sphere_theta_1m", "mock_dr_rppi"]
+TUNED = ["clustered_r_1m", "clustered_rppi_2m", "sphere_theta_1m", "mock_dr_rppi", "clustered_rppi_2m_wr"]
 
 
 @pytest.mark.parametrize("name", [n for n in TUNED if n in NAMES])
