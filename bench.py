@@ -418,11 +418,19 @@ BATCH_DESC = ("256 mock catalogues, periodic L=250, N log-uniform in [5e4, 8e5] 
               "sigma=1, DD(rp,pi) auto, 14 log rp bins 0.1-20, pimax=40 with 40 pi bins, float32")
 
 
-def _batch_setup(ncat):
+def _batch_setup(ncat, lo=5e4, hi=8e5):
     import gen
-    sizes = gen.batch_sizes()[:ncat]
+    # the first 256 sizes of a range are the same for any ncat (one seeded sequence)
+    sizes = gen.batch_sizes(max(256, ncat), lo, hi)[:ncat]
     cats = [gen.batch_catalogue(i, n) for i, n in enumerate(sizes)]
     return sizes, cats
+
+
+def _batch_desc(args, sizes):
+    if args.ncat == 256 and (args.batch_min, args.batch_max) == (5e4, 8e5):
+        return BATCH_DESC
+    return BATCH_DESC.replace("256", str(args.ncat)).replace(
+        "[5e4, 8e5] (sum 6.9e7)", f"[{args.batch_min:g}, {args.batch_max:g}] (sum {sum(sizes):.2g})")
 
 
 def _batch_params(cf):
@@ -443,7 +451,7 @@ def run_batch(args, world, rank, local):
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    sizes, cats = _batch_setup(args.ncat)
+    sizes, cats = _batch_setup(args.ncat, args.batch_min, args.batch_max)
     p = _batch_params(cf)
     pts = [_points(c, False, cf, dev) for c in cats]
     ctx = cf.cf_create(local, stream)
@@ -486,8 +494,8 @@ def run_batch(args, world, rank, local):
         "metric": "batched catalogues/s", "value": len(pts) / best, "unit": "catalogues/s", "n_gpus": 1,
         "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * best, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": BATCH_DESC if args.ncat == 256 else BATCH_DESC.replace("256", str(args.ncat)),
-                   "name": "batch", "ncat": len(pts), "points": int(sum(sizes)), "tuned": tuned},
+        "config": {"workload": _batch_desc(args, sizes), "name": "batch", "ncat": len(pts), "points": int(sum(sizes)),
+                   "tuned": tuned},
         "one_at_a_time": {"value": len(pts) / t_single, "unit": "catalogues/s", "seconds": t_single},
         "batched": {"value": len(pts) / t_batch, "seconds": t_batch},
         "graph_replay": {"value": len(pts) / t_graph, "seconds": t_graph},
@@ -675,6 +683,8 @@ def main(argv=None):
     ap.add_argument("--config", default="", help="pin the launch configuration instead of tuning, "
                     "e.g. variant=2,warps=8 (knobs of paper_1911_03545_gb300.tune)")
     ap.add_argument("--ncat", type=int, default=256)
+    ap.add_argument("--batch-min", type=float, default=5e4, help="smallest catalogue of the batch workload")
+    ap.add_argument("--batch-max", type=float, default=8e5, help="largest catalogue of the batch workload")
     ap.add_argument("--sweep-reps", type=int, default=3)
     ap.add_argument("--serve-load", type=float, default=0.8)
     ap.add_argument("--serve-requests", type=int, default=1024)
