@@ -414,7 +414,7 @@ def run_gpu(args, wl, world, rank, local):
 # batched and served forms (256 mock catalogues)
 # ---------------------------------------------------------------------------------------------
 
-BATCH_DESC = ("256 mock catalogues, periodic L=250, N log-uniform in [5e4, 8e5] (sum 6.9e7), 50-member clusters "
+BATCH_DESC = ("256 mock catalogues, periodic L=250, N log-uniform in [5e4, 8e5] (sum 7.4e7), 50-member clusters "
               "sigma=1, DD(rp,pi) auto, 14 log rp bins 0.1-20, pimax=40 with 40 pi bins, float32")
 
 
@@ -430,7 +430,7 @@ def _batch_desc(args, sizes):
     if args.ncat == 256 and (args.batch_min, args.batch_max) == (5e4, 8e5):
         return BATCH_DESC
     return BATCH_DESC.replace("256", str(args.ncat)).replace(
-        "[5e4, 8e5] (sum 6.9e7)", f"[{args.batch_min:g}, {args.batch_max:g}] (sum {sum(sizes):.2g})")
+        "[5e4, 8e5] (sum 7.4e7)", f"[{args.batch_min:g}, {args.batch_max:g}] (sum {sum(sizes):.2g})")
 
 
 def _batch_params(cf):
