@@ -130,7 +130,7 @@ typedef struct {
     float ms_total;            /* whole call, host wall clock */
     int kernel_launches;       /* CUDA kernels this library launched for the call */
     int fixed_sums;            /* rp-pi / mocks: bit 0 weight sums, bit 1 ravg sums kept per warp in
-                                  64-bit fixed point (each term within 2^-23 of itself); else FP64 */
+                                  fixed point (each term within 2^-22 of itself); else FP64 */
 } cf_stats;
 
 /* Create a context on `device` (its current-device state is restored on return), issuing all

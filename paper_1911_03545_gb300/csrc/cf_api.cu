@@ -406,6 +406,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.cfg.nlut_words = D.nlut_words;
     R.cfg.nfine = D.nfine;
     R.cfg.nslot = D.nslot;
+    R.cfg.nb = D.nb;
     R.cfg.warps = (int)C->opt[CF_OPT_WARPS];
     R.cfg.ctas_per_sm = (int)C->opt[CF_OPT_CTAS_PER_SM];
     // the mocks kind has the direct form only (a compacting form measured slower)
@@ -495,29 +496,29 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     return CF_OK;
 }
 
-// Power-of-two scale for fixed-point sums of terms in [tmin, tmax] (tmin > 0): tmax * scale < 2^35,
-// so that 2^28 terms (the most a warp holds between flushes) stay below 2^63, and tmin * scale >=
-// 2^22, so that rounding a term to an integer moves it by at most 2^-23 of itself.  0 (FP64 sums)
-// when no such scale exists or the terms are not normal float32 values.
+// Power-of-two scale for the fixed-point sums of terms in [tmin, tmax] (tmin > 0): tmax * scale <
+// 2^26, with 1/1024 of margin for the terms' FP32 rounding, so that the two 32-bit words a slot keeps
+// stay exact for 2^18 terms between flushes, and tmin * scale >= 2^21, so that rounding a term to an
+// integer moves it by at most 2^-22 of itself.  0 (FP64 sums) when no such scale exists.
 static float fixed_scale(double tmin, double tmax)
 {
     if (!(tmin > 1e-30) || !(tmax >= tmin) || !(tmax < 1e30)) return 0.f;
     int ex = 0;
-    std::frexp(tmax * (1.0 + 1.0 / 1024.0), &ex);   // the largest term, with margin for its FP32
-                                                    // rounding, is below 2^ex
-    const double s = std::ldexp(1.0, 35 - ex);
-    return tmin * s >= 4194304.0 ? (float)s : 0.f;
+    std::frexp(tmax * (1.0 + 1.0 / 1024.0), &ex);   // the largest term, with margin, is below 2^ex
+    const double s = std::ldexp(1.0, 26 - ex);
+    return tmin * s >= 2097152.0 ? (float)s : 0.f;
 }
 
 // Scales of the per-warp weight and ravg sums of rp-pi / mocks.  A term is w_i w_j (weights), rp
 // (ravg) or w_i w_j rp (both).  Weight products lie between the products of the sets' smallest
-// nonzero and largest |w| (zero products are exact); rp between the first and the last edge.
-// Negative weights (sums that may cancel) and, with ravg, a first edge of 0 keep FP64 for every
-// sum of the call.
+// nonzero and largest |w| (zero products are exact); the rp of a pair in rp bin k lies within 1e-5
+// of [e_k, e_k+1] (its FP32 value may sit a few roundings outside), so each rp bin's ravg sum has a
+// scale of its own.  Negative weights (sums that may cancel) and, with ravg, a first edge of 0 keep
+// FP64 for every sum of the call.
 static void fixed_point_scales(const CfRun &R, bool weighted, bool ravg, CfPairArgs &A)
 {
     A.fxw = A.fxr = 0.f;
-    A.ifxw = A.ifxr = 0.0;
+    A.ifxw = 0.0;
     double pmin = 1.0, pmax = 1.0;
     if (weighted) {
         if (R.wneg) return;
@@ -531,15 +532,17 @@ static void fixed_point_scales(const CfRun &R, bool weighted, bool ravg, CfPairA
         if (!std::isfinite(pmin)) pmin = pmax = 1.0;   // every product is 0
         A.fxw = fixed_scale(pmin, pmax);
     }
+    bool rok = true;
     if (ravg) {
-        const double e0 = R.edges.front(), e1 = R.edges.back();
-        // an FP32 rp of a pair in the first bin may sit a few roundings below its edge
-        A.fxr = fixed_scale(e0 * (1.0 - 1e-5) * pmin, e1 * pmax);
+        for (int k = 0; k + 1 < (int)R.edges.size(); k++) {
+            A.fxr_bin[k] = fixed_scale(R.edges[k] * (1.0 - 1e-5) * pmin, R.edges[k + 1] * (1.0 + 1e-5) * pmax);
+            rok = rok && A.fxr_bin[k] != 0.f;
+        }
+        A.fxr = rok ? 1.f : 0.f;
     }
     // one form for every sum the call keeps: fixed point only where all of them allow it
     if ((weighted && A.fxw == 0.f) || (ravg && A.fxr == 0.f)) A.fxw = A.fxr = 0.f;
     if (A.fxw != 0.f) A.ifxw = 1.0 / (double)A.fxw;
-    if (A.fxr != 0.f) A.ifxr = 1.0 / (double)A.fxr;
 }
 
 // work items -> pair kernel -> recheck -> readback (device only; records ev[1..3] when `timed`)
@@ -594,7 +597,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     if (per_warp && !R.cfg.ghist && cfp_pair_smem(R.cfg, 1) > (size_t)C->smem_optin) R.cfg.ghist = 1;
     if (R.cfg.ghist) R.cfg.variant = 1;       // that form is built direct only
     A.ghist = R.cfg.ghist;
-    // their per-warp sums go to 64-bit fixed point when the terms' range allows it; never in a
+    // their per-warp sums go to fixed point when the terms' range allows it; never in a
     // captured graph, whose replays bring new weights
     if (per_warp && !A.ghist && !C->capturing) fixed_point_scales(R, D.weighted != 0, R.cfg.ravg != 0, A);
     if (A.fxw != 0.f || A.fxr != 0.f) R.cfg.variant = 1;    // built direct only

@@ -55,9 +55,11 @@ struct CfPairArgs {
     int nb, npi, nslot;
     int ghist;                   // 1: rp-pi / mocks add straight into hcnt/hw/hr (global atomics):
                                  // their per-warp histogram does not fit in shared memory
-    float fxw, fxr;              // rp-pi / mocks per-warp weight / ravg sums: 64-bit fixed point at
-                                 // this power-of-two scale (0: FP64)
-    double ifxw, ifxr;           // 1 / fxw, 1 / fxr
+    float fxw;                   // rp-pi / mocks per-warp weight sums in fixed point (two 32-bit words
+                                 // per slot, see cf_pair.cuh) at this power-of-two scale (0: FP64)
+    float fxr;                   // nonzero: the ravg sums too, those of rp bin k at scale fxr_bin[k]
+    double ifxw;                 // 1 / fxw
+    float fxr_bin[CF_MAX_BINS];
 };
 
 // Static configuration of a pair-kernel launch (selects the template instance and the shared
@@ -67,6 +69,7 @@ struct CfPairCfg {
     int weighted, ravg, wrap, lo;
     int ghist;         // see CfPairArgs::ghist (no per-warp histogram in shared memory)
     int nlut_words, nfine, nslot;
+    int nb;            // r / rp / theta bins
     int warps;         // warps per CTA (0: automatic)
     int ctas_per_sm;   // 0: occupancy-derived
     int variant;       // 1 direct binning, 2 compacting ring (resolved from 0 by the caller)

@@ -27,9 +27,16 @@
 // Histograms live in shared memory per warp (Sec. 4.8: private histograms, merged once): for
 // r / theta / wp one private copy per lane (no bank conflicts, no contention; weighted sums
 // Kahan-compensated in FP32), for rp-pi one copy per warp updated by shared atomics (weight and
-// ravg sums in 64-bit fixed point where the host found a scale for the terms' range, else FP64).
-// They are merged into the global histogram when a warp moves to another job, after every 2^28
-// evaluated pairs, and at exit.
+// ravg sums in fixed point where the host found scales for the terms' range, else FP64).  They are
+// merged into the global histogram when a warp moves to another job, after every 2^28 evaluated
+// pairs (2^18 with fixed-point sums), and at exit.
+//
+// The fixed-point sums use 32-bit shared atomics only (64-bit shared atomics are several times
+// slower): a term t adds m = round(t * S) (S a power of two the host chose so that every term of
+// the sum lies in [2^21, 2^26) units, so that rounding moves a term by at most 2^-22 of itself) to
+// two 32-bit words of its slot, m modulo 2^32 and m >> 12.  A warp flushes before its slots can
+// hold 2^18 terms: the second word then stays below 2^32 and places the true sum within 2^30 below
+// its value times 2^12, and the first word gives the sum exactly (fx_sum).
 #pragma once
 #include "cf_build.h"
 #include "cf_device.cuh"
@@ -50,6 +57,17 @@ __host__ __device__ __forceinline__ uint32_t align16(uint32_t x) { return (x + 1
 // a warp flushes its histograms once it has evaluated more than this many pairs of one job;
 // with the item in hand that keeps every flushed batch at <= 2^28 pairs (an item: <= 2^16)
 constexpr uint32_t CF_FLUSH_PAIRS = (1u << 28) - (1u << 16);
+// with fixed-point sums: fewer than 2^18 terms per slot between flushes
+constexpr uint32_t FX_FLUSH_PAIRS = (1u << 18) - (1u << 16);
+constexpr uint32_t FX_HI_SHIFT = 12;
+
+// True sum of the fixed-point terms of a slot from its two words: lo = the sum modulo 2^32, hi = the
+// sum of (m >> 12).  For fewer than 2^18 terms below 2^26, hi * 2^12 lies in (T - 2^30, T].
+__device__ __forceinline__ unsigned long long fx_sum(uint32_t lo, uint32_t hi)
+{
+    const unsigned long long c = (unsigned long long)hi << FX_HI_SHIFT;
+    return c + (uint32_t)(lo - (uint32_t)c);
+}
 constexpr uint32_t JSTAGE = 32;
 constexpr uint32_t RING = 512;
 constexpr uint32_t RM = RING - 1;
@@ -203,7 +221,7 @@ static __device__ __noinline__ float mocks_rp(const CfPairArgs &a, uint32_t ip, 
 
 // GH (rp-pi and mocks only): no per-warp histogram; every pair adds straight into the job's global
 // histogram (CfPairArgs::ghist).  FX (rp-pi and mocks, per-warp histogram): the weight and ravg sums
-// are 64-bit fixed point at the scales CfPairArgs::fxw / fxr, else FP64.
+// are fixed point (two 32-bit words per slot) at the scales CfPairArgs::fxw / fxr_bin, else FP64.
 template <int KIND, bool W, bool R, bool WRAP, bool LO, bool GH, bool FX>
 struct Warp {
     const CfPairArgs &a;
@@ -211,7 +229,9 @@ struct Warp {
     const CfFine *fine;
     uint32_t *h_cnt;        // lane-private [nslot][32] or per-warp [nslot]
     float2 *h_w, *h_r;      // lane-private Kahan pairs (interleaved when both are kept)
-    double *h_wd, *h_rd;    // per-warp sums (rp-pi, mocks): FP64, or 64-bit fixed point with FX
+    double *h_wd, *h_rd;    // per-warp sums (rp-pi, mocks): FP64, or with FX two 32-bit words per slot
+                            // (nslot low words, then nslot high words)
+    const float *fxr_bin;   // with FX and ravg: the scale of each rp bin's ravg terms (shared memory)
     float *jst;             // j stage
     uint32_t *rv, *rz;      // ring: value bits, |dz| bits
     float *rw;              // ring: weight product
@@ -249,7 +269,7 @@ struct Warp {
         }
     }
 
-    __device__ __forceinline__ void acc_sh(uint32_t slot, float rp2, float wp)
+    __device__ __forceinline__ void acc_sh(uint32_t slot, uint32_t rbin, float rp2, float wp)
     {
         if (GH) {
             // no per-warp histogram: straight into the job's global one
@@ -266,18 +286,22 @@ struct Warp {
         if (W) add_sum(h_wd, slot, wp, a.fxw);
         if (R) {
             float r = f_sqrt_approx(rp2);
-            add_sum(h_rd, slot, W ? wp * r : r, a.fxr);
+            add_sum(h_rd, slot, W ? wp * r : r, FX ? fxr_bin[rbin] : 0.f);
         }
     }
 
-    // One term of a per-warp sum: with FX a 64-bit integer add of round(t * scale) (the scale is a
-    // power of two, so t * scale is exact; the host chose it so that every term is at least 2^22
-    // units, its rounding within 2^-23 of it, and flushes every 2^28 pairs keep the sum below
-    // 2^63), else an FP64 add.
-    static __device__ __forceinline__ void add_sum(double *h, uint32_t slot, float t, float scale)
+    // One term of a per-warp sum: with FX m = round(t * scale) into the slot's two 32-bit words (m
+    // and m >> 12; the scale is a power of two, so t * scale is exact), else an FP64 add.
+    __device__ __forceinline__ void add_sum(double *h, uint32_t slot, float t, float scale) const
     {
-        if (FX) atomicAdd(reinterpret_cast<unsigned long long *>(h) + slot, __float2ull_rn(t * scale));
-        else atomicAdd(h + slot, (double)t);
+        if (FX) {
+            uint32_t *w = reinterpret_cast<uint32_t *>(h);
+            const uint32_t m = __float2uint_rn(t * scale);
+            atomicAdd(w + slot, m);
+            atomicAdd(w + nslot + slot, m >> FX_HI_SHIFT);
+        } else {
+            atomicAdd(h + slot, (double)t);
+        }
     }
 
     // Histogram slot of N pairs that passed the FP32 cut (squared separation below cut_r and,
@@ -285,7 +309,8 @@ struct Warp {
     // every bin).  The table reads of all N are issued before any fine resolution.
     static constexpr uint32_t K_AMB = 0xFFFFFFFFu, K_OUT = 0xFFFFFFFEu;
     template <int N>
-    __device__ __forceinline__ void classify(const uint32_t (&vb)[N], const uint32_t (&zb)[N], uint32_t (&k)[N]) const
+    __device__ __forceinline__ void classify(const uint32_t (&vb)[N], const uint32_t (&zb)[N], uint32_t (&k)[N],
+                                             uint32_t (&kr)[N]) const
     {
         uint32_t cr[N], cz[N];
 #pragma unroll
@@ -304,13 +329,14 @@ struct Warp {
                 if (max(cr[n], cz[n]) < CFI_CLS_OUT) k[n] = KIND == KIND_RPPI ? cr[n] * npi + cz[n] : cr[n];
                 else k[n] = cr[n] != CFI_CLS_OUT ? K_AMB : K_OUT;
             }
+            kr[n] = cr[n];
         }
     }
 
-    __device__ __forceinline__ void finish(uint32_t k, uint32_t vb, float wp, uint32_t il, uint32_t j)
+    __device__ __forceinline__ void finish(uint32_t k, uint32_t kr, uint32_t vb, float wp, uint32_t il, uint32_t j)
     {
         if (k < K_OUT) {
-            if (warp_hist(KIND)) acc_sh(k, __uint_as_float(vb), wp);
+            if (warp_hist(KIND)) acc_sh(k, kr, __uint_as_float(vb), wp);
             else acc_lp(k, __uint_as_float(vb), wp);
         } else if (k == K_AMB) {
             push(ibeg + il, jbeg + j);
@@ -320,9 +346,9 @@ struct Warp {
     __device__ __forceinline__ void bin_in(uint32_t vb, uint32_t zb, float wp, uint32_t il, uint32_t j)
     {
         const uint32_t v[1] = {vb}, z[1] = {zb};
-        uint32_t k[1];
-        classify<1>(v, z, k);
-        finish(k[0], vb, wp, il, j);
+        uint32_t k[1], kr[1];
+        classify<1>(v, z, k, kr);
+        finish(k[0], kr[0], vb, wp, il, j);
     }
 
     // bin the ring's candidates with every lane busy: two per lane while 64 are queued, then
@@ -336,10 +362,10 @@ struct Warp {
             const uint32_t z[2] = {has_z(KIND) ? rz[e0] : 0u, has_z(KIND) ? rz[e1] : 0u};
             const uint32_t c0 = rc[e0], c1 = rc[e1];
             const float w0 = W ? rw[e0] : 0.f, w1 = W ? rw[e1] : 0.f;
-            uint32_t k[2];
-            classify<2>(v, z, k);
-            finish(k[0], v[0], w0, c0 & 0x7Fu, c0 >> 7);
-            finish(k[1], v[1], w1, c1 & 0x7Fu, c1 >> 7);
+            uint32_t k[2], kr[2];
+            classify<2>(v, z, k, kr);
+            finish(k[0], kr[0], v[0], w0, c0 & 0x7Fu, c0 >> 7);
+            finish(k[1], kr[1], v[1], w1, c1 & 0x7Fu, c1 >> 7);
             head += 64u;
         }
         for (;;) {
@@ -630,7 +656,7 @@ struct Warp {
             const float *bs = jst + ((j / JSTAGE) & 1u) * NA * JSTAGE;
             const float rr = mocks_rp<LO>(a, ibeg + il, bs, j % JSTAGE, ish[0], ish[1], ish[2], isl[0], isl[1],
                                           isl[2]);
-            add_sum(h_rd, slot, W ? wp * rr : rr, a.fxr);
+            add_sum(h_rd, slot, W ? wp * rr : rr, FX ? fxr_bin[cr] : 0.f);
         }
     }
 
@@ -795,12 +821,24 @@ struct Warp {
                 c = h_cnt[sl];
                 h_cnt[sl] = 0;
                 if (W) {
-                    ws = FX ? (double)reinterpret_cast<unsigned long long *>(h_wd)[sl] * a.ifxw : h_wd[sl];
-                    h_wd[sl] = 0.0;
+                    if (FX) {
+                        uint32_t *w = reinterpret_cast<uint32_t *>(h_wd);
+                        ws = (double)fx_sum(w[sl], w[nslot + sl]) * a.ifxw;
+                        w[sl] = w[nslot + sl] = 0u;
+                    } else {
+                        ws = h_wd[sl];
+                        h_wd[sl] = 0.0;
+                    }
                 }
                 if (R) {
-                    rs = FX ? (double)reinterpret_cast<unsigned long long *>(h_rd)[sl] * a.ifxr : h_rd[sl];
-                    h_rd[sl] = 0.0;
+                    if (FX) {
+                        uint32_t *w = reinterpret_cast<uint32_t *>(h_rd);
+                        rs = (double)fx_sum(w[sl], w[nslot + sl]) / (double)fxr_bin[sl / npi];
+                        w[sl] = w[nslot + sl] = 0u;
+                    } else {
+                        rs = h_rd[sl];
+                        h_rd[sl] = 0.0;
+                    }
                 }
             } else {
                 constexpr int ST = (W && R) ? 2 : 1;     // float2 stride of the Kahan sums
@@ -843,9 +881,12 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     const int nlw = P->nlut_words, nf = P->nfine;
     uint16_t *s_lut = (uint16_t *)smem;
     CfFine *s_fine = (CfFine *)(smem + align16(2u * nlw));
-    unsigned char *wbase = (unsigned char *)(s_fine + nf);
+    float *s_fxr = (float *)(s_fine + nf);      // rp-pi / mocks: per rp bin scale of the ravg terms
+    unsigned char *wbase = (unsigned char *)s_fxr + (warp_hist(KIND) ? align16(4u * (uint32_t)a.nb) : 0u);
     for (int i = threadIdx.x; i < nlw; i += blockDim.x) s_lut[i] = a.lut[i];
     for (int i = threadIdx.x; i < nf; i += blockDim.x) s_fine[i] = a.fine[i];
+    if (FX && R)
+        for (int i = threadIdx.x; i < a.nb; i += blockDim.x) s_fxr[i] = a.fxr_bin[i];
     const int hslots = GH ? 0 : a.nslot;        // slots of the per-warp histogram
     const uint32_t wb = warp_bytes(KIND, W, R, LO, hslots, COMPACT);
     const uint32_t hoff = warp_jbuf_bytes(W, LO) + (COMPACT ? warp_ring_bytes(KIND, W) : 0u);
@@ -864,6 +905,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     w.npi = a.npi;
     w.nslot = a.nslot;
     w.fine = s_fine;
+    w.fxr_bin = s_fxr;
     w.lr = {P->lr.base, P->lr.shift, P->lr.last, s_lut + P->lr.coff};
     w.lp = {P->lp.base, P->lp.shift, P->lp.last, s_lut + P->lp.coff};
     w.cut_r = P->cut_r;
@@ -920,7 +962,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
         CfItem nx;
         if (tn < nitems) nx = a.items[tn];
         const int job = (int)(it.meta & CFI_ITEM_JOBMASK);
-        if (job != cur || pend > CF_FLUSH_PAIRS) {
+        if (job != cur || pend > (FX ? FX_FLUSH_PAIRS : CF_FLUSH_PAIRS)) {
             if (cur >= 0) w.flush((uint32_t)cur);
             cur = job;
             pend = 0;

@@ -148,6 +148,7 @@ cudaError_t cfp_launch_mocks(const CfPairCfg &, const CfPairArgs &, int, cudaStr
 size_t cfp_pair_smem(const CfPairCfg &c, int warps)
 {
     size_t b = cfpair::align16(2u * (uint32_t)c.nlut_words) + (size_t)c.nfine * 16;
+    if (cfpair::warp_hist(c.kind)) b += cfpair::align16(4u * (uint32_t)c.nb);   // per rp bin ravg scales
     return b + (size_t)cfpair::warp_bytes(c.kind, c.weighted != 0, c.ravg != 0, c.lo != 0, c.ghist ? 0 : c.nslot,
                                           c.variant == 2) * warps;
 }

@@ -1,6 +1,6 @@
-"""How the pair kernel holds its sums: per-warp 64-bit fixed point for rp-pi and mocks where the
-terms' range allows it, FP64 otherwise, and flushes bounded in pairs so that no 32-bit count a
-warp holds can wrap.
+"""How the pair kernel holds its sums: per-warp fixed point (two 32-bit words per slot) for rp-pi
+and mocks where the terms' range allows it, FP64 otherwise, and flushes bounded in pairs so that
+no 32-bit count or fixed-point word a warp holds can wrap.
 
 Each case checks which form ran (cf_stats.fixed_sums) and compares with the FP64 oracle: counts
 bit-exact, sums within 1e-6 relative (negative weights: within 1e-6 of the sum of |terms|, the
