@@ -56,6 +56,28 @@ def check_hand_pairs(lib):
         assert np.array_equal(got, want), ((a, b, c, d), got.tolist())
 
 
+def check_hand_ravg(lib):
+    """ravg of the mocks is the mean of rp = sqrt(s.s - pi^2) (Appendix A.2.1, Sec. 6.5): for the
+    hand pairs rp = 2 sqrt(a^2 + b^2) exactly, so their ravg is that value; weighted, two pairs in
+    one slot average by their weights."""
+    for (a, b, c, d), expect in HAND:
+        if expect is None:
+            continue
+        out = _mocks(lib, _cat([(a, b, c), (-a, -b, d)]), mode="brute", ravg=True)
+        want = np.zeros((len(EDGES) - 1, NPI))
+        want[expect] = 2.0 * np.sqrt(a * a + b * b)
+        np.testing.assert_allclose(out["ravg"], want, rtol=1e-15, atol=0)
+    # slot (1, 1): P1 rp 1.5 pi 1.5 with weights 1, 2; P2 rp sqrt(2) pi 1.25 with weights 4, 2.
+    # Pairs across P1 and P2 are 12 apart along the line of sight (pi > pimax).
+    pts = [(0.0, 0.75, 8.0), (0.0, -0.75, 6.5), (0.5, 0.5, 20.0), (-0.5, -0.5, 18.75)]
+    out = _mocks(lib, _cat(pts, [1.0, 2.0, 4.0, 2.0]), mode="brute", ravg=True, weighted=True)
+    assert out["npairs"][1, 1] == 4 and int(out["npairs"].sum()) == 4
+    assert out["wsum"][1, 1] == 20.0
+    np.testing.assert_allclose(out["ravg"][1, 1], (2 * 1.5 + 8 * np.sqrt(2.0)) / 10, rtol=1e-15)
+    out = _mocks(lib, _cat(pts), mode="brute", ravg=True)
+    np.testing.assert_allclose(out["ravg"][1, 1], (1.5 + np.sqrt(2.0)) / 2, rtol=1e-15)
+
+
 def _numpy_cross_form(d):
     """rp^2 and pi^2 of every unordered pair from the cross product: |s x l|^2 / |l|^2."""
     v = np.stack([d.x, d.y, d.z], axis=1)
@@ -137,7 +159,7 @@ def check_modes_auto_cross_self(lib):
     assert with0[0, 0] >= 300 and (with0[0, 0] - 300) % 2 == 0
 
 
-MOCK_CHECKS = [check_hand_pairs, check_cross_product_form, check_exact_symmetries, check_far_field_limit,
+MOCK_CHECKS = [check_hand_pairs, check_hand_ravg, check_cross_product_form, check_exact_symmetries, check_far_field_limit,
                check_modes_auto_cross_self]
 
 

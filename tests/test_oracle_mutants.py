@@ -4,7 +4,8 @@ The mutations are applied to a copy of oracle/cf_oracle.c in a temporary directo
 compiled there (CPU only); the oracle itself is never modified.  This shows that the pins
 in test_oracle_pins.py constrain every part of the oracle a plausible mistake could touch:
 the separation, the periodic wrap, the bin edges, the doubling and self pairs of
-auto-correlations, the pi cut, the rp/pi split, angular edges, weights and ravg.
+auto-correlations (their counts and their weights), the pi cut, the rp/pi split, angular edges,
+weights and ravg (of r, of rp for DD(rp, pi) and wp, and of rp for the mocks).
 """
 import math
 import os
@@ -44,6 +45,16 @@ MUTANTS = {
                          "double c = 2.0 * sin(e * (M_PI / 180.0));\n            p->e2[k] = c * c;\n        } else {\n            p->e2[k] = e * e;\n        }\n    }\n    p->npi"),
     "weight_sum_not_product": ("double ww = wi * (w2 ? w2[j] : 1.0);", "double ww = wi + (w2 ? w2[j] : 1.0);"),
     "ravg_squared": ("double c = sqrt(s);", "double c = s;"),
+    "rppi_ravg_3d_separation": ("if (p->ravg) *sep = sqrt(s);\n    if (p->kind == OR_WP) return k;",
+                                "if (p->ravg) *sep = sqrt(s + dz * dz);\n    if (p->kind == OR_WP) return k;"),
+    "mocks_ravg_3d_separation": ("if (p->ravg) *sep = sqrt(rp2);", "if (p->ravg) *sep = sqrt(ss);"),
+    "mocks_ravg_is_pi": ("if (p->ravg) *sep = sqrt(rp2);", "if (p->ravg) *sep = sqrt(pi2);"),
+    "ravg_ignores_weights": ("if (P.ravg) hr[k] += (P.weighted ? ww : 1.0) * sep;", "if (P.ravg) hr[k] += sep;"),
+    "no_self_pair_weights": ("wsum[k] += sw;", ""),
+    "self_pair_weight_is_one": ("sw += w1 ? w1[i] * w1[i] : 1.0;", "sw += 1.0;"),
+    "self_pair_weight_not_squared": ("sw += w1 ? w1[i] * w1[i] : 1.0;", "sw += w1 ? w1[i] : 1.0;"),
+    "rows_self_pair_weight_is_one": ("if (k >= 0) { hc[k] += 1; hw[k] += wi * wi; }",
+                                     "if (k >= 0) { hc[k] += 1; hw[k] += 1.0; }"),
     "cross_skips_first_row": ("ra[0] = (mode == OR_ROWS || !autoc) ? 0 : i + 1;",
                               "ra[0] = (mode == OR_ROWS || !autoc) ? 1 : i + 1;"),
 }
@@ -82,6 +93,25 @@ def _pin_checks(lib):
         exp[0, 1], exp[1, 0], exp[2, 2] = 2, 4, 4
         assert (out["npairs"] == exp).all()
 
+    def rppi_ravg():
+        from tests.test_oracle_pins import RPPI_W
+        kw = dict(autocorr=True, periodic=False, pimax=3.0, npibins=3, mode="brute", lib=lib, ravg=True)
+        out = oracle.count("rppi", [1, 2, 3, 5, 6], Cat(RPPI), **kw)
+        np.testing.assert_allclose(out["ravg"][0, 1], 1.0, rtol=1e-15)
+        np.testing.assert_allclose(out["ravg"][1, 0], (2 + math.sqrt(5)) / 2, rtol=1e-15)
+        wp = oracle.count("wp", [1, 2, 3, 5, 6], Cat(RPPI, w=RPPI_W), weighted=True, **kw)
+        np.testing.assert_allclose(wp["ravg"][:3], [1.0, (1 + math.sqrt(5)) / 1.5,
+                                                   (8 * math.sqrt(20) + 2 * math.sqrt(13)) / 10], rtol=1e-15)
+
+    def self_pair_weights():
+        from tests.test_oracle_pins import PERIODIC_W
+        d = Cat(PERIODIC, w=PERIODIC_W)
+        kw = dict(periodic=True, box=8.0, weighted=True, ravg=True, autocorr=True, lib=lib)
+        for out in (oracle.count("r", [0, 2, 4, 5], d, mode="brute", **kw),
+                    oracle.count("r", [0, 2, 4, 5], d, rows=(0, 5), **kw)):
+            assert out["wsum"].tolist() == [34.3125, 2.0, 23.5]
+            np.testing.assert_allclose(out["ravg"][0], 5.0 / 34.3125, rtol=1e-15)
+
     def theta():
         d = Cat([(1, 0, 0), (0, 1, 0), (0, 0, 1), (-1, 0, 0)])
         out = oracle.count("theta", [60, 90, 180], d, autocorr=True, periodic=False, mode="brute",
@@ -109,7 +139,7 @@ def _pin_checks(lib):
             chk(lib)
         run.__name__ = chk.__name__
         mocks.append(run)
-    return [lattice, lattice_w, periodic, rppi, theta, totals, ckdtree] + mocks
+    return [lattice, lattice_w, periodic, rppi, rppi_ravg, self_pair_weights, theta, totals, ckdtree] + mocks
 
 
 def _build_mutant(tmp_path, name, old, new):

@@ -123,6 +123,74 @@ def test_rppi_and_wp_hand(orc):
     assert wp["npairs"].tolist() == [2, 4, 4, 0]
 
 
+# ravg of DD(rp, pi) and wp is the mean projected separation rp = sqrt(dx^2 + dy^2) of the pairs of a
+# bin (Appendix A.1: rp is the separation across the line of sight; Sec. 6.5: ravg is the mean
+# separation of a bin), not the 3-D separation.  On the same lattice (rp^2 exact):
+#   (rp0, pi1): AB rp 1                       -> 1
+#   (rp1, pi0): AC rp 2, BC rp sqrt(5)        -> (2 + sqrt 5) / 2
+#   (rp2, pi2): BD rp sqrt(20), CD rp sqrt(13) -> (sqrt 20 + sqrt 13) / 2
+# With dyadic weights w = (1, 2, 0.5, 4): pair weights AB 2, AC 0.5, BC 1, BD 8, CD 2, so
+#   wsum (doubled) (0,1): 4, (1,0): 3, (2,2): 20;
+#   weighted ravg (0,1): 1, (1,0): (0.5*2 + 1*sqrt 5)/1.5, (2,2): (8 sqrt 20 + 2 sqrt 13)/10.
+# wp sums over pi, so its per-rp-bin values are the same means.
+RPPI_W = [1.0, 2.0, 0.5, 4.0]
+
+
+def test_rppi_and_wp_ravg_hand(orc):
+    d = Cat(RPPI)
+    kw = dict(autocorr=True, periodic=False, pimax=3.0, npibins=3, mode="brute", lib=orc)
+    out = oracle.count("rppi", [1, 2, 3, 5, 6], d, ravg=True, **kw)
+    exp = np.zeros((4, 3))
+    exp[0, 1] = 1.0
+    exp[1, 0] = (2 + math.sqrt(5)) / 2
+    exp[2, 2] = (math.sqrt(20) + math.sqrt(13)) / 2
+    np.testing.assert_allclose(out["ravg"], exp, rtol=1e-15, atol=0)
+    wp = oracle.count("wp", [1, 2, 3, 5, 6], d, ravg=True, **kw)
+    np.testing.assert_allclose(wp["ravg"], [1.0, exp[1, 0], exp[2, 2], 0.0], rtol=1e-15, atol=0)
+    dw = Cat(RPPI, w=RPPI_W)
+    out = oracle.count("rppi", [1, 2, 3, 5, 6], dw, ravg=True, weighted=True, **kw)
+    wexp = np.zeros((4, 3))
+    wexp[0, 1], wexp[1, 0], wexp[2, 2] = 4.0, 3.0, 20.0
+    assert (out["wsum"] == wexp).all()
+    rexp = np.zeros((4, 3))
+    rexp[0, 1] = 1.0
+    rexp[1, 0] = (0.5 * 2 + 1 * math.sqrt(5)) / 1.5
+    rexp[2, 2] = (8 * math.sqrt(20) + 2 * math.sqrt(13)) / 10
+    np.testing.assert_allclose(out["ravg"], rexp, rtol=1e-15, atol=0)
+    wp = oracle.count("wp", [1, 2, 3, 5, 6], dw, ravg=True, weighted=True, **kw)
+    assert wp["wsum"].tolist() == [4.0, 3.0, 20.0, 0.0]
+    np.testing.assert_allclose(wp["ravg"], [1.0, rexp[1, 0], rexp[2, 2], 0.0], rtol=1e-15, atol=0)
+
+
+# The weighted self pairs of Appendix B (reading S10 of the design notes: a point paired with itself
+# has weight w_i^2 and separation 0).  PERIODIC with dyadic weights A 1, B 2, C 0.5, D 4, E 0.25 and
+# edges 0, 2, 4, 5 (squared 0, 4, 16, 25):
+#   bin0 [0,4):  AD s=0 (w 4), AC s=1 (w 0.5), CD s=1 (w 2) -> doubled: w 13, sum w*r 2*(0 + 0.5 + 2) = 5
+#                self pairs: sum w_i^2 = 1 + 4 + 0.25 + 16 + 0.0625 = 21.3125, separation 0
+#                -> wsum 34.3125, weighted ravg 5 / 34.3125, count 6 + 5 = 11
+#   bin1 [4,16): BC s=9 (w 1)                                 -> wsum 2, ravg 3, count 2
+#   bin2 [16,25): AB BD AE BE DE, s 16 16 20 20 20 (w 2 8 0.25 0.5 1)
+#                -> wsum 23.5, sum w*r 2*(4*2 + 4*8 + sqrt(20)*1.75) -> ravg (80 + 3.5 sqrt 20)/23.5, count 10
+PERIODIC_W = [1.0, 2.0, 0.5, 4.0, 0.25]
+
+
+def test_weighted_self_pairs_hand(orc):
+    d = Cat(PERIODIC, w=PERIODIC_W)
+    kw = dict(periodic=True, box=8.0, weighted=True, ravg=True, lib=orc)
+    wexp = [34.3125, 2.0, 23.5]
+    rexp = [5.0 / 34.3125, 3.0, (80.0 + 3.5 * math.sqrt(20.0)) / 23.5]
+    for out in (oracle.count("r", [0, 2, 4, 5], d, autocorr=True, mode="brute", **kw),
+                oracle.count("r", [0, 2, 4, 5], d, autocorr=True, mode="zwin", **kw),
+                oracle.count("r", [0, 2, 4, 5], d, autocorr=True, rows=(0, 5), **kw)):
+        assert out["npairs"].tolist() == [11, 2, 10]
+        assert out["wsum"].tolist() == wexp
+        np.testing.assert_allclose(out["ravg"], rexp, rtol=1e-15, atol=0)
+    # the cross count of the set with itself meets every point's self pair in the pair loop
+    cross = oracle.count("r", [0, 2, 4, 5], d, d, autocorr=False, mode="brute", **kw)
+    assert cross["npairs"].tolist() == [11, 2, 10]
+    assert cross["wsum"].tolist() == wexp
+
+
 def test_theta_hand(orc):
     # e_x, e_y, e_z, -e_x: five pairs at exactly 90 deg (chord^2 = 2) and one at 180 deg (chord^2 = 4).
     # Chord edges are c = 2 sin(theta pi/360) in FP64: 60 -> 0.9999999999999998, 90 ->
