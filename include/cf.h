@@ -233,16 +233,30 @@ cf_status cf_plan_probe(const cf_params *params, const double bbox[6], int64_t n
 /* Serving: continuous batching of autocorr requests with the same params.  A worker thread
  * admits requests while device memory (mem_budget_bytes) and slots (max_slots) allow, builds
  * their cell lists while earlier requests are counted, and counts every admitted request in
- * the next pair-kernel wave.  Inputs of a request must stay valid until its result is polled
- * or it is cancelled; results are copied into the cf_result given at submit. */
+ * the next pair-kernel wave.  The inputs and the cf_result arrays of a request are borrowed:
+ * they must stay valid until cf_server_poll has returned something other than CF_ERR_BUSY or
+ * CF_ERR_TIMEOUT for its ticket, or until cf_server_cancel has returned CF_OK for it.  A wave
+ * that fails is counted again one request at a time, so one bad catalogue fails only its own
+ * request.  If no worker can create its CUDA context, pending and later requests fail with
+ * CF_ERR_CUDA. */
 cf_status cf_server_start(void **server_out, int device, const cf_params *params,
                           size_t mem_budget_bytes, int max_slots);
+/* CF_ERR_ARG (invalid catalogue), CF_ERR_OOM (larger than the budget), CF_ERR_CANCELLED (stopping),
+ * CF_ERR_CUDA (no worker), else CF_OK with *ticket set. */
 cf_status cf_server_submit(void *server, const cf_points *cat, cf_result *out, uint64_t *ticket);
 /* CF_OK: done (result written); CF_ERR_BUSY: not yet (timeout_ms == 0); CF_ERR_TIMEOUT; or the
- * request's own error status. */
+ * request's own error status (CF_ERR_CANCELLED after a cancel).  Any status other than BUSY and
+ * TIMEOUT retires the ticket. */
 cf_status cf_server_poll(void *server, uint64_t ticket, int timeout_ms);
+/* Withdraw a queued request: CF_OK, after which the library no longer references its inputs or
+ * result arrays and cf_server_poll returns CF_ERR_CANCELLED for it.  CF_ERR_BUSY when the request
+ * is already in a wave on the GPU: it cannot be withdrawn, its buffers stay in use, and
+ * cf_server_poll returns its result.  CF_OK without effect when it has already finished.
+ * CF_ERR_ARG for an unknown ticket. */
 cf_status cf_server_cancel(void *server, uint64_t ticket);
 cf_status cf_server_stop(void *server);
+/* Message of the server's last failure, copied into storage owned by the calling thread (valid
+ * until that thread's next call). */
 const char *cf_server_last_error(const void *server);
 
 /* ---- allocation-free count (the paper has no counterpart) ----

@@ -212,8 +212,16 @@ def cf_server_poll(server: int, ticket: int, timeout_ms: int = 0):
     return keep[0].as_dict(_server_keep[server]["params"])
 
 
-def cf_server_cancel(server: int, ticket: int) -> None:
-    _check(_capi.lib().cf_server_cancel(server, ctypes.c_uint64(ticket)), server=server)
+def cf_server_cancel(server: int, ticket: int) -> bool:
+    """Withdraw a request.  True when the library no longer uses its buffers: it was queued and is
+    withdrawn (cf_server_poll then raises CF_ERR_CANCELLED), or it had already finished (poll
+    returns its result).  False when it is in a wave on the GPU: it runs to the end and
+    cf_server_poll returns its result."""
+    rc = _capi.lib().cf_server_cancel(server, ctypes.c_uint64(ticket))
+    if rc == _capi.CF_ERR_BUSY:
+        return False
+    _check(rc, server=server)
+    return True
 
 
 def cf_server_stop(server: int) -> None:
@@ -268,8 +276,25 @@ def cf_plan_probe(p: Params, bbox, npoints: int, any_f64: bool = False, which: i
 
 def cf_count_noalloc(p: Params, d1: Points, d2: Optional[Points], npairs, wsum=None, ravg=None, stream=None) -> None:
     """Allocation-free count into caller-owned device tensors (see include/cf.h): for callers that
-    cannot allocate device memory.  Enqueued on `stream`; returns without waiting."""
-    ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    cannot allocate device memory.  npairs is int64 (the counts' bits), wsum and ravg float64, each
+    a contiguous tensor on the current CUDA device with at least p.nout elements (ValueError
+    otherwise: the library writes p.nout entries through the raw pointers).  Enqueued on `stream`;
+    returns without waiting."""
+    import torch
+    dev = torch.cuda.current_device()
+
+    def ptr(t, name, dtype):
+        if t is None:
+            return None
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be a tensor on the current CUDA device (cuda:{dev})")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, not {t.dtype}")
+        if not t.is_contiguous() or t.numel() < p.nout:
+            raise ValueError(f"{name} must be contiguous with at least {p.nout} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    out = (ptr(npairs, "npairs", torch.int64), ptr(wsum, "wsum", torch.float64), ptr(ravg, "ravg", torch.float64))
     rc = _capi.lib().cf_count_noalloc(ctypes.byref(p.c), ctypes.byref(d1.c), ctypes.byref(d2.c) if d2 else None,
-                                      ptr(npairs), ptr(wsum), ptr(ravg), _stream_handle(stream))
+                                      *out, _stream_handle(stream))
     _check(rc)

@@ -11,6 +11,11 @@
 //
 // Waits are bounded: cf_server_poll takes a timeout, workers wake at least every 50 ms to
 // notice a stop request.
+//
+// Failures: a wave whose batched count fails is counted again one request at a time, so that
+// one bad catalogue fails only its own request.  A worker that cannot create its context
+// records the error; once no worker is left, every pending and every later request fails with
+// CF_ERR_CUDA instead of waiting.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -32,7 +37,6 @@ struct Request {
     cf_result out;
     size_t mem = 0;
     int status = CF_ERR_BUSY;    // CF_ERR_BUSY while queued or running
-    bool cancelled = false;
     bool running = false;
 };
 
@@ -50,6 +54,7 @@ struct Server {
     size_t mem_in_flight = 0;
     int slots_in_flight = 0;
     bool stopping = false;
+    int workers_alive = 0;       // workers whose context exists (set before they start)
     std::vector<std::thread> workers;
     std::vector<cudaStream_t> streams;
     std::string err;
@@ -73,7 +78,17 @@ void worker_main(Server *S, int wid)
 {
     cudaSetDevice(S->device);
     void *ctxv = nullptr;
-    if (cf_create(&ctxv, S->device, S->streams[wid]) != CF_OK) return;
+    if (cf_create(&ctxv, S->device, S->streams[wid]) != CF_OK) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->err = "a server worker could not create its CUDA context";
+        if (--S->workers_alive == 0) {
+            // nobody is left to serve: fail what waits instead of letting it time out
+            for (auto *r : S->pending) r->status = CF_ERR_CUDA;
+            S->pending.clear();
+        }
+        S->cv_done.notify_all();
+        return;
+    }
     CfCtx *C = (CfCtx *)ctxv;
     for (;;) {
         std::vector<Request *> wave;
@@ -85,10 +100,6 @@ void worker_main(Server *S, int wid)
             int slots = 0;
             while (!S->pending.empty()) {
                 Request *r = S->pending.front();
-                if (r->cancelled) {
-                    S->pending.pop_front();
-                    continue;
-                }
                 bool fits = S->mem_in_flight + mem + r->mem <= S->budget &&
                             S->slots_in_flight + slots + 1 <= S->max_slots;
                 if (!fits && !wave.empty()) break;
@@ -113,16 +124,26 @@ void worker_main(Server *S, int wid)
             outs[i] = wave[i]->out;
         }
         int rc = cf_batch_count(C, &S->p, cats.data(), (int)cats.size(), outs.data());
+        std::vector<int> st(wave.size(), rc);
         std::string msg = rc ? C->err : std::string();
+        if (rc && wave.size() > 1) {
+            // find the failing catalogue(s): count each request of the wave alone
+            msg.clear();
+            for (size_t i = 0; i < wave.size(); i++) {
+                st[i] = cf_batch_count(C, &S->p, &cats[i], 1, &outs[i]);
+                if (st[i] && msg.empty()) msg = C->err;
+            }
+        }
         {
             std::lock_guard<std::mutex> lk(S->mu);
             size_t mem = 0;
-            for (auto *r : wave) {
+            for (size_t i = 0; i < wave.size(); i++) {
+                Request *r = wave[i];
                 mem += r->mem;
                 r->running = false;
-                r->status = r->cancelled ? CF_ERR_CANCELLED : rc;
+                r->status = st[i];
             }
-            if (rc) S->err = msg;
+            if (!msg.empty()) S->err = msg;
             S->mem_in_flight -= mem;
             S->slots_in_flight -= (int)wave.size();
         }
@@ -162,6 +183,7 @@ cf_status cf_server_start(void **server_out, int device, const cf_params *params
         }
         S->streams.push_back(st);
     }
+    S->workers_alive = 2;
     for (int w = 0; w < 2; w++) S->workers.emplace_back(worker_main, S, w);
     *server_out = S;
     return CF_OK;
@@ -181,6 +203,10 @@ cf_status cf_server_submit(void *server, const cf_points *cat, cf_result *out, u
     if (S->stopping) {
         delete r;
         return (cf_status)S->fail(CF_ERR_CANCELLED, "server is stopping");
+    }
+    if (S->workers_alive == 0) {
+        delete r;
+        return (cf_status)S->fail(CF_ERR_CUDA, "no server worker could create its CUDA context");
     }
     if (r->mem > S->budget) {
         delete r;
@@ -222,8 +248,10 @@ cf_status cf_server_cancel(void *server, uint64_t ticket)
     auto it = S->all.find(ticket);
     if (it == S->all.end()) return (cf_status)S->fail(CF_ERR_ARG, "unknown ticket");
     Request *r = it->second;
-    r->cancelled = true;
-    if (!r->running && r->status == CF_ERR_BUSY) {
+    // a request in a wave on the GPU cannot be withdrawn: its inputs are still read and its result
+    // will be written, so the caller keeps its buffers and polls for it
+    if (r->running) return CF_ERR_BUSY;
+    if (r->status == CF_ERR_BUSY) {
         auto q = std::find(S->pending.begin(), S->pending.end(), r);
         if (q != S->pending.end()) S->pending.erase(q);
         r->status = CF_ERR_CANCELLED;
@@ -259,7 +287,12 @@ cf_status cf_server_stop(void *server)
 const char *cf_server_last_error(const void *server)
 {
     if (!server) return "null server";
-    return ((const Server *)server)->err.c_str();
+    // the workers assign err under the lock: copy it under the lock into this thread's buffer
+    static thread_local std::string msg;
+    Server *S = (Server *)server;
+    std::lock_guard<std::mutex> lk(S->mu);
+    msg = S->err;
+    return msg.c_str();
 }
 
 }  // extern "C"

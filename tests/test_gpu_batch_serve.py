@@ -3,7 +3,8 @@
 batched == one at a time == oracle (counts bit-exact); a captured graph replays to the same
 result; the server returns each catalogue's result identically whether it ran alone or mixed
 with other requests (counts bit-exact, sums within 1e-6), rejects requests above its memory
-budget, and cancels queued requests.
+budget, withdraws queued requests but lets a running one finish, and fails only the request of a
+bad catalogue in a wave.
 """
 import time
 
@@ -170,6 +171,70 @@ def test_server_budget_and_cancel(cf, cats):
     finally:
         cf.cf_server_stop(srv)
     assert done == len(tickets) - 1
+
+
+def test_server_cancel_running_and_queued(cf, cats):
+    """A cancel withdraws a queued request (poll then reports CF_ERR_CANCELLED) but not one whose
+    wave is on the GPU: that cancel returns False, the request's buffers stay in use, and poll
+    returns its full result.  One slot means one request on the GPU at a time, so most of a quick
+    burst is still queued when its cancel arrives."""
+    p = _params(cf)
+    srv = cf.cf_server_start(0, p, 1 << 30, 1)
+    order = [i % len(cats) for i in range(24)]
+    try:
+        tickets = [cf.cf_server_submit(srv, p, cf.points(cats[k].x, cats[k].y, cats[k].z)) for k in order]
+        withdrawn = [cf.cf_server_cancel(srv, t) for t in tickets]
+        outcome = []
+        for t in tickets:
+            try:
+                r = None
+                deadline = time.time() + 60
+                while r is None and time.time() < deadline:
+                    r = cf.cf_server_poll(srv, t, 500)
+                assert r is not None
+                outcome.append(r)
+            except cf.CfError as e:
+                assert e.status == -6
+                outcome.append(None)
+    finally:
+        cf.cf_server_stop(srv)
+    exp = [oracle.count("rppi", EDGES, c, autocorr=True, periodic=True, box=L, pimax=10.0, npibins=10)
+           for c in cats]
+    for k, w, r in zip(order, withdrawn, outcome):
+        if not w:                       # on the GPU when cancelled: ran to the end
+            assert r is not None
+        if r is not None:
+            assert np.array_equal(r["npairs"], exp[k]["npairs"])
+    assert sum(1 for w, r in zip(withdrawn, outcome) if w and r is None) > 0
+
+
+def test_server_one_bad_catalogue_fails_alone(cf, cats):
+    """A catalogue the library rejects (a periodic position outside [0, L]) fails its own request;
+    the requests counted in the same wave still get their results."""
+    p = _params(cf)
+    bad = gen.Catalogue(cats[0].x.copy(), cats[0].y.copy(), cats[0].z.copy())
+    bad.x[3] = np.float32(L * 1.5)
+    srv = cf.cf_server_start(0, p, 1 << 30, 16)
+    try:
+        pts = [cf.points(c.x, c.y, c.z) for c in cats[:3]] + [cf.points(bad.x, bad.y, bad.z)] + \
+              [cf.points(c.x, c.y, c.z) for c in cats[3:]]
+        tickets = [cf.cf_server_submit(srv, p, q) for q in pts]
+        got = []
+        for t in tickets:
+            try:
+                r = None
+                while r is None:
+                    r = cf.cf_server_poll(srv, t, 1000)
+                got.append(r)
+            except cf.CfError as e:
+                got.append(e.status)
+        msg = cf.cf_server_last_error(srv)
+    finally:
+        cf.cf_server_stop(srv)
+    assert got[3] == -1 and "[0, box]" in msg
+    for c, r in zip(cats, got[:3] + got[4:]):
+        exp = oracle.count("rppi", EDGES, c, autocorr=True, periodic=True, box=L, pimax=10.0, npibins=10)
+        assert np.array_equal(r["npairs"], exp["npairs"])
 
 
 def test_mocks_batched_and_served(cf):
