@@ -112,6 +112,27 @@ int CfCtx::ensure_host(size_t bytes)
     return CF_OK;
 }
 
+// Pinned staging for the per-call uploads: host-to-device copies from pinned memory are
+// asynchronous, so the call need not wait for them (from pageable memory they may synchronise).
+// The buffer is reused by the next call, which starts after this call's final synchronisation.
+int CfCtx::ensure_upload(size_t bytes)
+{
+    if (hup_cap >= bytes) return CF_OK;
+    if (hup) {
+        cudaStreamSynchronize(stream);
+        cudaFreeHost(hup);
+    }
+    hup = nullptr;
+    size_t want = bytes + bytes / 4 + 65536;
+    if (cudaMallocHost(&hup, want) != cudaSuccess) {
+        cudaGetLastError();
+        hup_cap = 0;
+        return fail(CF_ERR_OOM, "pinned host staging allocation failed");
+    }
+    hup_cap = want;
+    return CF_OK;
+}
+
 void CfCtx::drop_graph()
 {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -127,6 +148,7 @@ CfCtx::~CfCtx()
     for (auto &B : buf)
         if (B.p) cudaFree(B.p);
     if (hpin) cudaFreeHost(hpin);
+    if (hup) cudaFreeHost(hup);
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);
 }
@@ -375,26 +397,34 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_QUEUE, 16 * (size_t)R.qcap));
     CF_TRY(C->ensure_host(readback_bytes(R)));
 
-    if (!H.origin.empty())
-        CF_CU(cudaMemcpyAsync(C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size(), cudaMemcpyHostToDevice,
-                          st), "origins");
-    if (!H.bands.empty())
-        CF_CU(cudaMemcpyAsync(C->buf[B_BANDS].p, H.bands.data(), sizeof(CfBand) * H.bands.size(),
-                              cudaMemcpyHostToDevice, st),
-              "bands");
-    CF_CU(cudaMemcpyAsync(C->buf[B_PLAN].p, &D, sizeof(CfDevPlan), cudaMemcpyHostToDevice, st), "plan");
-    CF_CU(cudaMemcpyAsync(C->buf[B_LUT].p, H.lut.data(), sizeof(uint16_t) * H.lut.size(), cudaMemcpyHostToDevice, st),
-          "lut");
-    if (!H.fine.empty())
-        CF_CU(cudaMemcpyAsync(C->buf[B_FINE].p, H.fine.data(), sizeof(CfFine) * H.fine.size(), cudaMemcpyHostToDevice, st),
-              "fine");
-    CF_CU(cudaMemcpyAsync(C->buf[B_STENCIL].p, H.stencil.data(), sizeof(CfStencil) * H.stencil.size(),
-                          cudaMemcpyHostToDevice, st), "stencil");
-    CF_CU(cudaMemcpyAsync(C->buf[B_JOBS].p, R.jobs.data(), sizeof(CfJobDesc) * njobs, cudaMemcpyHostToDevice, st), "jobs");
-    CF_CU(cudaMemcpyAsync(C->buf[B_SETS].p, R.sets.data(), sizeof(CfSetDesc) * nsets, cudaMemcpyHostToDevice, st),
-          "sets");
-    // pageable uploads: the host copies (the plan, the vectors) must outlive the transfers
-    CF_CU(cudaStreamSynchronize(st), "upload sync");
+    {
+        // uploads through pinned staging: no wait for the transfers
+        struct Up {
+            void *dst;
+            const void *src;
+            size_t bytes;
+        };
+        const Up ups[] = {
+            {C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size()},
+            {C->buf[B_BANDS].p, H.bands.data(), sizeof(CfBand) * H.bands.size()},
+            {C->buf[B_PLAN].p, &D, sizeof(CfDevPlan)},
+            {C->buf[B_LUT].p, H.lut.data(), sizeof(uint16_t) * H.lut.size()},
+            {C->buf[B_FINE].p, H.fine.data(), sizeof(CfFine) * H.fine.size()},
+            {C->buf[B_STENCIL].p, H.stencil.data(), sizeof(CfStencil) * H.stencil.size()},
+            {C->buf[B_JOBS].p, R.jobs.data(), sizeof(CfJobDesc) * njobs},
+            {C->buf[B_SETS].p, R.sets.data(), sizeof(CfSetDesc) * nsets},
+        };
+        size_t total = 0;
+        for (const Up &u : ups) total += (u.bytes + 255) & ~(size_t)255;
+        CF_TRY(C->ensure_upload(total));
+        size_t off = 0;
+        for (const Up &u : ups) {
+            if (!u.bytes) continue;
+            std::memcpy((char *)C->hup + off, u.src, u.bytes);
+            CF_CU(cudaMemcpyAsync(u.dst, (char *)C->hup + off, u.bytes, cudaMemcpyHostToDevice, st), "plan upload");
+            off += (u.bytes + 255) & ~(size_t)255;
+        }
+    }
 
     // pair-kernel configuration
     std::memset(&R.cfg, 0, sizeof(R.cfg));
@@ -728,10 +758,20 @@ int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &p
     cudaStream_t st = C->stream;
     CF_CU(cudaEventRecord(C->ev[0], st), "event");
     CF_TRY(cf_enqueue_build(C, R));
-    // size the work list from the device count (one small readback)
-    CF_CU(cudaMemcpyAsync(C->hpin, (uint32_t *)C->buf[B_IOFF].p + R.nunit, 4, cudaMemcpyDeviceToHost, st), "items total");
-    CF_CU(cudaStreamSynchronize(st), "items sync");
-    R.items_cap = *(const uint32_t *)C->hpin;
+    // the work list depends on the plan and on the cell pruning and order options
+    const std::string ikey = C->plan_key + std::to_string(C->opt[CF_OPT_CELL_PRUNE]) + "/" +
+                             std::to_string(C->opt[CF_OPT_CELL_ORDER]);
+    if (C->items_hint && C->items_key == ikey) {
+        // a call on the same plan sized the work list before: take that size with headroom and
+        // let cf_finish count again in the rare case that the list outgrew it
+        R.items_cap = C->items_hint;
+    } else {
+        // size the work list from the device count (one small readback)
+        CF_CU(cudaMemcpyAsync(C->hpin, (uint32_t *)C->buf[B_IOFF].p + R.nunit, 4, cudaMemcpyDeviceToHost, st),
+              "items total");
+        CF_CU(cudaStreamSynchronize(st), "items sync");
+        R.items_cap = *(const uint32_t *)C->hpin;
+    }
     CF_TRY(C->ensure(B_ITEMS, sizeof(CfItem) * std::max<size_t>(1, R.items_cap)));
     for (int attempt = 0; attempt < 4; attempt++) {
         CF_TRY(cf_enqueue_count(C, R, true));
@@ -739,6 +779,9 @@ int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &p
         int retry = 0;
         CF_TRY(cf_finish(C, R, res, &retry));
         if (!retry) {
+            const uint32_t n = (uint32_t)C->stats.work_items;
+            C->items_hint = (uint32_t)std::min<uint64_t>(CF_MAX_ENTRIES, (uint64_t)n + n / 4 + 1024);
+            C->items_key = ikey;
             record_times(C, attempt == 0);
             C->stats.ms_total =
                 (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();

@@ -81,6 +81,10 @@ struct CfCtx {
     Buf buf[B_COUNT_];
     void *hpin = nullptr;
     size_t hpin_cap = 0;
+    void *hup = nullptr;           // pinned staging of the plan, tables and descriptors uploaded per call
+    size_t hup_cap = 0;
+    uint32_t items_hint = 0;       // work-list capacity for the next call with plan `items_key`
+    std::string items_key;
     int64_t opt[CF_OPT_COUNT_] = {0};
     uint32_t qcap_default = 1u << 20;
     cf_stats stats = {};
@@ -100,6 +104,7 @@ struct CfCtx {
     int cuda(cudaError_t e, const char *what);
     int ensure(int b, size_t bytes);
     int ensure_host(size_t bytes);
+    int ensure_upload(size_t bytes);
     void drop_graph();
     ~CfCtx();
 };
