@@ -211,20 +211,159 @@ def _points(cat, weighted, cf, dev=None):
     return cf.points(*t[:3], t[3] if weighted else None)
 
 
+# the other configurations, measured in the same run as the headline (each tuned, L2 flushed)
+EXTRA_WORKLOADS = ["uniform_r_20k", "clustered_rppi_2m", "clustered_wp_2m", "clustered_rppi_dr", "sphere_theta_1m",
+                   "clustered_rppi_2m_wr", "mock_dr_rppi"]
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def _fingerprint(*cats) -> str:
+    """sha256 of the generated arrays, in the stored histograms' format (x, y, z, w per set)."""
+    import numpy as np
+    h = hashlib.sha256()
+    for c in cats:
+        if c is None:
+            continue
+        for a in (c.x, c.y, c.z, c.w):
+            if a is not None:
+                h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()
+
+
+def _parity(name, got, cats) -> dict:
+    """The result against the FP64 oracle's stored histogram of the same seeded inputs
+    (tests/golden/full_<name>.json, written by tests/golden/make_golden.py): counts bit-exact,
+    weighted sums and ravg within 1e-6 relative."""
+    import numpy as np
+    try:
+        with open(os.path.join(GOLDEN, f"full_{name}.json")) as f:
+            gold = json.load(f)
+    except (OSError, ValueError):
+        return {"ok": None, "why": "no stored oracle histogram"}
+    if gold.get("fingerprint") != _fingerprint(*cats):
+        return {"ok": None, "why": "the generated inputs differ from the stored histogram's"}
+    counts = bool(np.array_equal(np.asarray(got["npairs"]).ravel().astype(np.uint64),
+                                 np.asarray(gold["npairs"], dtype=np.uint64)))
+    worst = 0.0
+    for k in ("wsum", "ravg"):
+        if k in gold and k in got:
+            g = np.asarray(got[k], dtype=np.float64).ravel()
+            e = np.asarray(gold[k], dtype=np.float64)
+            nz = e != 0
+            worst = max(worst, float(np.max(np.abs(g[nz] - e[nz]) / np.abs(e[nz]), initial=0.0)),
+                        float(np.max(np.abs(g[~nz]), initial=0.0)))
+    return {"ok": counts and worst <= 1e-6, "counts_equal": counts, "max_rel_err_sums": worst,
+            "against": f"tests/golden/full_{name}.json"}
+
+
+def _peak_pairs(dev, kind) -> float:
+    """R* in pairs/s: SMs x 128 FP32 lanes x the measured maximum SM clock / FP32 operations per pair."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(_peaks().get("sm_max_mhz", 2070.0))
+    return props.multi_processor_count * 128 * sm_max * 1e6 / FP32_INSTR_PER_PAIR_KIND.get(kind, FP32_INSTR_PER_PAIR)
+
+
+def _measure_workload(args, cf, tune, ctx, name, dev, flush) -> dict:
+    """One more configuration on the headline's context: tuned (cache honoured), 2 untimed calls,
+    then args.extra_steps calls with the L2 flushed before each, device-resident inputs."""
+    import numpy as np
+    import torch
+
+    import gen
+    stream = torch.cuda.current_stream(dev)
+    wl = gen.workload(name)
+    p = _wl_params(wl, cf)
+    d1 = _points(wl.d1, wl.weighted, cf, dev)
+    d2 = None if wl.autocorr else _points(wl.d2, wl.weighted, cf, dev)
+    npts = wl.d1.n + (0 if wl.autocorr else wl.d2.n)
+
+    def step_time():
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cf.cf_count(ctx, p, d1, d2)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    tune.reset(ctx)
+    tuned = tune.tune(ctx, p, d1, d2, device_name=torch.cuda.get_device_name(dev), npoints=npts, reps=3, passes=1,
+                      use_cache=not args.no_tune_cache, timer=step_time)
+    for _ in range(2):
+        out = cf.cf_count(ctx, p, d1, d2)
+    step_ms, pair_ms = [], []
+    for _ in range(args.extra_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = cf.cf_count(ctx, p, d1, d2)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        pair_ms.append(cf.cf_get_stats(ctx)["ms_pair"])
+    st = cf.cf_get_stats(ctx)
+    tune.reset(ctx)
+    ev = int(st["evaluated_pairs"])
+    step, pair = statistics.fmean(step_ms), statistics.fmean(pair_ms)
+    in_range = int(np.asarray(out["npairs"], dtype=np.float64).sum())
+    rec = {
+        "workload": WORKLOADS[name], "steps": args.extra_steps, "step_ms": step, "pair_kernel_ms": pair,
+        "evaluated_pairs_per_step": ev, "evaluated_pairs_per_s": ev / (step / 1e3),
+        "in_range_pairs_per_step": in_range, "in_range_pairs_per_s": in_range / (step / 1e3),
+        "roofline_frac": ev / (pair / 1e3) / _peak_pairs(dev, wl.kind),
+        "roofline_basis": f"{FP32_INSTR_PER_PAIR_KIND.get(wl.kind, FP32_INSTR_PER_PAIR)} FP32 operations per pair",
+        "rechecked_pairs_per_step": int(st["rechecked_pairs"]), "fixed_sums": int(st["fixed_sums"]),
+        "tuned": tuned, "parity_vs_golden": _parity(name, out, (wl.d1, None if wl.autocorr else wl.d2)),
+    }
+    del d1, d2
+    return rec
+
+
+def _extras(args, cf, tune, ctx, dev, local, flush) -> dict:
+    """Every configuration besides the headline: the other single-catalogue workloads, and the
+    256-catalogue batch counted one at a time, batched, graph-replayed and served."""
+    import numpy as np
+    out = {"workloads": {name: _measure_workload(args, cf, tune, ctx, name, dev, flush) for name in EXTRA_WORKLOADS}}
+    sizes, cats = _batch_setup(256)
+    b = _batch_measure(args, cf, tune, dev, local, sizes, cats, 2)
+    r = _serve_measure(args, cf, dev, local, cats, args.extra_requests)
+    lat = r["lat"]
+    n = b["ncat"]
+    out["batch256"] = {
+        "workload": BATCH_DESC, "catalogues_per_s_batched": n / b["best"],
+        "catalogues_per_s_one_at_a_time": n / b["t_single"], "speedup_vs_one_at_a_time": b["t_single"] / b["best"],
+        "seconds_batched": b["t_batch"], "seconds_graph_replay": b["t_graph"], "seconds_one_at_a_time": b["t_single"],
+        "pair_kernel_ms": b["pair_ms"], "roofline_frac": b["achieved"] / b["peak"],
+        "evaluated_pairs": int(b["st"]["evaluated_pairs"]), "tuned": b["tuned"],
+        "parity_batched_vs_single": b["same"], "parity_vs_golden": b["golden"],
+    }
+    out["serve"] = {
+        "workload": BATCH_DESC, "arrivals": "Poisson", "load": args.serve_load, "requests": r["nreq"],
+        "capacity_catalogues_per_s": r["capacity"], "served_catalogues_per_s": r["nreq"] / r["t_total"],
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
+                       "p99": float(np.percentile(lat, 99)), "max": float(np.max(lat))},
+        "results_equal_batched": r["ok"], "inputs": "host numpy arrays (copied by the server)",
+    }
+    return out
+
+
 # ---------------------------------------------------------------------------------------------
 # CPU oracle legs
 # ---------------------------------------------------------------------------------------------
 
-def _oracle_rows_rate(wl, seconds: float, seed: int = 0):
+def _oracle_rows(wl, seconds: float, seed: int = 0, mode: str = "rows"):
     """Time the oracle (as it stands) on a bounded random sample of rows of the workload: each
-    row is every ordered pair (i, j) of one point i.  Returns (evals/s, cores, sample text)."""
+    row is every ordered pair (i, j) of one point i, by brute force (mode "rows") or through the
+    z window (mode "zwin", pinned equal to brute force on the same rows).  The sample grows until
+    its rows take about `seconds` beyond the call's fixed cost.  Returns (rows, seconds, cores,
+    fixed seconds of one call)."""
     import numpy as np
 
     import oracle
     lib = oracle.load()
     cores = os.cpu_count() or 1
     n1 = wl.d1.n
-    n2 = wl.d1.n if wl.autocorr else wl.d2.n
     rng = np.random.Generator(np.random.PCG64(seed))
 
     def run(rows):
@@ -232,20 +371,51 @@ def _oracle_rows_rate(wl, seconds: float, seed: int = 0):
         t0 = time.perf_counter()
         oracle.count(wl.kind, wl.edges, wl.d1, None if wl.autocorr else wl.d2, autocorr=wl.autocorr,
                      periodic=wl.periodic, box=wl.box, pimax=wl.pimax, npibins=wl.npibins, weighted=wl.weighted,
-                     ravg=wl.ravg, rows=(start, start + rows), nthreads=cores, lib=lib)
+                     ravg=wl.ravg, rows=(start, start + rows), mode=mode, nthreads=cores, lib=lib)
         return time.perf_counter() - t0
 
+    # the fixed cost of a call (loading, threads, the z window's sort of the second set), paid once
+    # by a whole-workload run as well
+    t_fix = min(run(1), run(1))
     rows = 16
     t = run(rows)
-    while t < 0.2 and rows < n1:
+    while t - t_fix < 0.2 and rows < n1:
         rows = min(n1, rows * 4)
         t = run(rows)
-    rows = int(min(n1, max(1, rows * seconds / max(t, 1e-6))))
-    t = run(rows)
+    for _ in range(2):      # twice: a short calibration run understates the per-row rate
+        rows = int(min(n1, max(1, rows * seconds / max(t - t_fix, 1e-6))))
+        t = run(rows)
+    return rows, t, cores, t_fix
+
+
+def _oracle_rows_rate(wl, seconds: float, seed: int = 0):
+    """Brute-force oracle rate on a row sample, in evaluated pairs per second.  Returns
+    (evals/s, cores, sample text, seconds)."""
+    rows, t, cores, _ = _oracle_rows(wl, seconds, seed, "rows")
+    n2 = wl.d1.n if wl.autocorr else wl.d2.n
     evals = rows * (n2 - (1 if wl.autocorr else 0))
     sample = (f"{rows} consecutive rows (random start) of the workload, each against all {n2} points, "
               f"brute-force FP64 oracle, {cores} threads, {t:.1f} s")
     return evals / t, cores, sample, t
+
+
+def _cpu_baseline(wl, seconds: float) -> dict:
+    """The oracle beside the GPU on the box's own cores: its brute-force rate on a row sample (the
+    line's unit), and the z-window oracle's time for the whole workload, extrapolated from a row
+    sample (an auto-correlation bins only j > i of each row's window, about half of it)."""
+    rate, cores, sample, _ = _oracle_rows_rate(wl, 0.5 * seconds)
+    zrows, zt, _, zfix = _oracle_rows(wl, 0.5 * seconds, seed=1, mode="zwin")
+    n1 = wl.d1.n
+    # a row of the whole auto-correlation scans its full window but bins only j > i: between half
+    # and all of an ordered row's cost
+    per_rows = (zt - zfix) * n1 / zrows
+    lo, hi = (zfix + 0.5 * per_rows, zfix + per_rows) if wl.autocorr else (zfix + per_rows, zfix + per_rows)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "zwin_seconds_full_est": 0.5 * (lo + hi), "zwin_seconds_full_range": [lo, hi],
+            "zwin_sample": f"{zrows} consecutive rows (random start) through the z window, {cores} threads, "
+                           f"{zt:.2f} s, of which {zfix:.2f} s the call's fixed cost (the z sort); rows scaled by "
+                           f"{n1}/{zrows}" + ("; the whole auto-correlation bins only j > i of each row's window, "
+                                              "so its time lies in the range given" if wl.autocorr else "")}
 
 
 def run_reference(args, wl, world, rank):
@@ -398,9 +568,11 @@ def run_gpu(args, wl, world, rank, local):
         "work_items": int(stats[-1]["work_items"]),
         "wall_s_timed_region": wall,
     }
+    line["parity_vs_golden"] = _parity(args.workload, out, (wl.d1, None if wl.autocorr else wl.d2))
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.update(_extras(args, cf, tune, ctx, dev, local, flush))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample, _ = _oracle_rows_rate(wl, args.cpu_seconds)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
     if rank == 0:
         print(json.dumps(line), flush=True)
     cf.cf_destroy(ctx)
@@ -439,19 +611,13 @@ def _batch_params(cf):
                      pimax=40.0, npibins=40)
 
 
-def run_batch(args, world, rank, local):
+def _batch_measure(args, cf, tune, dev, local, sizes, cats, steps) -> dict:
+    """Config 4 counted one catalogue at a time (one cf_count each), batched (one cell build and one
+    persistent pair kernel over all catalogues), and graph-replayed; device-resident inputs."""
     import numpy as np
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_1911_03545_gb300 as cf
-    from paper_1911_03545_gb300 import tune
-
-    dev = torch.device(f"cuda:{local}")
-    torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
-    sizes, cats = _batch_setup(args.ncat, args.batch_min, args.batch_max)
     p = _batch_params(cf)
     pts = [_points(c, False, cf, dev) for c in cats]
     ctx = cf.cf_create(local, stream)
@@ -464,11 +630,10 @@ def run_batch(args, world, rank, local):
     t0 = time.perf_counter()
     singles = [cf.cf_count(ctx, p, q) for q in pts]
     t_single = time.perf_counter() - t0
-    pair_ms_single = 0.0
     # batched: one cell build + one persistent pair kernel over all catalogues
     outs = cf.cf_batch_count(ctx, p, pts)
     times, pair_ms = [], []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, steps)):
         t0 = time.perf_counter()
         outs = cf.cf_batch_count(ctx, p, pts)
         times.append(time.perf_counter() - t0)
@@ -477,57 +642,74 @@ def run_batch(args, world, rank, local):
     # graph-captured replay of the same batch
     cf.cf_batch_capture(ctx, p, pts)
     gtimes = []
-    for _ in range(max(1, args.steps)):
+    for _ in range(max(1, steps)):
         t0 = time.perf_counter()
         gouts = cf.cf_batch_replay(ctx, p, len(pts))
         gtimes.append(time.perf_counter() - t0)
-    parity = all(np.array_equal(a["npairs"], b["npairs"]) and np.array_equal(a["npairs"], g["npairs"])
-                 for a, b, g in zip(singles, outs, gouts))
-    t_batch = min(times)
-    t_graph = min(gtimes)
-    best = min(t_batch, t_graph)
-    peaks = _peaks()
-    props = torch.cuda.get_device_properties(dev)
-    peak = props.multi_processor_count * 128 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / FP32_INSTR_PER_PAIR
-    achieved = st["evaluated_pairs"] / (min(pair_ms) / 1e3)
-    line = {
-        "metric": "batched catalogues/s", "value": len(pts) / best, "unit": "catalogues/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * best, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": _batch_desc(args, sizes), "name": "batch", "ncat": len(pts), "points": int(sum(sizes)),
-                   "tuned": tuned},
-        "one_at_a_time": {"value": len(pts) / t_single, "unit": "catalogues/s", "seconds": t_single},
-        "batched": {"value": len(pts) / t_batch, "seconds": t_batch},
-        "graph_replay": {"value": len(pts) / t_graph, "seconds": t_graph},
-        "speedup_vs_one_at_a_time": t_single / best,
-        "parity_batched_vs_single": parity,
-        "evaluated_pairs": int(st["evaluated_pairs"]), "work_items": int(st["work_items"]),
-        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Gpair/s",
-                     "frac": achieved / peak, "traffic": None},
-        "pair_kernel_ms": min(pair_ms), "gpu_launches": int(st["kernel_launches"]),
-    }
-    print(json.dumps(line), flush=True)
+    same = all(np.array_equal(a["npairs"], b["npairs"]) and np.array_equal(a["npairs"], g["npairs"])
+               for a, b, g in zip(singles, outs, gouts))
+    # the catalogues whose oracle histograms are stored
+    checked = {}
+    for i, c in enumerate(cats):
+        par = _parity(f"batch_{i}", outs[i], (c,))
+        if par["ok"] is not None:
+            checked[f"batch_{i}"] = par["ok"]
     cf.cf_destroy(ctx)
-    return 0
+    t_batch, t_graph = min(times), min(gtimes)
+    best = min(t_batch, t_graph)
+    peak = _peak_pairs(dev, "rppi")
+    achieved = st["evaluated_pairs"] / (min(pair_ms) / 1e3)
+    return {"ncat": len(pts), "points": int(sum(sizes)), "tuned": tuned, "t_single": t_single, "t_batch": t_batch,
+            "t_graph": t_graph, "best": best, "same": same, "golden": checked, "st": st, "pair_ms": min(pair_ms),
+            "achieved": achieved, "peak": peak}
 
 
-def run_serve(args, world, rank, local):
-    """Poisson arrivals at a fraction of the measured capacity; p50 / p99 latency."""
-    import numpy as np
+def run_batch(args, world, rank, local):
     import torch
 
     import __graft_entry__
     __graft_entry__.build()
     import paper_1911_03545_gb300 as cf
+    from paper_1911_03545_gb300 import tune
 
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
-    sizes, cats = _batch_setup(args.ncat)
+    sizes, cats = _batch_setup(args.ncat, args.batch_min, args.batch_max)
+    b = _batch_measure(args, cf, tune, dev, local, sizes, cats, args.steps)
+    n, st = b["ncat"], b["st"]
+    line = {
+        "metric": "batched catalogues/s", "value": n / b["best"], "unit": "catalogues/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": 1, "ms_per_step": 1e3 * b["best"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": _batch_desc(args, sizes), "name": "batch", "ncat": n, "points": b["points"],
+                   "tuned": b["tuned"]},
+        "one_at_a_time": {"value": n / b["t_single"], "unit": "catalogues/s", "seconds": b["t_single"]},
+        "batched": {"value": n / b["t_batch"], "seconds": b["t_batch"]},
+        "graph_replay": {"value": n / b["t_graph"], "seconds": b["t_graph"]},
+        "speedup_vs_one_at_a_time": b["t_single"] / b["best"],
+        "parity_batched_vs_single": b["same"], "parity_vs_golden": b["golden"],
+        "evaluated_pairs": int(st["evaluated_pairs"]), "work_items": int(st["work_items"]),
+        "roofline": {"bound": "alu", "achieved": b["achieved"] / 1e9, "peak": b["peak"] / 1e9, "unit": "Gpair/s",
+                     "frac": b["achieved"] / b["peak"], "traffic": None},
+        "pair_kernel_ms": b["pair_ms"], "gpu_launches": int(st["kernel_launches"]),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _serve_measure(args, cf, dev, local, cats, nreq) -> dict:
+    """Poisson arrivals at args.serve_load of the capacity measured in the same session (everything
+    submitted at once); p50 / p99 latency from submit to the poll that returns the result."""
+    import threading
+
+    import numpy as np
+    import torch
+
     p = _batch_params(cf)
     hosts = [cf.points(c.x, c.y, c.z) for c in cats]
     srv = cf.cf_server_start(local, p, args.serve_budget << 30, args.serve_slots)
 
-    def drain(tickets, t_sub, done):
+    def drain(tickets, done):
         pending = dict(tickets)
         while pending:
             for tk in list(pending):
@@ -541,19 +723,15 @@ def run_serve(args, world, rank, local):
         t0 = time.perf_counter()
         tks = {cf.cf_server_submit(srv, p, h): i for i, h in enumerate(hosts)}
         done = {}
-        drain(tks, None, done)
+        drain(tks, done)
         cap_s = time.perf_counter() - t0
     capacity = len(hosts) / cap_s
     rate = args.serve_load * capacity
     rng = np.random.Generator(np.random.PCG64(7))
-    nreq = args.serve_requests
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=nreq))
     order = rng.integers(0, len(hosts), size=nreq)
-    import threading
-    submit_t = {}
-    tickets = {}
+    submit_t, tickets, finished = {}, {}, {}
     lock = threading.Lock()
-    finished = {}
     stop = threading.Event()
 
     def poller():
@@ -583,23 +761,40 @@ def run_serve(args, world, rank, local):
     stop.set()
     th.join()
     t_total = time.perf_counter() - t_start
+    cf.cf_server_stop(srv)
     lat = np.array([finished[k][0] - submit_t[k] for k in range(nreq)]) * 1e3
     # every served result equals the batched result of the same catalogue
     ctx = cf.cf_create(local, torch.cuda.current_stream(dev))
     ref = cf.cf_batch_count(ctx, p, [_points(c, False, cf, dev) for c in cats])
     cf.cf_destroy(ctx)
     ok = all(np.array_equal(finished[k][1]["npairs"], ref[int(order[k])]["npairs"]) for k in range(nreq))
-    cf.cf_server_stop(srv)
+    return {"nreq": nreq, "t_total": t_total, "capacity": capacity, "lat": lat, "ok": ok}
+
+
+def run_serve(args, world, rank, local):
+    """Poisson arrivals at a fraction of the measured capacity; p50 / p99 latency."""
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1911_03545_gb300 as cf
+
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    sizes, cats = _batch_setup(args.ncat)
+    r = _serve_measure(args, cf, dev, local, cats, args.serve_requests)
+    lat = r["lat"]
     line = {
-        "metric": "served catalogues/s", "value": nreq / t_total, "unit": "catalogues/s", "n_gpus": 1,
-        "steps": nreq, "warmup": 2, "ms_per_step": float(np.mean(lat)), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": "served catalogues/s", "value": r["nreq"] / r["t_total"], "unit": "catalogues/s", "n_gpus": 1,
+        "steps": r["nreq"], "warmup": 2, "ms_per_step": float(np.mean(lat)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": BATCH_DESC, "name": "serve", "arrivals": "Poisson", "load": args.serve_load,
-                   "capacity_catalogues_per_s": capacity, "budget_gib": args.serve_budget, "slots": args.serve_slots,
-                   "inputs": "host numpy arrays (copied by the server)"},
+                   "capacity_catalogues_per_s": r["capacity"], "budget_gib": args.serve_budget,
+                   "slots": args.serve_slots, "inputs": "host numpy arrays (copied by the server)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p90": float(np.percentile(lat, 90)),
                        "p99": float(np.percentile(lat, 99)), "mean": float(np.mean(lat)), "max": float(np.max(lat))},
-        "results_equal_batched": ok,
+        "results_equal_batched": r["ok"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -690,6 +885,10 @@ def main(argv=None):
     ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--serve-budget", type=int, default=16, help="GiB")
     ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="measure the headline workload only (not the other configurations, batch and serving)")
+    ap.add_argument("--extra-steps", type=int, default=5, help="timed steps of each other workload")
+    ap.add_argument("--extra-requests", type=int, default=1024, help="Poisson requests of the serving run")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         args.warmup = 3

@@ -31,7 +31,7 @@ _lock = threading.Lock()
 _lib = None
 
 KINDS = {"r": 0, "rppi": 1, "wp": 2, "theta": 3, "mocks": 4}
-MODES = {"brute": 0, "zwin": 1, "rows": 2}
+MODES = {"brute": 0, "zwin": 1, "rows": 2, "zrows": 3}
 
 
 class _Params(ctypes.Structure):
@@ -132,8 +132,9 @@ def count(kind: str, edges, d1, d2=None, *, autocorr: bool, periodic: bool, box=
         r0, r1 = 0, len(a1[0])
         md = MODES[mode]
     else:
+        # a row range: every ordered pair of those rows, by brute force or through the z window
         r0, r1 = rows
-        md = MODES["rows"]
+        md = MODES["zrows"] if mode == "zwin" else MODES["rows"]
     rc = lib.or_count(ctypes.byref(p), len(a1[0]), *[_ptr(a) for a in a1], _ptr(w1),
                       n2, *[_ptr(a) for a in a2], _ptr(w2), md, int(nthreads), int(r0), int(r1),
                       npairs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _ptr(wsum), _ptr(rsum))

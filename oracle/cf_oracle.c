@@ -46,6 +46,9 @@
  *   OR_ROWS   for each i in [row_lo, row_hi) every ordered pair (i, j): j over all of the
  *             second set (cross), or all j != i plus the self pair when the first edge is 0
  *             (auto).  No doubling.  Summed over all rows this equals the full auto result.
+ *   OR_ZROWS  OR_ROWS with OR_ZWIN's window: the same pairs of the same rows, only j inside the
+ *             z window visited; bit-identical to OR_ROWS for the reason given for OR_ZWIN.  It
+ *             times the z-window oracle on a sample of rows.
  */
 #include <math.h>
 #include <stdint.h>
@@ -64,6 +67,7 @@
 #define OR_BRUTE 0
 #define OR_ZWIN 1
 #define OR_ROWS 2
+#define OR_ZROWS 3
 
 typedef struct {
     int kind;
@@ -241,7 +245,8 @@ int or_count(const or_params *in, int64_t n1, const double *x1, const double *y1
     if (autoc) { n2 = n1; x2 = x1; y2 = y1; z2 = z1; w2 = w1; }
     const int nout = or_nout(&P);
     for (int k = 0; k < nout; k++) { npairs[k] = 0; wsum[k] = 0; rsum[k] = 0; }
-    if (mode != OR_ROWS) { row_lo = 0; row_hi = n1; }
+    const int rowwise = (mode == OR_ROWS || mode == OR_ZROWS);   /* ordered pairs of a row range */
+    if (!rowwise) { row_lo = 0; row_hi = n1; }
     if (row_lo < 0) row_lo = 0;
     if (row_hi > n1) row_hi = n1;
 
@@ -250,7 +255,7 @@ int or_count(const or_params *in, int64_t n1, const double *x1, const double *y1
     double *zs = NULL;
     double zmax = or_zmax(&P);
     double Lz = P.box[2];
-    int use_window = (mode == OR_ZWIN);
+    int use_window = (mode == OR_ZWIN || mode == OR_ZROWS);
     if (use_window && P.periodic && 2.0 * zmax * (1.0 + 1e-9) >= 0.5 * Lz) use_window = 0;
     if (use_window) {
         or_zkey *keys = (or_zkey *)malloc(sizeof(or_zkey) * (size_t)(n2 > 0 ? n2 : 1));
@@ -289,7 +294,7 @@ int or_count(const or_params *in, int64_t n1, const double *x1, const double *y1
                 int64_t ra[3], rb[3];
                 int nr = 0;
                 if (!use_window) {
-                    ra[0] = (mode == OR_ROWS || !autoc) ? 0 : i + 1;
+                    ra[0] = (rowwise || !autoc) ? 0 : i + 1;
                     rb[0] = n2;
                     nr = 1;
                 } else {
@@ -306,7 +311,7 @@ int or_count(const or_params *in, int64_t n1, const double *x1, const double *y1
                     for (int64_t t = ra[q]; t < rb[q]; t++) {
                         int64_t j = use_window ? order[t] : t;
                         if (autoc) {
-                            if (mode == OR_ROWS) { if (j == i) continue; }
+                            if (rowwise) { if (j == i) continue; }
                             else if (j <= i) continue;
                         }
                         double sep = 0.0;
@@ -319,7 +324,7 @@ int or_count(const or_params *in, int64_t n1, const double *x1, const double *y1
                     }
                 }
                 /* Appendix B: the self pair of i, counted once, when the first bin starts at 0 */
-                if (autoc && mode == OR_ROWS && in->edges[0] == 0.0) {
+                if (autoc && rowwise && in->edges[0] == 0.0) {
                     double sep = 0.0;
                     int k = or_bin_pair(&P, xi, yi, zi, xi, yi, zi, &sep);
                     if (k >= 0) { hc[k] += 1; hw[k] += wi * wi; }
@@ -336,7 +341,7 @@ int or_count(const or_params *in, int64_t n1, const double *x1, const double *y1
     free(zs);
     if (status) return status;
 
-    if (autoc && mode != OR_ROWS) {
+    if (autoc && !rowwise) {
         /* Sec. 4.3: unique pairs were counted; double them */
         for (int k = 0; k < nout; k++) { npairs[k] *= 2; wsum[k] *= 2.0; rsum[k] *= 2.0; }
         /* Appendix B: add the N self pairs once if the first bin starts at 0 */

@@ -28,3 +28,29 @@ def test_batch_description_follows_the_options():
     assert min(small) >= 1e3 and max(small) <= 2e4
     d = bench._batch_desc(_args(ncat=1024, batch_min=1e3, batch_max=2e4), small)
     assert d.startswith("1024 mock catalogues") and "[1000, 20000]" in d and "5e4" not in d
+
+
+def test_parity_flag_against_the_stored_histograms():
+    """bench.py's parity flag: the stored oracle histogram itself passes, a count off by one or a
+    sum off by 2e-6 fails, and inputs that differ from the stored ones give no verdict."""
+    import json
+    import os
+
+    import numpy as np
+
+    import bench
+    from tests.golden.make_golden import fingerprint
+    wl = gen.workload("uniform_r_20k")
+    assert bench._fingerprint(wl.d1) == fingerprint(wl.d1)
+    with open(os.path.join(bench.GOLDEN, "full_uniform_r_20k.json")) as f:
+        gold = json.load(f)
+    got = {"npairs": np.asarray(gold["npairs"], dtype=np.uint64), "wsum": np.asarray(gold["wsum"])}
+    assert bench._parity("uniform_r_20k", got, (wl.d1,))["ok"] is True
+    bad = dict(got, npairs=got["npairs"].copy())
+    bad["npairs"][5] += 1
+    assert bench._parity("uniform_r_20k", bad, (wl.d1,))["ok"] is False
+    off = dict(got, wsum=got["wsum"] * (1 + 2e-6))
+    assert bench._parity("uniform_r_20k", off, (wl.d1,))["ok"] is False
+    other = gen.uniform_box(100, 250.0, 1, dtype=np.float64)
+    assert bench._parity("uniform_r_20k", got, (other,))["ok"] is None
+    assert bench._parity("no_such_workload", got, (wl.d1,))["ok"] is None

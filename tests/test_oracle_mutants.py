@@ -55,8 +55,8 @@ MUTANTS = {
     "self_pair_weight_not_squared": ("sw += w1 ? w1[i] * w1[i] : 1.0;", "sw += w1 ? w1[i] : 1.0;"),
     "rows_self_pair_weight_is_one": ("if (k >= 0) { hc[k] += 1; hw[k] += wi * wi; }",
                                      "if (k >= 0) { hc[k] += 1; hw[k] += 1.0; }"),
-    "cross_skips_first_row": ("ra[0] = (mode == OR_ROWS || !autoc) ? 0 : i + 1;",
-                              "ra[0] = (mode == OR_ROWS || !autoc) ? 1 : i + 1;"),
+    "cross_skips_first_row": ("ra[0] = (rowwise || !autoc) ? 0 : i + 1;",
+                              "ra[0] = (rowwise || !autoc) ? 1 : i + 1;"),
 }
 
 

@@ -414,3 +414,42 @@ def test_permutation_invariance(orc):
     p = np.random.Generator(np.random.PCG64(5)).permutation(d.n)
     b = oracle.count("r", e, d.subset(p), autocorr=True, periodic=True, box=40.0, lib=orc)
     assert (a["npairs"] == b["npairs"]).all()
+
+
+# ------------------------------------------------------------------------------------------
+# The z-window on a row sample (the timed CPU baseline) equals brute force on the same rows
+# ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,autocorr,periodic", [("r", True, True), ("r", False, False), ("rppi", True, True),
+                                                    ("wp", False, True), ("theta", True, False),
+                                                    ("mocks", True, False)])
+def test_zwin_rows_equal_brute_rows(orc, kind, autocorr, periodic):
+    """Rows i in [r0, r1) against every j: through the z window (mode zwin with rows) and by brute
+    force (mode rows) the counts are bit-identical (Sec. 4.6: a pair outside the window has
+    |dz| >= zmax, so it is rejected anyway) and the sums equal up to their order of addition; the
+    window's rows summed over all rows give the full ordered result."""
+    if kind == "theta":
+        d1 = gen.sphere_patch(3000, 0.0, 40.0, -10.0, 30.0, 81)
+        d2 = gen.sphere_patch(2000, 0.0, 40.0, -10.0, 30.0, 82)
+        edges, kw = gen.log_edges(0.01, 2.0, 10), {}
+    elif kind == "mocks":
+        d1 = gen.survey_cone(3000, 0.0, 30.0, 10.0, 40.0, 60.0, 90.0, 83, members=30, sigma=1.2)
+        d2 = gen.survey_cone(2000, 0.0, 30.0, 10.0, 40.0, 60.0, 90.0, 84)
+        edges, kw = gen.log_edges(0.1, 6.0, 10), dict(pimax=8.0, npibins=8)
+    else:
+        d1 = gen.clustered_box(60, 50, 1.5, 80.0, 85, dtype=np.float64)
+        d2 = gen.uniform_box(2500, 80.0, 86, dtype=np.float64)
+        edges, kw = gen.log_edges(0.1, 9.0, 12), dict(pimax=9.0, npibins=9)
+    for d in (d1, d2):
+        d.w = gen.uniform_weights(d.n, 0.5, 1.5, 87).astype(np.float64)
+    kw.update(autocorr=autocorr, periodic=periodic, box=80.0, weighted=True, ravg=True, lib=orc)
+    other = None if autocorr else d2
+    for r0, r1 in ((0, 200), (1111, 1500), (d1.n - 150, d1.n)):
+        z = oracle.count(kind, edges, d1, other, rows=(r0, r1), mode="zwin", **kw)
+        b = oracle.count(kind, edges, d1, other, rows=(r0, r1), mode="rows", **kw)
+        assert np.array_equal(z["npairs"], b["npairs"])
+        np.testing.assert_allclose(z["wsum"], b["wsum"], rtol=1e-12, atol=0)
+        np.testing.assert_allclose(z["rsum"], b["rsum"], rtol=1e-12, atol=0)
+    full = oracle.count(kind, edges, d1, other, mode="zwin", **kw)
+    allrows = oracle.count(kind, edges, d1, other, rows=(0, d1.n), mode="zwin", **kw)
+    assert np.array_equal(full["npairs"], allrows["npairs"])
