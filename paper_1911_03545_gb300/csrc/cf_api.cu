@@ -133,6 +133,24 @@ int CfCtx::ensure_upload(size_t bytes)
     return CF_OK;
 }
 
+int CfCtx::ensure_bbox_host(size_t bytes)
+{
+    if (hbb_cap >= bytes) return CF_OK;
+    if (hbb) {
+        cudaStreamSynchronize(stream);
+        cudaFreeHost(hbb);
+    }
+    hbb = nullptr;
+    const size_t want = std::max<size_t>(bytes, 4096);
+    if (cudaMallocHost(&hbb, want) != cudaSuccess) {
+        cudaGetLastError();
+        hbb_cap = 0;
+        return fail(CF_ERR_OOM, "pinned host staging allocation failed");
+    }
+    hbb_cap = want;
+    return CF_OK;
+}
+
 void CfCtx::drop_graph()
 {
     if (graph_exec) cudaGraphExecDestroy(graph_exec);
@@ -149,6 +167,7 @@ CfCtx::~CfCtx()
         if (B.p) cudaFree(B.p);
     if (hpin) cudaFreeHost(hpin);
     if (hup) cudaFreeHost(hup);
+    if (hbb) cudaFreeHost(hbb);
     for (auto &e : ev)
         if (e) cudaEventDestroy(e);
 }
@@ -173,6 +192,47 @@ static int check_points(CfCtx *C, const cf_params *p, const cf_points *d)
         if (rc_) return rc_;   \
     } while (0)
 #define CF_CU(x, what) CF_TRY(C->cuda((x), what))
+
+// The bbox pass's readback (CFB_BBOX_WORDS per point set): reject non-finite values and periodic
+// positions outside [0, L]; record each set's weight range and the union of the sets' boxes, the
+// largest | |v|^2 - 1 | and the smallest |v|^2.
+static int cf_check_bbox(CfCtx *C, CfRun &R, const unsigned long long *bb, double bbox[6], double &norm_dev,
+                         double &vmin2)
+{
+    const cf_params *p = &R.p;
+    const size_t bbw = CFB_BBOX_WORDS;
+    for (int a = 0; a < 6; a++) bbox[a] = a < 3 ? INFINITY : -INFINITY;
+    norm_dev = 0.0;
+    vmin2 = INFINITY;
+    R.wmin.assign(R.nsets, INFINITY);
+    R.wmax.assign(R.nsets, 0.0);
+    R.wneg = false;
+    for (int s = 0; s < R.nsets; s++) {
+        if (R.sets[s].n == 0) continue;
+        const unsigned long long *b = bb + bbw * s;
+        if (b[6]) return C->fail(CF_ERR_ARG, "non-finite coordinate or weight");
+        if (R.sets[s].w) {
+            if (b[9] != ~0ull) std::memcpy(&R.wmin[s], &b[9], 8);
+            std::memcpy(&R.wmax[s], &b[10], 8);
+            R.wneg = R.wneg || b[11] != 0;
+        }
+        double nd, r2;
+        std::memcpy(&nd, &b[7], 8);
+        std::memcpy(&r2, &b[8], 8);
+        norm_dev = std::max(norm_dev, nd);
+        vmin2 = std::min(vmin2, r2);
+        for (int a = 0; a < 3; a++) {
+            double lo = dkey_to_double(b[a]), hi = dkey_to_double(b[3 + a]);
+            if (p->periodic && (lo < 0.0 || hi > p->box[a]))
+                return C->fail(CF_ERR_ARG, "periodic positions must lie in [0, box] (axis " + std::to_string(a) + ")");
+            bbox[a] = std::min(bbox[a], lo);
+            bbox[3 + a] = std::max(bbox[3 + a], hi);
+        }
+    }
+    for (int a = 0; a < 3; a++)
+        if (!(bbox[a] <= bbox[3 + a])) { bbox[a] = 0.0; bbox[3 + a] = 0.0; }
+    return CF_OK;
+}
 
 int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &pts,
                const std::vector<CfJobDesc> &jobs, CfRun &R)
@@ -261,42 +321,32 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_CU(cfb_bbox((const CfSetDesc *)C->buf[B_SETS].p, nsets, std::max<int64_t>(R.nmax, 1),
                    (unsigned long long *)C->buf[B_BBOX].p, st), "bbox kernel");
     C->launches = 1;
-    CF_CU(cudaMemcpyAsync(C->hpin, C->buf[B_BBOX].p, 8 * bbw * (size_t)nsets, cudaMemcpyDeviceToHost, st),
-          "bbox readback");
-    CF_CU(cudaStreamSynchronize(st), "bbox sync");
+    // Periodic inputs whose sums need no weight range (no fixed-point per-warp sums) are planned from
+    // the box alone; their bbox readback is checked after the call's final synchronisation instead
+    // of waiting for it here.  Invalid data cannot fault in the meantime: cell indices clamp to the
+    // grid and a non-finite separation fails every cut.
+    const bool warp_sums = (p->kind == CF_DD_RPPI || p->kind == CF_DD_RPPI_MOCKS) &&
+                           (p->weight == CF_W_PAIR_PRODUCT || p->output_ravg);
+    R.bbox_deferred = p->periodic && !warp_sums && !C->capturing;
     double bbox[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     double norm_dev = 0.0;   // largest | |v|^2 - 1 | over the points
     double vmin2 = INFINITY;  // smallest |v|^2 over the points
-    R.wmin.assign(nsets, INFINITY);
-    R.wmax.assign(nsets, 0.0);
-    R.wneg = false;
-    {
-        const unsigned long long *bb = (const unsigned long long *)C->hpin;
-        for (int s = 0; s < nsets; s++) {
-            if (R.sets[s].n == 0) continue;
-            const unsigned long long *b = bb + bbw * s;
-            if (b[6]) return C->fail(CF_ERR_ARG, "non-finite coordinate or weight");
-            if (R.sets[s].w) {
-                if (b[9] != ~0ull) std::memcpy(&R.wmin[s], &b[9], 8);
-                std::memcpy(&R.wmax[s], &b[10], 8);
-                R.wneg = R.wneg || b[11] != 0;
-            }
-            double nd, r2;
-            std::memcpy(&nd, &b[7], 8);
-            std::memcpy(&r2, &b[8], 8);
-            norm_dev = std::max(norm_dev, nd);
-            vmin2 = std::min(vmin2, r2);
-            for (int a = 0; a < 3; a++) {
-                double lo = dkey_to_double(b[a]), hi = dkey_to_double(b[3 + a]);
-                if (p->periodic && (lo < 0.0 || hi > p->box[a]))
-                    return C->fail(CF_ERR_ARG,
-                                   "periodic positions must lie in [0, box] (axis " + std::to_string(a) + ")");
-                bbox[a] = std::min(bbox[a], lo);
-                bbox[3 + a] = std::max(bbox[3 + a], hi);
-            }
+    if (R.bbox_deferred) {
+        CF_TRY(C->ensure_bbox_host(8 * bbw * (size_t)nsets));
+        CF_CU(cudaMemcpyAsync(C->hbb, C->buf[B_BBOX].p, 8 * bbw * (size_t)nsets, cudaMemcpyDeviceToHost, st),
+              "bbox readback");
+        R.wmin.assign(nsets, INFINITY);
+        R.wmax.assign(nsets, 0.0);
+        R.wneg = false;
+        for (int a = 0; a < 3; a++) {
+            bbox[a] = 0.0;
+            bbox[3 + a] = p->box[a];
         }
-        for (int a = 0; a < 3; a++)
-            if (!(bbox[a] <= bbox[3 + a])) { bbox[a] = 0.0; bbox[3 + a] = 0.0; }
+    } else {
+        CF_CU(cudaMemcpyAsync(C->hpin, C->buf[B_BBOX].p, 8 * bbw * (size_t)nsets, cudaMemcpyDeviceToHost, st),
+              "bbox readback");
+        CF_CU(cudaStreamSynchronize(st), "bbox sync");
+        CF_TRY(cf_check_bbox(C, R, (const unsigned long long *)C->hpin, bbox, norm_dev, vmin2));
     }
 
     // ---- plan ----
@@ -367,6 +417,8 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     const size_t norigin = D.ang ? 3 * (size_t)D.g.ncell : H.origin.size();
     CF_TRY(C->ensure(B_ORIGIN, sizeof(double) * norigin));
     D.origin = (const double *)C->buf[B_ORIGIN].p;
+    CF_TRY(C->ensure(B_ORIGIN32, sizeof(float) * std::max<size_t>(1, norigin)));
+    D.origin32 = (const float *)C->buf[B_ORIGIN32].p;
     CF_TRY(C->ensure(B_BANDS, sizeof(CfBand) * std::max<size_t>(1, H.bands.size())));
     D.band = (const CfBand *)C->buf[B_BANDS].p;
     CF_TRY(C->ensure(B_PLAN, sizeof(CfDevPlan)));
@@ -406,6 +458,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
         };
         const Up ups[] = {
             {C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size()},
+            {C->buf[B_ORIGIN32].p, H.origin32.data(), sizeof(float) * H.origin32.size()},
             {C->buf[B_BANDS].p, H.bands.data(), sizeof(CfBand) * H.bands.size()},
             {C->buf[B_PLAN].p, &D, sizeof(CfDevPlan)},
             {C->buf[B_LUT].p, H.lut.data(), sizeof(uint16_t) * H.lut.size()},
@@ -491,7 +544,8 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     uint32_t *misc = (uint32_t *)C->buf[B_MISC].p;
     uint32_t *fstart = (uint32_t *)C->buf[B_FSTART].p;
     if (R.plan.d.ang) {
-        CF_CU(cfb_ang_origins(dplan, R.plan.d.g.ncell, (double *)C->buf[B_ORIGIN].p, st), "cell origins");
+        CF_CU(cfb_ang_origins(dplan, R.plan.d.g.ncell, (double *)C->buf[B_ORIGIN].p, (float *)C->buf[B_ORIGIN32].p, st),
+              "cell origins");
         C->launches += 1;
     }
     CF_CU(cudaMemsetAsync(cnt, 0, 4 * (size_t)R.nfine, st), "memset counts");
@@ -776,6 +830,11 @@ int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &p
     for (int attempt = 0; attempt < 4; attempt++) {
         CF_TRY(cf_enqueue_count(C, R, true));
         CF_CU(cudaStreamSynchronize(st), "count sync");
+        if (R.bbox_deferred && attempt == 0) {
+            // the inputs' check that a periodic call did not wait for (its plan needs only L)
+            double bb[6], nd, v2;
+            CF_TRY(cf_check_bbox(C, R, (const unsigned long long *)C->hbb, bb, nd, v2));
+        }
         int retry = 0;
         CF_TRY(cf_finish(C, R, res, &retry));
         if (!retry) {

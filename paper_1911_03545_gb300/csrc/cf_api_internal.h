@@ -12,7 +12,7 @@
 enum CfBuf {
     B_IN, B_SETS, B_BBOX, B_PLAN, B_LUT, B_FINE, B_STENCIL, B_JOBS, B_CNT, B_CSTART, B_CELLID, B_SLOT,
     B_PA, B_PB, B_PLO, B_ORIG, B_SCAN, B_ICNT, B_IOFF, B_ITEMS, B_HCNT, B_HW, B_HR, B_QUEUE, B_WSQ, B_MISC, B_ORIGIN,
-    B_CBOX, B_FSTART, B_BANDS, B_COUNT_
+    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_COUNT_
 };
 
 struct DeviceGuard {
@@ -58,6 +58,7 @@ struct CfRun {
     double bbox[6] = {0, 0, 0, 0, 0, 0};   // union of the sets' boxes the plan was made for
     double vmin2 = 0.0;            // smallest |v|^2 over the points (mocks: the plan's near-observer test)
     bool angular = false;          // DD(theta) on the angular grid (needs unit vectors)
+    bool bbox_deferred = false;    // periodic call planned from L: its bbox is checked after the final sync
     size_t bb_off = 0;             // captured graph: offset of its bbox readback in pinned memory
     std::vector<double> wmin, wmax;   // per point set: smallest nonzero |w| (inf: none), largest |w|
     bool wneg = false;                // some weight is negative
@@ -81,6 +82,8 @@ struct CfCtx {
     Buf buf[B_COUNT_];
     void *hpin = nullptr;
     size_t hpin_cap = 0;
+    void *hbb = nullptr;           // pinned bbox readback checked after the final synchronisation
+    size_t hbb_cap = 0;
     void *hup = nullptr;           // pinned staging of the plan, tables and descriptors uploaded per call
     size_t hup_cap = 0;
     uint32_t items_hint = 0;       // work-list capacity for the next call with plan `items_key`
@@ -105,6 +108,7 @@ struct CfCtx {
     int ensure(int b, size_t bytes);
     int ensure_host(size_t bytes);
     int ensure_upload(size_t bytes);
+    int ensure_bbox_host(size_t bytes);
     void drop_graph();
     ~CfCtx();
 };

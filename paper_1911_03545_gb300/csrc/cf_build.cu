@@ -196,8 +196,21 @@ __global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSet
     const CfSetDesc S = sets[blockIdx.y];
     const CfGrid &g = plan->g;
     const uint32_t ns = (uint32_t)(sub * sub * sub);
+    const bool f32 = S.dtype == CF_F32;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double x[3] = {cf_load(S.x, S.dtype, i), cf_load(S.y, S.dtype, i), cf_load(S.z, S.dtype, i)};
+        // float32 inputs stay float32 here (the FP64 pipe runs at a small fraction of the FP32 rate)
+        float xf[3];
+        double xd[3] = {0.0, 0.0, 0.0};
+        if (f32) {
+            xf[0] = ((const float *)S.x)[i];
+            xf[1] = ((const float *)S.y)[i];
+            xf[2] = ((const float *)S.z)[i];
+        } else {
+            xd[0] = ((const double *)S.x)[i];
+            xd[1] = ((const double *)S.y)[i];
+            xd[2] = ((const double *)S.z)[i];
+            for (int a = 0; a < 3; a++) xf[a] = (float)xd[a];
+        }
         uint32_t sa[3] = {0u, 0u, 0u};
         uint32_t c;
         if (plan->ang) {
@@ -205,9 +218,8 @@ __global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSet
             // length: independent of |v| and well conditioned at the poles), then right-ascension
             // cell in [0, 2 pi).  Float32 is enough: any cell choice is correct as long as the point
             // lies in the cell's box, whose margin (2e-6) is far above these ~1e-7 errors.
-            const float xf = (float)x[0], yf = (float)x[1], zf = (float)x[2];
-            const double dec = (double)atan2f(zf, sqrtf(xf * xf + yf * yf));
-            double ra = (double)atan2f(yf, xf);
+            const double dec = (double)atan2f(xf[2], sqrtf(xf[0] * xf[0] + xf[1] * xf[1]));
+            double ra = (double)atan2f(xf[1], xf[0]);
             if (ra < 0.0) ra += 2.0 * M_PI;
             int b = (int)floor((dec - plan->adlo) / plan->ah);
             b = b < 0 ? 0 : (b > plan->nband - 1 ? plan->nband - 1 : b);
@@ -224,11 +236,26 @@ __global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSet
         } else {
             int ia[3];
             for (int a = 0; a < 3; a++) {
-                const double t = (x[a] - g.lo[a]) * g.inv[a];
-                int cc = (int)floor(t);
+                // the cell coordinate in float32 decides the cell as the FP64 one would, unless it
+                // lies within the plan's guard of a cell boundary: then (and for float64 inputs) FP64
+                float fr;
+                int cc;
+                const float t32 = (xf[a] - plan->lo32[a]) * plan->inv32[a];
+                const float f32c = floorf(t32), r32 = t32 - f32c;
+                if (f32 && r32 >= plan->cguard[a] && r32 <= 1.0f - plan->cguard[a]) {
+                    cc = (int)f32c;
+                    fr = r32;
+                } else {
+                    const double x = f32 ? (double)xf[a] : xd[a];
+                    const double t = (x - g.lo[a]) * g.inv[a];
+                    const double ft = floor(t);
+                    cc = (int)ft;
+                    fr = (float)(t - ft);
+                }
                 cc = cc < 0 ? 0 : (cc > g.n[a] - 1 ? g.n[a] - 1 : cc);
                 ia[a] = cc;
-                const int s = (int)((t - (double)cc) * sub);
+                // the sub-cell orders points inside the cell; it does not change any result
+                const int s = (int)(fr * (float)sub);
                 sa[a] = (uint32_t)(s < 0 ? 0 : (s > sub - 1 ? sub - 1 : s));
             }
             c = (uint32_t)((ia[0] * g.n[1] + ia[1]) * g.n[2] + ia[2]);
@@ -270,7 +297,8 @@ __device__ double cf_origin_of_interval(double lo, double hi)
     return lo > 0.0 ? floor(lo / sp) * sp : ceil(hi / sp) * sp;
 }
 
-__global__ void cf_ang_origin_kernel(const CfDevPlan *__restrict__ plan, int ncell, double *__restrict__ origin)
+__global__ void cf_ang_origin_kernel(const CfDevPlan *__restrict__ plan, int ncell, double *__restrict__ origin,
+                                     float *__restrict__ origin32)
 {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
         const int b = cf_band_of(plan, c);
@@ -284,8 +312,11 @@ __global__ void cf_ang_origin_kernel(const CfDevPlan *__restrict__ plan, int nce
         cf_trig_range(r * B.w, (r + 1) * B.w, 0, sa0, sa1);
         const double lo[3] = {ca0 >= 0 ? cmin * ca0 : cmax * ca0, sa0 >= 0 ? cmin * sa0 : cmax * sa0, zmn};
         const double hi[3] = {ca1 >= 0 ? cmax * ca1 : cmin * ca1, sa1 >= 0 ? cmax * sa1 : cmin * sa1, zmx};
-        for (int a = 0; a < 3; a++)
-            origin[3 * c + a] = cf_origin_of_interval(lo[a] - 1e-3 * fabs(lo[a]) - 2e-6, hi[a] + 1e-3 * fabs(hi[a]) + 2e-6);
+        for (int a = 0; a < 3; a++) {
+            const double o = cf_origin_of_interval(lo[a] - 1e-3 * fabs(lo[a]) - 2e-6, hi[a] + 1e-3 * fabs(hi[a]) + 2e-6);
+            origin[3 * c + a] = o;
+            origin32[3 * c + a] = (float)o;     // exact: a multiple of the float32 spacing
+        }
     }
 }
 
@@ -405,6 +436,21 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
         int iy = (c / g.n[2]) % g.n[1];
         int ix = c / (g.n[2] * g.n[1]);
         int64_t dst = fstart[k] + slot[p];
+        const bool mocks = plan->kind == CF_DD_RPPI_MOCKS;
+        if (S.dtype == CF_F32 && !lo) {
+            // float32 inputs: x - o is exact in float32 (o is a multiple of the float32 spacing at
+            // the cell's magnitude and lies between 0 and x), the same value the FP64 form rounds to
+            const float vx = ((const float *)S.x)[i], vy = ((const float *)S.y)[i], vz = ((const float *)S.z)[i];
+            const float xf = vx - cf_cell_origin32(plan, 0, (int)c, ix);
+            const float yf = vy - cf_cell_origin32(plan, 1, (int)c, iy);
+            const float zf = vz - cf_cell_origin32(plan, 2, (int)c, iz);
+            const float w = S.w ? ((const float *)S.w)[i] : 1.0f;
+            const float ax = mocks ? vx : -xf, ay = mocks ? vy : -yf, az = mocks ? vz : -zf;
+            pa[dst] = make_float4(-xf, ax, -yf, ay);
+            pb[dst] = make_float4(-zf, az, w, w);
+            orig[dst] = (uint32_t)i;
+            continue;
+        }
         const double vx = cf_load(S.x, S.dtype, i), vy = cf_load(S.y, S.dtype, i), vz = cf_load(S.z, S.dtype, i);
         double X = vx - cf_cell_origin(plan, 0, (int)c, ix);
         double Y = vy - cf_cell_origin(plan, 1, (int)c, iy);
@@ -412,7 +458,6 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
         float xf = (float)X, yf = (float)Y, zf = (float)Z;
         float w = S.w ? (float)cf_load(S.w, S.dtype, i) : 1.0f;
         // second copies: X again, or for mocks the absolute position (its line of sight)
-        const bool mocks = plan->kind == CF_DD_RPPI_MOCKS;
         const float ax = mocks ? (float)vx : -xf, ay = mocks ? (float)vy : -yf, az = mocks ? (float)vz : -zf;
         pa[dst] = make_float4(-xf, ax, -yf, ay);
         pb[dst] = make_float4(-zf, az, w, w);
@@ -479,9 +524,8 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
     // box pruning needs the cell pair's own shift, which wrap axes (explicit minimum image) lack
     const bool prune = cbox != nullptr && !g.wrap[0] && !g.wrap[1] && !g.wrap[2];
     const bool zsep = plan->kind == CF_DD_RPPI || plan->kind == CF_WP;
-    // mocks: the line of sight varies, so only |s| < sqrt(rmax^2 + pimax^2) bounds a counted pair
-    const double e2max = plan->kind == CF_DD_RPPI_MOCKS ? plan->smax2 : plan->e2[plan->nb];
-    const double zmax = zsep ? (double)plan->pimax : 0.0;
+    // (the plan's e2max32 bounds a counted pair's squared separation: for mocks, whose line of sight
+    // varies, |s|^2 < rmax^2 + pimax^2; zmax32 bounds |dz| for rp-pi and wp)
     const int64_t nunit = (int64_t)g.ncell * plan->njobs;
     const uint32_t tile = plan->tile, jchunk = plan->jchunk;
     const uint32_t lane = threadIdx.x & 31u;
@@ -529,9 +573,9 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                 const int s = s0 + (int)lane;
                 uint32_t cnt = 0, jb = 0, nb = 0, ntj = 0, tsj = 0;
                 bool diag = false;
-                double shift[3] = {0.0, 0.0, 0.0};
+                int ct = 0, tj[3] = {0, 0, 0};
+                double delta[3] = {0.0, 0.0, 0.0};      // image of the j point: x_j + delta
                 if (s < ncand) {
-                    int ct = 0;
                     bool ok = true;
                     if (plan->ang) {
                         int q = 0, off = s;
@@ -540,24 +584,18 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                         int rr = (blo[q] + off) % Bj.nra;
                         if (rr < 0) rr += Bj.nra;
                         ct = Bj.base + rr;
-                        if (mode == 1 || prune)
-                            for (int a = 0; a < 3; a++) shift[a] = plan->origin[3 * c + a] - plan->origin[3 * ct + a];
                     } else {
-                        int tj[3];
                         for (int a = 0; a < 3; a++) {
                             int v = ci[a] + stencil[s].d[a];
-                            double delta = 0.0;        // image of the j point: x_j + delta
                             if (g.wrap[a]) {
                                 v %= g.n[a];
                             } else if (g.periodic) {
-                                if (v < 0) { v += g.n[a]; delta = -g.L[a]; }
-                                else if (v >= g.n[a]) { v -= g.n[a]; delta = g.L[a]; }
+                                if (v < 0) { v += g.n[a]; delta[a] = -g.L[a]; }
+                                else if (v >= g.n[a]) { v -= g.n[a]; delta[a] = g.L[a]; }
                             } else if (v < 0 || v >= g.n[a]) {
                                 ok = false;
                             }
                             tj[a] = v;
-                            if (ok && (mode == 1 || prune))
-                                shift[a] = cf_origin(plan, a, ci[a]) - cf_origin(plan, a, v) - delta;
                         }
                         ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
                     }
@@ -566,20 +604,24 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                             jb = cell_start[B.cbeg + ct];
                             nb = cell_start[B.cbeg + ct + 1] - jb;
                             if (nb && prune) {
-                                // separation range of the two boxes per axis under this shift; each
-                                // gap is shrunk by a margin far above the rounding of the cell-relative
-                                // coordinates, so a skipped pair is out of every bin in FP64 as well
+                                // separation range of the two boxes per axis under this shift, in
+                                // float32; each gap is shrunk by a margin above this arithmetic's
+                                // rounding and that of the cell-relative coordinates, so a skipped
+                                // pair is out of every bin in FP64 as well
                                 const float *bi = cbox + 6 * (A.cbeg + c), *bj = cbox + 6 * (B.cbeg + ct);
-                                double s2 = 0.0, gz = 0.0;
+                                float s2 = 0.f, gz = 0.f;
                                 for (int a = 0; a < 3; a++) {
-                                    const double lo = (double)bi[a] + shift[a] - (double)bj[3 + a];
-                                    const double hi = (double)bi[3 + a] + shift[a] - (double)bj[a];
-                                    double gap = lo > 0.0 ? lo : (hi < 0.0 ? -hi : 0.0);
-                                    gap = fmax(0.0, gap - 1e-5 * g.width[a]);
+                                    const float sh = plan->ang ? plan->origin32[3 * c + a] - plan->origin32[3 * ct + a]
+                                                               : (cf_cell_origin32(plan, a, c, ci[a]) -
+                                                                  cf_cell_origin32(plan, a, ct, tj[a])) - (float)delta[a];
+                                    const float lo = (bi[a] + sh) - bj[3 + a];
+                                    const float hi = (bi[3 + a] + sh) - bj[a];
+                                    float gap = lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
+                                    gap = fmaxf(0.f, gap - plan->pmargin[a]);
                                     if (zsep && a == 2) gz = gap;
-                                    else s2 += gap * gap;
+                                    else s2 = fmaf(gap, gap, s2);
                                 }
-                                if (s2 >= e2max || (zsep && gz >= zmax)) nb = 0;
+                                if (s2 >= plan->e2max32 || (zsep && gz >= plan->zmax32)) nb = 0;
                             }
                             if (nb) {
                                 diag = J.autoc && ct == c;
@@ -606,10 +648,13 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                 }
                 if (mode == 1 && cnt) {
                     uint32_t o = base + total + (incl - cnt);
+                    // the item's shift in FP64, split into float32 hi + lo (Sec. 4.4 applied per cell)
                     float sh[3], sl[3];
                     for (int a = 0; a < 3; a++) {
-                        sh[a] = (float)shift[a];
-                        sl[a] = (float)(shift[a] - (double)sh[a]);
+                        const double shift = plan->ang ? plan->origin[3 * c + a] - plan->origin[3 * ct + a]
+                                                       : cf_origin(plan, a, ci[a]) - cf_origin(plan, a, tj[a]) - delta[a];
+                        sh[a] = (float)shift;
+                        sl[a] = (float)(shift - (double)sh[a]);
                     }
                     for (uint32_t a0 = 0; a0 < nti; a0++) {
                         const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
@@ -694,9 +739,9 @@ cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, 
     return cudaGetLastError();
 }
 
-cudaError_t cfb_ang_origins(const CfDevPlan *plan, int ncell, double *origin, cudaStream_t st)
+cudaError_t cfb_ang_origins(const CfDevPlan *plan, int ncell, double *origin, float *origin32, cudaStream_t st)
 {
-    cf_ang_origin_kernel<<<blocks_for(ncell, 256, 4096), 256, 0, st>>>(plan, ncell, origin);
+    cf_ang_origin_kernel<<<blocks_for(ncell, 256, 4096), 256, 0, st>>>(plan, ncell, origin, origin32);
     return cudaGetLastError();
 }
 

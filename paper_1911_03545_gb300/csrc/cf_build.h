@@ -14,7 +14,7 @@ cudaError_t cfb_bbox_init(unsigned long long *out, int nsets, cudaStream_t st);
 cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
                        uint32_t *count, uint32_t *key, uint32_t *slot, cudaStream_t st);
 // origins of the angular grid's cells (3 per cell) from their (RA, DEC) boxes
-cudaError_t cfb_ang_origins(const CfDevPlan *plan, int ncell, double *origin, cudaStream_t st);
+cudaError_t cfb_ang_origins(const CfDevPlan *plan, int ncell, double *origin, float *origin32, cudaStream_t st);
 // cell_start[c] = fstart[c * sub^3] for c in [0, ncell_all]
 cudaError_t cfb_cell_starts(const uint32_t *fstart, int64_t ncell_all, int sub, uint32_t *cell_start, cudaStream_t st);
 int64_t cfb_scan_tmp_words(int64_t n);

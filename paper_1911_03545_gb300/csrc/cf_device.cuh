@@ -75,6 +75,11 @@ __device__ __forceinline__ double cf_cell_origin(const CfDevPlan *plan, int a, i
 {
     return plan->ang ? plan->origin[3 * c + a] : plan->origin[plan->ooff[a] + ia];
 }
+// the same origin as float32 (exact)
+__device__ __forceinline__ float cf_cell_origin32(const CfDevPlan *plan, int a, int c, int ia)
+{
+    return plan->ang ? plan->origin32[3 * c + a] : plan->origin32[plan->ooff[a] + ia];
+}
 // band of a cell of the angular grid (binary search over the band bases)
 __device__ __forceinline__ int cf_band_of(const CfDevPlan *plan, int c)
 {

@@ -140,6 +140,13 @@ struct CfDevPlan {
                            // recheck when its s.s - cut_r is below cut_su (0: no candidate can be)
     float cut_su;
     double smax2;          // mocks: largest |s|^2 of a counted pair (rmax^2 + pimax^2, widened)
+    // float32 helpers of the cell build (the FP64 pipe runs at a small fraction of the FP32 rate):
+    const float *origin32; // float32 copies of `origin` (exact: origins are multiples of the float32
+                           // spacing at their cell's magnitude)
+    float inv32[3], lo32[3];   // n / extent and the lower corner per axis, float32
+    float cguard[3];       // a float32 cell coordinate within cguard of an integer is recomputed in FP64
+    float pmargin[3];      // cell-pair pruning in float32: each gap is shrunk by this (its rounding)
+    float e2max32, zmax32; // the largest squared separation / |dz| of a counted pair, rounded up
     double e2[CF_MAX_BINS + 1];     // squared edges (FP64, host-computed)
     double pe[CF_MAX_PIBINS + 1];   // pi edges (mocks: squared pi edges)
 };

@@ -448,6 +448,37 @@ int cfp_make_plan(const cf_params *p, const double bbox[6], int64_t npoints, int
         }
     }
 
+    // ---- float32 helpers of the cell build ----
+    // The build's cell index, cell-relative coordinates and cell-pair pruning run in float32 for
+    // float32 inputs; these bounds keep every decision the FP64 one (or a conservative one).
+    H.origin32.assign(H.origin.begin(), H.origin.end());   // exact: snapped to the float32 grid
+    {
+        auto ceilf32 = [](double v) {
+            const uint32_t b = cfp_float_ceil_bits(v);
+            float f;
+            std::memcpy(&f, &b, 4);
+            return f;
+        };
+        for (int a = 0; a < 3; a++) {
+            const double amax = D.ang ? 1.01 : std::max(std::fabs(G.lo[a]), std::fabs(G.lo[a] + extent[a]));
+            D.inv32[a] = (float)G.inv[a];
+            D.lo32[a] = (float)G.lo[a];
+            // t32 = fl(fl(x - lo32) * inv32) is within 2^-24 (inv |lo| + 3 n + 1) of the exact cell
+            // coordinate (x - lo) * n / extent of a point inside the grid; the kernel redoes in
+            // FP64 any t32 within four times that of an integer (a cell boundary)
+            D.cguard[a] = ceilf32(4 * U32 * (G.inv[a] * std::fabs(G.lo[a]) + 3.0 * G.n[a] + 1.0));
+            // the gap of two cell boxes under a shift, fl(fl(b_i + s) - b_j) with
+            // s = fl(fl(o_i - o_j) - fl(delta)), carries at most 6 roundings at magnitudes up to
+            // 2 amax + 2 L + 4 w (and fl(delta) is within 2^-24 L of delta); on top of the FP64
+            // form's margin of 1e-5 w
+            D.pmargin[a] = ceilf32(1e-5 * G.width[a] + 8 * U32 * (2 * amax + 2 * G.L[a] + 4 * G.width[a]));
+        }
+        // squared gaps summed in float32 are within 3 roundings below the exact sum of the shrunk
+        // gaps' squares: prune only at or above the bound raised by 2^-20
+        D.e2max32 = ceilf32((mocks ? D.smax2 : D.e2[D.nb]) * (1.0 + 1.0 / 1048576.0));
+        D.zmax32 = ceilf32(p->pimax * (1.0 + 1.0 / 1048576.0));
+    }
+
     // ---- FP32 error model: a per-axis bound on the separation's error, then a band per edge ----
     // stored cell-relative coordinates X are exact for float32 inputs (snapped origins);
     // float64 inputs round to float32 (epsX), or keep a lo part when ravg is requested.

@@ -12,6 +12,7 @@ struct CfHostPlan {
     std::vector<CfStencil> stencil;    // neighbour offsets after pruning
     std::vector<double> origin;        // cell origins per axis (see cfp_origin), n0 + n1 + n2 values
                                        // (angular grid: 3 per cell)
+    std::vector<float> origin32;       // the same origins as float32 (exact)
     std::vector<CfBand> bands;         // angular grid: the DEC bands
     double W[3];                       // largest separation a counted pair can have, per axis
     double band_r[CF_MAX_BINS + 1];    // FP32 error band of each squared edge
