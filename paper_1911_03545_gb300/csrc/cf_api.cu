@@ -439,11 +439,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.nfine, R.nunit))));
     CF_TRY(C->ensure(B_ICNT, 4 * (size_t)std::max<int64_t>(R.nunit, 1)));
     CF_TRY(C->ensure(B_IOFF, 4 * (size_t)(R.nunit + 1)));
-    CF_TRY(C->ensure(B_MISC, 4096));
-    CF_TRY(C->ensure(B_HCNT, 8 * R.hsz));
-    CF_TRY(C->ensure(B_HW, 8 * R.hsz));
-    CF_TRY(C->ensure(B_HR, 8 * R.hsz));
-    CF_TRY(C->ensure(B_WSQ, 8 * (size_t)nsets));
+    CF_TRY(C->ensure(B_OUT, readback_bytes(R)));
     R.qcap = C->opt[CF_OPT_QUEUE] > 0 ? (uint32_t)std::min<int64_t>(CF_MAX_ENTRIES, C->opt[CF_OPT_QUEUE])
                                       : C->qcap_default;
     CF_TRY(C->ensure(B_QUEUE, 16 * (size_t)R.qcap));
@@ -541,7 +537,7 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     const CfSetDesc *dsets = (const CfSetDesc *)C->buf[B_SETS].p;
     const CfJobDesc *djobs = (const CfJobDesc *)C->buf[B_JOBS].p;
     uint32_t *cnt = (uint32_t *)C->buf[B_CNT].p, *cstart = (uint32_t *)C->buf[B_CSTART].p;
-    uint32_t *misc = (uint32_t *)C->buf[B_MISC].p;
+    char *out = (char *)C->buf[B_OUT].p;
     uint32_t *fstart = (uint32_t *)C->buf[B_FSTART].p;
     if (R.plan.d.ang) {
         CF_CU(cfb_ang_origins(dplan, R.plan.d.g.ncell, (double *)C->buf[B_ORIGIN].p, (float *)C->buf[B_ORIGIN32].p, st),
@@ -549,7 +545,7 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
         C->launches += 1;
     }
     CF_CU(cudaMemsetAsync(cnt, 0, 4 * (size_t)R.nfine, st), "memset counts");
-    CF_CU(cudaMemsetAsync(misc, 0, 4096, st), "memset misc");
+    CF_CU(cudaMemsetAsync(out, 0, OUT_EVAL, st), "memset work-list counters");
     CF_CU(cfb_assign(dplan, dsets, R.nsets, R.np, R.sub, cnt, (uint32_t *)C->buf[B_CELLID].p,
                      (uint32_t *)C->buf[B_SLOT].p, st),
           "assign");
@@ -570,12 +566,11 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     R.cbox = cbox;
     uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
     // the work list's length in 64 bits, next to its 32-bit scan (checked in cf_finish)
-    unsigned long long *items64 = (unsigned long long *)(misc + 18);
-    CF_CU(cudaMemsetAsync(items64, 0, 8, st), "memset");
+    unsigned long long *items64 = (unsigned long long *)(out + OUT_ITEMS64);
     CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, cstart, cbox, R.nunit, 0, icnt, nullptr,
                     nullptr, 0, items64, st),
           "items count");
-    CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, st), "scan items");
+    CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, st, (uint32_t *)(out + OUT_NITEMS)), "scan items");
     C->launches += 10;   // assign, 3 scan, cell starts, scatter, items count, 3 scan
     return CF_OK;
 }
@@ -637,20 +632,19 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     const CfSetDesc *dsets = (const CfSetDesc *)C->buf[B_SETS].p;
     const CfJobDesc *djobs = (const CfJobDesc *)C->buf[B_JOBS].p;
     const CfDevPlan &D = R.plan.d;
-    uint32_t *misc = (uint32_t *)C->buf[B_MISC].p;
+    char *out = (char *)C->buf[B_OUT].p;
     uint32_t *ioff = (uint32_t *)C->buf[B_IOFF].p;
-    unsigned long long *evaluated = (unsigned long long *)(misc + 16);
-    CF_CU(cudaMemsetAsync(misc, 0, 16, st), "memset");
-    CF_CU(cudaMemsetAsync(evaluated, 0, 8, st), "memset");
-    CF_CU(cudaMemsetAsync(misc + 20, 0, 8, st), "memset");     // recheck queue count (64-bit)
+    unsigned long long *evaluated = (unsigned long long *)(out + OUT_EVAL);
+    const size_t hsz = R.hsz;
+    unsigned long long *hcnt = (unsigned long long *)(out + OUT_HIST);
+    double *hw = (double *)(out + OUT_HIST + 8 * hsz), *hr = (double *)(out + OUT_HIST + 16 * hsz);
+    double *wsq = (double *)(out + OUT_HIST + 24 * hsz);
+    // evaluated pairs, the work cursor, the queue length, the histograms and w^2 sums: one memset
+    CF_CU(cudaMemsetAsync(out + OUT_EVAL, 0, readback_bytes(R) - OUT_EVAL, st), "memset");
     CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, (const uint32_t *)C->buf[B_CSTART].p,
                     R.cbox, R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap,
                     evaluated, st),
           "items emit");
-    CF_CU(cudaMemsetAsync(C->buf[B_HCNT].p, 0, 8 * R.hsz, st), "memset");
-    CF_CU(cudaMemsetAsync(C->buf[B_HW].p, 0, 8 * R.hsz, st), "memset");
-    CF_CU(cudaMemsetAsync(C->buf[B_HR].p, 0, 8 * R.hsz, st), "memset");
-    CF_CU(cudaMemsetAsync(C->buf[B_WSQ].p, 0, 8 * (size_t)R.nsets, st), "memset");
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[1], st, C->capturing ? cudaEventRecordExternal : 0), "event");
     CfPairArgs &A = R.args;
     std::memset(&A, 0, sizeof(A));
@@ -661,15 +655,15 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     A.nitems_dev = ioff + R.nunit;
     A.items_cap = R.items_cap;
     A.qcap = R.qcap;
-    A.cursor = misc;
-    A.qcount = (unsigned long long *)(misc + 20);
+    A.cursor = (uint32_t *)(out + OUT_CURSOR);
+    A.qcount = (unsigned long long *)(out + OUT_QCOUNT);
     A.pa = (const ulonglong2 *)C->buf[B_PA].p;
     A.pb = (const ulonglong2 *)C->buf[B_PB].p;
     A.plo = (const ulonglong2 *)C->buf[B_PLO].p;
     A.orig = (const uint32_t *)C->buf[B_ORIG].p;
-    A.hcnt = (unsigned long long *)C->buf[B_HCNT].p;
-    A.hw = (double *)C->buf[B_HW].p;
-    A.hr = (double *)C->buf[B_HR].p;
+    A.hcnt = hcnt;
+    A.hw = hw;
+    A.hr = hr;
     A.queue = (uint4 *)C->buf[B_QUEUE].p;
     for (int a = 0; a < 3; a++) A.L[a] = D.g.wrap[a] ? (float)D.g.L[a] : 0.f;
     A.nb = D.nb;
@@ -699,25 +693,13 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[2], st, C->capturing ? cudaEventRecordExternal : 0), "event");
     CF_CU(cfp_launch_recheck(dplan, dsets, djobs, A.queue, A.qcount, R.qcap, A.hcnt, A.hw, A.hr, C->num_sms, st), "recheck");
     if (R.self_pairs && D.weighted) {
-        CF_CU(cfb_wsq(dsets, R.nsets, R.np, (double *)C->buf[B_WSQ].p, st), "self-pair weights");
+        CF_CU(cfb_wsq(dsets, R.nsets, R.np, wsq, st), "self-pair weights");
         C->launches++;
     }
     C->launches += 2 + (R.items_cap > 0 ? 1 : 0);   // items emit, recheck, pair
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[3], st, C->capturing ? cudaEventRecordExternal : 0), "event");
-    // readback: [cursor, pad, items total, pad] [evaluated] [items total, 64-bit] [queued pairs, 64-bit]
-    // [hcnt] [hw] [hr] [wsq]
-    char *h = (char *)C->hpin;
-    const size_t hsz = R.hsz;
-    CF_CU(cudaMemcpyAsync(h, misc, 8, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 8, ioff + R.nunit, 4, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 16, evaluated, 8, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 24, misc + 18, 8, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 32, misc + 20, 8, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 64, C->buf[B_HCNT].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 64 + 8 * hsz, C->buf[B_HW].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 64 + 16 * hsz, C->buf[B_HR].p, 8 * hsz, cudaMemcpyDeviceToHost, st), "readback");
-    CF_CU(cudaMemcpyAsync(h + 64 + 24 * hsz, C->buf[B_WSQ].p, 8 * (size_t)R.nsets, cudaMemcpyDeviceToHost, st),
-          "readback");
+    // readback: the whole B_OUT block (counters, histograms, w^2 sums) in one copy
+    CF_CU(cudaMemcpyAsync(C->hpin, out, readback_bytes(R), cudaMemcpyDeviceToHost, st), "readback");
     return CF_OK;
 }
 
@@ -725,15 +707,15 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
 int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
 {
     const char *h = (const char *)C->hpin;
-    const unsigned long long qn = *(const unsigned long long *)(h + 32);
-    const uint32_t nitems = ((const uint32_t *)h)[2];
+    const unsigned long long qn = *(const unsigned long long *)(h + OUT_QCOUNT);
+    const uint32_t nitems = *(const uint32_t *)(h + OUT_NITEMS);
     *retry = 0;
     // work items and queue entries are indexed in 32 bits, with headroom for the grid-stride
     // loops and the work cursor's overshoot
-    if (*(const unsigned long long *)(h + 24) > CF_MAX_ENTRIES)
+    if (*(const unsigned long long *)(h + OUT_ITEMS64) > CF_MAX_ENTRIES)
         return C->fail(CF_ERR_ARG, "the work list exceeds 2^32 - 2^20 items (fewer points per call, or a coarser grid)");
     // the audit queues every evaluated pair
-    if (C->opt[CF_OPT_AUDIT] && *(const unsigned long long *)(h + 16) >= 0xF0000000ull)
+    if (C->opt[CF_OPT_AUDIT] && *(const unsigned long long *)(h + OUT_EVAL) >= 0xF0000000ull)
         return C->fail(CF_ERR_ARG, "CF_OPT_AUDIT needs fewer than 2^32 - 2^28 evaluated pairs");
     if (qn > CF_MAX_ENTRIES)
         return C->fail(CF_ERR_ARG, "more than 2^32 - 2^20 pairs lie within the FP32 error bands of the edges "
@@ -750,10 +732,10 @@ int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
         return CF_OK;
     }
     const size_t nslot = R.nslot, hsz = R.hsz;
-    const unsigned long long *hc = (const unsigned long long *)(h + 64);
-    const double *hw = (const double *)(h + 64 + 8 * hsz);
-    const double *hr = (const double *)(h + 64 + 16 * hsz);
-    const double *wsq = (const double *)(h + 64 + 24 * hsz);
+    const unsigned long long *hc = (const unsigned long long *)(h + OUT_HIST);
+    const double *hw = (const double *)(h + OUT_HIST + 8 * hsz);
+    const double *hr = (const double *)(h + OUT_HIST + 16 * hsz);
+    const double *wsq = (const double *)(h + OUT_HIST + 24 * hsz);
     const CfDevPlan &D = R.plan.d;
     res.assign(R.njobs, CfJobResult());
     for (int j = 0; j < R.njobs; j++) {
@@ -779,7 +761,7 @@ int cf_finish(CfCtx *C, CfRun &R, std::vector<CfJobResult> &res, int *retry)
         Q.autoc = autoc;
     }
     C->stats.rechecked_pairs = qn;
-    C->stats.evaluated_pairs = (int64_t) * (const unsigned long long *)(h + 16);
+    C->stats.evaluated_pairs = (int64_t) * (const unsigned long long *)(h + OUT_EVAL);
     C->stats.work_items = nitems;
     C->stats.cells = R.ncell;
     for (int a = 0; a < 3; a++) {

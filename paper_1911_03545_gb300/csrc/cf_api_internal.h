@@ -12,8 +12,20 @@
 enum CfBuf {
     B_IN, B_SETS, B_BBOX, B_PLAN, B_LUT, B_FINE, B_STENCIL, B_JOBS, B_CNT, B_CSTART, B_CELLID, B_SLOT,
     B_PA, B_PB, B_PLO, B_ORIG, B_SCAN, B_ICNT, B_IOFF, B_ITEMS, B_HCNT, B_HW, B_HR, B_QUEUE, B_WSQ, B_MISC, B_ORIGIN,
-    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_COUNT_
+    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_COUNT_
 };
+
+// B_OUT: the counters and histograms one call reads back, laid out as the host copy of them (one
+// device-to-host copy): work-list length (u32, also at the end of its scan), the same in 64 bits,
+// evaluated pairs, the pair kernel's work cursor (u32), recheck-queue length, then from OUT_HIST
+// hcnt[hsz] (u64), hw[hsz], hr[hsz] (f64) and the sum of w^2 per point set (f64).  The count phase
+// zeroes everything from OUT_EVAL on with one memset.
+#define OUT_NITEMS 0
+#define OUT_ITEMS64 8
+#define OUT_EVAL 16
+#define OUT_CURSOR 24
+#define OUT_QCOUNT 32
+#define OUT_HIST 64
 
 struct DeviceGuard {
     int prev = -1;

@@ -404,7 +404,7 @@ __global__ void cf_scan_totals(uint32_t *__restrict__ tile_tot, int ntiles, uint
 }
 
 __global__ void cf_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ tile_off,
-                            const uint32_t *__restrict__ grand)
+                            const uint32_t *__restrict__ grand, uint32_t *__restrict__ total_copy)
 {
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
     uint32_t off = tile_off[blockIdx.x];
@@ -412,7 +412,10 @@ __global__ void cf_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_
         int64_t i = base + k;
         if (i < n) out[i] += off;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = *grand;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[n] = *grand;
+        if (total_copy) *total_copy = *grand;
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -754,14 +757,14 @@ cudaError_t cfb_cell_starts(const uint32_t *fstart, int64_t ncell_all, int sub, 
 
 int64_t cfb_scan_tmp_words(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 8; }
 
-cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st)
+cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st, uint32_t *total_copy)
 {
     int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntiles < 1) ntiles = 1;
     uint32_t *grand = tmp + ntiles;
     cf_scan_tiles<<<(unsigned)ntiles, SCAN_T, 0, st>>>(in, out, n, tmp);
     cf_scan_totals<<<1, SCAN_T, 0, st>>>(tmp, (int)ntiles, grand);
-    cf_scan_add<<<(unsigned)ntiles, SCAN_T, 0, st>>>(out, n, tmp, grand);
+    cf_scan_add<<<(unsigned)ntiles, SCAN_T, 0, st>>>(out, n, tmp, grand, total_copy);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,9 @@ cudaError_t cfb_ang_origins(const CfDevPlan *plan, int ncell, double *origin, fl
 // cell_start[c] = fstart[c * sub^3] for c in [0, ncell_all]
 cudaError_t cfb_cell_starts(const uint32_t *fstart, int64_t ncell_all, int sub, uint32_t *cell_start, cudaStream_t st);
 int64_t cfb_scan_tmp_words(int64_t n);
-cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st);
+// exclusive scan of n counts into out[0..n) and the total into out[n] (and *total_copy if given)
+cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st,
+                     uint32_t *total_copy = nullptr);
 cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
                         const uint32_t *fstart, const uint32_t *key, const uint32_t *slot, float4 *pa,
                         float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st);
