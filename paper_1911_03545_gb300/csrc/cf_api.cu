@@ -305,21 +305,23 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     }
 
     // ---- bbox + validation (Sec. 4.1: the grid covers every data set of the call) ----
-    CF_TRY(C->ensure(B_SETS, sizeof(CfSetDesc) * nsets));
+    // B_BBOX holds the pass's starting values (then its results) and, after them, the point sets'
+    // descriptors: both go up in one copy from pinned memory
     const size_t bbw = CFB_BBOX_WORDS;
-    CF_TRY(C->ensure(B_BBOX, 8 * bbw * (size_t)nsets));
-    CF_TRY(C->ensure_host(std::max<size_t>(8 * bbw * (size_t)nsets, 4096)));
-    CF_CU(cudaMemcpyAsync(C->buf[B_SETS].p, R.sets.data(), sizeof(CfSetDesc) * nsets, cudaMemcpyHostToDevice, st),
-          "sets upload");
+    const size_t soff = (8 * bbw * (size_t)nsets + 255) & ~(size_t)255;
+    CF_TRY(C->ensure(B_BBOX, soff + sizeof(CfSetDesc) * nsets));
+    CF_TRY(C->ensure_host(std::max<size_t>(soff + sizeof(CfSetDesc) * nsets, 4096)));
     {
         unsigned long long *init = (unsigned long long *)C->hpin;
         for (int s = 0; s < nsets; s++)
             for (size_t a = 0; a < bbw; a++) init[bbw * s + a] = (a < 3 || a == 8 || a == 9) ? ~0ull : 0ull;
-        CF_CU(cudaMemcpyAsync(C->buf[B_BBOX].p, init, 8 * bbw * (size_t)nsets, cudaMemcpyHostToDevice, st),
-              "bbox init");
+        std::memcpy((char *)C->hpin + soff, R.sets.data(), sizeof(CfSetDesc) * nsets);
+        CF_CU(cudaMemcpyAsync(C->buf[B_BBOX].p, C->hpin, soff + sizeof(CfSetDesc) * nsets, cudaMemcpyHostToDevice, st),
+              "bbox init and sets");
     }
-    CF_CU(cfb_bbox((const CfSetDesc *)C->buf[B_SETS].p, nsets, std::max<int64_t>(R.nmax, 1),
-                   (unsigned long long *)C->buf[B_BBOX].p, st), "bbox kernel");
+    R.bb_sets = (const CfSetDesc *)((char *)C->buf[B_BBOX].p + soff);
+    CF_CU(cfb_bbox(R.bb_sets, nsets, std::max<int64_t>(R.nmax, 1), (unsigned long long *)C->buf[B_BBOX].p, st),
+          "bbox kernel");
     C->launches = 1;
     // Periodic inputs whose sums need no weight range (no fixed-point per-warp sums) are planned from
     // the box alone; their bbox readback is checked after the call's final synchronisation instead
@@ -415,17 +417,31 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     // ---- device buffers (allocated here so that the device phases never allocate) ----
     // the angular grid's origins (3 per cell) are computed on the device by the build
     const size_t norigin = D.ang ? 3 * (size_t)D.g.ncell : H.origin.size();
-    CF_TRY(C->ensure(B_ORIGIN, sizeof(double) * norigin));
-    D.origin = (const double *)C->buf[B_ORIGIN].p;
-    CF_TRY(C->ensure(B_ORIGIN32, sizeof(float) * std::max<size_t>(1, norigin)));
-    D.origin32 = (const float *)C->buf[B_ORIGIN32].p;
-    CF_TRY(C->ensure(B_BANDS, sizeof(CfBand) * std::max<size_t>(1, H.bands.size())));
-    D.band = (const CfBand *)C->buf[B_BANDS].p;
-    CF_TRY(C->ensure(B_PLAN, sizeof(CfDevPlan)));
-    CF_TRY(C->ensure(B_LUT, sizeof(uint16_t) * H.lut.size()));
-    CF_TRY(C->ensure(B_FINE, sizeof(CfFine) * std::max<size_t>(1, H.fine.size())));
-    CF_TRY(C->ensure(B_STENCIL, sizeof(CfStencil) * H.stencil.size()));
-    CF_TRY(C->ensure(B_JOBS, sizeof(CfJobDesc) * njobs));
+    // The plan, its tables and the call's descriptors share one device block, filled from the
+    // pinned staging by one copy: plan | LUT | fine entries | stencil | jobs | sets | bands |
+    // origins (FP64) | origins (float32).  The angular grid's origins are computed on the device.
+    const size_t piece[9] = {sizeof(CfDevPlan), sizeof(uint16_t) * H.lut.size(), sizeof(CfFine) * H.fine.size(),
+                             sizeof(CfStencil) * H.stencil.size(), sizeof(CfJobDesc) * njobs,
+                             sizeof(CfSetDesc) * nsets, sizeof(CfBand) * H.bands.size(), sizeof(double) * norigin,
+                             sizeof(float) * norigin};
+    size_t poff[10];
+    poff[0] = 0;
+    for (int k = 0; k < 9; k++) poff[k + 1] = poff[k] + ((std::max<size_t>(piece[k], 1) + 255) & ~(size_t)255);
+    CF_TRY(C->ensure(B_PLANBLK, poff[9]));
+    {
+        char *blk = (char *)C->buf[B_PLANBLK].p;
+        R.d_plan = (const CfDevPlan *)(blk + poff[0]);
+        R.d_lut = (const uint16_t *)(blk + poff[1]);
+        R.d_fine = (const CfFine *)(blk + poff[2]);
+        R.d_stencil = (const CfStencil *)(blk + poff[3]);
+        R.d_jobs = (const CfJobDesc *)(blk + poff[4]);
+        R.d_sets = (const CfSetDesc *)(blk + poff[5]);
+        D.band = (const CfBand *)(blk + poff[6]);
+        R.d_origin = (double *)(blk + poff[7]);
+        R.d_origin32 = (float *)(blk + poff[8]);
+        D.origin = R.d_origin;
+        D.origin32 = R.d_origin32;
+    }
     CF_TRY(C->ensure(B_CNT, 4 * (size_t)(R.nfine + 1)));
     CF_TRY(C->ensure(B_FSTART, 4 * (size_t)(R.nfine + 1)));
     CF_TRY(C->ensure(B_CSTART, 4 * (size_t)(R.ncell_all + 1)));
@@ -446,33 +462,15 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure_host(readback_bytes(R)));
 
     {
-        // uploads through pinned staging: no wait for the transfers
-        struct Up {
-            void *dst;
-            const void *src;
-            size_t bytes;
-        };
-        const Up ups[] = {
-            {C->buf[B_ORIGIN].p, H.origin.data(), sizeof(double) * H.origin.size()},
-            {C->buf[B_ORIGIN32].p, H.origin32.data(), sizeof(float) * H.origin32.size()},
-            {C->buf[B_BANDS].p, H.bands.data(), sizeof(CfBand) * H.bands.size()},
-            {C->buf[B_PLAN].p, &D, sizeof(CfDevPlan)},
-            {C->buf[B_LUT].p, H.lut.data(), sizeof(uint16_t) * H.lut.size()},
-            {C->buf[B_FINE].p, H.fine.data(), sizeof(CfFine) * H.fine.size()},
-            {C->buf[B_STENCIL].p, H.stencil.data(), sizeof(CfStencil) * H.stencil.size()},
-            {C->buf[B_JOBS].p, R.jobs.data(), sizeof(CfJobDesc) * njobs},
-            {C->buf[B_SETS].p, R.sets.data(), sizeof(CfSetDesc) * nsets},
-        };
-        size_t total = 0;
-        for (const Up &u : ups) total += (u.bytes + 255) & ~(size_t)255;
-        CF_TRY(C->ensure_upload(total));
-        size_t off = 0;
-        for (const Up &u : ups) {
-            if (!u.bytes) continue;
-            std::memcpy((char *)C->hup + off, u.src, u.bytes);
-            CF_CU(cudaMemcpyAsync(u.dst, (char *)C->hup + off, u.bytes, cudaMemcpyHostToDevice, st), "plan upload");
-            off += (u.bytes + 255) & ~(size_t)255;
-        }
+        // one upload through pinned staging (no wait for the transfer); the angular grid's origins
+        // are left to the device
+        const void *src[9] = {&D, H.lut.data(), H.fine.data(), H.stencil.data(), R.jobs.data(), R.sets.data(),
+                              H.bands.data(), H.origin.data(), H.origin32.data()};
+        const int npieces = D.ang ? 7 : 9;
+        CF_TRY(C->ensure_upload(poff[npieces]));
+        for (int k = 0; k < npieces; k++)
+            if (piece[k]) std::memcpy((char *)C->hup + poff[k], src[k], piece[k]);
+        CF_CU(cudaMemcpyAsync(C->buf[B_PLANBLK].p, C->hup, poff[npieces], cudaMemcpyHostToDevice, st), "plan upload");
     }
 
     // pair-kernel configuration
@@ -502,7 +500,7 @@ static int cf_enqueue_bbox(CfCtx *C, CfRun &R)
     cudaStream_t st = C->stream;
     unsigned long long *bb = (unsigned long long *)C->buf[B_BBOX].p;
     CF_CU(cfb_bbox_init(bb, R.nsets, st), "bbox init");
-    CF_CU(cfb_bbox((const CfSetDesc *)C->buf[B_SETS].p, R.nsets, std::max<int64_t>(R.nmax, 1), bb, st), "bbox kernel");
+    CF_CU(cfb_bbox(R.bb_sets, R.nsets, std::max<int64_t>(R.nmax, 1), bb, st), "bbox kernel");
     CF_CU(cudaMemcpyAsync((char *)C->hpin + R.bb_off, bb, 8 * CFB_BBOX_WORDS * (size_t)R.nsets, cudaMemcpyDeviceToHost,
                           st), "bbox readback");
     C->launches += 2;
@@ -533,15 +531,14 @@ static bool bbox_within(const CfRun &R, const unsigned long long *bb)
 int cf_enqueue_build(CfCtx *C, CfRun &R)
 {
     cudaStream_t st = C->stream;
-    const CfDevPlan *dplan = (const CfDevPlan *)C->buf[B_PLAN].p;
-    const CfSetDesc *dsets = (const CfSetDesc *)C->buf[B_SETS].p;
-    const CfJobDesc *djobs = (const CfJobDesc *)C->buf[B_JOBS].p;
+    const CfDevPlan *dplan = R.d_plan;
+    const CfSetDesc *dsets = R.d_sets;
+    const CfJobDesc *djobs = R.d_jobs;
     uint32_t *cnt = (uint32_t *)C->buf[B_CNT].p, *cstart = (uint32_t *)C->buf[B_CSTART].p;
     char *out = (char *)C->buf[B_OUT].p;
     uint32_t *fstart = (uint32_t *)C->buf[B_FSTART].p;
     if (R.plan.d.ang) {
-        CF_CU(cfb_ang_origins(dplan, R.plan.d.g.ncell, (double *)C->buf[B_ORIGIN].p, (float *)C->buf[B_ORIGIN32].p, st),
-              "cell origins");
+        CF_CU(cfb_ang_origins(dplan, R.plan.d.g.ncell, R.d_origin, R.d_origin32, st), "cell origins");
         C->launches += 1;
     }
     CF_CU(cudaMemsetAsync(cnt, 0, 4 * (size_t)R.nfine, st), "memset counts");
@@ -567,7 +564,7 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
     // the work list's length in 64 bits, next to its 32-bit scan (checked in cf_finish)
     unsigned long long *items64 = (unsigned long long *)(out + OUT_ITEMS64);
-    CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, cstart, cbox, R.nunit, 0, icnt, nullptr,
+    CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, cstart, cbox, R.nunit, 0, icnt, nullptr,
                     nullptr, 0, items64, st),
           "items count");
     CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, st, (uint32_t *)(out + OUT_NITEMS)), "scan items");
@@ -628,9 +625,9 @@ static void fixed_point_scales(const CfRun &R, bool weighted, bool ravg, CfPairA
 int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
 {
     cudaStream_t st = C->stream;
-    const CfDevPlan *dplan = (const CfDevPlan *)C->buf[B_PLAN].p;
-    const CfSetDesc *dsets = (const CfSetDesc *)C->buf[B_SETS].p;
-    const CfJobDesc *djobs = (const CfJobDesc *)C->buf[B_JOBS].p;
+    const CfDevPlan *dplan = R.d_plan;
+    const CfSetDesc *dsets = R.d_sets;
+    const CfJobDesc *djobs = R.d_jobs;
     const CfDevPlan &D = R.plan.d;
     char *out = (char *)C->buf[B_OUT].p;
     uint32_t *ioff = (uint32_t *)C->buf[B_IOFF].p;
@@ -641,7 +638,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     double *wsq = (double *)(out + OUT_HIST + 24 * hsz);
     // evaluated pairs, the work cursor, the queue length, the histograms and w^2 sums: one memset
     CF_CU(cudaMemsetAsync(out + OUT_EVAL, 0, readback_bytes(R) - OUT_EVAL, st), "memset");
-    CF_CU(cfb_items(dplan, dsets, djobs, (const CfStencil *)C->buf[B_STENCIL].p, (const uint32_t *)C->buf[B_CSTART].p,
+    CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p,
                     R.cbox, R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap,
                     evaluated, st),
           "items emit");
@@ -649,8 +646,8 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     CfPairArgs &A = R.args;
     std::memset(&A, 0, sizeof(A));
     A.plan = dplan;
-    A.lut = (const uint16_t *)C->buf[B_LUT].p;
-    A.fine = (const CfFine *)C->buf[B_FINE].p;
+    A.lut = R.d_lut;
+    A.fine = R.d_fine;
     A.items = (const CfItem *)C->buf[B_ITEMS].p;
     A.nitems_dev = ioff + R.nunit;
     A.items_cap = R.items_cap;

@@ -12,7 +12,7 @@
 enum CfBuf {
     B_IN, B_SETS, B_BBOX, B_PLAN, B_LUT, B_FINE, B_STENCIL, B_JOBS, B_CNT, B_CSTART, B_CELLID, B_SLOT,
     B_PA, B_PB, B_PLO, B_ORIG, B_SCAN, B_ICNT, B_IOFF, B_ITEMS, B_HCNT, B_HW, B_HR, B_QUEUE, B_WSQ, B_MISC, B_ORIGIN,
-    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_COUNT_
+    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_PLANBLK, B_COUNT_
 };
 
 // B_OUT: the counters and histograms one call reads back, laid out as the host copy of them (one
@@ -71,6 +71,16 @@ struct CfRun {
     double vmin2 = 0.0;            // smallest |v|^2 over the points (mocks: the plan's near-observer test)
     bool angular = false;          // DD(theta) on the angular grid (needs unit vectors)
     bool bbox_deferred = false;    // periodic call planned from L: its bbox is checked after the final sync
+    // the call's plan, tables and descriptors inside the B_PLANBLK device block
+    const CfDevPlan *d_plan = nullptr;
+    const uint16_t *d_lut = nullptr;
+    const CfFine *d_fine = nullptr;
+    const CfStencil *d_stencil = nullptr;
+    const CfJobDesc *d_jobs = nullptr;
+    const CfSetDesc *d_sets = nullptr;
+    const CfSetDesc *bb_sets = nullptr;   // the sets' descriptors the bbox pass reads (in B_BBOX)
+    double *d_origin = nullptr;
+    float *d_origin32 = nullptr;
     size_t bb_off = 0;             // captured graph: offset of its bbox readback in pinned memory
     std::vector<double> wmin, wmax;   // per point set: smallest nonzero |w| (inf: none), largest |w|
     bool wneg = false;                // some weight is negative
