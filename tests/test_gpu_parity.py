@@ -434,3 +434,38 @@ def test_band_audit_agrees(ctx, kind):
     assert int(np.asarray(audited["npairs"]).sum()) // 2 <= sa["rechecked_pairs"] <= sa["evaluated_pairs"]
     assert_match(normal, audited, True, True)
     assert_match(audited, oracle.count(kind, edges, d, **kw), True, True)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_points_on_and_beside_cell_boundaries(ctx, periodic):
+    """The cell build computes cell coordinates, cell-relative positions and cell-pair gaps in float32
+    for float32 inputs, and redoes a coordinate in FP64 within a guard band of a cell boundary.  Here
+    the cells are exactly as wide as the largest edge, so a point put in the wrong neighbour cell
+    would lose pairs just inside that edge; every coordinate lies on a boundary, 1-3 ulps beside
+    one, or half a cell in, on a grid that starts at 0 (periodic) or at -30 (non-periodic)."""
+    L, w = 60.0, 6.0
+    edges = gen.log_edges(0.5, w, 8)                       # 10 cells of width 6 = the last edge
+    lo = 0.0 if periodic else -30.0
+    rng = np.random.Generator(np.random.PCG64(404))
+    vals = []
+    for k in range(11):
+        b = np.float32(lo + w * k)
+        for d in (-3, -2, -1, 0, 1, 2, 3):
+            v = b
+            for _ in range(abs(d)):
+                v = np.nextafter(v, np.float32(np.inf) if d > 0 else np.float32(-np.inf), dtype=np.float32)
+            vals.append(v)
+        vals.append(np.float32(lo + w * k + 0.5 * w))
+    vals = np.array(sorted(set(float(v) for v in vals)), dtype=np.float32)
+    vals = vals[(vals >= lo) & (vals <= lo + L)] if periodic else vals[(vals >= lo) & (vals <= lo + 60.0)]
+    if periodic:
+        vals = vals[vals < L]                              # x = L is the same place as 0
+    n = 3000
+    pts = vals[rng.integers(0, len(vals), size=(n, 3))]
+    d = gen.Catalogue(pts[:, 0].copy(), pts[:, 1].copy(), pts[:, 2].copy(),
+                      gen.uniform_weights(n, 0.5, 1.5, 405))
+    kw = dict(autocorr=True, periodic=periodic, box=L, weighted=True, ravg=True)
+    got = gpu_count(ctx, "r", edges, d, **kw)
+    exp = oracle.count("r", edges, d, **kw)
+    assert_match(got, exp, True, True)
+    assert int(np.asarray(exp["npairs"]).sum()) > 10000
