@@ -330,6 +330,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     const bool warp_sums = (p->kind == CF_DD_RPPI || p->kind == CF_DD_RPPI_MOCKS) &&
                            (p->weight == CF_W_PAIR_PRODUCT || p->output_ravg);
     R.bbox_deferred = p->periodic && !warp_sums && !C->capturing;
+    R.fused_items = false;
     double bbox[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     double norm_dev = 0.0;   // largest | |v|^2 - 1 | over the points
     double vmin2 = INFINITY;  // smallest |v|^2 over the points
@@ -542,12 +543,15 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
         C->launches += 1;
     }
     CF_CU(cudaMemsetAsync(cnt, 0, 4 * (size_t)R.nfine, st), "memset counts");
-    CF_CU(cudaMemsetAsync(out, 0, OUT_EVAL, st), "memset work-list counters");
+    CF_CU(cudaMemsetAsync(out, 0, OUT_HIST, st), "memset work-list counters");
     CF_CU(cfb_assign(dplan, dsets, R.nsets, R.np, R.sub, cnt, (uint32_t *)C->buf[B_CELLID].p,
                      (uint32_t *)C->buf[B_SLOT].p, st),
           "assign");
-    CF_CU(cfb_scan(cnt, fstart, R.nfine, (uint32_t *)C->buf[B_SCAN].p, st), "scan cells");
-    CF_CU(cfb_cell_starts(fstart, R.ncell_all, R.sub, cstart, st), "cell starts");
+    // sub-cell starts, and the cell starts among them (sub^3 = 2^(3 log2 sub) sub-cells per cell)
+    const int sub_shift = R.sub == 4 ? 6 : (R.sub == 2 ? 3 : 0);
+    CF_CU(cfb_scan(cnt, fstart, R.nfine, (uint32_t *)C->buf[B_SCAN].p, (uint32_t *)(out + OUT_SCAN), st, nullptr,
+                   cstart, sub_shift),
+          "scan cells");
     CF_CU(cfb_scatter(dplan, dsets, R.nsets, R.np, R.sub, fstart, (uint32_t *)C->buf[B_CELLID].p,
                       (uint32_t *)C->buf[B_SLOT].p, (float4 *)C->buf[B_PA].p, (float4 *)C->buf[B_PB].p,
                       (float4 *)C->buf[B_PLO].p, (uint32_t *)C->buf[B_ORIG].p, st),
@@ -561,14 +565,18 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
         C->launches += 1;
     }
     R.cbox = cbox;
+    C->launches += 4;    // assign, 2 scan, scatter
+    if (R.fused_items) return CF_OK;    // the count pass writes the work list in one go
     uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
     // the work list's length in 64 bits, next to its 32-bit scan (checked in cf_finish)
     unsigned long long *items64 = (unsigned long long *)(out + OUT_ITEMS64);
     CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, cstart, cbox, R.nunit, 0, icnt, nullptr,
-                    nullptr, 0, items64, st),
+                    nullptr, 0, items64, nullptr, st),
           "items count");
-    CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, st, (uint32_t *)(out + OUT_NITEMS)), "scan items");
-    C->launches += 10;   // assign, 3 scan, cell starts, scatter, items count, 3 scan
+    CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, (uint32_t *)(out + OUT_SCAN + 4), st,
+                   (uint32_t *)(out + OUT_NITEMS)),
+          "scan items");
+    C->launches += 3;    // items count, 2 scan
     return CF_OK;
 }
 
@@ -636,12 +644,23 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     unsigned long long *hcnt = (unsigned long long *)(out + OUT_HIST);
     double *hw = (double *)(out + OUT_HIST + 8 * hsz), *hr = (double *)(out + OUT_HIST + 16 * hsz);
     double *wsq = (double *)(out + OUT_HIST + 24 * hsz);
-    // evaluated pairs, the work cursor, the queue length, the histograms and w^2 sums: one memset
-    CF_CU(cudaMemsetAsync(out + OUT_EVAL, 0, readback_bytes(R) - OUT_EVAL, st), "memset");
-    CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p,
-                    R.cbox, R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap,
-                    evaluated, st),
-          "items emit");
+    // evaluated pairs, the work cursor, the queue length, the histograms and w^2 sums (and for the
+    // one-pass work list its two length counters): one memset
+    const size_t zero_from = R.fused_items ? 0 : OUT_EVAL;
+    CF_CU(cudaMemsetAsync(out + zero_from, 0, readback_bytes(R) - zero_from, st), "memset");
+    uint32_t *nitems_dev = ioff + R.nunit;
+    if (R.fused_items) {
+        nitems_dev = (uint32_t *)(out + OUT_NITEMS);
+        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.nunit, 2,
+                        nitems_dev, nullptr, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
+                        (unsigned long long *)(out + OUT_ITEMS64), st),
+              "items");
+    } else {
+        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.nunit, 1,
+                        (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
+                        nullptr, st),
+              "items emit");
+    }
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[1], st, C->capturing ? cudaEventRecordExternal : 0), "event");
     CfPairArgs &A = R.args;
     std::memset(&A, 0, sizeof(A));
@@ -649,7 +668,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     A.lut = R.d_lut;
     A.fine = R.d_fine;
     A.items = (const CfItem *)C->buf[B_ITEMS].p;
-    A.nitems_dev = ioff + R.nunit;
+    A.nitems_dev = nitems_dev;
     A.items_cap = R.items_cap;
     A.qcap = R.qcap;
     A.cursor = (uint32_t *)(out + OUT_CURSOR);
@@ -789,14 +808,16 @@ int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &p
     C->drop_graph();
     CF_TRY(cf_prepare(C, p, pts, jobs, R));
     cudaStream_t st = C->stream;
-    CF_CU(cudaEventRecord(C->ev[0], st), "event");
-    CF_TRY(cf_enqueue_build(C, R));
     // the work list depends on the plan and on the cell pruning and order options
     const std::string ikey = C->plan_key + std::to_string(C->opt[CF_OPT_CELL_PRUNE]) + "/" +
                              std::to_string(C->opt[CF_OPT_CELL_ORDER]);
-    if (C->items_hint && C->items_key == ikey) {
-        // a call on the same plan sized the work list before: take that size with headroom and
-        // let cf_finish count again in the rare case that the list outgrew it
+    // a call on the same plan sized the work list before: take that size with headroom, count and
+    // write the list in one pass, and let cf_finish run the count again in the rare case that the
+    // list outgrew it
+    R.fused_items = C->items_hint && C->items_key == ikey;
+    CF_CU(cudaEventRecord(C->ev[0], st), "event");
+    CF_TRY(cf_enqueue_build(C, R));
+    if (R.fused_items) {
         R.items_cap = C->items_hint;
     } else {
         // size the work list from the device count (one small readback)

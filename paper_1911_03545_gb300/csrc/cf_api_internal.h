@@ -18,13 +18,15 @@ enum CfBuf {
 // B_OUT: the counters and histograms one call reads back, laid out as the host copy of them (one
 // device-to-host copy): work-list length (u32, also at the end of its scan), the same in 64 bits,
 // evaluated pairs, the pair kernel's work cursor (u32), recheck-queue length, then from OUT_HIST
-// hcnt[hsz] (u64), hw[hsz], hr[hsz] (f64) and the sum of w^2 per point set (f64).  The count phase
-// zeroes everything from OUT_EVAL on with one memset.
+// hcnt[hsz] (u64), hw[hsz], hr[hsz] (f64) and the sum of w^2 per point set (f64); at OUT_SCAN the
+// tickets of the build's two scans.  The build zeroes the first OUT_HIST bytes, the count phase
+// everything from OUT_EVAL on (from 0 for the one-pass work list), each with one memset.
 #define OUT_NITEMS 0
 #define OUT_ITEMS64 8
 #define OUT_EVAL 16
 #define OUT_CURSOR 24
 #define OUT_QCOUNT 32
+#define OUT_SCAN 40
 #define OUT_HIST 64
 
 struct DeviceGuard {
@@ -71,6 +73,7 @@ struct CfRun {
     double vmin2 = 0.0;            // smallest |v|^2 over the points (mocks: the plan's near-observer test)
     bool angular = false;          // DD(theta) on the angular grid (needs unit vectors)
     bool bbox_deferred = false;    // periodic call planned from L: its bbox is checked after the final sync
+    bool fused_items = false;      // the work list is counted and written in one pass (size known)
     // the call's plan, tables and descriptors inside the B_PLANBLK device block
     const CfDevPlan *d_plan = nullptr;
     const uint16_t *d_lut = nullptr;

@@ -16,21 +16,23 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
     unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0, 0, 0}, bad = 0, nrm = 0, rmin = ~0ull;
     unsigned long long wmn = ~0ull, wmx = 0, wng = 0;    // |w| range (nonzero minimum), negatives
     const void *P[3] = {S.x, S.y, S.z};
+    bool warp_reduced = false;
     if (S.dtype == CF_F32) {
         // float32 inputs: minima, maxima, |v|^2 and its deviation from 1 in float32 (the FP64 pipe
-        // runs at a small fraction of the FP32 rate); keys once per thread.  |v|^2 carries <= 3
-        // roundings here, which its users allow for.
+        // runs at a small fraction of the FP32 rate), four points per thread and step through
+        // 16-byte loads when the arrays allow it, reduced across the warp in float32; keys once per
+        // warp.  |v|^2 carries <= 3 roundings here, which its users allow for.
         const float *X = (const float *)S.x, *Y = (const float *)S.y, *Z = (const float *)S.z;
         const float *Wt = (const float *)S.w;
         float fmn[3] = {INFINITY, INFINITY, INFINITY}, fmx[3] = {-INFINITY, -INFINITY, -INFINITY};
         float fnrm = 0.f, frmin = INFINITY, fwmn = INFINITY, fwmx = 0.f;
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < S.n;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            const float v[3] = {X[i], Y[i], Z[i]};
+        uint32_t nbad = 0, nneg = 0;
+        auto visit = [&](float x, float y, float z) {
+            const float v[3] = {x, y, z};
             bool ok = true;
             for (int a = 0; a < 3; a++) {
                 if (!isfinite(v[a])) {
-                    bad++;
+                    nbad++;
                     ok = false;
                     continue;
                 }
@@ -42,27 +44,62 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
                 fnrm = fmaxf(fnrm, fabsf(r2 - 1.0f));
                 frmin = fminf(frmin, r2);
             }
-            if (Wt) {
-                const float w = Wt[i];
-                if (!isfinite(w)) {
-                    bad++;
-                } else {
-                    const float aw = fabsf(w);
-                    if (w < 0.f) wng++;
-                    if (aw > 0.f) fwmn = fminf(fwmn, aw);
-                    fwmx = fmaxf(fwmx, aw);
-                }
+        };
+        auto visit_w = [&](float w) {
+            if (!isfinite(w)) {
+                nbad++;
+            } else {
+                const float aw = fabsf(w);
+                if (w < 0.f) nneg++;
+                if (aw > 0.f) fwmn = fminf(fwmn, aw);
+                fwmx = fmaxf(fwmx, aw);
             }
+        };
+        const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nthr = (int64_t)gridDim.x * blockDim.x;
+        const bool vec = (((uintptr_t)X | (uintptr_t)Y | (uintptr_t)Z | (uintptr_t)Wt) & 15u) == 0;
+        const int64_t n4 = vec ? S.n / 4 : 0;
+        for (int64_t q = tid; q < n4; q += nthr) {
+            const float4 x = ((const float4 *)X)[q], y = ((const float4 *)Y)[q], z = ((const float4 *)Z)[q];
+            visit(x.x, y.x, z.x);
+            visit(x.y, y.y, z.y);
+            visit(x.z, y.z, z.z);
+            visit(x.w, y.w, z.w);
+            if (Wt) {
+                const float4 w = ((const float4 *)Wt)[q];
+                visit_w(w.x);
+                visit_w(w.y);
+                visit_w(w.z);
+                visit_w(w.w);
+            }
+        }
+        for (int64_t i = 4 * n4 + tid; i < S.n; i += nthr) {
+            visit(X[i], Y[i], Z[i]);
+            if (Wt) visit_w(Wt[i]);
+        }
+        for (int o = 16; o; o >>= 1) {
+            for (int a = 0; a < 3; a++) {
+                fmn[a] = fminf(fmn[a], __shfl_xor_sync(CF_FULL, fmn[a], o));
+                fmx[a] = fmaxf(fmx[a], __shfl_xor_sync(CF_FULL, fmx[a], o));
+            }
+            fnrm = fmaxf(fnrm, __shfl_xor_sync(CF_FULL, fnrm, o));
+            frmin = fminf(frmin, __shfl_xor_sync(CF_FULL, frmin, o));
+            fwmn = fminf(fwmn, __shfl_xor_sync(CF_FULL, fwmn, o));
+            fwmx = fmaxf(fwmx, __shfl_xor_sync(CF_FULL, fwmx, o));
+            nbad += __shfl_xor_sync(CF_FULL, nbad, o);
+            nneg += __shfl_xor_sync(CF_FULL, nneg, o);
         }
         for (int a = 0; a < 3; a++)
             if (fmn[a] <= fmx[a]) {
                 mn[a] = cf_dkey((double)fmn[a]);
                 mx[a] = cf_dkey((double)fmx[a]);
             }
+        bad = nbad;
+        wng = nneg;
         nrm = (unsigned long long)__double_as_longlong((double)fnrm);
         if (frmin < INFINITY) rmin = (unsigned long long)__double_as_longlong((double)frmin);
         if (fwmn < INFINITY) wmn = (unsigned long long)__double_as_longlong((double)fwmn);
         wmx = (unsigned long long)__double_as_longlong((double)fwmx);
+        warp_reduced = true;
     }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; S.dtype != CF_F32 && i < S.n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -94,7 +131,7 @@ __global__ void cf_bbox_kernel(const CfSetDesc *__restrict__ sets, unsigned long
             }
         }
     }
-    for (int o = 16; o; o >>= 1) {
+    for (int o = 16; !warp_reduced && o; o >>= 1) {
         for (int a = 0; a < 3; a++) {
             unsigned long long t = __shfl_xor_sync(CF_FULL, mn[a], o);
             mn[a] = t < mn[a] ? t : mn[a];
@@ -321,16 +358,10 @@ __global__ void cf_ang_origin_kernel(const CfDevPlan *__restrict__ plan, int nce
 }
 
 // cell start of every cell from the start of its first sub-cell (and the total at the end)
-__global__ void cf_cell_starts_kernel(const uint32_t *__restrict__ fstart, int64_t ncell_all, uint32_t ns,
-                                      uint32_t *__restrict__ cell_start)
-{
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c <= ncell_all; c += (int64_t)gridDim.x * blockDim.x)
-        cell_start[c] = fstart[c * ns];
-}
-
 // ---------------------------------------------------------------------------------------------
-// Exclusive scan of u32 counts into u32 offsets (+ total at out[n]), three phases:
-// tile scans -> scan of tile totals -> add tile offsets.  Tiles of 4096 values.
+// Exclusive scan of u32 counts into u32 offsets (+ total at out[n]) in two passes over tiles of
+// 4096 values: tile totals (the last block to finish scans them), then each tile's own scan plus
+// its offset.  The input is read twice and the output written once.
 // ---------------------------------------------------------------------------------------------
 #define SCAN_T 256
 #define SCAN_V 16
@@ -361,60 +392,110 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, ui
     return pre;
 }
 
-__global__ void cf_scan_tiles(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
-                              uint32_t *__restrict__ tile_tot)
+// this thread's SCAN_V consecutive values (0 past n), through 16-byte loads where they can be used
+__device__ __forceinline__ void scan_load(const uint32_t *__restrict__ in, int64_t n, int64_t base, uint32_t *v)
 {
-    __shared__ uint32_t sh[SCAN_T / 32];
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_V;
-    uint32_t v[SCAN_V], s = 0;
-    for (int k = 0; k < SCAN_V; k++) {
-        v[k] = (base + k < n) ? in[base + k] : 0u;
-        s += v[k];
+    if (base + SCAN_V <= n && ((uintptr_t)in & 15u) == 0) {
+        const uint4 *q = (const uint4 *)(in + base);
+#pragma unroll
+        for (int k = 0; k < SCAN_V / 4; k++) {
+            const uint4 t = q[k];
+            v[4 * k] = t.x;
+            v[4 * k + 1] = t.y;
+            v[4 * k + 2] = t.z;
+            v[4 * k + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_V; k++) v[k] = (base + k < n) ? in[base + k] : 0u;
     }
-    uint32_t tot;
-    uint32_t pre = block_excl_scan(s, sh, &tot);
-    for (int k = 0; k < SCAN_V; k++) {
-        if (base + k < n) out[base + k] = pre;
-        pre += v[k];
-    }
-    if (threadIdx.x == 0) tile_tot[blockIdx.x] = tot;
 }
 
-// single block: exclusive scan of up to SCAN_TILE tile totals in place; writes the grand total
-__global__ void cf_scan_totals(uint32_t *__restrict__ tile_tot, int ntiles, uint32_t *__restrict__ grand)
+// pass 1: tile totals into tile_tot[]; the block that finishes last (one ticket per block on
+// *done, zeroed by the caller) turns them into exclusive tile offsets and writes the grand total
+// at tile_tot[ntiles]
+__global__ void cf_scan_reduce(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ tile_tot,
+                               uint32_t *__restrict__ done)
 {
     __shared__ uint32_t sh[SCAN_T / 32];
+    __shared__ bool last;
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_V;
+    uint32_t v[SCAN_V], s = 0;
+    scan_load(in, n, base, v);
+#pragma unroll
+    for (int k = 0; k < SCAN_V; k++) s += v[k];
+    uint32_t tot;
+    block_excl_scan(s, sh, &tot);
+    if (threadIdx.x == 0) {
+        tile_tot[blockIdx.x] = tot;
+        __threadfence();                              // the total is visible before the ticket
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int ntiles = (int)gridDim.x;
     uint32_t carry = 0;
     for (int base0 = 0; base0 < ntiles; base0 += SCAN_TILE) {
-        int base = base0 + threadIdx.x * SCAN_V;
-        uint32_t v[SCAN_V], s = 0;
+        const int b = base0 + threadIdx.x * SCAN_V;
+        uint32_t t[SCAN_V], ts = 0;
+#pragma unroll
         for (int k = 0; k < SCAN_V; k++) {
-            v[k] = (base + k < ntiles) ? tile_tot[base + k] : 0u;
-            s += v[k];
+            t[k] = (b + k < ntiles) ? __ldcg(tile_tot + b + k) : 0u;    // from L2: other blocks wrote them
+            ts += t[k];
         }
-        uint32_t tot;
-        uint32_t pre = block_excl_scan(s, sh, &tot) + carry;
+        uint32_t ttot;
+        uint32_t pre = block_excl_scan(ts, sh, &ttot) + carry;
+#pragma unroll
         for (int k = 0; k < SCAN_V; k++) {
-            if (base + k < ntiles) tile_tot[base + k] = pre;
-            pre += v[k];
+            if (b + k < ntiles) tile_tot[b + k] = pre;
+            pre += t[k];
         }
-        carry += tot;
+        carry += ttot;
     }
-    if (threadIdx.x == 0) *grand = carry;
+    if (threadIdx.x == 0) tile_tot[ntiles] = carry;
 }
 
-__global__ void cf_scan_add(uint32_t *__restrict__ out, int64_t n, const uint32_t *__restrict__ tile_off,
-                            const uint32_t *__restrict__ grand, uint32_t *__restrict__ total_copy)
+// pass 2: each tile's scan plus its offset.  every (optional) receives out[i] at each multiple i of
+// 2^every_shift, i.e. every[i >> every_shift] (the start of each cell among its sub-cell starts);
+// n is a multiple of that stride.
+__global__ void cf_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
+                              const uint32_t *__restrict__ tile_off, uint32_t *__restrict__ total_copy,
+                              uint32_t *__restrict__ every, int every_shift)
 {
-    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
-    uint32_t off = tile_off[blockIdx.x];
-    for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_T) {
-        int64_t i = base + k;
-        if (i < n) out[i] += off;
+    __shared__ uint32_t sh[SCAN_T / 32];
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_V;
+    uint32_t v[SCAN_V], s = 0;
+    scan_load(in, n, base, v);
+#pragma unroll
+    for (int k = 0; k < SCAN_V; k++) s += v[k];
+    uint32_t pre = block_excl_scan(s, sh, nullptr) + tile_off[blockIdx.x];
+    uint32_t o[SCAN_V];
+#pragma unroll
+    for (int k = 0; k < SCAN_V; k++) {
+        o[k] = pre;
+        pre += v[k];
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        out[n] = *grand;
-        if (total_copy) *total_copy = *grand;
+    if (base + SCAN_V <= n && ((uintptr_t)out & 15u) == 0) {
+        uint4 *q = (uint4 *)(out + base);
+#pragma unroll
+        for (int k = 0; k < SCAN_V / 4; k++) q[k] = make_uint4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < SCAN_V; k++)
+            if (base + k < n) out[base + k] = o[k];
+    }
+    if (every) {
+        const int64_t mask = ((int64_t)1 << every_shift) - 1;
+#pragma unroll
+        for (int k = 0; k < SCAN_V; k++)
+            if (base + k < n && ((base + k) & mask) == 0) every[(base + k) >> every_shift] = o[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        const uint32_t grand = tile_off[gridDim.x];
+        out[n] = grand;
+        if (total_copy) *total_copy = grand;
+        if (every) every[n >> every_shift] = grand;
     }
 }
 
@@ -514,13 +595,16 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
 // remainder tile, so a tile wastes at most 31 pair-kernel slots; j ranges split evenly (<= jchunk).
 // mode 0 writes the item count of each (job, cell) and adds the number of items, counted in 64 bits,
 // to *evaluated (the 32-bit scan of the counts would wrap silently past 2^32 items); mode 1 writes
-// the items at the scanned offsets and adds the pairs they hold to *evaluated.
+// the items at the scanned offsets and adds the pairs they hold to *evaluated.  Mode 2 needs no
+// count pass: each warp reserves the items of 32 stencil entries with one atomic on counts[0] (the
+// list's length when the kernel ends), adds their number in 64 bits to *total64, and writes them
+// like mode 1.  The list's order then follows the warps' arrival instead of (job, cell).
 __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
                                 const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox, int mode,
                                 uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets,
                                 CfItem *__restrict__ items, uint32_t items_cap,
-                                unsigned long long *__restrict__ evaluated)
+                                unsigned long long *__restrict__ evaluated, unsigned long long *__restrict__ total64)
 {
     const CfGrid &g = plan->g;
     const int nst = g.nstencil;
@@ -532,7 +616,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
     const int64_t nunit = (int64_t)g.ncell * plan->njobs;
     const uint32_t tile = plan->tile, jchunk = plan->jchunk;
     const uint32_t lane = threadIdx.x & 31u;
-    unsigned long long ev = 0;
+    unsigned long long ev = 0, nres = 0;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < nunit; u += wstride) {
         const int job = (int)(u / g.ncell);
@@ -649,8 +733,16 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                     const uint32_t v = __shfl_up_sync(CF_FULL, incl, o);
                     if ((int)lane >= o) incl += v;
                 }
-                if (mode == 1 && cnt) {
-                    uint32_t o = base + total + (incl - cnt);
+                uint32_t cbase = base + total;
+                if (mode == 2) {
+                    const uint32_t ctot = __shfl_sync(CF_FULL, incl, 31);
+                    uint32_t r = 0;
+                    if (lane == 0 && ctot) r = atomicAdd(counts, ctot);
+                    cbase = __shfl_sync(CF_FULL, r, 0);
+                    nres += ctot;
+                }
+                if (mode != 0 && cnt) {
+                    uint32_t o = cbase + (incl - cnt);
                     // the item's shift in FP64, split into float32 hi + lo (Sec. 4.4 applied per cell)
                     float sh[3], sl[3];
                     for (int a = 0; a < 3; a++) {
@@ -685,6 +777,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
         for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(CF_FULL, ev, o);
         if ((threadIdx.x & 31) == 0 && ev) atomicAdd(evaluated, ev);
     }
+    if (mode == 2 && lane == 0 && nres) atomicAdd(total64, nres);     // nres is the same in every lane
 }
 
 // sum of w^2 per set (self pairs of a weighted auto-correlation whose first edge is 0)
@@ -729,7 +822,7 @@ cudaError_t cfb_bbox_init(unsigned long long *out, int nsets, cudaStream_t st)
 
 cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st)
 {
-    dim3 grid(blocks_for(nmax, 256, 1024), nsets);
+    dim3 grid(blocks_for((nmax + 3) / 4, 256, 1024), nsets);     // four float32 points per thread and step
     cf_bbox_kernel<<<grid, 256, 0, st>>>(sets, out);
     return cudaGetLastError();
 }
@@ -748,23 +841,15 @@ cudaError_t cfb_ang_origins(const CfDevPlan *plan, int ncell, double *origin, fl
     return cudaGetLastError();
 }
 
-cudaError_t cfb_cell_starts(const uint32_t *fstart, int64_t ncell_all, int sub, uint32_t *cell_start, cudaStream_t st)
-{
-    cf_cell_starts_kernel<<<blocks_for(ncell_all + 1, 256, 4096), 256, 0, st>>>(fstart, ncell_all,
-                                                                               (uint32_t)(sub * sub * sub), cell_start);
-    return cudaGetLastError();
-}
-
 int64_t cfb_scan_tmp_words(int64_t n) { return (n + SCAN_TILE - 1) / SCAN_TILE + 8; }
 
-cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st, uint32_t *total_copy)
+cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, uint32_t *done, cudaStream_t st,
+                     uint32_t *total_copy, uint32_t *every, int every_shift)
 {
     int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (ntiles < 1) ntiles = 1;
-    uint32_t *grand = tmp + ntiles;
-    cf_scan_tiles<<<(unsigned)ntiles, SCAN_T, 0, st>>>(in, out, n, tmp);
-    cf_scan_totals<<<1, SCAN_T, 0, st>>>(tmp, (int)ntiles, grand);
-    cf_scan_add<<<(unsigned)ntiles, SCAN_T, 0, st>>>(out, n, tmp, grand, total_copy);
+    cf_scan_reduce<<<(unsigned)ntiles, SCAN_T, 0, st>>>(in, n, tmp, done);
+    cf_scan_apply<<<(unsigned)ntiles, SCAN_T, 0, st>>>(in, out, n, tmp, total_copy, every, every_shift);
     return cudaGetLastError();
 }
 
@@ -788,11 +873,11 @@ cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const flo
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
                       const uint32_t *cell_start, const float *cbox, int64_t nunits, int mode, uint32_t *counts,
                       const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
-                      cudaStream_t st)
+                      unsigned long long *total64, cudaStream_t st)
 {
     cf_items_kernel<<<blocks_for(nunits * 32, 256, 8192), 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox,
                                                                        mode, counts, offsets, items, items_cap,
-                                                                       evaluated);
+                                                                       evaluated, total64);
     return cudaGetLastError();
 }
 

@@ -15,23 +15,27 @@ cudaError_t cfb_assign(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, 
                        uint32_t *count, uint32_t *key, uint32_t *slot, cudaStream_t st);
 // origins of the angular grid's cells (3 per cell) from their (RA, DEC) boxes
 cudaError_t cfb_ang_origins(const CfDevPlan *plan, int ncell, double *origin, float *origin32, cudaStream_t st);
-// cell_start[c] = fstart[c * sub^3] for c in [0, ncell_all]
-cudaError_t cfb_cell_starts(const uint32_t *fstart, int64_t ncell_all, int sub, uint32_t *cell_start, cudaStream_t st);
 int64_t cfb_scan_tmp_words(int64_t n);
-// exclusive scan of n counts into out[0..n) and the total into out[n] (and *total_copy if given)
-cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, cudaStream_t st,
-                     uint32_t *total_copy = nullptr);
+// exclusive scan of n counts into out[0..n) and the total into out[n] (and *total_copy if given);
+// tmp holds cfb_scan_tmp_words(n) words, *done must be 0 (a ticket counter).  every, if given,
+// receives every[i >> every_shift] = out[i] for the multiples i of 2^every_shift up to n (the cell
+// starts among the sub-cell starts: cell_start[c] = fstart[c * sub^3]).
+cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp, uint32_t *done, cudaStream_t st,
+                     uint32_t *total_copy = nullptr, uint32_t *every = nullptr, int every_shift = 0);
 cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
                         const uint32_t *fstart, const uint32_t *key, const uint32_t *slot, float4 *pa,
                         float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st);
 // tight point bounding box per cell (6 floats: lo xyz, hi xyz, cell-relative), for cell-pair pruning
 cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const float4 *pa, const float4 *pb, float *box,
                         cudaStream_t st);
-// cbox: the boxes above, or nullptr to visit every stencil neighbour
+// cbox: the boxes above, or nullptr to visit every stencil neighbour.  mode 0: per-unit item counts
+// into counts[], their number in 64 bits added to *evaluated; mode 1: items at offsets[]; mode 2:
+// count and emit in one pass, items reserved on the counter counts[0] (zeroed by the caller), their
+// number added to *total64.  Modes 1 and 2 add the pairs the stored items hold to *evaluated.
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
                       const uint32_t *cell_start, const float *cbox, int64_t nunits, int mode, uint32_t *counts,
                       const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
-                      cudaStream_t st);
+                      unsigned long long *total64, cudaStream_t st);
 cudaError_t cfb_wsq(const CfSetDesc *sets, int nsets, int64_t nmax, double *out, cudaStream_t st);
 
 // ---- pair counting ----
