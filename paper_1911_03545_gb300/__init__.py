@@ -108,14 +108,19 @@ def points(x, y, z, w=None) -> Points:
 
 
 class _Out:
+    """The four result arrays of one catalogue in one host block (the library writes every entry of
+    each: npairs, wsum, ravg, wp); the cf_result's pointers are filled from the block's address."""
+
     def __init__(self, nout: int, nb: int):
-        self.npairs = np.zeros(nout, dtype=np.uint64)
-        self.wsum = np.zeros(nout)
-        self.ravg = np.zeros(nout)
-        self.wp = np.zeros(nb)
-        D = ctypes.POINTER(ctypes.c_double)
-        self.c = _capi.cf_result(self.npairs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
-                                 self.wsum.ctypes.data_as(D), self.ravg.ctypes.data_as(D), self.wp.ctypes.data_as(D))
+        buf = np.empty(3 * nout + nb)
+        self.npairs = buf[:nout].view(np.uint64)
+        self.wsum = buf[nout:2 * nout]
+        self.ravg = buf[2 * nout:3 * nout]
+        self.wp = buf[3 * nout:]
+        a = buf.ctypes.data
+        self.c = _capi.cf_result()
+        ctypes.memmove(ctypes.addressof(self.c), (ctypes.c_size_t * 4)(a, a + 8 * nout, a + 16 * nout, a + 24 * nout),
+                       ctypes.sizeof(self.c))
 
     def as_dict(self, p: Params) -> dict:
         d = {"npairs": self.npairs, "wsum": self.wsum}

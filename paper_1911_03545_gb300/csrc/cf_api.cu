@@ -133,6 +133,15 @@ int CfCtx::ensure_upload(size_t bytes)
     return CF_OK;
 }
 
+int CfCtx::ensure_aux()
+{
+    if (aux) return CF_OK;
+    int rc;
+    if ((rc = cuda(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming), "event"))) return rc;
+    if ((rc = cuda(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming), "event"))) return rc;
+    return cuda(cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking), "stream");
+}
+
 int CfCtx::ensure_bbox_host(size_t bytes)
 {
     if (hbb_cap >= bytes) return CF_OK;
@@ -163,6 +172,9 @@ CfCtx::~CfCtx()
 {
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (aux) cudaStreamDestroy(aux);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     for (auto &B : buf)
         if (B.p) cudaFree(B.p);
     if (hpin) cudaFreeHost(hpin);
@@ -268,6 +280,13 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     cudaStream_t st = C->stream;
     const int nsets = R.nsets, njobs = R.njobs;
 
+    // a call that failed between its side-stream bbox pass and the join left that pass unjoined:
+    // order it before this call's uploads
+    if (C->aux_pending) {
+        CF_CU(cudaStreamWaitEvent(st, C->ev_join, 0), "stream wait");
+        C->aux_pending = false;
+    }
+
     // ---- stage inputs (host arrays are copied; device arrays are used in place) ----
     if (in_bytes) CF_TRY(C->ensure(B_IN, in_bytes));
     R.sets.assign(nsets, CfSetDesc());
@@ -320,24 +339,36 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
               "bbox init and sets");
     }
     R.bb_sets = (const CfSetDesc *)((char *)C->buf[B_BBOX].p + soff);
-    CF_CU(cfb_bbox(R.bb_sets, nsets, std::max<int64_t>(R.nmax, 1), (unsigned long long *)C->buf[B_BBOX].p, st),
-          "bbox kernel");
-    C->launches = 1;
     // Periodic inputs whose sums need no weight range (no fixed-point per-warp sums) are planned from
-    // the box alone; their bbox readback is checked after the call's final synchronisation instead
-    // of waiting for it here.  Invalid data cannot fault in the meantime: cell indices clamp to the
-    // grid and a non-finite separation fails every cut.
+    // the box alone; their bbox pass runs on a side stream beside the build, and its readback is
+    // checked after the call's final synchronisation instead of being waited for here.  Invalid
+    // data cannot fault in the meantime: cell indices clamp to the grid and a non-finite separation
+    // fails every cut.
     const bool warp_sums = (p->kind == CF_DD_RPPI || p->kind == CF_DD_RPPI_MOCKS) &&
                            (p->weight == CF_W_PAIR_PRODUCT || p->output_ravg);
     R.bbox_deferred = p->periodic && !warp_sums && !C->capturing;
+    R.bbox_aux = false;
     R.fused_items = false;
+    cudaStream_t bst = st;
+    if (R.bbox_deferred) {
+        CF_TRY(C->ensure_aux());
+        CF_TRY(C->ensure_bbox_host(8 * bbw * (size_t)nsets));
+        CF_CU(cudaEventRecord(C->ev_fork, st), "event");
+        C->aux_pending = true;
+        CF_CU(cudaStreamWaitEvent(C->aux, C->ev_fork, 0), "stream wait");
+        bst = C->aux;
+        R.bbox_aux = true;
+    }
+    CF_CU(cfb_bbox(R.bb_sets, nsets, std::max<int64_t>(R.nmax, 1), (unsigned long long *)C->buf[B_BBOX].p, bst),
+          "bbox kernel");
+    C->launches = 1;
     double bbox[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
     double norm_dev = 0.0;   // largest | |v|^2 - 1 | over the points
     double vmin2 = INFINITY;  // smallest |v|^2 over the points
     if (R.bbox_deferred) {
-        CF_TRY(C->ensure_bbox_host(8 * bbw * (size_t)nsets));
-        CF_CU(cudaMemcpyAsync(C->hbb, C->buf[B_BBOX].p, 8 * bbw * (size_t)nsets, cudaMemcpyDeviceToHost, st),
+        CF_CU(cudaMemcpyAsync(C->hbb, C->buf[B_BBOX].p, 8 * bbw * (size_t)nsets, cudaMemcpyDeviceToHost, bst),
               "bbox readback");
+        CF_CU(cudaEventRecord(C->ev_join, bst), "event");
         R.wmin.assign(nsets, INFINITY);
         R.wmax.assign(nsets, 0.0);
         R.wneg = false;
@@ -714,6 +745,11 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     }
     C->launches += 2 + (R.items_cap > 0 ? 1 : 0);   // items emit, recheck, pair
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[3], st, C->capturing ? cudaEventRecordExternal : 0), "event");
+    // the side stream's bbox pass joins here, so that the call's synchronisation covers it
+    if (R.bbox_aux) {
+        CF_CU(cudaStreamWaitEvent(st, C->ev_join, 0), "stream wait");
+        C->aux_pending = false;
+    }
     // readback: the whole B_OUT block (counters, histograms, w^2 sums) in one copy
     CF_CU(cudaMemcpyAsync(C->hpin, out, readback_bytes(R), cudaMemcpyDeviceToHost, st), "readback");
     return CF_OK;
@@ -1017,6 +1053,9 @@ cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *
     if (rc) return (cf_status)rc;
     CfRun &R = C->run;
     R.items_cap = R.items_cap + R.items_cap / 4 + 1024;
+    // the graph sizes its work list here (one pass writes it) and runs its own bbox pass in line
+    R.fused_items = true;
+    R.bbox_aux = false;
     if ((rc = C->ensure(B_ITEMS, sizeof(CfItem) * (size_t)R.items_cap))) return (cf_status)rc;
     R.qcap = std::max(R.qcap, (uint32_t)std::min<int64_t>(CF_MAX_ENTRIES, C->stats.rechecked_pairs * 2 + 4096));
     if ((rc = C->ensure(B_QUEUE, 16 * (size_t)R.qcap))) return (cf_status)rc;

@@ -74,6 +74,7 @@ struct CfRun {
     bool angular = false;          // DD(theta) on the angular grid (needs unit vectors)
     bool bbox_deferred = false;    // periodic call planned from L: its bbox is checked after the final sync
     bool fused_items = false;      // the work list is counted and written in one pass (size known)
+    bool bbox_aux = false;         // the bbox pass runs on the side stream: join before the readback
     // the call's plan, tables and descriptors inside the B_PLANBLK device block
     const CfDevPlan *d_plan = nullptr;
     const uint16_t *d_lut = nullptr;
@@ -127,12 +128,16 @@ struct CfCtx {
     int graph_ncat = 0;
     bool capturing = false;
     cudaStream_t cap_stream = nullptr;   // stream used to record the batch graph
+    cudaStream_t aux = nullptr;          // side stream of the deferred bbox pass (runs beside the build)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool aux_pending = false;            // side-stream work not yet joined into `stream`
 
     int fail(int status, const std::string &msg);
     int cuda(cudaError_t e, const char *what);
     int ensure(int b, size_t bytes);
     int ensure_host(size_t bytes);
     int ensure_upload(size_t bytes);
+    int ensure_aux();
     int ensure_bbox_host(size_t bytes);
     void drop_graph();
     ~CfCtx();

@@ -596,9 +596,12 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
 // mode 0 writes the item count of each (job, cell) and adds the number of items, counted in 64 bits,
 // to *evaluated (the 32-bit scan of the counts would wrap silently past 2^32 items); mode 1 writes
 // the items at the scanned offsets and adds the pairs they hold to *evaluated.  Mode 2 needs no
-// count pass: each warp reserves the items of 32 stencil entries with one atomic on counts[0] (the
-// list's length when the kernel ends), adds their number in 64 bits to *total64, and writes them
-// like mode 1.  The list's order then follows the warps' arrival instead of (job, cell).
+// count pass: a block stages the items of its warps' cells in shared memory (each warp reserves
+// the items of 32 stencil entries there with a shared atomic), then reserves them in the global
+// list with one atomic on counts[0] (the list's length when the kernel ends) and copies them out
+// with 16-byte stores.  Entries that do not fit the stage reserve and write globally.  Their
+// number is added in 64 bits to *total64.  The list's order then follows the blocks' arrival
+// instead of (job, cell).
 __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
                                 const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox, int mode,
@@ -617,161 +620,204 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
     const uint32_t tile = plan->tile, jchunk = plan->jchunk;
     const uint32_t lane = threadIdx.x & 31u;
     unsigned long long ev = 0, nres = 0;
-    const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < nunit; u += wstride) {
-        const int job = (int)(u / g.ncell);
-        const int c = (int)(u - (int64_t)job * g.ncell);
-        const CfJobDesc J = jobs[job];
-        const CfSetDesc &A = sets[J.a];
-        const CfSetDesc &B = sets[J.b];
-        const uint32_t ia = cell_start[A.cbeg + c], na = cell_start[A.cbeg + c + 1] - ia;
-        uint32_t total = 0;
-        if (na) {
-            const int ci[3] = {c / (g.n[2] * g.n[1]), (c / g.n[2]) % g.n[1], c % g.n[2]};
-            const uint32_t nti = (na + tile - 1) / tile;
-            const uint32_t base = mode == 1 ? offsets[u] : 0u;
-            // target cells: the 3-D stencil, or for the angular grid the RA cells of the bands
-            // within k of this one whose RA range comes within the search angle: two points at
-            // declinations up to dm apart by an angle <= t differ in RA by at most
-            // 2 asin(sin(t / 2) / cos dm) (from the haversine formula)
-            int ncand = nst, bsel[2 * CFI_MAX_ANG_K + 1], blo[2 * CFI_MAX_ANG_K + 1], bn[2 * CFI_MAX_ANG_K + 1], nbs = 0;
-            if (plan->ang) {
-                const int ab = cf_band_of(plan, c);
-                const CfBand &Bi = plan->band[ab];
-                const int ar = c - Bi.base, k = g.k[0];
-                ncand = 0;
-                for (int b2 = max(0, ab - k); b2 <= min(plan->nband - 1, ab + k); b2++) {
-                    const CfBand &Bj = plan->band[b2];
-                    const double da = Bi.da[b2 - ab + k];
-                    int lo = 0, n = Bj.nra;
-                    if (da >= 0.0) {
-                        lo = (int)floor((ar * Bi.w - da) * Bj.inv_w);
-                        n = (int)floor(((ar + 1) * Bi.w + da) * Bj.inv_w) - lo + 1;
-                        if (n >= Bj.nra) { lo = 0; n = Bj.nra; }
-                    }
-                    bsel[nbs] = b2;
-                    blo[nbs] = lo;
-                    bn[nbs] = n;
-                    nbs++;
-                    ncand += n;
-                }
-            }
-            for (int s0 = 0; s0 < ncand; s0 += 32) {
-                const int s = s0 + (int)lane;
-                uint32_t cnt = 0, jb = 0, nb = 0, ntj = 0, tsj = 0;
-                bool diag = false;
-                int ct = 0, tj[3] = {0, 0, 0};
-                double delta[3] = {0.0, 0.0, 0.0};      // image of the j point: x_j + delta
-                if (s < ncand) {
-                    bool ok = true;
-                    if (plan->ang) {
-                        int q = 0, off = s;
-                        while (off >= bn[q]) { off -= bn[q]; q++; }
-                        const CfBand &Bj = plan->band[bsel[q]];
-                        int rr = (blo[q] + off) % Bj.nra;
-                        if (rr < 0) rr += Bj.nra;
-                        ct = Bj.base + rr;
-                    } else {
-                        for (int a = 0; a < 3; a++) {
-                            int v = ci[a] + stencil[s].d[a];
-                            if (g.wrap[a]) {
-                                v %= g.n[a];
-                            } else if (g.periodic) {
-                                if (v < 0) { v += g.n[a]; delta[a] = -g.L[a]; }
-                                else if (v >= g.n[a]) { v -= g.n[a]; delta[a] = g.L[a]; }
-                            } else if (v < 0 || v >= g.n[a]) {
-                                ok = false;
-                            }
-                            tj[a] = v;
-                        }
-                        ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
-                    }
-                    if (ok) {
-                        if (!(J.autoc && ct < c)) {
-                            jb = cell_start[B.cbeg + ct];
-                            nb = cell_start[B.cbeg + ct + 1] - jb;
-                            if (nb && prune) {
-                                // separation range of the two boxes per axis under this shift, in
-                                // float32; each gap is shrunk by a margin above this arithmetic's
-                                // rounding and that of the cell-relative coordinates, so a skipped
-                                // pair is out of every bin in FP64 as well
-                                const float *bi = cbox + 6 * (A.cbeg + c), *bj = cbox + 6 * (B.cbeg + ct);
-                                float s2 = 0.f, gz = 0.f;
-                                for (int a = 0; a < 3; a++) {
-                                    const float sh = plan->ang ? plan->origin32[3 * c + a] - plan->origin32[3 * ct + a]
-                                                               : (cf_cell_origin32(plan, a, c, ci[a]) -
-                                                                  cf_cell_origin32(plan, a, ct, tj[a])) - (float)delta[a];
-                                    const float lo = (bi[a] + sh) - bj[3 + a];
-                                    const float hi = (bi[3 + a] + sh) - bj[a];
-                                    float gap = lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
-                                    gap = fmaxf(0.f, gap - plan->pmargin[a]);
-                                    if (zsep && a == 2) gz = gap;
-                                    else s2 = fmaf(gap, gap, s2);
-                                }
-                                if (s2 >= plan->e2max32 || (zsep && gz >= plan->zmax32)) nb = 0;
-                            }
-                            if (nb) {
-                                diag = J.autoc && ct == c;
-                                if (diag) {
-                                    ntj = nti;
-                                    tsj = tile;
-                                } else {
-                                    ntj = (nb + jchunk - 1) / jchunk;
-                                    tsj = (nb + ntj - 1) / ntj;
-                                }
-                                cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
-                                if (mode == 0)
-                                    ev += diag ? (unsigned long long)nti * (nti + 1) / 2
-                                               : (unsigned long long)nti * ntj;
-                            }
-                        }
-                    }
-                }
-                uint32_t incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t v = __shfl_up_sync(CF_FULL, incl, o);
-                    if ((int)lane >= o) incl += v;
-                }
-                uint32_t cbase = base + total;
-                if (mode == 2) {
-                    const uint32_t ctot = __shfl_sync(CF_FULL, incl, 31);
-                    uint32_t r = 0;
-                    if (lane == 0 && ctot) r = atomicAdd(counts, ctot);
-                    cbase = __shfl_sync(CF_FULL, r, 0);
-                    nres += ctot;
-                }
-                if (mode != 0 && cnt) {
-                    uint32_t o = cbase + (incl - cnt);
-                    // the item's shift in FP64, split into float32 hi + lo (Sec. 4.4 applied per cell)
-                    float sh[3], sl[3];
-                    for (int a = 0; a < 3; a++) {
-                        const double shift = plan->ang ? plan->origin[3 * c + a] - plan->origin[3 * ct + a]
-                                                       : cf_origin(plan, a, ci[a]) - cf_origin(plan, a, tj[a]) - delta[a];
-                        sh[a] = (float)shift;
-                        sl[a] = (float)(shift - (double)sh[a]);
-                    }
-                    for (uint32_t a0 = 0; a0 < nti; a0++) {
-                        const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
-                        for (uint32_t b = diag ? a0 : 0; b < ntj; b++) {
-                            const uint32_t j0 = b * tsj, jc = min(tsj, nb - j0);
-                            CfItem it;
-                            it.ibeg = ia + i0;
-                            it.jbeg = jb + j0;
-                            it.cnt = ic | (jc << 16);
-                            it.meta = (uint32_t)job | ((diag && b == a0) ? CFI_ITEM_DIAG : 0u);
-                            it.s[0] = sh[0]; it.s[1] = sh[1]; it.s[2] = sh[2]; it.pad0 = 0.f;
-                            it.slo[0] = sl[0]; it.slo[1] = sl[1]; it.slo[2] = sl[2]; it.pad1 = 0.f;
-                            if (o < items_cap) items[o] = it;
-                            o++;
-                            ev += (unsigned long long)ic * jc;
-                        }
-                    }
-                }
-                total += __shfl_sync(CF_FULL, incl, 31);
-            }
+    __shared__ uint32_t s_n, s_base;
+    __shared__ __align__(16) CfItem s_items[CFB_ITEM_STAGE];
+    // every warp of a block runs the same number of iterations (block-wide barriers in mode 2)
+    const int64_t wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
+    for (int64_t ub = blockIdx.x * wpb; ub < nunit; ub += (int64_t)gridDim.x * wpb) {
+        if (mode == 2) {
+            if (threadIdx.x == 0) s_n = 0;
+            __syncthreads();
         }
-        if (mode == 0 && lane == 0) counts[u] = total;
+        const int64_t u = ub + warp;
+        if (u < nunit) {
+            const int job = (int)(u / g.ncell);
+            const int c = (int)(u - (int64_t)job * g.ncell);
+            const CfJobDesc J = jobs[job];
+            const CfSetDesc &A = sets[J.a];
+            const CfSetDesc &B = sets[J.b];
+            const uint32_t ia = cell_start[A.cbeg + c], na = cell_start[A.cbeg + c + 1] - ia;
+            uint32_t total = 0;
+            if (na) {
+                const int ci[3] = {c / (g.n[2] * g.n[1]), (c / g.n[2]) % g.n[1], c % g.n[2]};
+                const uint32_t nti = (na + tile - 1) / tile;
+                const uint32_t base = mode == 1 ? offsets[u] : 0u;
+                // target cells: the 3-D stencil, or for the angular grid the RA cells of the bands
+                // within k of this one whose RA range comes within the search angle: two points at
+                // declinations up to dm apart by an angle <= t differ in RA by at most
+                // 2 asin(sin(t / 2) / cos dm) (from the haversine formula)
+                int ncand = nst, nbs = 0;
+                int bsel[2 * CFI_MAX_ANG_K + 1], blo[2 * CFI_MAX_ANG_K + 1], bn[2 * CFI_MAX_ANG_K + 1];
+                if (plan->ang) {
+                    const int ab = cf_band_of(plan, c);
+                    const CfBand &Bi = plan->band[ab];
+                    const int ar = c - Bi.base, k = g.k[0];
+                    ncand = 0;
+                    for (int b2 = max(0, ab - k); b2 <= min(plan->nband - 1, ab + k); b2++) {
+                        const CfBand &Bj = plan->band[b2];
+                        const double da = Bi.da[b2 - ab + k];
+                        int lo = 0, n = Bj.nra;
+                        if (da >= 0.0) {
+                            lo = (int)floor((ar * Bi.w - da) * Bj.inv_w);
+                            n = (int)floor(((ar + 1) * Bi.w + da) * Bj.inv_w) - lo + 1;
+                            if (n >= Bj.nra) { lo = 0; n = Bj.nra; }
+                        }
+                        bsel[nbs] = b2;
+                        blo[nbs] = lo;
+                        bn[nbs] = n;
+                        nbs++;
+                        ncand += n;
+                    }
+                }
+                for (int s0 = 0; s0 < ncand; s0 += 32) {
+                    const int s = s0 + (int)lane;
+                    uint32_t cnt = 0, jb = 0, nb = 0, ntj = 0, tsj = 0;
+                    bool diag = false;
+                    int ct = 0, tj[3] = {0, 0, 0};
+                    double delta[3] = {0.0, 0.0, 0.0};      // image of the j point: x_j + delta
+                    if (s < ncand) {
+                        bool ok = true;
+                        if (plan->ang) {
+                            int q = 0, off = s;
+                            while (off >= bn[q]) { off -= bn[q]; q++; }
+                            const CfBand &Bj = plan->band[bsel[q]];
+                            int rr = (blo[q] + off) % Bj.nra;
+                            if (rr < 0) rr += Bj.nra;
+                            ct = Bj.base + rr;
+                        } else {
+                            for (int a = 0; a < 3; a++) {
+                                int v = ci[a] + stencil[s].d[a];
+                                if (g.wrap[a]) {
+                                    v %= g.n[a];
+                                } else if (g.periodic) {
+                                    if (v < 0) { v += g.n[a]; delta[a] = -g.L[a]; }
+                                    else if (v >= g.n[a]) { v -= g.n[a]; delta[a] = g.L[a]; }
+                                } else if (v < 0 || v >= g.n[a]) {
+                                    ok = false;
+                                }
+                                tj[a] = v;
+                            }
+                            ct = (tj[0] * g.n[1] + tj[1]) * g.n[2] + tj[2];
+                        }
+                        if (ok) {
+                            if (!(J.autoc && ct < c)) {
+                                jb = cell_start[B.cbeg + ct];
+                                nb = cell_start[B.cbeg + ct + 1] - jb;
+                                if (nb && prune) {
+                                    // separation range of the two boxes per axis under this shift, in
+                                    // float32; each gap is shrunk by a margin above this arithmetic's
+                                    // rounding and that of the cell-relative coordinates, so a skipped
+                                    // pair is out of every bin in FP64 as well
+                                    const float *bi = cbox + 6 * (A.cbeg + c), *bj = cbox + 6 * (B.cbeg + ct);
+                                    float s2 = 0.f, gz = 0.f;
+                                    for (int a = 0; a < 3; a++) {
+                                        const float sh =
+                                            plan->ang ? plan->origin32[3 * c + a] - plan->origin32[3 * ct + a]
+                                                      : (cf_cell_origin32(plan, a, c, ci[a]) -
+                                                         cf_cell_origin32(plan, a, ct, tj[a])) - (float)delta[a];
+                                        const float lo = (bi[a] + sh) - bj[3 + a];
+                                        const float hi = (bi[3 + a] + sh) - bj[a];
+                                        float gap = lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
+                                        gap = fmaxf(0.f, gap - plan->pmargin[a]);
+                                        if (zsep && a == 2) gz = gap;
+                                        else s2 = fmaf(gap, gap, s2);
+                                    }
+                                    if (s2 >= plan->e2max32 || (zsep && gz >= plan->zmax32)) nb = 0;
+                                }
+                                if (nb) {
+                                    diag = J.autoc && ct == c;
+                                    if (diag) {
+                                        ntj = nti;
+                                        tsj = tile;
+                                    } else {
+                                        ntj = (nb + jchunk - 1) / jchunk;
+                                        tsj = (nb + ntj - 1) / ntj;
+                                    }
+                                    cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
+                                    if (mode == 0)
+                                        ev += diag ? (unsigned long long)nti * (nti + 1) / 2
+                                                   : (unsigned long long)nti * ntj;
+                                }
+                            }
+                        }
+                    }
+                    uint32_t incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t v = __shfl_up_sync(CF_FULL, incl, o);
+                        if ((int)lane >= o) incl += v;
+                    }
+                    uint32_t cbase = base + total;
+                    bool staged = false;
+                    if (mode == 2) {
+                        const uint32_t ctot = __shfl_sync(CF_FULL, incl, 31);
+                        uint32_t r = 0, st = 0;
+                        if (lane == 0 && ctot) {
+                            // a place in the stage when the entries fit (the CAS only fails when another
+                            // warp of the block reserved; bounded, then global), else in the list
+                            uint32_t old = *(volatile uint32_t *)&s_n;
+                            for (int t = 0; t < 64 && old + ctot <= CFB_ITEM_STAGE; t++) {
+                                const uint32_t seen = atomicCAS(&s_n, old, old + ctot);
+                                if (seen == old) {
+                                    r = old;
+                                    st = 1;
+                                    break;
+                                }
+                                old = seen;
+                            }
+                            if (!st) r = atomicAdd(counts, ctot);
+                        }
+                        cbase = __shfl_sync(CF_FULL, r, 0);
+                        staged = __shfl_sync(CF_FULL, st, 0) != 0;
+                        nres += ctot;
+                    }
+                    if (mode != 0 && cnt) {
+                        uint32_t o = cbase + (incl - cnt);
+                        // the item's shift in FP64, split into float32 hi + lo (Sec. 4.4 applied per cell)
+                        float sh[3], sl[3];
+                        for (int a = 0; a < 3; a++) {
+                            const double shift =
+                                plan->ang ? plan->origin[3 * c + a] - plan->origin[3 * ct + a]
+                                          : cf_origin(plan, a, ci[a]) - cf_origin(plan, a, tj[a]) - delta[a];
+                            sh[a] = (float)shift;
+                            sl[a] = (float)(shift - (double)sh[a]);
+                        }
+                        for (uint32_t a0 = 0; a0 < nti; a0++) {
+                            const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
+                            for (uint32_t b = diag ? a0 : 0; b < ntj; b++) {
+                                const uint32_t j0 = b * tsj, jc = min(tsj, nb - j0);
+                                CfItem it;
+                                it.ibeg = ia + i0;
+                                it.jbeg = jb + j0;
+                                it.cnt = ic | (jc << 16);
+                                it.meta = (uint32_t)job | ((diag && b == a0) ? CFI_ITEM_DIAG : 0u);
+                                it.s[0] = sh[0]; it.s[1] = sh[1]; it.s[2] = sh[2]; it.pad0 = 0.f;
+                                it.slo[0] = sl[0]; it.slo[1] = sl[1]; it.slo[2] = sl[2]; it.pad1 = 0.f;
+                                if (staged) s_items[o] = it;
+                                else if (o < items_cap) items[o] = it;
+                                o++;
+                                ev += (unsigned long long)ic * jc;
+                            }
+                        }
+                    }
+                    total += __shfl_sync(CF_FULL, incl, 31);
+                }
+            }
+            if (mode == 0 && lane == 0) counts[u] = total;
+        }
+        if (mode == 2) {
+            // the block's staged items: one reservation, then 16-byte stores (48-byte items)
+            __syncthreads();
+            const uint32_t n = s_n;
+            if (threadIdx.x == 0 && n) s_base = atomicAdd(counts, n);
+            __syncthreads();
+            const uint32_t b0 = s_base;
+            const uint4 *src = (const uint4 *)s_items;
+            uint4 *dst = (uint4 *)(items + b0);
+            for (uint32_t k = threadIdx.x; k < 3u * n; k += blockDim.x)
+                if (b0 + k / 3u < items_cap) dst[k] = src[k];
+            __syncthreads();
+        }
     }
     if (evaluated) {
         for (int o = 16; o; o >>= 1) ev += __shfl_xor_sync(CF_FULL, ev, o);

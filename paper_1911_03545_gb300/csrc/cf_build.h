@@ -7,6 +7,7 @@
 // per point set: 3 min keys, 3 max keys, bad, norm deviation, min |v|^2, smallest nonzero |w|,
 // largest |w|, negative weights
 #define CFB_BBOX_WORDS 12
+#define CFB_ITEM_STAGE 256      // work items a block of the one-pass work list stages in shared memory
 cudaError_t cfb_bbox(const CfSetDesc *sets, int nsets, int64_t nmax, unsigned long long *out, cudaStream_t st);
 // fills out[nsets * CFB_BBOX_WORDS] with the starting values cfb_bbox reduces into
 cudaError_t cfb_bbox_init(unsigned long long *out, int nsets, cudaStream_t st);
