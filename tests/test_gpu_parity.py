@@ -469,3 +469,26 @@ def test_points_on_and_beside_cell_boundaries(ctx, periodic):
     exp = oracle.count("r", edges, d, **kw)
     assert_match(got, exp, True, True)
     assert int(np.asarray(exp["npairs"]).sum()) > 10000
+
+
+def test_work_list_outgrows_the_previous_size(ctx):
+    """A repeat call on the same plan writes its work list in one pass, into the previous call's
+    size plus a quarter.  A catalogue with many more cell pairs than the one before it overflows
+    that capacity; the call then counts again with the size it measured.  Every call equals the
+    oracle."""
+    import torch
+    import paper_1911_03545_gb300 as cf
+    c = cf.cf_create(0, torch.cuda.current_stream())
+    try:
+        edges = gen.log_edges(0.2, 5.0, 8)
+        dense = gen.clustered_box(1, 20000, 0.5, 100.0, 71)     # a few cells
+        spread = gen.uniform_box(20000, 100.0, 72)              # every cell
+        items = []
+        for d in (dense, spread, dense, spread):
+            got, exp = both(c, "r", edges, d, autocorr=True, periodic=True, box=100.0)
+            assert_match(got, exp)
+            items.append(cf.cf_get_stats(c)["work_items"])
+        assert items[1] > items[0] + items[0] // 4 + 1024
+        assert items[3] == items[1] and items[2] == items[0]
+    finally:
+        cf.cf_destroy(c)
