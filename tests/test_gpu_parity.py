@@ -492,3 +492,22 @@ def test_work_list_outgrows_the_previous_size(ctx):
         assert items[3] == items[1] and items[2] == items[0]
     finally:
         cf.cf_destroy(c)
+
+
+def test_scan_over_many_tiles(ctx):
+    """The cell scan's tile offsets are scanned by the last block in chunks of 4096 tiles: 68^3
+    cells with 64 Morton sub-cells each make 2.0e7 keys (4913 tiles), so the second chunk runs.
+    Two calls (the second writes its work list in one pass) equal the oracle."""
+    import torch
+    import paper_1911_03545_gb300 as cf
+    c = cf.cf_create(0, torch.cuda.current_stream())
+    try:
+        cf.cf_set_option(c, cf.CF_OPT_CELL_ORDER, 4)
+        edges = gen.log_edges(0.1, 1.0, 6)
+        d = gen.uniform_box(200000, 68.0, 81)
+        for _ in range(2):
+            got, exp = both(c, "r", edges, d, autocorr=True, periodic=True, box=68.0)
+            assert_match(got, exp)
+        assert cf.cf_get_stats(c)["cells"] == 68 ** 3
+    finally:
+        cf.cf_destroy(c)
