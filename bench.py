@@ -399,23 +399,96 @@ def _oracle_rows_rate(wl, seconds: float, seed: int = 0):
     return evals / t, cores, sample, t
 
 
+def _zwin_estimate(wl, seconds: float, seed: int = 1) -> dict:
+    """The z-window oracle's time for the whole workload, extrapolated from row samples.  The cost
+    of a row is the slope between a sample of R rows and one of 2R rows (each call also pays a fixed
+    cost: converting the arrays and the z sort, which the slope cancels); the whole run is that
+    fixed cost plus n1 rows.  A row of an auto-correlation scans its full window but bins only
+    j > i: between half and all of an ordered row's cost, so the estimate is a range."""
+    import numpy as np
+
+    import oracle
+    lib = oracle.load()
+    cores = os.cpu_count() or 1
+    n1 = wl.d1.n
+    rng = np.random.Generator(np.random.PCG64(seed + 100))
+
+    def run(rows):
+        start = int(rng.integers(0, max(1, n1 - rows)))
+        t0 = time.perf_counter()
+        oracle.count(wl.kind, wl.edges, wl.d1, None if wl.autocorr else wl.d2, autocorr=wl.autocorr,
+                     periodic=wl.periodic, box=wl.box, pimax=wl.pimax, npibins=wl.npibins, weighted=wl.weighted,
+                     ravg=wl.ravg, rows=(start, start + rows), mode="zwin", nthreads=cores, lib=lib)
+        return time.perf_counter() - t0
+
+    # the oracle hands rows to its threads 64 at a time: a sample of fewer than a few chunks per
+    # thread would time one thread's work; grow it while the rows take under `seconds`
+    r1 = max(1, min(n1 // 2, 128 * cores))
+    t1, t2 = run(r1), run(2 * r1)
+    while t2 - t1 < 0.25 * seconds and 4 * r1 <= n1:
+        r1 *= 2
+        t1, t2 = t2, run(2 * r1)
+    per_row = max(t2 - t1, 1e-9) / r1
+    fix = max(0.0, t1 - per_row * r1)
+    rows_t = per_row * n1
+    lo, hi = (fix + 0.5 * rows_t, fix + rows_t) if wl.autocorr else (fix + rows_t, fix + rows_t)
+    return {"zwin_seconds_full_est": 0.5 * (lo + hi), "zwin_seconds_full_range": [lo, hi],
+            "zwin_sample": f"{r1} and {2 * r1} consecutive rows (random starts) through the z window, {cores} "
+                           f"threads, {t1:.2f} s and {t2:.2f} s: {1e3 * per_row:.4f} ms per row, {fix:.2f} s per "
+                           f"call; scaled to {n1} rows" + ("; the whole auto-correlation bins only j > i of each "
+                                                          "row's window, so its time lies in the range given"
+                                                          if wl.autocorr else "")}
+
+
 def _cpu_baseline(wl, seconds: float) -> dict:
     """The oracle beside the GPU on the box's own cores: its brute-force rate on a row sample (the
     line's unit), and the z-window oracle's time for the whole workload, extrapolated from a row
-    sample (an auto-correlation bins only j > i of each row's window, about half of it)."""
+    sample."""
     rate, cores, sample, _ = _oracle_rows_rate(wl, 0.5 * seconds)
-    zrows, zt, _, zfix = _oracle_rows(wl, 0.5 * seconds, seed=1, mode="zwin")
-    n1 = wl.d1.n
-    # a row of the whole auto-correlation scans its full window but bins only j > i: between half
-    # and all of an ordered row's cost
-    per_rows = (zt - zfix) * n1 / zrows
-    lo, hi = (zfix + 0.5 * per_rows, zfix + per_rows) if wl.autocorr else (zfix + per_rows, zfix + per_rows)
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
-            "zwin_seconds_full_est": 0.5 * (lo + hi), "zwin_seconds_full_range": [lo, hi],
-            "zwin_sample": f"{zrows} consecutive rows (random start) through the z window, {cores} threads, "
-                           f"{zt:.2f} s, of which {zfix:.2f} s the call's fixed cost (the z sort); rows scaled by "
-                           f"{n1}/{zrows}" + ("; the whole auto-correlation bins only j > i of each row's window, "
-                                              "so its time lies in the range given" if wl.autocorr else "")}
+    out = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    out.update(_zwin_estimate(wl, 0.5 * seconds))
+    return out
+
+
+def _oracle_beside(seconds: float) -> dict:
+    """The oracle's time for every other configuration on the same cores: the 20,000-point one run
+    whole (brute force and z window), the others through the z window extrapolated from row samples,
+    and the 256-catalogue batch from row samples of four of its catalogues, scaled by the sum of
+    N^2 (a catalogue's pairs within the window grow as N^2 at a fixed box)."""
+    import gen
+    import oracle
+    lib = oracle.load()
+    cores = os.cpu_count() or 1
+    out = {}
+    for name in EXTRA_WORKLOADS:
+        wl = gen.workload(name)
+        if name == "uniform_r_20k":
+            kw = dict(autocorr=wl.autocorr, periodic=wl.periodic, box=wl.box, weighted=wl.weighted, ravg=wl.ravg,
+                      nthreads=cores, lib=lib)
+            t = {}
+            for mode in ("brute", "zwin"):
+                t0 = time.perf_counter()
+                oracle.count(wl.kind, wl.edges, wl.d1, None, mode=mode, **kw)
+                t[mode] = time.perf_counter() - t0
+            n = wl.d1.n
+            out[name] = {"brute_seconds": t["brute"], "brute_pairs_per_s": n * (n - 1) / t["brute"],
+                         "zwin_seconds": t["zwin"], "sample": f"the whole workload, {cores} threads"}
+            continue
+        out[name] = _zwin_estimate(wl, seconds)
+    sizes, cats = _batch_setup(256)
+    per_n2 = []
+    for i in (0, 64, 128, 192):
+        wl = gen.Workload(f"batch_{i}", "rppi", True, True, 250.0, gen.log_edges(0.1, 20.0, 14), cats[i],
+                          pimax=40.0, npibins=40)
+        e = _zwin_estimate(wl, 0.25 * seconds, seed=2)
+        per_n2.append([x / sizes[i] ** 2 for x in e["zwin_seconds_full_range"]])
+    sn2 = float(sum(n * n for n in sizes))
+    lo = sn2 * statistics.fmean(r[0] for r in per_n2)
+    hi = sn2 * statistics.fmean(r[1] for r in per_n2)
+    out["batch256"] = {"zwin_seconds_full_est": 0.5 * (lo + hi), "zwin_seconds_full_range": [lo, hi],
+                       "zwin_sample": f"row samples of catalogues 0, 64, 128 and 192 through the z window, {cores} "
+                                      f"threads; seconds per N^2 averaged and scaled by the batch's sum of N^2"}
+    return out
 
 
 def run_reference(args, wl, world, rank):
@@ -573,6 +646,8 @@ def run_gpu(args, wl, world, rank, local):
         line.update(_extras(args, cf, tune, ctx, dev, local, flush))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(wl, args.cpu_seconds)
+        if not args.no_extras:
+            line["cpu_baseline"]["other_configs"] = _oracle_beside(args.cpu_seconds / 6)
     if rank == 0:
         print(json.dumps(line), flush=True)
     cf.cf_destroy(ctx)

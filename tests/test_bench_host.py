@@ -54,3 +54,22 @@ def test_parity_flag_against_the_stored_histograms():
     other = gen.uniform_box(100, 250.0, 1, dtype=np.float64)
     assert bench._parity("uniform_r_20k", got, (other,))["ok"] is None
     assert bench._parity("no_such_workload", got, (wl.d1,))["ok"] is None
+
+
+def test_zwin_estimate_brackets_a_whole_run():
+    """The CPU baseline's z-window estimate (slope between two row samples plus the call's fixed
+    cost) on a scaled-down clustered workload: a range with lo <= hi, within a factor 4 of the time
+    of the whole run it stands for."""
+    import time
+
+    import bench
+    import oracle
+    wl = gen.workload("clustered_r_1m", scale=0.05)
+    est = bench._zwin_estimate(wl, 0.5)
+    lo, hi = est["zwin_seconds_full_range"]
+    assert 0.0 < lo <= hi and lo <= est["zwin_seconds_full_est"] <= hi
+    t0 = time.perf_counter()
+    oracle.count(wl.kind, wl.edges, wl.d1, None, autocorr=True, periodic=True, box=wl.box, weighted=True, ravg=True,
+                 mode="zwin")
+    t = time.perf_counter() - t0
+    assert hi >= t / 4 and lo <= 4 * t, (lo, hi, t)
