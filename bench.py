@@ -264,9 +264,10 @@ def _peak_pairs(dev, kind) -> float:
     return props.multi_processor_count * 128 * sm_max * 1e6 / FP32_INSTR_PER_PAIR_KIND.get(kind, FP32_INSTR_PER_PAIR)
 
 
-def _measure_workload(args, cf, tune, ctx, name, dev, flush) -> dict:
-    """One more configuration on the headline's context: tuned (cache honoured), 2 untimed calls,
-    then args.extra_steps calls with the L2 flushed before each, device-resident inputs."""
+def _measure_workload(args, cf, tune, ctx, name, dev, flush, force: dict | None = None) -> dict:
+    """One more configuration on the headline's context: tuned (cache honoured; `force` then
+    overrides knobs), 2 untimed calls, then args.extra_steps calls with the L2 flushed before each,
+    device-resident inputs."""
     import numpy as np
     import torch
 
@@ -290,6 +291,9 @@ def _measure_workload(args, cf, tune, ctx, name, dev, flush) -> dict:
     tune.reset(ctx)
     tuned = tune.tune(ctx, p, d1, d2, device_name=torch.cuda.get_device_name(dev), npoints=npts, reps=3, passes=1,
                       use_cache=not args.no_tune_cache, timer=step_time)
+    if force:
+        tuned = dict(tuned, **force)
+        tune.apply(ctx, tuned)
     for _ in range(2):
         out = cf.cf_count(ctx, p, d1, d2)
     step_ms, pair_ms = [], []
@@ -325,6 +329,10 @@ def _extras(args, cf, tune, ctx, dev, local, flush) -> dict:
     256-catalogue batch counted one at a time, batched, graph-replayed and served."""
     import numpy as np
     out = {"workloads": {name: _measure_workload(args, cf, tune, ctx, name, dev, flush) for name in EXTRA_WORKLOADS}}
+    # the same workloads with the pair kernel given only the 32-point groups within reach (an
+    # option the line's other figures leave off: it lowers the evaluated-pair count they measure)
+    out["block_prune"] = {name: _measure_workload(args, cf, tune, ctx, name, dev, flush, force={"block": 1})
+                          for name in ("clustered_r_1m", "clustered_rppi_2m", "clustered_rppi_dr")}
     sizes, cats = _batch_setup(256)
     b = _batch_measure(args, cf, tune, dev, local, sizes, cats, 2)
     r = _serve_measure(args, cf, dev, local, cats, args.extra_requests)

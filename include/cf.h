@@ -173,7 +173,14 @@ typedef enum {
     CF_OPT_THETA_GRID = 13,  /* DD(theta) cell list: 0 (default) a 3-D grid over the unit vectors,
                                 1 declination bands x right-ascension cells (Sec. 4.1.2), for wide or
                                 near-polar footprints.  Results are the same for both */
-    CF_OPT_COUNT_ = 14
+    CF_OPT_BLOCK_PRUNE = 14, /* 1: inside a cell pair kept by CF_OPT_CELL_PRUNE, test each i tile
+                                against every group of 32 consecutive points of the j cell and give
+                                the pair kernel only the runs of groups that may hold a pair within
+                                the largest edge (or pimax): the late entry / early exit of Sec. 4.5
+                                at group granularity; skipped pairs are not evaluated.  0 (default):
+                                whole cells.  No effect with CF_OPT_CELL_PRUNE = 1.  Results are the
+                                same either way */
+    CF_OPT_COUNT_ = 15
 } cf_option;
 cf_status cf_set_option(void *ctx, int option, int64_t value);
 

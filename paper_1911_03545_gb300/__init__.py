@@ -20,7 +20,7 @@ import numpy as np
 from . import _capi
 from ._capi import (  # noqa: F401
     CF_DD_R, CF_DD_RPPI, CF_DD_RPPI_MOCKS, CF_DD_THETA, CF_F32, CF_F64, CF_OK, CF_OPT_AUDIT, CF_OPT_CTAS_PER_SM, CF_OPT_ITER_LIMIT,
-    CF_OPT_CELL_ORDER, CF_OPT_CELL_PRUNE, CF_OPT_JCHUNK, CF_OPT_MEM_CAP, CF_OPT_QUEUE, CF_OPT_REFINE, CF_OPT_THETA_GRID, CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS,
+    CF_OPT_BLOCK_PRUNE, CF_OPT_CELL_ORDER, CF_OPT_CELL_PRUNE, CF_OPT_JCHUNK, CF_OPT_MEM_CAP, CF_OPT_QUEUE, CF_OPT_REFINE, CF_OPT_THETA_GRID, CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS,
     CF_W_NONE, CF_W_PAIR_PRODUCT, CF_WP, STATUS_NAMES,
 )
 

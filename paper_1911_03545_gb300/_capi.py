@@ -22,7 +22,8 @@ CF_W_NONE, CF_W_PAIR_PRODUCT = 0, 1
 CF_MAX_BINS = 252
 CF_MAX_PIBINS = 252
 (CF_OPT_MEM_CAP, CF_OPT_VARIANT, CF_OPT_TILE, CF_OPT_JCHUNK, CF_OPT_QUEUE, CF_OPT_CTAS_PER_SM, CF_OPT_AUDIT,
- CF_OPT_ITER_LIMIT, CF_OPT_WARPS, CF_OPT_REFINE, CF_OPT_CELL_PRUNE, CF_OPT_CELL_ORDER, CF_OPT_THETA_GRID) = range(1, 14)
+ CF_OPT_ITER_LIMIT, CF_OPT_WARPS, CF_OPT_REFINE, CF_OPT_CELL_PRUNE, CF_OPT_CELL_ORDER, CF_OPT_THETA_GRID,
+ CF_OPT_BLOCK_PRUNE) = range(1, 15)
 
 STATUS_NAMES = {0: "CF_OK", -1: "CF_ERR_ARG", -2: "CF_ERR_OOM", -3: "CF_ERR_CUDA", -4: "CF_ERR_TIMEOUT",
                 -5: "CF_ERR_BUSY", -6: "CF_ERR_CANCELLED", -7: "CF_ERR_INTERNAL"}

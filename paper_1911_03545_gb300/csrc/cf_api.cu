@@ -483,6 +483,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_PB, 16 * (size_t)R.np));
     CF_TRY(C->ensure(B_ORIG, 4 * (size_t)R.np));
     CF_TRY(C->ensure(B_CBOX, 24 * (size_t)R.ncell_all));
+    if (C->opt[CF_OPT_CELL_PRUNE] == 0 && C->opt[CF_OPT_BLOCK_PRUNE] == 1) CF_TRY(C->ensure(B_GBOX, 24 * (size_t)R.np));
     if (D.f64lo) CF_TRY(C->ensure(B_PLO, 32 * (size_t)R.np));
     CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.nfine, R.nunit))));
     CF_TRY(C->ensure(B_ICNT, 4 * (size_t)std::max<int64_t>(R.nunit, 1)));
@@ -588,20 +589,24 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
                       (float4 *)C->buf[B_PLO].p, (uint32_t *)C->buf[B_ORIG].p, st),
           "scatter");
     const float *cbox = nullptr;
+    float *gbox = nullptr;
     if (C->opt[CF_OPT_CELL_PRUNE] == 0) {
+        // and, when asked for, the boxes of the cells' 32-point groups
+        gbox = C->opt[CF_OPT_BLOCK_PRUNE] == 1 ? (float *)C->buf[B_GBOX].p : nullptr;
         CF_CU(cfb_cellbox(cstart, R.ncell_all, (const float4 *)C->buf[B_PA].p, (const float4 *)C->buf[B_PB].p,
-                          (float *)C->buf[B_CBOX].p, st),
+                          (float *)C->buf[B_CBOX].p, gbox, st),
               "cell boxes");
         cbox = (const float *)C->buf[B_CBOX].p;
         C->launches += 1;
     }
     R.cbox = cbox;
+    R.gbox = gbox;
     C->launches += 4;    // assign, 2 scan, scatter
     if (R.fused_items) return CF_OK;    // the count pass writes the work list in one go
     uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
     // the work list's length in 64 bits, next to its 32-bit scan (checked in cf_finish)
     unsigned long long *items64 = (unsigned long long *)(out + OUT_ITEMS64);
-    CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, cstart, cbox, R.nunit, 0, icnt, nullptr,
+    CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, cstart, cbox, gbox, R.nunit, 0, icnt, nullptr,
                     nullptr, 0, items64, nullptr, st),
           "items count");
     CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, (uint32_t *)(out + OUT_SCAN + 4), st,
@@ -682,12 +687,12 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     uint32_t *nitems_dev = ioff + R.nunit;
     if (R.fused_items) {
         nitems_dev = (uint32_t *)(out + OUT_NITEMS);
-        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.nunit, 2,
+        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.gbox, R.nunit, 2,
                         nitems_dev, nullptr, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
                         (unsigned long long *)(out + OUT_ITEMS64), st),
               "items");
     } else {
-        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.nunit, 1,
+        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.gbox, R.nunit, 1,
                         (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
                         nullptr, st),
               "items emit");
@@ -844,9 +849,10 @@ int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &p
     C->drop_graph();
     CF_TRY(cf_prepare(C, p, pts, jobs, R));
     cudaStream_t st = C->stream;
-    // the work list depends on the plan and on the cell pruning and order options
+    // the work list depends on the plan and on the pruning and order options
     const std::string ikey = C->plan_key + std::to_string(C->opt[CF_OPT_CELL_PRUNE]) + "/" +
-                             std::to_string(C->opt[CF_OPT_CELL_ORDER]);
+                             std::to_string(C->opt[CF_OPT_CELL_ORDER]) + "/" +
+                             std::to_string(C->opt[CF_OPT_BLOCK_PRUNE]);
     // a call on the same plan sized the work list before: take that size with headroom, count and
     // write the list in one pass, and let cf_finish run the count again in the rare case that the
     // list outgrew it

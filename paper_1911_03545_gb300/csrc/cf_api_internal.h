@@ -12,7 +12,7 @@
 enum CfBuf {
     B_IN, B_SETS, B_BBOX, B_PLAN, B_LUT, B_FINE, B_STENCIL, B_JOBS, B_CNT, B_CSTART, B_CELLID, B_SLOT,
     B_PA, B_PB, B_PLO, B_ORIG, B_SCAN, B_ICNT, B_IOFF, B_ITEMS, B_HCNT, B_HW, B_HR, B_QUEUE, B_WSQ, B_MISC, B_ORIGIN,
-    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_PLANBLK, B_COUNT_
+    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_PLANBLK, B_GBOX, B_COUNT_
 };
 
 // B_OUT: the counters and histograms one call reads back, laid out as the host copy of them (one
@@ -65,6 +65,7 @@ struct CfRun {
     int nsets = 0, njobs = 0;
     int64_t npts = 0, nmax = 0, np = 1, ncell = 0, ncell_all = 0, nst = 0, nunit = 0;
     const float *cbox = nullptr;   // cell boxes for pruning (nullptr: every stencil neighbour)
+    const float *gbox = nullptr;   // 32-point group boxes for pruning inside cell pairs (or nullptr)
     int sub = 1;                   // Morton sub-cells per axis inside a cell (1, 2, 4)
     int64_t nfine = 0;             // ncell_all * sub^3 counting-sort keys
     size_t nslot = 0, hsz = 0;

@@ -562,22 +562,38 @@ __global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSe
 // kernel (x - origin; lo then hi per axis, 6 floats per cell of every point set).  One warp per
 // cell; an empty cell keeps (+inf, -inf).  The work list uses it to skip cell pairs whose points
 // are all farther apart than the largest edge: the paper's late entry / early exit (Sec. 4.5) at
-// the granularity of cells.
+// the granularity of cells.  With gbox, also the box of every group of 32 consecutive points of a
+// cell (counted from the cell's first point), at gbox[6 p] for the group's first point p; the work
+// list prunes at that granularity.
 // ---------------------------------------------------------------------------------------------
 __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64_t ncell_all,
-                                  const float4 *__restrict__ pa, const float4 *__restrict__ pb, float *__restrict__ box)
+                                  const float4 *__restrict__ pa, const float4 *__restrict__ pb, float *__restrict__ box,
+                                  float *__restrict__ gbox)
 {
     const uint32_t lane = threadIdx.x & 31u;
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncell_all; c += wstride) {
         const uint32_t b = cell_start[c], e = cell_start[c + 1];
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-        for (uint32_t p = b + lane; p < e; p += 32u) {
-            const float4 A = pa[p], B = pb[p];
-            const float v[3] = {-A.x, -A.z, -B.x};
+        for (uint32_t p0 = b; p0 < e; p0 += 32u) {
+            float glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            const uint32_t p = p0 + lane;
+            if (p < e) {
+                const float4 A = pa[p], B = pb[p];
+                const float v[3] = {-A.x, -A.z, -B.x};
+                for (int a = 0; a < 3; a++) glo[a] = ghi[a] = v[a];
+            }
+            if (gbox) {
+                for (int o = 16; o; o >>= 1)
+                    for (int a = 0; a < 3; a++) {
+                        glo[a] = fminf(glo[a], __shfl_xor_sync(CF_FULL, glo[a], o));
+                        ghi[a] = fmaxf(ghi[a], __shfl_xor_sync(CF_FULL, ghi[a], o));
+                    }
+                if (lane < 6u) gbox[6 * (size_t)p0 + lane] = lane < 3u ? glo[lane] : ghi[lane - 3u];
+            }
             for (int a = 0; a < 3; a++) {
-                lo[a] = fminf(lo[a], v[a]);
-                hi[a] = fmaxf(hi[a], v[a]);
+                lo[a] = fminf(lo[a], glo[a]);
+                hi[a] = fmaxf(hi[a], ghi[a]);
             }
         }
         for (int o = 16; o; o >>= 1)
@@ -593,6 +609,9 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
 // +-k per axis, periodic shift per cell pair, auto keeps cj >= ci), a warp prefix sum orders the
 // items of the cell, and an empty i cell costs one load.  i tiles are full (tile points) plus one
 // remainder tile, so a tile wastes at most 31 pair-kernel slots; j ranges split evenly (<= jchunk).
+// With group boxes (gbox), each i tile is tested against every 32-point group of the j cell with
+// the cell-pair test's margins, and only runs of groups that may hold a pair within the largest
+// edge become j ranges (<= jchunk): the late entry / early exit of Sec. 4.5 at group granularity.
 // mode 0 writes the item count of each (job, cell) and adds the number of items, counted in 64 bits,
 // to *evaluated (the 32-bit scan of the counts would wrap silently past 2^32 items); mode 1 writes
 // the items at the scanned offsets and adds the pairs they hold to *evaluated.  Mode 2 needs no
@@ -604,7 +623,8 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
 // instead of (job, cell).
 __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
-                                const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox, int mode,
+                                const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox,
+                                const float *__restrict__ gbox, int mode,
                                 uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets,
                                 CfItem *__restrict__ items, uint32_t items_cap,
                                 unsigned long long *__restrict__ evaluated, unsigned long long *__restrict__ total64)
@@ -613,6 +633,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
     const int nst = g.nstencil;
     // box pruning needs the cell pair's own shift, which wrap axes (explicit minimum image) lack
     const bool prune = cbox != nullptr && !g.wrap[0] && !g.wrap[1] && !g.wrap[2];
+    const bool gp = prune && gbox != nullptr && (plan->tile & 31u) == 0u && plan->jchunk >= 32u;
     const bool zsep = plan->kind == CF_DD_RPPI || plan->kind == CF_WP;
     // (the plan's e2max32 bounds a counted pair's squared separation: for mocks, whose line of sight
     // varies, |s|^2 < rmax^2 + pimax^2; zmax32 bounds |dz| for rp-pi and wp)
@@ -642,6 +663,55 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                 const int ci[3] = {c / (g.n[2] * g.n[1]), (c / g.n[2]) % g.n[1], c % g.n[2]};
                 const uint32_t nti = (na + tile - 1) / tile;
                 const uint32_t base = mode == 1 ? offsets[u] : 0u;
+                // the items of one cell pair under group pruning, in a fixed order (the count and
+                // the write enumerate the same ones): for each i tile its box from the groups it
+                // holds, then the tile with itself (a cell with itself), then the runs of j groups
+                // within reach, each cut into ranges of at most jchunk points
+                auto group_items = [&](bool dg, uint32_t jb0, uint32_t nbj, const float (&shv)[3], auto &&emit) {
+                    const uint32_t gpt = tile >> 5, gpc = jchunk >> 5;
+                    const uint32_t ngi = (na + 31u) >> 5, ngj = (nbj + 31u) >> 5;
+                    for (uint32_t a0 = 0; a0 < nti; a0++) {
+                        const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
+                        float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+                        for (uint32_t k = a0 * gpt; k < min((a0 + 1u) * gpt, ngi); k++) {
+                            const float *q = gbox + 6 * (size_t)(ia + 32u * k);
+                            for (int a = 0; a < 3; a++) {
+                                blo[a] = fminf(blo[a], q[a]);
+                                bhi[a] = fmaxf(bhi[a], q[3 + a]);
+                            }
+                        }
+                        if (dg) emit(i0, ic, i0, ic, true);
+                        auto within = [&](uint32_t k) {
+                            const float *q = gbox + 6 * (size_t)(jb0 + 32u * k);
+                            float s2 = 0.f, gz = 0.f;
+                            for (int a = 0; a < 3; a++) {
+                                const float lo = (blo[a] + shv[a]) - q[3 + a];
+                                const float hi = (bhi[a] + shv[a]) - q[a];
+                                float gap = lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
+                                gap = fmaxf(0.f, gap - plan->pmargin[a]);
+                                if (zsep && a == 2) gz = gap;
+                                else s2 = fmaf(gap, gap, s2);
+                            }
+                            return !(s2 >= plan->e2max32 || (zsep && gz >= plan->zmax32));
+                        };
+                        // the tests of up to 32 groups are independent (their loads overlap); the
+                        // runs of set bits then give the j ranges
+                        for (uint32_t kb = dg ? (a0 + 1u) * gpt : 0u; kb < ngj; kb += 32u) {
+                            const uint32_t kn = min(32u, ngj - kb);
+                            uint32_t m = 0;
+#pragma unroll 4
+                            for (uint32_t t = 0; t < kn; t++) m |= (within(kb + t) ? 1u : 0u) << t;
+                            while (m) {
+                                const uint32_t t0 = __ffs(m) - 1u;
+                                const uint32_t rest = ~(m >> t0);          // zero bits past the run
+                                const uint32_t len = min(rest ? __ffs(rest) - 1u : 32u - t0, gpc);
+                                const uint32_t k = kb + t0, k1 = k + len;
+                                emit(i0, ic, 32u * k, min(32u * k1, nbj) - 32u * k, false);
+                                m &= len + t0 >= 32u ? 0u : ~((1u << (t0 + len)) - 1u);
+                            }
+                        }
+                    }
+                };
                 // target cells: the 3-D stencil, or for the angular grid the RA cells of the bands
                 // within k of this one whose RA range comes within the search angle: two points at
                 // declinations up to dm apart by an angle <= t differ in RA by at most
@@ -675,6 +745,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                     bool diag = false;
                     int ct = 0, tj[3] = {0, 0, 0};
                     double delta[3] = {0.0, 0.0, 0.0};      // image of the j point: x_j + delta
+                    float sh32[3] = {0.f, 0.f, 0.f};        // the cell pair's shift in float32 (pruning)
                     if (s < ncand) {
                         bool ok = true;
                         if (plan->ang) {
@@ -715,6 +786,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                                             plan->ang ? plan->origin32[3 * c + a] - plan->origin32[3 * ct + a]
                                                       : (cf_cell_origin32(plan, a, c, ci[a]) -
                                                          cf_cell_origin32(plan, a, ct, tj[a])) - (float)delta[a];
+                                        sh32[a] = sh;
                                         const float lo = (bi[a] + sh) - bj[3 + a];
                                         const float hi = (bi[3 + a] + sh) - bj[a];
                                         float gap = lo > 0.f ? lo : (hi < 0.f ? -hi : 0.f);
@@ -734,9 +806,12 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                                         tsj = (nb + ntj - 1) / ntj;
                                     }
                                     cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
-                                    if (mode == 0)
-                                        ev += diag ? (unsigned long long)nti * (nti + 1) / 2
-                                                   : (unsigned long long)nti * ntj;
+                                    if (gp) {
+                                        cnt = 0;
+                                        group_items(diag, jb, nb, sh32,
+                                                    [&](uint32_t, uint32_t, uint32_t, uint32_t, bool) { cnt++; });
+                                    }
+                                    if (mode == 0) ev += cnt;
                                 }
                             }
                         }
@@ -782,21 +857,28 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                             sh[a] = (float)shift;
                             sl[a] = (float)(shift - (double)sh[a]);
                         }
-                        for (uint32_t a0 = 0; a0 < nti; a0++) {
-                            const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
-                            for (uint32_t b = diag ? a0 : 0; b < ntj; b++) {
-                                const uint32_t j0 = b * tsj, jc = min(tsj, nb - j0);
-                                CfItem it;
-                                it.ibeg = ia + i0;
-                                it.jbeg = jb + j0;
-                                it.cnt = ic | (jc << 16);
-                                it.meta = (uint32_t)job | ((diag && b == a0) ? CFI_ITEM_DIAG : 0u);
-                                it.s[0] = sh[0]; it.s[1] = sh[1]; it.s[2] = sh[2]; it.pad0 = 0.f;
-                                it.slo[0] = sl[0]; it.slo[1] = sl[1]; it.slo[2] = sl[2]; it.pad1 = 0.f;
-                                if (staged) s_items[o] = it;
-                                else if (o < items_cap) items[o] = it;
-                                o++;
-                                ev += (unsigned long long)ic * jc;
+                        auto put = [&](uint32_t i0, uint32_t ic, uint32_t j0, uint32_t jc, bool dflag) {
+                            CfItem it;
+                            it.ibeg = ia + i0;
+                            it.jbeg = jb + j0;
+                            it.cnt = ic | (jc << 16);
+                            it.meta = (uint32_t)job | (dflag ? CFI_ITEM_DIAG : 0u);
+                            it.s[0] = sh[0]; it.s[1] = sh[1]; it.s[2] = sh[2]; it.pad0 = 0.f;
+                            it.slo[0] = sl[0]; it.slo[1] = sl[1]; it.slo[2] = sl[2]; it.pad1 = 0.f;
+                            if (staged) s_items[o] = it;
+                            else if (o < items_cap) items[o] = it;
+                            o++;
+                            ev += (unsigned long long)ic * jc;
+                        };
+                        if (gp) {
+                            group_items(diag, jb, nb, sh32, put);
+                        } else {
+                            for (uint32_t a0 = 0; a0 < nti; a0++) {
+                                const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
+                                for (uint32_t b = diag ? a0 : 0; b < ntj; b++) {
+                                    const uint32_t j0 = b * tsj, jc = min(tsj, nb - j0);
+                                    put(i0, ic, j0, jc, diag && b == a0);
+                                }
                             }
                         }
                     }
@@ -910,19 +992,19 @@ cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets,
 }
 
 cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const float4 *pa, const float4 *pb, float *box,
-                        cudaStream_t st)
+                        float *gbox, cudaStream_t st)
 {
-    cf_cellbox_kernel<<<blocks_for(ncell_all * 32, 256, 8192), 256, 0, st>>>(cell_start, ncell_all, pa, pb, box);
+    cf_cellbox_kernel<<<blocks_for(ncell_all * 32, 256, 8192), 256, 0, st>>>(cell_start, ncell_all, pa, pb, box, gbox);
     return cudaGetLastError();
 }
 
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
-                      const uint32_t *cell_start, const float *cbox, int64_t nunits, int mode, uint32_t *counts,
-                      const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
-                      unsigned long long *total64, cudaStream_t st)
+                      const uint32_t *cell_start, const float *cbox, const float *gbox, int64_t nunits, int mode,
+                      uint32_t *counts, const uint32_t *offsets, CfItem *items, uint32_t items_cap,
+                      unsigned long long *evaluated, unsigned long long *total64, cudaStream_t st)
 {
     cf_items_kernel<<<blocks_for(nunits * 32, 256, 8192), 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox,
-                                                                       mode, counts, offsets, items, items_cap,
+                                                                       gbox, mode, counts, offsets, items, items_cap,
                                                                        evaluated, total64);
     return cudaGetLastError();
 }

@@ -26,17 +26,19 @@ cudaError_t cfb_scan(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *tmp
 cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets, int64_t nmax, int sub,
                         const uint32_t *fstart, const uint32_t *key, const uint32_t *slot, float4 *pa,
                         float4 *pb, float4 *plo, uint32_t *orig, cudaStream_t st);
-// tight point bounding box per cell (6 floats: lo xyz, hi xyz, cell-relative), for cell-pair pruning
+// tight point bounding box per cell (6 floats: lo xyz, hi xyz, cell-relative), for cell-pair pruning;
+// with gbox (6 floats per point) also the box of every 32-point group of a cell at its first point
 cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const float4 *pa, const float4 *pb, float *box,
-                        cudaStream_t st);
-// cbox: the boxes above, or nullptr to visit every stencil neighbour.  mode 0: per-unit item counts
+                        float *gbox, cudaStream_t st);
+// cbox: the boxes above, or nullptr to visit every stencil neighbour; gbox: the group boxes, or
+// nullptr for j ranges over whole cells.  mode 0: per-unit item counts
 // into counts[], their number in 64 bits added to *evaluated; mode 1: items at offsets[]; mode 2:
 // count and emit in one pass, items reserved on the counter counts[0] (zeroed by the caller), their
 // number added to *total64.  Modes 1 and 2 add the pairs the stored items hold to *evaluated.
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
-                      const uint32_t *cell_start, const float *cbox, int64_t nunits, int mode, uint32_t *counts,
-                      const uint32_t *offsets, CfItem *items, uint32_t items_cap, unsigned long long *evaluated,
-                      unsigned long long *total64, cudaStream_t st);
+                      const uint32_t *cell_start, const float *cbox, const float *gbox, int64_t nunits, int mode,
+                      uint32_t *counts, const uint32_t *offsets, CfItem *items, uint32_t items_cap,
+                      unsigned long long *evaluated, unsigned long long *total64, cudaStream_t st);
 cudaError_t cfb_wsq(const CfSetDesc *sets, int nsets, int64_t nmax, double *out, cudaStream_t st);
 
 // ---- pair counting ----

@@ -10,6 +10,8 @@ Knobs (all results are identical across them; only speed changes):
   jchunk  j range per work item (staging depth of the j stream): 128, 256, 512
   noprune 1 visits every stencil neighbour; 0 skips cell pairs whose points' bounding boxes are
           farther apart than the largest edge (costs one pass over the points)
+  block   (set by hand, not searched) 1 gives the pair kernel only the 32-point groups of a j cell
+          that may come within the largest edge of the i tile; 0 whole cells
   thetagrid DD(theta) only: 0 the 3-D grid over unit vectors, 1 declination bands x RA cells
 
 The tuner times `cf_count` on the caller's own catalogue (coordinate descent from the default,
@@ -26,14 +28,16 @@ import math
 import os
 import time
 
-from . import (CF_DD_RPPI_MOCKS, CF_DD_THETA, CF_OPT_CELL_PRUNE, CF_OPT_JCHUNK, CF_OPT_REFINE, CF_OPT_THETA_GRID,
-               CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS, cf_count, cf_get_stats, cf_set_option)
+from . import (CF_DD_RPPI_MOCKS, CF_DD_THETA, CF_OPT_BLOCK_PRUNE, CF_OPT_CELL_PRUNE, CF_OPT_JCHUNK, CF_OPT_REFINE,
+               CF_OPT_THETA_GRID, CF_OPT_TILE, CF_OPT_VARIANT, CF_OPT_WARPS, cf_count, cf_get_stats, cf_set_option)
 
 KNOBS = {"variant": [1, 2], "refine": [1, 2, 3], "warps": [0, 12, 8, 6, 4], "tile": [128, 64],
          "jchunk": [512, 256, 128], "noprune": [0, 1], "thetagrid": [0, 1]}
 OPT = {"variant": CF_OPT_VARIANT, "refine": CF_OPT_REFINE, "warps": CF_OPT_WARPS, "tile": CF_OPT_TILE,
-       "jchunk": CF_OPT_JCHUNK, "noprune": CF_OPT_CELL_PRUNE, "thetagrid": CF_OPT_THETA_GRID}
-DEFAULT = {"variant": 1, "refine": 1, "warps": 0, "tile": 128, "jchunk": 512, "noprune": 0, "thetagrid": 0}
+       "jchunk": CF_OPT_JCHUNK, "noprune": CF_OPT_CELL_PRUNE, "block": CF_OPT_BLOCK_PRUNE,
+       "thetagrid": CF_OPT_THETA_GRID}
+DEFAULT = {"variant": 1, "refine": 1, "warps": 0, "tile": 128, "jchunk": 512, "noprune": 0, "block": 0,
+           "thetagrid": 0}
 MARGIN = 0.01
 
 

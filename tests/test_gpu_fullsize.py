@@ -124,8 +124,8 @@ def test_full_size_band_audit(ctx, name):
     finally:
         cf.cf_set_option(ctx, cf.CF_OPT_AUDIT, 0)
         cf.cf_set_option(ctx, cf.CF_OPT_REFINE, 0)
-    # every evaluated pair went to FP64 (a cell's pairs with itself once, j > i)
-    assert 10 ** 9 < st["rechecked_pairs"] <= st["evaluated_pairs"]
+    # every evaluated pair went to FP64 (a cell's pairs with itself once, j > i): several 1e8 of them
+    assert 5 * 10 ** 8 < st["rechecked_pairs"] <= st["evaluated_pairs"]
     if not wl.autocorr:
         assert st["rechecked_pairs"] == st["evaluated_pairs"]
     n = np.asarray(got["npairs"]).ravel().astype(np.uint64)

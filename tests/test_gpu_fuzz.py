@@ -84,7 +84,7 @@ def _case(seed):
     opts = dict(refine=(int(r.integers(1, 4)),) * 3)
     knobs = {"variant": int(r.integers(1, 3)), "tile": int(r.choice([128, 64])),
              "jchunk": int(r.choice([512, 128])), "noprune": int(r.integers(0, 2)),
-             "thetagrid": int(r.integers(0, 2))}
+             "thetagrid": int(r.integers(0, 2)), "block": int(r.integers(0, 2))}
     return kind, edges, d1, d2, kw, opts, knobs
 
 

@@ -338,8 +338,9 @@ def test_tile_shapes_wrap_and_diagonal(ctx, variant):
 
 
 def test_cell_pruning_keeps_results(ctx):
-    """Skipping cell pairs by their points' bounding boxes (the default) changes neither counts nor
-    sums, and on clustered data it removes evaluated pairs."""
+    """Skipping cell pairs by their points' bounding boxes (the default), and inside a kept cell pair
+    the 32-point groups of the j cell out of reach of an i tile (CF_OPT_BLOCK_PRUNE), changes
+    neither counts nor sums, and on clustered data each removes evaluated pairs."""
     import paper_1911_03545_gb300 as cf
     d = gen.clustered_box(120, 40, 0.7, 60.0, 93)
     d.w = gen.uniform_weights(d.n, 0.5, 1.5, 94)
@@ -351,15 +352,20 @@ def test_cell_pruning_keeps_results(ctx):
     exp_w = oracle.count("wp", edges, d, **kw_p)
     evaluated = {}
     for prune in (0, 1):
-        cf.cf_set_option(ctx, cf.CF_OPT_CELL_PRUNE, prune)
-        try:
-            assert_match(gpu_count(ctx, "r", edges, d, **kw_r), exp_r, True, True)
-            evaluated[prune] = cf.cf_get_stats(ctx)["evaluated_pairs"]
-            assert_match(gpu_count(ctx, "rppi", edges, d, **kw_p), exp_p)
-            assert_match(gpu_count(ctx, "wp", edges, d, **kw_p), exp_w)
-        finally:
-            cf.cf_set_option(ctx, cf.CF_OPT_CELL_PRUNE, 0)
-    assert evaluated[0] < evaluated[1]
+        for block in (0, 1):
+            cf.cf_set_option(ctx, cf.CF_OPT_CELL_PRUNE, prune)
+            cf.cf_set_option(ctx, cf.CF_OPT_BLOCK_PRUNE, block)
+            try:
+                assert_match(gpu_count(ctx, "r", edges, d, **kw_r), exp_r, True, True)
+                evaluated[prune, block] = cf.cf_get_stats(ctx)["evaluated_pairs"]
+                assert_match(gpu_count(ctx, "rppi", edges, d, **kw_p), exp_p)
+                assert_match(gpu_count(ctx, "wp", edges, d, **kw_p), exp_w)
+            finally:
+                cf.cf_set_option(ctx, cf.CF_OPT_CELL_PRUNE, 0)
+                cf.cf_set_option(ctx, cf.CF_OPT_BLOCK_PRUNE, 0)
+    assert evaluated[0, 0] < evaluated[1, 0]
+    # block pruning works from the cells' group boxes, which only cell pruning builds
+    assert evaluated[0, 1] < evaluated[0, 0] and evaluated[1, 1] == evaluated[1, 0]
 
 
 def test_cell_pruning_at_the_largest_edge(ctx):
@@ -373,12 +379,15 @@ def test_cell_pruning_at_the_largest_edge(ctx):
             pts.append((22.0 + delta, y + 0.01 * m, 50.0))
     a = np.array(pts, dtype=np.float64)
     d = gen.Catalogue(a[:, 0].astype(np.float32), a[:, 1].astype(np.float32), a[:, 2].astype(np.float32))
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 95).astype(np.float32)
     edges = np.array([1.0, 5.0, 9.99, 10.0])
-    for kind, kw in (("r", {}), ("rppi", dict(pimax=10.0, npibins=10)), ("wp", dict(pimax=10.0, npibins=10))):
+    for kind, kw in (("r", {}), ("r", dict(weighted=True, ravg=True)), ("rppi", dict(pimax=10.0, npibins=10)),
+                     ("wp", dict(pimax=10.0, npibins=10))):
+        wr = kw.get("weighted", False)
         got, exp = both(ctx, kind, edges, d, autocorr=True, periodic=True, box=100.0, **kw)
-        assert_match(got, exp)
+        assert_match(got, exp, wr, wr)
         got, exp = both(ctx, kind, edges, d, d, autocorr=False, periodic=True, box=100.0, **kw)
-        assert_match(got, exp)
+        assert_match(got, exp, wr, wr)
 
 
 def test_maximum_bin_counts(ctx):
@@ -423,14 +432,22 @@ def test_band_audit_agrees(ctx, kind):
     kw.update(weighted=True, ravg=True)
     normal = gpu_count(ctx, kind, edges, d, **kw)
     st = cf.cf_get_stats(ctx)
+    cf.cf_set_option(ctx, cf.CF_OPT_BLOCK_PRUNE, 1)
+    try:
+        assert_match(gpu_count(ctx, kind, edges, d, **kw), normal, True, True)
+        sp = cf.cf_get_stats(ctx)
+    finally:
+        cf.cf_set_option(ctx, cf.CF_OPT_BLOCK_PRUNE, 0)
     cf.cf_set_option(ctx, cf.CF_OPT_AUDIT, 1)
     try:
         audited = gpu_count(ctx, kind, edges, d, **kw)
         sa = cf.cf_get_stats(ctx)
     finally:
         cf.cf_set_option(ctx, cf.CF_OPT_AUDIT, 0)
-    # every evaluated pair is queued: a cell's pairs with itself once (j > i), the rest i x j
-    assert sa["evaluated_pairs"] == st["evaluated_pairs"]
+    # every pair of the work items is queued: a cell's pairs with itself once (j > i), the rest
+    # i x j.  Block pruning evaluates fewer (how many fewer varies a little from call to call: the
+    # points of a sub-cell take their places, and so their 32-point groups, by atomic ranks).
+    assert sa["evaluated_pairs"] == st["evaluated_pairs"] and sp["evaluated_pairs"] <= st["evaluated_pairs"]
     assert int(np.asarray(audited["npairs"]).sum()) // 2 <= sa["rechecked_pairs"] <= sa["evaluated_pairs"]
     assert_match(normal, audited, True, True)
     assert_match(audited, oracle.count(kind, edges, d, **kw), True, True)

@@ -34,8 +34,8 @@ def test_tuner_finds_the_fastest_configuration(monkeypatch):
         return t
     tune, timer = _fake(monkeypatch, times, noise=0.002)
     cfg = tune.tune(None, _P(), None, use_cache=False, timer=timer)
-    assert (cfg["jchunk"], cfg["tile"], cfg["warps"], cfg["refine"], cfg["variant"], cfg["noprune"]) == \
-        (128, 64, 8, 2, 1, 0)
+    assert (cfg["jchunk"], cfg["tile"], cfg["warps"], cfg["refine"], cfg["variant"], cfg["noprune"],
+            cfg["block"]) == (128, 64, 8, 2, 1, 0, 0)
 
 
 def test_tuner_keeps_the_default_within_the_margin(monkeypatch):
@@ -56,3 +56,4 @@ def test_tuner_knobs_follow_the_kind():
     assert "thetagrid" in tune.knobs_for(K(CF_DD_THETA)) and "variant" in tune.knobs_for(K(CF_DD_THETA))
     assert "thetagrid" not in tune.knobs_for(K(0))
     assert "variant" not in tune.knobs_for(K(CF_DD_RPPI_MOCKS))
+    assert all("block" not in tune.knobs_for(K(k)) for k in range(5))      # set by hand only
