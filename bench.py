@@ -201,13 +201,16 @@ def _wl_params(wl, cf):
                      pimax=wl.pimax, npibins=wl.npibins, ravg=wl.ravg, weighted=wl.weighted)
 
 
-def _points(cat, weighted, cf, dev=None):
+def _points(cat, weighted, cf, dev=None, pinned=False):
+    """Device tensors (dev), pinned host tensors (pinned: the library copies them in every call), or
+    pageable numpy arrays."""
     import numpy as np
     import torch
     arrs = [cat.x, cat.y, cat.z] + ([cat.w] if weighted else [])
-    if dev is None:
+    if dev is None and not pinned:
         return cf.points(*[np.ascontiguousarray(a) for a in arrs[:3]], arrs[3] if weighted else None)
-    t = [torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in arrs]
+    t = [torch.from_numpy(np.ascontiguousarray(a)) for a in arrs]
+    t = [x.pin_memory() for x in t] if dev is None else [x.to(dev) for x in t]
     return cf.points(*t[:3], t[3] if weighted else None)
 
 
@@ -598,9 +601,9 @@ def run_gpu(args, wl, world, rank, local):
     pair_ms = [s["ms_pair"] for s in stats]
     launches = sum(s["kernel_launches"] for s in stats)
 
-    # ---- e2e through the public API with host buffers (H2D of inputs, D2H of results inside) ----
-    h1 = _points(wl.d1, wl.weighted, cf)
-    h2 = None if wl.autocorr else _points(wl.d2, wl.weighted, cf)
+    # ---- e2e through the public API with pinned host buffers (H2D of inputs, D2H of results inside) ----
+    h1 = _points(wl.d1, wl.weighted, cf, pinned=True)
+    h2 = None if wl.autocorr else _points(wl.d2, wl.weighted, cf, pinned=True)
     cf.cf_count(ctx, p, h1, h2)
     e2e_steps = max(3, min(args.steps, 50))
     torch.cuda.synchronize(dev)
