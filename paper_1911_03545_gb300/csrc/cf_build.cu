@@ -621,6 +621,8 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
 // with 16-byte stores.  Entries that do not fit the stage reserve and write globally.  Their
 // number is added in 64 bits to *total64.  The list's order then follows the blocks' arrival
 // instead of (job, cell).
+// GP: the instance with group pruning (its group code holds registers the other need not pay for)
+template <bool GP>
 __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
                                 const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox,
@@ -633,7 +635,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
     const int nst = g.nstencil;
     // box pruning needs the cell pair's own shift, which wrap axes (explicit minimum image) lack
     const bool prune = cbox != nullptr && !g.wrap[0] && !g.wrap[1] && !g.wrap[2];
-    const bool gp = prune && gbox != nullptr && (plan->tile & 31u) == 0u && plan->jchunk >= 32u;
+    const bool gp = GP && prune && gbox != nullptr && (plan->tile & 31u) == 0u && plan->jchunk >= 32u;
     const bool zsep = plan->kind == CF_DD_RPPI || plan->kind == CF_WP;
     // (the plan's e2max32 bounds a counted pair's squared separation: for mocks, whose line of sight
     // varies, |s|^2 < rmax^2 + pimax^2; zmax32 bounds |dz| for rp-pi and wp)
@@ -806,7 +808,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                                         tsj = (nb + ntj - 1) / ntj;
                                     }
                                     cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
-                                    if (gp) {
+                                    if (GP && gp) {
                                         cnt = 0;
                                         group_items(diag, jb, nb, sh32,
                                                     [&](uint32_t, uint32_t, uint32_t, uint32_t, bool) { cnt++; });
@@ -870,7 +872,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                             o++;
                             ev += (unsigned long long)ic * jc;
                         };
-                        if (gp) {
+                        if (GP && gp) {
                             group_items(diag, jb, nb, sh32, put);
                         } else {
                             for (uint32_t a0 = 0; a0 < nti; a0++) {
@@ -1003,9 +1005,13 @@ cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobD
                       uint32_t *counts, const uint32_t *offsets, CfItem *items, uint32_t items_cap,
                       unsigned long long *evaluated, unsigned long long *total64, cudaStream_t st)
 {
-    cf_items_kernel<<<blocks_for(nunits * 32, 256, 8192), 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox,
-                                                                       gbox, mode, counts, offsets, items, items_cap,
-                                                                       evaluated, total64);
+    const int nb = blocks_for(nunits * 32, 256, 8192);
+    if (gbox)
+        cf_items_kernel<true><<<nb, 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox, gbox, mode, counts,
+                                                  offsets, items, items_cap, evaluated, total64);
+    else
+        cf_items_kernel<false><<<nb, 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox, nullptr, mode, counts,
+                                                   offsets, items, items_cap, evaluated, total64);
     return cudaGetLastError();
 }
 
