@@ -486,6 +486,8 @@ struct Warp {
                 const u64 xj = *reinterpret_cast<const u64 *>(bs + jj);
                 const u64 yj = *reinterpret_cast<const u64 *>(bs + JSTAGE + jj);
                 const u64 zj = *reinterpret_cast<const u64 *>(bs + 2 * JSTAGE + jj);
+                // the j weights, read once for all slots (rp-pi / wp bin where formed)
+                const u64 wjd = (W && !SPLIT && !COMPACT) ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
                 u64 lx = 0, ly = 0, lz = 0;
                 if (LO) {
                     lx = *reinterpret_cast<const u64 *>(bs + 4 * JSTAGE + jj);
@@ -545,19 +547,19 @@ struct Warp {
                         m |= (in1 ? 2u : 0u) << (2 * q);
                     } else if (!SPLIT && (in0 || in1)) {
                         // direct form, rp-pi / wp: bin where formed
-                        const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
-                        const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
+                        const u64 wp = W ? f2_mul(wi[q], wjd) : 0ull;
                         if (in0) bin_in(f2_lo_bits(v2[q]), f2_lo_bits(az[q]), f2_lo(wp), il, j);
                         if (in1) bin_in(f2_hi_bits(v2[q]), f2_hi_bits(az[q]), f2_hi(wp), il, j + 1);
                     }
                 }
                 if (!COMPACT && SPLIT) {
-                    // direct form, r / theta: bin after every slot's distances are issued
+                    // direct form, r / theta: bin after every slot's distances are issued (the j
+                    // weights read once for all slots)
+                    const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
 #pragma unroll
                     for (int q = 0; q < Q; q++) {
                         if (p0[q] || p1[q]) {
                             const uint32_t il = lane + 32u * q;
-                            const u64 wj = W ? *reinterpret_cast<const u64 *>(bs + 3 * JSTAGE + jj) : 0ull;
                             const u64 wp = W ? f2_mul(wi[q], wj) : 0ull;
                             if (p0[q]) bin_in(f2_lo_bits(v2[q]), f2_lo_bits(az[q]), f2_lo(wp), il, j);
                             if (p1[q]) bin_in(f2_hi_bits(v2[q]), f2_hi_bits(az[q]), f2_hi(wp), il, j + 1);
