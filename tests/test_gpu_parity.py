@@ -279,6 +279,21 @@ def test_errors_leave_context_usable(ctx):
     nan.y[5] = np.nan
     with pytest.raises(cf.CfError):
         gpu_count(ctx, "r", edges, nan, autocorr=True, periodic=False)
+    # a periodic call checks its inputs after the count (its bounding-box pass runs beside the
+    # build): a NaN, an infinite weight or a point past L still fails the call, and the next works
+    for bad_w in (False, True):
+        bad = gen.uniform_box(3000, 10.0, 5)
+        bad.w = gen.uniform_weights(bad.n, 0.5, 1.5, 6)
+        if bad_w:
+            bad.w[17] = np.inf
+        else:
+            bad.z[2999] = np.nan
+        with pytest.raises(cf.CfError) as ei:
+            gpu_count(ctx, "r", edges, bad, autocorr=True, periodic=True, box=10.0, weighted=True)
+        assert ei.value.status == -1
+        good = gen.uniform_box(3000, 10.0, 7)
+        got, exp = both(ctx, "r", edges, good, autocorr=True, periodic=True, box=10.0)
+        assert_match(got, exp)
     with pytest.raises(cf.CfError):
         gpu_count(ctx, "r", [1.0, 0.5], nan, autocorr=True, periodic=False)
     import torch
@@ -528,3 +543,36 @@ def test_scan_over_many_tiles(ctx):
         assert cf.cf_get_stats(c)["cells"] == 68 ** 3
     finally:
         cf.cf_destroy(c)
+
+
+@pytest.mark.parametrize("kind", ["r", "theta", "rppi"])
+def test_device_views_not_16_byte_aligned(ctx, kind):
+    """Device inputs may be views that start 4 bytes into an allocation (x = t[1:]): the passes that
+    read four float32 points per 16-byte load take their per-point path then, with the same
+    results (a periodic call, whose input check runs beside the build, and a non-periodic one)."""
+    import torch
+
+    import paper_1911_03545_gb300 as cf
+    if kind == "theta":
+        d = gen.sphere_patch(5001, 0.0, 30.0, -10.0, 20.0, 97)
+        edges = gen.log_edges(0.01, 2.0, 10)
+        kws = [dict(autocorr=True, periodic=False)]
+    else:
+        d = gen.clustered_box(50, 100, 1.0, 40.0, 98)
+        edges = gen.log_edges(0.1, 6.0, 10)
+        kws = [dict(autocorr=True, periodic=True, box=40.0), dict(autocorr=True, periodic=False)]
+        if kind == "rppi":
+            kws = [dict(k, pimax=8.0, npibins=8) for k in kws]
+    d.w = gen.uniform_weights(d.n, 0.5, 1.5, 99)
+    for kw in kws:
+        kw = dict(kw, weighted=True, ravg=True)
+        ts = []
+        for a in (d.x, d.y, d.z, d.w):
+            t = torch.empty(d.n + 1, dtype=torch.float32, device="cuda:0")
+            t[1:] = torch.from_numpy(np.ascontiguousarray(a)).to("cuda:0")
+            ts.append(t[1:])
+        assert ts[0].data_ptr() % 16 != 0
+        p = cf.params(kind=kind, edges=edges, **{k: v for k, v in kw.items() if k != "ravg"}, ravg=True)
+        got = cf.cf_count(ctx, p, cf.points(*ts))
+        exp = oracle.count(kind, edges, d, **kw)
+        assert_match(got, exp, True, True)
