@@ -32,7 +32,7 @@ def test_batch_description_follows_the_options():
 
 def test_parity_flag_against_the_stored_histograms():
     """bench.py's parity flag: the stored oracle histogram itself passes, a count off by one or a
-    sum off by 2e-6 fails, and inputs that differ from the stored ones give no verdict."""
+    sum off by 2e-6 fails, and inputs that differ from the stored ones get no flag (None)."""
     import json
     import os
 
