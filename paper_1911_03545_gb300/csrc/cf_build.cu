@@ -623,7 +623,7 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
 // instead of (job, cell).
 // GP: the instance with group pruning (its group code holds registers the other need not pay for)
 template <bool GP>
-__global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
+__global__ void __launch_bounds__(256, GP ? 3 : 4) cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
                                 const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox,
                                 const float *__restrict__ gbox, int mode,
@@ -668,12 +668,32 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                 // the items of one cell pair under group pruning, in a fixed order (the count and
                 // the write enumerate the same ones): for each i tile its box from the groups it
                 // holds, then the tile with itself (a cell with itself), then the runs of j groups
-                // within reach, each cut into ranges of at most jchunk points
-                auto group_items = [&](bool dg, uint32_t jb0, uint32_t nbj, const float (&shv)[3], auto &&emit) {
+                // within reach, each cut into ranges of at most jchunk points.  cache 1 keeps the
+                // masks of tiles 0 and 1 when each fits one word, cache 2 takes them from there.
+                auto group_items = [&](bool dg, uint32_t jb0, uint32_t nbj, const float (&shv)[3], uint32_t (&mc)[2],
+                                       int cache, auto &&emit) {
                     const uint32_t gpt = tile >> 5, gpc = jchunk >> 5;
                     const uint32_t ngi = (na + 31u) >> 5, ngj = (nbj + 31u) >> 5;
                     for (uint32_t a0 = 0; a0 < nti; a0++) {
                         const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
+                        // the runs of set bits of m (groups kb + t) give the j ranges
+                        auto runs = [&](uint32_t m, uint32_t kb) {
+                            while (m) {
+                                const uint32_t t0 = __ffs(m) - 1u;
+                                const uint32_t rest = ~(m >> t0);          // zero bits past the run
+                                const uint32_t len = min(rest ? __ffs(rest) - 1u : 32u - t0, gpc);
+                                const uint32_t k = kb + t0, k1 = k + len;
+                                emit(i0, ic, 32u * k, min(32u * k1, nbj) - 32u * k, false);
+                                m &= len + t0 >= 32u ? 0u : ~((1u << (t0 + len)) - 1u);
+                            }
+                        };
+                        if (dg) emit(i0, ic, i0, ic, true);
+                        const uint32_t kb0 = dg ? (a0 + 1u) * gpt : 0u;
+                        const bool one = a0 < 2u && ngj <= kb0 + 32u;
+                        if (cache == 2 && one) {
+                            runs(a0 == 0u ? mc[0] : mc[1], kb0);
+                            continue;
+                        }
                         float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
                         for (uint32_t k = a0 * gpt; k < min((a0 + 1u) * gpt, ngi); k++) {
                             const float *q = gbox + 6 * (size_t)(ia + 32u * k);
@@ -682,7 +702,6 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                                 bhi[a] = fmaxf(bhi[a], q[3 + a]);
                             }
                         }
-                        if (dg) emit(i0, ic, i0, ic, true);
                         auto within = [&](uint32_t k) {
                             const float *q = gbox + 6 * (size_t)(jb0 + 32u * k);
                             float s2 = 0.f, gz = 0.f;
@@ -696,21 +715,21 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                             }
                             return !(s2 >= plan->e2max32 || (zsep && gz >= plan->zmax32));
                         };
-                        // the tests of up to 32 groups are independent (their loads overlap); the
-                        // runs of set bits then give the j ranges
-                        for (uint32_t kb = dg ? (a0 + 1u) * gpt : 0u; kb < ngj; kb += 32u) {
+                        if (cache == 1 && one) {
+                            if (a0 == 0u) mc[0] = 0u;
+                            else mc[1] = 0u;
+                        }
+                        // the tests of up to 32 groups are independent (their loads overlap)
+                        for (uint32_t kb = kb0; kb < ngj; kb += 32u) {
                             const uint32_t kn = min(32u, ngj - kb);
                             uint32_t m = 0;
 #pragma unroll 4
                             for (uint32_t t = 0; t < kn; t++) m |= (within(kb + t) ? 1u : 0u) << t;
-                            while (m) {
-                                const uint32_t t0 = __ffs(m) - 1u;
-                                const uint32_t rest = ~(m >> t0);          // zero bits past the run
-                                const uint32_t len = min(rest ? __ffs(rest) - 1u : 32u - t0, gpc);
-                                const uint32_t k = kb + t0, k1 = k + len;
-                                emit(i0, ic, 32u * k, min(32u * k1, nbj) - 32u * k, false);
-                                m &= len + t0 >= 32u ? 0u : ~((1u << (t0 + len)) - 1u);
+                            if (cache == 1 && one) {
+                                if (a0 == 0u) mc[0] = m;
+                                else mc[1] = m;
                             }
+                            runs(m, kb);
                         }
                     }
                 };
@@ -748,6 +767,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                     int ct = 0, tj[3] = {0, 0, 0};
                     double delta[3] = {0.0, 0.0, 0.0};      // image of the j point: x_j + delta
                     float sh32[3] = {0.f, 0.f, 0.f};        // the cell pair's shift in float32 (pruning)
+                    uint32_t mc[2] = {0u, 0u};              // group masks of the first two i tiles
                     if (s < ncand) {
                         bool ok = true;
                         if (plan->ang) {
@@ -810,7 +830,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                                     cnt = diag ? nti * (nti + 1) / 2 : nti * ntj;
                                     if (GP && gp) {
                                         cnt = 0;
-                                        group_items(diag, jb, nb, sh32,
+                                        group_items(diag, jb, nb, sh32, mc, 1,
                                                     [&](uint32_t, uint32_t, uint32_t, uint32_t, bool) { cnt++; });
                                     }
                                     if (mode == 0) ev += cnt;
@@ -873,7 +893,7 @@ __global__ void cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetD
                             ev += (unsigned long long)ic * jc;
                         };
                         if (GP && gp) {
-                            group_items(diag, jb, nb, sh32, put);
+                            group_items(diag, jb, nb, sh32, mc, 2, put);
                         } else {
                             for (uint32_t a0 = 0; a0 < nti; a0++) {
                                 const uint32_t i0 = a0 * tile, ic = min(tile, na - i0);
