@@ -687,14 +687,14 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     uint32_t *nitems_dev = ioff + R.nunit;
     if (R.fused_items) {
         nitems_dev = (uint32_t *)(out + OUT_NITEMS);
-        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.gbox, R.nunit, 2,
-                        nitems_dev, nullptr, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
+        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.gbox,
+                        R.nunit, 2, nitems_dev, nullptr, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
                         (unsigned long long *)(out + OUT_ITEMS64), st),
               "items");
     } else {
-        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.gbox, R.nunit, 1,
-                        (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
-                        nullptr, st),
+        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.gbox,
+                        R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap,
+                        evaluated, nullptr, st),
               "items emit");
     }
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[1], st, C->capturing ? cudaEventRecordExternal : 0), "event");

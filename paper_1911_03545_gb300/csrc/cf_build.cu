@@ -623,7 +623,8 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
 // instead of (job, cell).
 // GP: the instance with group pruning (its group code holds registers the other need not pay for)
 template <bool GP>
-__global__ void __launch_bounds__(256, GP ? 3 : 4) cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
+__global__ void __launch_bounds__(256, GP ? 3 : 4)
+    cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
                                 const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox,
                                 const float *__restrict__ gbox, int mode,
