@@ -502,6 +502,14 @@ def _oracle_beside(seconds: float) -> dict:
     return out
 
 
+def _line_config(args, world) -> dict:
+    """The workload's description, the same in the GPU line and the reference arm's line (the launch
+    shape the GPU arm tuned goes under "launch")."""
+    return {"workload": WORKLOADS[args.workload], "name": args.workload,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed between timed steps (512 MB write outside the step events)"}
+
+
 def run_reference(args, wl, world, rank):
     if rank != 0:
         return 0
@@ -519,7 +527,7 @@ def run_reference(args, wl, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "name": args.workload},
+        "config": _line_config(args, world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -632,10 +640,8 @@ def run_gpu(args, wl, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "name": args.workload,
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "flushed between timed steps (512 MB write outside the step events)",
-                   "grid": stats[-1]["grid"], "refine": stats[-1]["refine"], "tuned": tuned},
+        "config": _line_config(args, world),
+        "launch": {"grid": stats[-1]["grid"], "refine": stats[-1]["refine"], "tuned": tuned},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "steps": e2e_steps},
         "gpu_launches": int(launches),
