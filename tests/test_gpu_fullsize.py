@@ -31,8 +31,12 @@ def ctx():
     cf.cf_destroy(c)
 
 
-@pytest.mark.parametrize("name", NAMES)
-def test_full_size_against_oracle(ctx, name):
+BLOCK = ["clustered_r_1m", "clustered_rppi_2m_wr", "clustered_rppi_dr", "mock_dr_rppi"]
+
+
+@pytest.mark.parametrize("name,block", [(n, 0) for n in NAMES] + [(n, 1) for n in BLOCK if n in NAMES])
+def test_full_size_against_oracle(ctx, name, block):
+    """Default options, and for some workloads with the work list's group pruning on."""
     import paper_1911_03545_gb300 as cf
     with open(os.path.join(GOLDEN, f"full_{name}.json")) as f:
         gold = json.load(f)
@@ -46,7 +50,11 @@ def test_full_size_against_oracle(ctx, name):
         t = to_dev(c, "cuda:0", wl.weighted)
         return cf.points(*t[:3], t[3] if wl.weighted else None)
 
-    got = cf.cf_count(ctx, p, pts(wl.d1), None if wl.autocorr else pts(wl.d2))
+    cf.cf_set_option(ctx, cf.CF_OPT_BLOCK_PRUNE, block)
+    try:
+        got = cf.cf_count(ctx, p, pts(wl.d1), None if wl.autocorr else pts(wl.d2))
+    finally:
+        cf.cf_set_option(ctx, cf.CF_OPT_BLOCK_PRUNE, 0)
     if name == "clustered_rppi_2m_wr":
         assert cf.cf_get_stats(ctx)["fixed_sums"] == 3     # weights in [0.5, 1.5): fixed-point sums
     n = np.asarray(got["npairs"]).ravel().astype(np.uint64)
