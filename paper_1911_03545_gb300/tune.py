@@ -10,8 +10,9 @@ Knobs (all results are identical across them; only speed changes):
   jchunk  j range per work item (staging depth of the j stream): 128, 256, 512
   noprune 1 visits every stencil neighbour; 0 skips cell pairs whose points' bounding boxes are
           farther apart than the largest edge (costs one pass over the points)
-  block   (set by hand, not searched) 1 gives the pair kernel only the 32-point groups of a j cell
-          that may come within the largest edge of the i tile; 0 whole cells
+  block   1 gives the pair kernel only the 32-point groups of a j cell that may come within the
+          largest edge of the i tile; 0 whole cells.  Searched only with tune(..., block=True): it
+          lowers the evaluated-pair count, so evaluated-pair rates with and without it differ
   thetagrid DD(theta) only: 0 the 3-D grid over unit vectors, 1 declination bands x RA cells
 
 The tuner times `cf_count` on the caller's own catalogue (coordinate descent from the default,
@@ -41,7 +42,7 @@ DEFAULT = {"variant": 1, "refine": 1, "warps": 0, "tile": 128, "jchunk": 512, "n
 MARGIN = 0.01
 
 
-def knobs_for(p) -> dict:
+def knobs_for(p, block: bool = False) -> dict:
     """The knobs that can change anything for this kind: the angular grid exists for DD(theta)
     only, and the mocks kind has the direct form only."""
     k = dict(KNOBS)
@@ -49,6 +50,8 @@ def knobs_for(p) -> dict:
         k.pop("thetagrid")
     if p.kind == CF_DD_RPPI_MOCKS:
         k.pop("variant")
+    if block:
+        k["block"] = [0, 1]
     return k
 
 
@@ -107,12 +110,12 @@ def _duel(ctx, p, d1, d2, a: dict, b: dict, reps: int, timer=None):
 
 
 def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, reps: int = 5,
-         passes: int = 2, use_cache: bool = True, log=None, timer=None) -> dict:
+         passes: int = 2, use_cache: bool = True, log=None, timer=None, block: bool = False) -> dict:
     """Return the best configuration for this workload (and leave it applied on ctx).  timer:
     optional callable that runs one count on ctx and returns its time in seconds (so that the
     tuner ranks configurations by the caller's own measurement); by default the library's event
-    times of build, pair kernel and recheck."""
-    key = _key(device_name, p, npoints or 1) if use_cache else ""
+    times of build, pair kernel and recheck.  block: also search the group pruning knob."""
+    key = (_key(device_name, p, npoints or 1) + ("|block" if block else "")) if use_cache else ""
     path = cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -133,7 +136,7 @@ def tune(ctx, p, d1, d2=None, *, device_name: str = "gpu", npoints: int = 0, rep
     # coordinate descent, repeated: a knob's best value can change once later knobs have moved
     for _ in range(passes):
         moved = False
-        for knob, values in knobs_for(p).items():
+        for knob, values in knobs_for(p, block).items():
             for v in values:
                 if v == cfg[knob]:
                     continue

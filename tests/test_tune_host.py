@@ -56,4 +56,14 @@ def test_tuner_knobs_follow_the_kind():
     assert "thetagrid" in tune.knobs_for(K(CF_DD_THETA)) and "variant" in tune.knobs_for(K(CF_DD_THETA))
     assert "thetagrid" not in tune.knobs_for(K(0))
     assert "variant" not in tune.knobs_for(K(CF_DD_RPPI_MOCKS))
-    assert all("block" not in tune.knobs_for(K(k)) for k in range(5))      # set by hand only
+    assert all("block" not in tune.knobs_for(K(k)) for k in range(5))      # searched only on request
+    assert tune.knobs_for(K(0), block=True)["block"] == [0, 1]
+
+
+def test_tuner_searches_group_pruning_on_request(monkeypatch):
+    # group pruning 10 % faster: found only when the caller asks for it
+    def times(c):
+        return 1.0 * (0.9 if c["block"] else 1.0)
+    tune, timer = _fake(monkeypatch, times, noise=0.002, seed=5)
+    assert tune.tune(None, _P(), None, use_cache=False, timer=timer)["block"] == 0
+    assert tune.tune(None, _P(), None, use_cache=False, timer=timer, block=True)["block"] == 1
