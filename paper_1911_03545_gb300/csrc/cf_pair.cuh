@@ -870,9 +870,10 @@ struct Warp {
 
 // CTA shape the register budget is sized for.  With weights or ravg the lane-private histograms
 // (about 13 KB per warp for 20 bins) hold an SM to one CTA, so it may take up to 16 warps (the
-// launcher takes as many as fit); count-only CTAs are small and run 3 per SM.
+// launcher takes as many as fit); count-only CTAs are small, and a budget for 4 of 256 threads per
+// SM (64 registers, no spills in the rp-pi instances) keeps more of them resident than one for 3.
 __host__ __device__ constexpr int pair_max_threads(bool W, bool R) { return (W || R) ? 512 : 256; }
-__host__ __device__ constexpr int pair_min_blocks(bool W, bool R) { return (!W && !R) ? 3 : 1; }
+__host__ __device__ constexpr int pair_min_blocks(bool W, bool R) { return (!W && !R) ? 4 : 1; }
 
 template <int KIND, bool W, bool R, bool WRAP, bool LO, bool COMPACT, bool GH, bool FX>
 __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
