@@ -226,7 +226,7 @@ __device__ __forceinline__ uint32_t cf_morton3(uint32_t x, uint32_t y, uint32_t 
            ((y & 1u) << 1) | (z & 1u);
 }
 
-__global__ void cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets, int sub,
+__global__ void __launch_bounds__(256, 6) cf_assign_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets, int sub,
                                  uint32_t *__restrict__ count, uint32_t *__restrict__ key,
                                  uint32_t *__restrict__ slot)
 {
@@ -503,7 +503,7 @@ __global__ void cf_scan_apply(const uint32_t *__restrict__ in, uint32_t *__restr
 // Scatter into cell order (Sec. 4.3).  Writes the packed j-side layout pa/pb (cell-relative,
 // negated, duplicated), the FP64 residual plo when requested, and the original index.
 // ---------------------------------------------------------------------------------------------
-__global__ void cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
+__global__ void __launch_bounds__(256, 6) cf_scatter_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                   uint32_t ns, const uint32_t *__restrict__ fstart, const uint32_t *__restrict__ key,
                                   const uint32_t *__restrict__ slot, float4 *__restrict__ pa,
                                   float4 *__restrict__ pb, float4 *__restrict__ plo,
