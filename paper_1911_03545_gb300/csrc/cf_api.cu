@@ -205,6 +205,16 @@ static int check_points(CfCtx *C, const cf_params *p, const cf_points *d)
     } while (0)
 #define CF_CU(x, what) CF_TRY(C->cuda((x), what))
 
+// the work list and the order the pair kernel takes it in (one index per item, then the ordering
+// pass's per-block class sizes)
+static int ensure_items(CfCtx *C, size_t cap)
+{
+    cap = std::max<size_t>(1, cap);
+    CF_TRY(C->ensure(B_ITEMS, sizeof(CfItem) * cap));
+    const size_t part = (size_t)CFI_ITEM_CLASSES * cfb_order_blocks((uint32_t)cap, C->num_sms);
+    return C->ensure(B_ORDER, sizeof(uint32_t) * (cap + part));
+}
+
 // The bbox pass's readback (CFB_BBOX_WORDS per point set): reject non-finite values and periodic
 // positions outside [0, L]; record each set's weight range and the union of the sets' boxes, the
 // largest | |v|^2 - 1 | and the smallest |v|^2.
@@ -525,7 +535,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     return CF_OK;
 }
 
-size_t readback_bytes(const CfRun &R) { return 64 + 24 * R.hsz + 8 * (size_t)R.nsets; }
+size_t readback_bytes(const CfRun &R) { return OUT_HIST + 24 * R.hsz + 8 * (size_t)R.nsets; }
 
 // bbox pass of a captured graph: starting values, the pass, its readback at R.bb_off
 static int cf_enqueue_bbox(CfCtx *C, CfRun &R)
@@ -697,6 +707,13 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
                         evaluated, nullptr, st),
               "items emit");
     }
+    // a short list is taken as it is: the two ordering passes would cost more than they save (the
+    // capacity of a repeat call's list holds 25 % headroom)
+    const bool ordered = R.items_cap >= CF_ORDER_MIN_ITEMS;
+    if (ordered)
+        CF_CU(cfb_order((const CfItem *)C->buf[B_ITEMS].p, nitems_dev, R.items_cap, (uint32_t *)C->buf[B_ORDER].p,
+                        (uint32_t *)C->buf[B_ORDER].p + R.items_cap, C->num_sms, st),
+              "work-list order");
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[1], st, C->capturing ? cudaEventRecordExternal : 0), "event");
     CfPairArgs &A = R.args;
     std::memset(&A, 0, sizeof(A));
@@ -704,6 +721,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     A.lut = R.d_lut;
     A.fine = R.d_fine;
     A.items = (const CfItem *)C->buf[B_ITEMS].p;
+    A.order = ordered ? (const uint32_t *)C->buf[B_ORDER].p : nullptr;
     A.nitems_dev = nitems_dev;
     A.items_cap = R.items_cap;
     A.qcap = R.qcap;
@@ -748,7 +766,7 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
         CF_CU(cfb_wsq(dsets, R.nsets, R.np, wsq, st), "self-pair weights");
         C->launches++;
     }
-    C->launches += 2 + (R.items_cap > 0 ? 1 : 0);   // items emit, recheck, pair
+    C->launches += 2 + (R.items_cap > 0 ? 1 : 0) + (ordered ? 2 : 0);   // items emit, recheck, pair, order
     if (timed) CF_CU(cudaEventRecordWithFlags(C->ev[3], st, C->capturing ? cudaEventRecordExternal : 0), "event");
     // the side stream's bbox pass joins here, so that the call's synchronisation covers it
     if (R.bbox_aux) {
@@ -868,7 +886,7 @@ int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &p
         CF_CU(cudaStreamSynchronize(st), "items sync");
         R.items_cap = *(const uint32_t *)C->hpin;
     }
-    CF_TRY(C->ensure(B_ITEMS, sizeof(CfItem) * std::max<size_t>(1, R.items_cap)));
+    CF_TRY(ensure_items(C, R.items_cap));
     for (int attempt = 0; attempt < 4; attempt++) {
         CF_TRY(cf_enqueue_count(C, R, true));
         CF_CU(cudaStreamSynchronize(st), "count sync");
@@ -889,7 +907,7 @@ int cf_run(CfCtx *C, const cf_params *p, const std::vector<const cf_points *> &p
             return CF_OK;
         }
         if (retry == 1) CF_TRY(C->ensure(B_QUEUE, 16 * (size_t)R.qcap));
-        if (retry == 2) CF_TRY(C->ensure(B_ITEMS, sizeof(CfItem) * (size_t)R.items_cap));
+        if (retry == 2) CF_TRY(ensure_items(C, R.items_cap));
     }
     return C->fail(CF_ERR_INTERNAL, "recheck queue kept overflowing");
 }
@@ -1062,7 +1080,7 @@ cf_status cf_batch_capture(void *ctx, const cf_params *params, const cf_points *
     // the graph sizes its work list here (one pass writes it) and runs its own bbox pass in line
     R.fused_items = true;
     R.bbox_aux = false;
-    if ((rc = C->ensure(B_ITEMS, sizeof(CfItem) * (size_t)R.items_cap))) return (cf_status)rc;
+    if ((rc = ensure_items(C, R.items_cap))) return (cf_status)rc;
     R.qcap = std::max(R.qcap, (uint32_t)std::min<int64_t>(CF_MAX_ENTRIES, C->stats.rechecked_pairs * 2 + 4096));
     if ((rc = C->ensure(B_QUEUE, 16 * (size_t)R.qcap))) return (cf_status)rc;
     // the graph also re-runs the bbox pass, read back past the results, so that a replay can

@@ -12,7 +12,7 @@
 enum CfBuf {
     B_IN, B_SETS, B_BBOX, B_PLAN, B_LUT, B_FINE, B_STENCIL, B_JOBS, B_CNT, B_CSTART, B_CELLID, B_SLOT,
     B_PA, B_PB, B_PLO, B_ORIG, B_SCAN, B_ICNT, B_IOFF, B_ITEMS, B_HCNT, B_HW, B_HR, B_QUEUE, B_WSQ, B_MISC, B_ORIGIN,
-    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_PLANBLK, B_GBOX, B_COUNT_
+    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_PLANBLK, B_GBOX, B_ORDER, B_COUNT_
 };
 
 // B_OUT: the counters and histograms one call reads back, laid out as the host copy of them (one

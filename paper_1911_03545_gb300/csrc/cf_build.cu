@@ -931,6 +931,126 @@ __global__ void __launch_bounds__(256, GP ? 3 : 4)
     if (mode == 2 && lane == 0 && nres) atomicAdd(total64, nres);     // nres is the same in every lane
 }
 
+// ---------------------------------------------------------------------------------------------
+// Order of the work list: the pair kernel dispatches each item to one of four instances of its
+// loop (cf_item_class).  Taken in list order, neighbouring warps of an SM would run all four at
+// once, and their code together does not stay in the instruction cache; taken class by class, an
+// SM runs one at a time (largest tiles first, so the small ones fill the end of the launch).
+// A counting sort by class without atomics: block b owns the items [b C, (b + 1) C) with
+// C = ceil(n / blocks); the first pass writes each block's class sizes to part[b][k], the second
+// finds its offsets from them (the classes before k, the blocks before b) and writes each item's
+// index in list order.  The order is the same on every call.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void order_chunk(uint32_t n, uint32_t &beg, uint32_t &end)
+{
+    const uint32_t per = (n + gridDim.x - 1) / gridDim.x;
+    beg = min(n, blockIdx.x * per);
+    end = min(n, beg + per);
+}
+
+__device__ __forceinline__ uint32_t order_class(const CfItem *__restrict__ items, uint32_t i, uint32_t end)
+{
+    if (i >= end) return CFI_ITEM_CLASSES;
+    const uint2 cm = *reinterpret_cast<const uint2 *>(&items[i].cnt);       // cnt, meta
+    return cf_item_class(cm.x, cm.y);
+}
+
+__global__ void __launch_bounds__(256) cf_order_count_kernel(const CfItem *__restrict__ items,
+                                                             const uint32_t *__restrict__ nitems_dev,
+                                                             uint32_t items_cap, uint32_t *__restrict__ part)
+{
+    __shared__ uint32_t s_c[8][CFI_ITEM_CLASSES];
+    uint32_t beg, end;
+    order_chunk(min(*nitems_dev, items_cap), beg, end);
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    uint32_t cnt[CFI_ITEM_CLASSES] = {};
+    for (uint32_t t = beg; t < end; t += 256u) {
+        const uint32_t c = order_class(items, t + threadIdx.x, end);
+#pragma unroll
+        for (uint32_t k = 0; k < CFI_ITEM_CLASSES; k++) cnt[k] += (uint32_t)__popc(__ballot_sync(CF_FULL, c == k));
+    }
+    if (lane == 0)
+        for (uint32_t k = 0; k < CFI_ITEM_CLASSES; k++) s_c[warp][k] = cnt[k];
+    __syncthreads();
+    if (threadIdx.x < CFI_ITEM_CLASSES) {
+        uint32_t s = 0;
+        for (uint32_t w = 0; w < (blockDim.x >> 5); w++) s += s_c[w][threadIdx.x];
+        part[blockIdx.x * CFI_ITEM_CLASSES + threadIdx.x] = s;
+    }
+}
+
+__global__ void __launch_bounds__(256) cf_order_scatter_kernel(const CfItem *__restrict__ items,
+                                                               const uint32_t *__restrict__ nitems_dev,
+                                                               uint32_t items_cap, const uint32_t *__restrict__ part,
+                                                               uint32_t *__restrict__ order)
+{
+    __shared__ uint32_t s_w[8][CFI_ITEM_CLASSES];      // per warp: before this block, then per tile
+    __shared__ uint32_t s_base[CFI_ITEM_CLASSES];      // where this block's next item of class k goes
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    {
+        // the classes' sizes over all blocks, and over the blocks before this one
+        uint32_t tot[CFI_ITEM_CLASSES] = {}, pre[CFI_ITEM_CLASSES] = {};
+        for (uint32_t b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+            for (uint32_t k = 0; k < CFI_ITEM_CLASSES; k++) {
+                const uint32_t v = part[b * CFI_ITEM_CLASSES + k];
+                tot[k] += v;
+                pre[k] += b < blockIdx.x ? v : 0u;
+            }
+        for (uint32_t k = 0; k < CFI_ITEM_CLASSES; k++)
+            for (int o = 16; o; o >>= 1) {
+                tot[k] += __shfl_xor_sync(CF_FULL, tot[k], o);
+                pre[k] += __shfl_xor_sync(CF_FULL, pre[k], o);
+            }
+        __shared__ uint32_t s_tot[8][CFI_ITEM_CLASSES];
+        if (lane == 0)
+            for (uint32_t k = 0; k < CFI_ITEM_CLASSES; k++) {
+                s_tot[warp][k] = tot[k];
+                s_w[warp][k] = pre[k];
+            }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t off = 0;
+            for (uint32_t k = 0; k < CFI_ITEM_CLASSES; k++) {
+                uint32_t t = 0, p = 0;
+                for (uint32_t w = 0; w < nw; w++) {
+                    t += s_tot[w][k];
+                    p += s_w[w][k];
+                }
+                s_base[k] = off + p;
+                off += t;
+            }
+        }
+        __syncthreads();
+    }
+    uint32_t beg, end;
+    order_chunk(min(*nitems_dev, items_cap), beg, end);
+    const uint32_t below = (1u << lane) - 1u;
+    for (uint32_t t = beg; t < end; t += 256u) {
+        const uint32_t i = t + threadIdx.x;
+        const uint32_t c = order_class(items, i, end);
+        uint32_t mine = 0;      // the ballot of this thread's class
+#pragma unroll
+        for (uint32_t k = 0; k < CFI_ITEM_CLASSES; k++) {
+            const uint32_t m = __ballot_sync(CF_FULL, c == k);
+            if (c == k) mine = m;
+            if (lane == 0) s_w[warp][k] = (uint32_t)__popc(m);
+        }
+        __syncthreads();
+        if (c < CFI_ITEM_CLASSES) {
+            uint32_t r = s_base[c] + (uint32_t)__popc(mine & below);
+            for (uint32_t w = 0; w < warp; w++) r += s_w[w][c];
+            order[r] = i;       // r < n: the class's place plus its rank among the class's n_k items
+        }
+        __syncthreads();
+        if (threadIdx.x < CFI_ITEM_CLASSES) {
+            uint32_t s = 0;
+            for (uint32_t w = 0; w < nw; w++) s += s_w[w][threadIdx.x];
+            s_base[threadIdx.x] += s;
+        }
+        __syncthreads();
+    }
+}
+
 // sum of w^2 per set (self pairs of a weighted auto-correlation whose first edge is 0)
 __global__ void cf_wsq_kernel(const CfSetDesc *__restrict__ sets, double *__restrict__ out)
 {
@@ -1033,6 +1153,15 @@ cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobD
     else
         cf_items_kernel<false><<<nb, 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox, nullptr, mode, counts,
                                                    offsets, items, items_cap, evaluated, total64);
+    return cudaGetLastError();
+}
+
+cudaError_t cfb_order(const CfItem *items, const uint32_t *nitems_dev, uint32_t items_cap, uint32_t *order,
+                      uint32_t *part, int num_sms, cudaStream_t st)
+{
+    const int nb = cfb_order_blocks(items_cap, num_sms);
+    cf_order_count_kernel<<<nb, 256, 0, st>>>(items, nitems_dev, items_cap, part);
+    cf_order_scatter_kernel<<<nb, 256, 0, st>>>(items, nitems_dev, items_cap, part, order);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,23 @@ cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobD
                       const uint32_t *cell_start, const float *cbox, const float *gbox, int64_t nunits, int mode,
                       uint32_t *counts, const uint32_t *offsets, CfItem *items, uint32_t items_cap,
                       unsigned long long *evaluated, unsigned long long *total64, cudaStream_t st);
+// work lists of a smaller capacity are taken in list order (CfPairArgs::order = NULL): the two
+// ordering passes cost about 15 us, the pair kernel saves 3-7 %, so they pay from about 0.3 ms of
+// pair kernel (some 30,000 items)
+#define CF_ORDER_MIN_ITEMS 40960u
+// the order in which the pair kernel takes the work list: the indices of the items of each class
+// (cf_item_class) together, classes in increasing order and each class in list order, so that the
+// warps of an SM run one instance's code at a time.  order[] needs min(*nitems_dev, items_cap)
+// entries; part[] CFI_ITEM_CLASSES words per block of the launch (cfb_order_blocks), no initial
+// value.
+inline int cfb_order_blocks(uint32_t items_cap, int num_sms)
+{
+    const int cap = num_sms > 0 ? 4 * num_sms : 4;
+    const int64_t b = ((int64_t)items_cap + 255) / 256;
+    return b < 1 ? 1 : (b > cap ? cap : (int)b);
+}
+cudaError_t cfb_order(const CfItem *items, const uint32_t *nitems_dev, uint32_t items_cap, uint32_t *order,
+                      uint32_t *part, int num_sms, cudaStream_t st);
 cudaError_t cfb_wsq(const CfSetDesc *sets, int nsets, int64_t nmax, double *out, cudaStream_t st);
 
 // ---- pair counting ----
@@ -47,6 +64,7 @@ struct CfPairArgs {
     const uint16_t *lut;         // coarse LUT entries (global copy; staged into shared memory)
     const CfFine *fine;          // fine LUT entries
     const CfItem *items;
+    const uint32_t *order;       // the items in the order they are taken (cfb_order; NULL: list order)
     const uint32_t *nitems_dev;  // item count written by the work-list scan
     uint32_t items_cap;          // items beyond this were not stored
     uint32_t qcap;

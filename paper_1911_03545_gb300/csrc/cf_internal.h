@@ -44,6 +44,22 @@ struct CfItem {
 #define CFI_ITEM_DIAG (1u << 30)
 #define CFI_ITEM_JOBMASK 0xFFFFFu
 
+// The pair-kernel instance an item runs in (the kernel dispatches on the same thresholds): 0 an
+// i tile of more than 96 points (four slots per lane), 1 a cell with itself, 2 a tile of 65-96
+// points (three slots), 3 one of 33-64 (two), 4 one of at most 32 (one).  The work list is handed
+// to the pair kernel in this order of classes.  (The mocks kind runs classes 0 and 2 in its
+// four-slot instance.)
+#define CFI_ITEM_CLASSES 5
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline uint32_t cf_item_class(uint32_t cnt, uint32_t meta)
+{
+    if (meta & CFI_ITEM_DIAG) return 1u;
+    const uint32_t ic = cnt & 0xFFFFu;
+    return ic > 96u ? 0u : (ic > 64u ? 2u : (ic > 32u ? 3u : 4u));
+}
+
 // A point set (input view + where its sorted points and cells live)
 struct CfSetDesc {
     const void *x, *y, *z, *w;   // device pointers of the input arrays

@@ -2,7 +2,8 @@
 //
 // Sec. 4.3-4.7 on a GPU.  Every warp repeatedly takes one work item -- an i tile of one cell
 // (<= 128 points) against a j range (<= 512 points) of a neighbour cell -- from a global atomic
-// cursor.  Lane l holds the i points l + 32 q (q < Q; Q = 1, 2 or 4 by the tile's size) in
+// cursor (in the order of cfb_order: items of one instance together).  Lane l holds the i points
+// l + 32 q (q < Q; Q = 1 to 4 by the tile's size, mocks 1, 2 or 4) in
 // registers, already translated by the cell-pair shift (Sec. 4.4, Code corrfunc_pbc: the shift
 // is added once per i, not per pair), each duplicated into both halves of a packed FP32 pair.
 // The j points stream through a double-buffered shared-memory stage (cp.async) as float arrays
@@ -956,14 +957,14 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
     if (w.lane == 0) t = atomicAdd(a.cursor, 1u);
     t = __shfl_sync(CF_FULL, t, 0);
     CfItem it;
-    if (t < nitems) it = a.items[t];
+    if (t < nitems) it = a.items[a.order ? a.order[t] : t];
     for (;;) {
         if (t >= nitems) break;
         uint32_t tn = 0;
         if (w.lane == 0) tn = atomicAdd(a.cursor, 1u);
         tn = __shfl_sync(CF_FULL, tn, 0);
         CfItem nx;
-        if (tn < nitems) nx = a.items[tn];
+        if (tn < nitems) nx = a.items[a.order ? a.order[tn] : tn];
         const int job = (int)(it.meta & CFI_ITEM_JOBMASK);
         if (job != cur || pend > (FX ? FX_FLUSH_PAIRS : CF_FLUSH_PAIRS)) {
             if (cur >= 0) w.flush((uint32_t)cur);
@@ -973,6 +974,9 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
         const bool diag = (it.meta & CFI_ITEM_DIAG) != 0;
         const uint32_t ic = it.cnt & 0xFFFFu;
         pend += ic * (it.cnt >> 16);
+        // the instances below are the classes of cf_item_class; the work list comes ordered by
+        // class, so the warps of an SM mostly run one instance (its code stays in the
+        // instruction cache)
         if (KIND == KIND_MOCKS) {
             if (diag) w.template run_mocks<4, true>(it);
             else if (ic <= 32u) w.template run_mocks<1, false>(it);
@@ -982,6 +986,7 @@ __global__ void __launch_bounds__(pair_max_threads(W, R), pair_min_blocks(W, R))
             if (diag) w.template run<4, true, COMPACT>(it);
             else if (ic <= 32u) w.template run<1, false, COMPACT>(it);
             else if (ic <= 64u) w.template run<2, false, COMPACT>(it);
+            else if (ic <= 96u) w.template run<3, false, COMPACT>(it);
             else w.template run<4, false, COMPACT>(it);
         }
         t = tn;

@@ -545,6 +545,31 @@ def test_scan_over_many_tiles(ctx):
         cf.cf_destroy(c)
 
 
+def test_work_list_in_instance_order(ctx):
+    """A work list long enough to be handed to the pair kernel ordered by instance (tiles of up to
+    128 points of cells holding from a few to several hundred clustered points, so every tile size
+    and cells with themselves; j ranges of 32: tens of thousands of items).  Two calls (the second
+    writes its list in one pass) equal the oracle for weighted DD(r) with ravg and for DD(rp, pi)."""
+    import torch
+    import paper_1911_03545_gb300 as cf
+    c = cf.cf_create(0, torch.cuda.current_stream())
+    try:
+        cf.cf_set_option(c, cf.CF_OPT_TILE, 128)
+        cf.cf_set_option(c, cf.CF_OPT_JCHUNK, 32)
+        d = gen.clustered_box(800, 100, 1.0, 40.0, 131)
+        d.w = gen.uniform_weights(d.n, 0.5, 1.5, 132)
+        edges = gen.log_edges(0.1, 6.0, 12)
+        kw_r = dict(autocorr=True, periodic=True, box=40.0, weighted=True, ravg=True)
+        kw_p = dict(autocorr=True, periodic=True, box=40.0, pimax=6.0, npibins=6)
+        exp_r, exp_p = oracle.count("r", edges, d, **kw_r), oracle.count("rppi", edges, d, **kw_p)
+        for _ in range(2):
+            assert_match(gpu_count(c, "r", edges, d, **kw_r), exp_r, True, True)
+            assert cf.cf_get_stats(c)["work_items"] >= 40960
+            assert_match(gpu_count(c, "rppi", edges, d, **kw_p), exp_p)
+    finally:
+        cf.cf_destroy(c)
+
+
 @pytest.mark.parametrize("kind", ["r", "theta", "rppi"])
 def test_device_views_not_16_byte_aligned(ctx, kind):
     """Device inputs may be views that start 4 bytes into an allocation (x = t[1:]): the passes that
