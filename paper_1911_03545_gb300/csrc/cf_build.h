@@ -40,7 +40,7 @@ cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobD
                       uint32_t *counts, const uint32_t *offsets, CfItem *items, uint32_t items_cap,
                       unsigned long long *evaluated, unsigned long long *total64, cudaStream_t st);
 // work lists of a smaller capacity are taken in list order (CfPairArgs::order = NULL): the two
-// ordering passes cost about 15 us, the pair kernel saves 3-7 %, so they pay from about 0.3 ms of
+// ordering passes cost 12-15 us, the pair kernel saves 3-7 %, so they pay from about 0.3 ms of
 // pair kernel (some 30,000 items)
 #define CF_ORDER_MIN_ITEMS 40960u
 // the order in which the pair kernel takes the work list: the indices of the items of each class
