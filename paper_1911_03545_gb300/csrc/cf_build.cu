@@ -574,6 +574,11 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
     const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncell_all; c += wstride) {
         const uint32_t b = cell_start[c], e = cell_start[c + 1];
+        if (b == e) {
+            // most cells of a fine grid are empty: no reduction for them (b, e are warp-uniform)
+            if (lane < 6u) box[6 * c + lane] = lane < 3u ? INFINITY : -INFINITY;
+            continue;
+        }
         float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
         for (uint32_t p0 = b; p0 < e; p0 += 32u) {
             float glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
