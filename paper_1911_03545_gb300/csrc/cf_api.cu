@@ -452,6 +452,9 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     R.nunit = (int64_t)njobs * R.ncell;      // work-list units: one per (job, i cell)
     if (R.nunit >= ((int64_t)1 << 31)) return C->fail(CF_ERR_ARG, "work list too large");
     R.np = std::max<int64_t>(R.npts, 1);
+    // a grid with more cells than points (most of them empty): list the units with points first,
+    // so that the work-list pass does not spend a warp iteration on each empty cell
+    R.live_units = R.nunit >= 65536 && R.nunit > R.npts;
     R.nslot = (size_t)D.nslot;
     R.hsz = R.nslot * njobs;
     R.self_pairs = p->edges[0] == 0.0;
@@ -498,6 +501,7 @@ int cf_prepare(CfCtx *C, const cf_params *p, const std::vector<const cf_points *
     CF_TRY(C->ensure(B_SCAN, 4 * (size_t)cfb_scan_tmp_words(std::max(R.nfine, R.nunit))));
     CF_TRY(C->ensure(B_ICNT, 4 * (size_t)std::max<int64_t>(R.nunit, 1)));
     CF_TRY(C->ensure(B_IOFF, 4 * (size_t)(R.nunit + 1)));
+    if (R.live_units) CF_TRY(C->ensure(B_LIVE, 4 * (size_t)R.nunit));
     CF_TRY(C->ensure(B_OUT, readback_bytes(R)));
     R.qcap = C->opt[CF_OPT_QUEUE] > 0 ? (uint32_t)std::min<int64_t>(CF_MAX_ENTRIES, C->opt[CF_OPT_QUEUE])
                                       : C->qcap_default;
@@ -616,7 +620,18 @@ int cf_enqueue_build(CfCtx *C, CfRun &R)
     uint32_t *icnt = (uint32_t *)C->buf[B_ICNT].p, *ioff = (uint32_t *)C->buf[B_IOFF].p;
     // the work list's length in 64 bits, next to its 32-bit scan (checked in cf_finish)
     unsigned long long *items64 = (unsigned long long *)(out + OUT_ITEMS64);
-    CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, cstart, cbox, gbox, R.nunit, 0, icnt, nullptr,
+    const uint32_t *live = nullptr, *nlive = nullptr;
+    if (R.live_units) {
+        // the units with points (the count phase keeps the list: its memset starts past OUT_NLIVE);
+        // the others count no items
+        live = (const uint32_t *)C->buf[B_LIVE].p;
+        nlive = (const uint32_t *)(out + OUT_NLIVE);
+        CF_CU(cudaMemsetAsync(icnt, 0, 4 * (size_t)R.nunit, st), "memset item counts");
+        CF_CU(cfb_live_units(dplan, dsets, djobs, cstart, R.nunit, (uint32_t *)live, (uint32_t *)nlive, st),
+              "live units");
+        C->launches += 1;
+    }
+    CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, cstart, cbox, gbox, live, nlive, R.nunit, 0, icnt, nullptr,
                     nullptr, 0, items64, nullptr, st),
           "items count");
     CF_CU(cfb_scan(icnt, ioff, R.nunit, (uint32_t *)C->buf[B_SCAN].p, (uint32_t *)(out + OUT_SCAN + 4), st,
@@ -695,16 +710,25 @@ int cf_enqueue_count(CfCtx *C, CfRun &R, bool timed)
     const size_t zero_from = R.fused_items ? 0 : OUT_EVAL;
     CF_CU(cudaMemsetAsync(out + zero_from, 0, readback_bytes(R) - zero_from, st), "memset");
     uint32_t *nitems_dev = ioff + R.nunit;
+    const uint32_t *cstart = (const uint32_t *)C->buf[B_CSTART].p;
+    const uint32_t *live = R.live_units ? (const uint32_t *)C->buf[B_LIVE].p : nullptr;
+    const uint32_t *nlive = R.live_units ? (const uint32_t *)(out + OUT_NLIVE) : nullptr;
     if (R.fused_items) {
         nitems_dev = (uint32_t *)(out + OUT_NITEMS);
-        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.gbox,
-                        R.nunit, 2, nitems_dev, nullptr, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
+        if (R.live_units) {
+            // the memset above cleared the list's count: list the units with points again
+            CF_CU(cfb_live_units(dplan, dsets, djobs, cstart, R.nunit, (uint32_t *)live, (uint32_t *)nlive, st),
+                  "live units");
+            C->launches += 1;
+        }
+        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, cstart, R.cbox, R.gbox, live, nlive, R.nunit, 2,
+                        nitems_dev, nullptr, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
                         (unsigned long long *)(out + OUT_ITEMS64), st),
               "items");
     } else {
-        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, (const uint32_t *)C->buf[B_CSTART].p, R.cbox, R.gbox,
-                        R.nunit, 1, (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap,
-                        evaluated, nullptr, st),
+        CF_CU(cfb_items(dplan, dsets, djobs, R.d_stencil, cstart, R.cbox, R.gbox, live, nlive, R.nunit, 1,
+                        (uint32_t *)C->buf[B_ICNT].p, ioff, (CfItem *)C->buf[B_ITEMS].p, R.items_cap, evaluated,
+                        nullptr, st),
               "items emit");
     }
     // a short list is taken as it is: the two ordering passes would cost more than they save (the

@@ -12,16 +12,18 @@
 enum CfBuf {
     B_IN, B_SETS, B_BBOX, B_PLAN, B_LUT, B_FINE, B_STENCIL, B_JOBS, B_CNT, B_CSTART, B_CELLID, B_SLOT,
     B_PA, B_PB, B_PLO, B_ORIG, B_SCAN, B_ICNT, B_IOFF, B_ITEMS, B_HCNT, B_HW, B_HR, B_QUEUE, B_WSQ, B_MISC, B_ORIGIN,
-    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_PLANBLK, B_GBOX, B_ORDER, B_COUNT_
+    B_CBOX, B_FSTART, B_BANDS, B_ORIGIN32, B_OUT, B_PLANBLK, B_GBOX, B_ORDER, B_LIVE, B_COUNT_
 };
 
 // B_OUT: the counters and histograms one call reads back, laid out as the host copy of them (one
-// device-to-host copy): work-list length (u32, also at the end of its scan), the same in 64 bits,
+// device-to-host copy): work-list length (u32, also at the end of its scan), at OUT_NLIVE the number
+// of units with points in their i cell (u32, when the work list visits only those), the same length in 64 bits,
 // evaluated pairs, the pair kernel's work cursor (u32), recheck-queue length, then from OUT_HIST
 // hcnt[hsz] (u64), hw[hsz], hr[hsz] (f64) and the sum of w^2 per point set (f64); at OUT_SCAN the
 // tickets of the build's two scans.  The build zeroes the first OUT_HIST bytes, the count phase
 // everything from OUT_EVAL on (from 0 for the one-pass work list), each with one memset.
 #define OUT_NITEMS 0
+#define OUT_NLIVE 4
 #define OUT_ITEMS64 8
 #define OUT_EVAL 16
 #define OUT_CURSOR 24
@@ -75,6 +77,7 @@ struct CfRun {
     bool angular = false;          // DD(theta) on the angular grid (needs unit vectors)
     bool bbox_deferred = false;    // periodic call planned from L: its bbox is checked after the final sync
     bool fused_items = false;      // the work list is counted and written in one pass (size known)
+    bool live_units = false;       // the work list visits only the units whose i cell holds points
     bool bbox_aux = false;         // the bbox pass runs on the side stream: join before the readback
     // the call's plan, tables and descriptors inside the B_PLANBLK device block
     const CfDevPlan *d_plan = nullptr;

@@ -610,6 +610,33 @@ __global__ void cf_cellbox_kernel(const uint32_t *__restrict__ cell_start, int64
     }
 }
 
+// The units (job, i cell) whose i cell holds points, in any order, and their number in *nlive
+// (zeroed by the caller): on a grid with far more cells than points the work-list pass then skips
+// the empty ones without a warp iteration each.  One thread per unit, one atomic per warp.
+__global__ void cf_live_units_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
+                                     const CfJobDesc *__restrict__ jobs, const uint32_t *__restrict__ cell_start,
+                                     uint32_t *__restrict__ live, uint32_t *__restrict__ nlive)
+{
+    const CfGrid &g = plan->g;
+    const int64_t nunit = (int64_t)g.ncell * plan->njobs;
+    const uint32_t lane = threadIdx.x & 31u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;      // a multiple of 32: warp-uniform loop
+    for (int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~(int64_t)31; b < nunit; b += stride) {
+        const int64_t u = b + lane;
+        bool has = false;
+        if (u < nunit) {
+            const int job = (int)(u / g.ncell);
+            const int64_t c = sets[jobs[job].a].cbeg + (u - (int64_t)job * g.ncell);
+            has = cell_start[c + 1] > cell_start[c];
+        }
+        const uint32_t m = __ballot_sync(CF_FULL, has);
+        uint32_t base = 0;
+        if (lane == 0 && m) base = atomicAdd(nlive, (uint32_t)__popc(m));
+        base = __shfl_sync(CF_FULL, base, 0);
+        if (has) live[base + (uint32_t)__popc(m & ((1u << lane) - 1u))] = (uint32_t)u;
+    }
+}
+
 // Work items, one warp per (job, i cell).  The lanes walk the cell's stencil (Sec. 4.3: neighbours
 // +-k per axis, periodic shift per cell pair, auto keeps cj >= ci), a warp prefix sum orders the
 // items of the cell, and an empty i cell costs one load.  i tiles are full (tile points) plus one
@@ -632,7 +659,8 @@ __global__ void __launch_bounds__(256, GP ? 3 : 4)
     cf_items_kernel(const CfDevPlan *__restrict__ plan, const CfSetDesc *__restrict__ sets,
                                 const CfJobDesc *__restrict__ jobs, const CfStencil *__restrict__ stencil,
                                 const uint32_t *__restrict__ cell_start, const float *__restrict__ cbox,
-                                const float *__restrict__ gbox, int mode,
+                                const float *__restrict__ gbox, const uint32_t *__restrict__ live,
+                                const uint32_t *__restrict__ nlive, int mode,
                                 uint32_t *__restrict__ counts, const uint32_t *__restrict__ offsets,
                                 CfItem *__restrict__ items, uint32_t items_cap,
                                 unsigned long long *__restrict__ evaluated, unsigned long long *__restrict__ total64)
@@ -653,13 +681,15 @@ __global__ void __launch_bounds__(256, GP ? 3 : 4)
     __shared__ __align__(16) CfItem s_items[CFB_ITEM_STAGE];
     // every warp of a block runs the same number of iterations (block-wide barriers in mode 2)
     const int64_t wpb = blockDim.x >> 5, warp = threadIdx.x >> 5;
-    for (int64_t ub = blockIdx.x * wpb; ub < nunit; ub += (int64_t)gridDim.x * wpb) {
+    // with a list of the units whose i cell holds points, only those (the same count in every thread)
+    const int64_t nloop = live ? (int64_t)min(*nlive, (uint32_t)nunit) : nunit;
+    for (int64_t ub = blockIdx.x * wpb; ub < nloop; ub += (int64_t)gridDim.x * wpb) {
         if (mode == 2) {
             if (threadIdx.x == 0) s_n = 0;
             __syncthreads();
         }
-        const int64_t u = ub + warp;
-        if (u < nunit) {
+        if (ub + warp < nloop) {
+            const int64_t u = live ? (int64_t)live[ub + warp] : ub + warp;
             const int job = (int)(u / g.ncell);
             const int c = (int)(u - (int64_t)job * g.ncell);
             const CfJobDesc J = jobs[job];
@@ -1146,18 +1176,27 @@ cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const flo
     return cudaGetLastError();
 }
 
+cudaError_t cfb_live_units(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs,
+                           const uint32_t *cell_start, int64_t nunits, uint32_t *live, uint32_t *nlive,
+                           cudaStream_t st)
+{
+    cf_live_units_kernel<<<blocks_for(nunits, 256, 4096), 256, 0, st>>>(plan, sets, jobs, cell_start, live, nlive);
+    return cudaGetLastError();
+}
+
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
-                      const uint32_t *cell_start, const float *cbox, const float *gbox, int64_t nunits, int mode,
-                      uint32_t *counts, const uint32_t *offsets, CfItem *items, uint32_t items_cap,
-                      unsigned long long *evaluated, unsigned long long *total64, cudaStream_t st)
+                      const uint32_t *cell_start, const float *cbox, const float *gbox, const uint32_t *live,
+                      const uint32_t *nlive, int64_t nunits, int mode, uint32_t *counts, const uint32_t *offsets,
+                      CfItem *items, uint32_t items_cap, unsigned long long *evaluated, unsigned long long *total64,
+                      cudaStream_t st)
 {
     const int nb = blocks_for(nunits * 32, 256, 8192);
     if (gbox)
-        cf_items_kernel<true><<<nb, 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox, gbox, mode, counts,
-                                                  offsets, items, items_cap, evaluated, total64);
+        cf_items_kernel<true><<<nb, 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox, gbox, live, nlive,
+                                                  mode, counts, offsets, items, items_cap, evaluated, total64);
     else
-        cf_items_kernel<false><<<nb, 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox, nullptr, mode, counts,
-                                                   offsets, items, items_cap, evaluated, total64);
+        cf_items_kernel<false><<<nb, 256, 0, st>>>(plan, sets, jobs, stencil, cell_start, cbox, nullptr, live, nlive,
+                                                   mode, counts, offsets, items, items_cap, evaluated, total64);
     return cudaGetLastError();
 }
 

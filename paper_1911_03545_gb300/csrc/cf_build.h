@@ -30,15 +30,23 @@ cudaError_t cfb_scatter(const CfDevPlan *plan, const CfSetDesc *sets, int nsets,
 // with gbox (6 floats per point) also the box of every 32-point group of a cell at its first point
 cudaError_t cfb_cellbox(const uint32_t *cell_start, int64_t ncell_all, const float4 *pa, const float4 *pb, float *box,
                         float *gbox, cudaStream_t st);
+// the units (job, i cell) whose i cell holds points, appended to live[] (nunits entries) at the
+// zeroed counter *nlive
+cudaError_t cfb_live_units(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs,
+                           const uint32_t *cell_start, int64_t nunits, uint32_t *live, uint32_t *nlive,
+                           cudaStream_t st);
 // cbox: the boxes above, or nullptr to visit every stencil neighbour; gbox: the group boxes, or
-// nullptr for j ranges over whole cells.  mode 0: per-unit item counts
+// nullptr for j ranges over whole cells; live / nlive: the units to visit (cfb_live_units), or
+// nullptr for all of them (with a list, mode 0 writes the counts of the listed units only: the
+// caller zeroes the rest).  mode 0: per-unit item counts
 // into counts[], their number in 64 bits added to *evaluated; mode 1: items at offsets[]; mode 2:
 // count and emit in one pass, items reserved on the counter counts[0] (zeroed by the caller), their
 // number added to *total64.  Modes 1 and 2 add the pairs the stored items hold to *evaluated.
 cudaError_t cfb_items(const CfDevPlan *plan, const CfSetDesc *sets, const CfJobDesc *jobs, const CfStencil *stencil,
-                      const uint32_t *cell_start, const float *cbox, const float *gbox, int64_t nunits, int mode,
-                      uint32_t *counts, const uint32_t *offsets, CfItem *items, uint32_t items_cap,
-                      unsigned long long *evaluated, unsigned long long *total64, cudaStream_t st);
+                      const uint32_t *cell_start, const float *cbox, const float *gbox, const uint32_t *live,
+                      const uint32_t *nlive, int64_t nunits, int mode, uint32_t *counts, const uint32_t *offsets,
+                      CfItem *items, uint32_t items_cap, unsigned long long *evaluated, unsigned long long *total64,
+                      cudaStream_t st);
 // work lists of a smaller capacity are taken in list order (CfPairArgs::order = NULL): the two
 // ordering passes cost 12-15 us, the pair kernel saves 3-7 %, so they pay from about 0.3 ms of
 // pair kernel (some 30,000 items)
