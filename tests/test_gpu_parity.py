@@ -529,7 +529,8 @@ def test_work_list_outgrows_the_previous_size(ctx):
 def test_scan_over_many_tiles(ctx):
     """The cell scan's tile offsets are scanned by the last block in chunks of 4096 tiles: 68^3
     cells with 64 Morton sub-cells each make 2.0e7 keys (4913 tiles), so the second chunk runs.
-    Two calls (the second writes its work list in one pass) equal the oracle."""
+    The grid has more cells than points, so the work list visits only the listed cells that hold
+    points.  Two calls (the second writes its work list in one pass) equal the oracle."""
     import torch
     import paper_1911_03545_gb300 as cf
     c = cf.cf_create(0, torch.cuda.current_stream())
